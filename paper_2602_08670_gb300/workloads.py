@@ -1,0 +1,252 @@
+"""Seeded synthetic inputs: initial states and request streams.
+
+This module only *builds inputs*.  It holds none of the scheme's arithmetic
+(no reconstruction, no flux, no time step) and imports nothing else from this
+package, so both the CUDA path and the FP64 CPU oracle draw their inputs from
+it without depending on one another.
+
+Every generator returns float64 numpy arrays in the state layout used across
+the project: ``q[B][C][ny][nx]`` (x fastest), cell-centre point values on the
+periodic unit square with ``N`` cells per direction and centres at
+``(i + 1/2) * dx`` (Section 2.3.1, "The grid", read with N cells and dx = 1/N).
+C = 3 for shallow water ``(h, hu, hv)`` and C = 4 for Euler
+``(rho, rho*u, rho*v, E)``.
+
+Randomness comes from numpy's Philox counter-based generator, seeded
+explicitly, so a workload is reproducible from its seed alone.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+G_GRAVITY = 9.81      # g used by every shallow-water workload
+GAMMA_IDEAL = 1.4     # ratio of specific heats for every Euler workload
+
+
+def _rng(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.Philox(int(seed)))
+
+
+def cell_centres(n: int, length: float = 1.0) -> np.ndarray:
+    """Centres x_i = (i + 1/2) * length / n, i = 0..n-1."""
+    return (np.arange(n, dtype=np.float64) + 0.5) * (length / n)
+
+
+def _mesh(nx: int, ny: int):
+    x = cell_centres(nx)
+    y = cell_centres(ny)
+    return np.meshgrid(x, y, indexing="xy")  # X[j, i], Y[j, i]
+
+
+def swe_gaussian_bump(nx: int, ny: int, amp: float = 0.1, width2: float = 0.005,
+                      h0: float = 1.0) -> np.ndarray:
+    """Shallow water at rest with a centred Gaussian hump.
+
+    h = h0 + amp * exp(-((x-1/2)^2 + (y-1/2)^2) / width2), hu = hv = 0.
+    With the defaults this is the 128x128 oracle workload and the 4096x4096
+    throughput workload.  Returns ``[1][3][ny][nx]``.
+    """
+    X, Y = _mesh(nx, ny)
+    h = h0 + amp * np.exp(-((X - 0.5) ** 2 + (Y - 0.5) ** 2) / width2)
+    q = np.zeros((1, 3, ny, nx))
+    q[0, 0] = h
+    return q
+
+
+def euler_kelvin_helmholtz(nx: int, ny: int, seed: int = 0,
+                           gamma: float = GAMMA_IDEAL) -> np.ndarray:
+    """Kelvin-Helmholtz shear layer for 2D Euler.
+
+    Inner strip 1/4 <= y < 3/4: rho = 2, u = +0.5; outside: rho = 1, u = -0.5.
+    v = 0.01 sin(4 pi x) + 1e-3 U(-1, 1) (seeded), uniform pressure p = 2.5.
+    Returns conserved variables ``[1][4][ny][nx]`` with
+    E = p / (gamma - 1) + rho (u^2 + v^2) / 2.
+    """
+    X, Y = _mesh(nx, ny)
+    inner = (Y >= 0.25) & (Y < 0.75)
+    rho = np.where(inner, 2.0, 1.0)
+    u = np.where(inner, 0.5, -0.5)
+    noise = _rng(seed).uniform(-1.0, 1.0, size=(ny, nx))
+    v = 0.01 * np.sin(4.0 * math.pi * X) + 1e-3 * noise
+    p = np.full_like(rho, 2.5)
+    q = np.zeros((1, 4, ny, nx))
+    q[0, 0] = rho
+    q[0, 1] = rho * u
+    q[0, 2] = rho * v
+    q[0, 3] = p / (gamma - 1.0) + 0.5 * rho * (u * u + v * v)
+    return q
+
+
+@dataclasses.dataclass
+class BumpSpec:
+    centres: np.ndarray   # [K, 2]
+    amps: np.ndarray      # [K]
+    widths: np.ndarray    # [K]
+
+
+def random_bump_specs(seed: int, members: int) -> list[BumpSpec]:
+    """Draw, per member, K ~ U{1..5} bumps with A ~ U[0.05, 0.2],
+    w ~ U[0.02, 0.1] and centres ~ U[0, 1)^2."""
+    rng = _rng(seed)
+    out = []
+    for _ in range(members):
+        k = int(rng.integers(1, 6))
+        out.append(BumpSpec(centres=rng.uniform(0.0, 1.0, size=(k, 2)),
+                            amps=rng.uniform(0.05, 0.2, size=k),
+                            widths=rng.uniform(0.02, 0.1, size=k)))
+    return out
+
+
+def swe_random_bumps(n: int, seed: int, members: int) -> np.ndarray:
+    """Training / ensemble initial states: h = 1 + sum_k A_k exp(-d_k^2 / w_k^2),
+    d_k the periodic minimum-image distance to centre k, hu = hv = 0.
+
+    The same seed gives the same bumps at every resolution, so a 256x256 run
+    and its 64x64 coarse counterpart start from the same continuous field.
+    Returns ``[members][3][n][n]``.
+    """
+    X, Y = _mesh(n, n)
+    q = np.zeros((members, 3, n, n))
+    for b, spec in enumerate(random_bump_specs(seed, members)):
+        h = np.ones((n, n))
+        for (cx, cy), a, w in zip(spec.centres, spec.amps, spec.widths):
+            dx = np.abs(X - cx)
+            dx = np.minimum(dx, 1.0 - dx)
+            dy = np.abs(Y - cy)
+            dy = np.minimum(dy, 1.0 - dy)
+            h += a * np.exp(-(dx * dx + dy * dy) / (w * w))
+        q[b, 0] = h
+    return q
+
+
+def swe_dam_break(nx: int, ny: int, h_left: float = 1.0, h_right: float = 0.35,
+                  x0: float = 0.5) -> np.ndarray:
+    """y-uniform dam break: h = h_left for x < x0, h_right otherwise, at rest.
+    On the periodic square this holds two Riemann problems (at x0 and at 0)."""
+    X, _ = _mesh(nx, ny)
+    q = np.zeros((1, 3, ny, nx))
+    q[0, 0] = np.where(X < x0, h_left, h_right)
+    return q
+
+
+def euler_sod(nx: int, ny: int, gamma: float = GAMMA_IDEAL, x0: float = 0.5,
+              axis: str = "x") -> np.ndarray:
+    """Sod shock tube, uniform across the other direction:
+    (rho, u, p) = (1, 0, 1) left of x0 and (0.125, 0, 0.1) right of it."""
+    X, Y = _mesh(nx, ny)
+    s = X if axis == "x" else Y
+    left = s < x0
+    rho = np.where(left, 1.0, 0.125)
+    p = np.where(left, 1.0, 0.1)
+    q = np.zeros((1, 4, ny, nx))
+    q[0, 0] = rho
+    q[0, 3] = p / (gamma - 1.0)
+    return q
+
+
+def swe_linear_wave(nx: int, ny: int, k: int = 1, eps: float = 1e-6,
+                    depth: float = 1.0, g: float = G_GRAVITY) -> np.ndarray:
+    """Small right-going gravity wave along x: h = H + eps sin(2 pi k x),
+    hu = h * sqrt(g/H) * eps sin(2 pi k x) / H, hv = 0."""
+    X, _ = _mesh(nx, ny)
+    eta = eps * np.sin(2.0 * math.pi * k * X)
+    h = depth + eta
+    u = math.sqrt(g / depth) * eta / depth
+    q = np.zeros((1, 3, ny, nx))
+    q[0, 0] = h
+    q[0, 1] = h * u
+    return q
+
+
+def euler_acoustic_wave(nx: int, ny: int, k: int = 1, eps: float = 1e-6,
+                        rho0: float = 1.0, p0: float = 1.0,
+                        gamma: float = GAMMA_IDEAL) -> np.ndarray:
+    """Small right-going acoustic wave along x: rho = rho0 (1 + eps s),
+    u = c eps s, p = p0 + rho0 c^2 eps s with s = sin(2 pi k x),
+    c = sqrt(gamma p0 / rho0)."""
+    X, _ = _mesh(nx, ny)
+    s = np.sin(2.0 * math.pi * k * X)
+    c = math.sqrt(gamma * p0 / rho0)
+    rho = rho0 * (1.0 + eps * s)
+    u = c * eps * s
+    p = p0 + rho0 * c * c * eps * s
+    q = np.zeros((1, 4, ny, nx))
+    q[0, 0] = rho
+    q[0, 1] = rho * u
+    q[0, 3] = p / (gamma - 1.0) + 0.5 * rho * u * u
+    return q
+
+
+def random_smooth_swe(n: int, seed: int, members: int = 1, amp: float = 0.05,
+                      vel: float = 0.05) -> np.ndarray:
+    """Smooth random SWE states with non-zero velocity (few Fourier modes).
+    Used where a test needs every term of the flux active."""
+    rng = _rng(seed)
+    X, Y = _mesh(n, n)
+    q = np.zeros((members, 3, n, n))
+    for b in range(members):
+        fields = []
+        for _ in range(3):
+            f = np.zeros((n, n))
+            for _m in range(4):
+                kx, ky = rng.integers(-3, 4, size=2)
+                ph = rng.uniform(0, 2 * math.pi)
+                f += rng.normal() * np.cos(2 * math.pi * (kx * X + ky * Y) + ph)
+            fields.append(f / 4.0)
+        h = 1.0 + amp * fields[0]
+        q[b, 0] = h
+        q[b, 1] = h * vel * fields[1]
+        q[b, 2] = h * vel * fields[2]
+    return q
+
+
+@dataclasses.dataclass
+class Request:
+    """One solve request of the serving workload."""
+    arrival_s: float
+    eq: str           # "swe" or "euler"
+    learned: bool
+    n: int            # grid is n x n
+    nsteps: int
+    seed: int
+
+
+def serving_requests(count: int, rate_per_s: float, seed: int = 42,
+                     sizes=(64, 128, 256, 512, 1024, 2048),
+                     horizon=(100, 5000)) -> list[Request]:
+    """Poisson arrivals at ``rate_per_s``; grid side uniform over ``sizes``;
+    horizon uniform integer in ``horizon``; 50 % learned SWE, 25 % plain SWE,
+    25 % plain Euler (the learned variant exists for shallow water only)."""
+    rng = _rng(seed)
+    t = 0.0
+    out = []
+    for i in range(count):
+        t += rng.exponential(1.0 / rate_per_s)
+        kind = rng.uniform()
+        if kind < 0.5:
+            eq, learned = "swe", True
+        elif kind < 0.75:
+            eq, learned = "swe", False
+        else:
+            eq, learned = "euler", False
+        out.append(Request(arrival_s=t, eq=eq, learned=learned,
+                           n=int(rng.choice(np.asarray(sizes))),
+                           nsteps=int(rng.integers(horizon[0], horizon[1] + 1)),
+                           seed=int(seed * 1_000_003 + i)))
+    return out
+
+
+def request_initial_state(req: Request) -> np.ndarray:
+    """Initial state of one request: random bumps (SWE) or KH (Euler)."""
+    if req.eq == "swe":
+        return swe_random_bumps(req.n, req.seed, 1)
+    return euler_kelvin_helmholtz(req.n, req.n, seed=req.seed)
+
+
+def as_f32_exact(q: np.ndarray) -> np.ndarray:
+    """Round to FP32 and back: the exact values an FP32 GPU state starts from,
+    which is what the oracle must be given for a like-for-like comparison."""
+    return np.asarray(q, dtype=np.float32).astype(np.float64)
