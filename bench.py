@@ -1,0 +1,305 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the finite-volume hot path on GB300.
+
+One *step* = one SSP-RK2 step (both stages, MUSCL-minmod + HLL) of the two
+plain-solver workloads run back to back:
+  * 2D Euler, 2048 x 2048 periodic, gamma = 1.4, Kelvin-Helmholtz shear layer;
+  * 2D shallow water, 4096 x 4096 periodic, Gaussian bump (g = 9.81);
+both FP32 with the adaptive CFL 0.5 time step.  The default step count is the
+workload's horizon of 2000 steps.  `value` is cell-updates per second summed
+over both grids (and over all ranks); one cell-update is one cell advanced by
+one full SSP-RK2 step.
+
+``--impl reference`` times the FP64 CPU oracle on the host cores instead (the
+only reference implementation there is), on a bounded sample per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-updates/s plain vs learned at matched L2 error; p50/p99 request latency"
+UNIT = "cell-updates/s"
+N_SWE = 4096
+N_EULER = 2048
+SWE_BYTES_PER_CELL_UPDATE = 60     # stage 1: 12 + 12; stage 2: 12 + 12 + 12 (FP32, C = 3)
+EULER_BYTES_PER_CELL_UPDATE = 80   # C = 4
+CHUNK = 32                          # steps per enqueue between timing events
+WORKLOAD = "plain FV step: Euler KH 2048^2 + SWE Gaussian bump 4096^2, FP32, SSP-RK2, CFL 0.5"
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.2)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k] == "Active"})
+        # median over samples under load (clock above idle)
+        top = max(sm) if sm else 0.0
+        loaded = [v for v in sm if v >= 0.5 * top] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (the reference arm, and the cpu_baseline of our arm)
+# ---------------------------------------------------------------------------
+
+def oracle_sample(steps: int, n_swe: int, n_euler: int):
+    """Time the FP64 oracle as it stands: `steps` SSP-RK2 steps of an SWE
+    bump n_swe^2 and an Euler KH n_euler^2.  Returns (cell-updates/s, seconds,
+    threads)."""
+    import torch
+
+    from oracle import fv as ofv
+    from paper_2602_08670_gb300 import workloads as W
+    qs = torch.tensor(W.swe_gaussian_bump(n_swe, n_swe))
+    qe = torch.tensor(W.euler_kelvin_helmholtz(n_euler, n_euler, seed=0))
+    t0 = time.perf_counter()
+    ofv.run(qs, ofv.SWE, steps)
+    ofv.run(qe, ofv.EULER, steps)
+    dt = time.perf_counter() - t0
+    cells = (n_swe * n_swe + n_euler * n_euler) * steps
+    return cells / dt, dt, torch.get_num_threads()
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    n_swe, n_euler = 128, 128
+    oracle_sample(max(1, args.warmup), 32, 32)     # warm-up
+    rate, secs, threads = oracle_sample(args.steps, n_swe, n_euler)
+    sample = f"{args.steps} steps of SWE bump {n_swe}^2 + Euler KH {n_euler}^2 (FP64 oracle)"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD + " (oracle on a bounded sample)"},
+        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2602_08670_gb300 import fv
+    from paper_2602_08670_gb300 import workloads as W
+
+    bs = torch.cuda.Stream()
+    q_swe = torch.tensor(W.swe_gaussian_bump(N_SWE, N_SWE), dtype=torch.float32)
+    q_eul = torch.tensor(W.euler_kelvin_helmholtz(N_EULER, N_EULER, seed=0), dtype=torch.float32)
+    with torch.cuda.stream(bs):
+        swe = fv.swe_init(q_swe.cuda(), cfl=0.5)
+        eul = fv.euler_init(q_eul.cuda(), cfl=0.5)
+    assert swe.stream == bs.cuda_stream and eul.stream == bs.cuda_stream
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    # warm-up (also captures the graphs)
+    for _ in range(max(args.warmup, 3)):
+        fv.fv_enqueue_steps(swe, 1)
+        fv.fv_enqueue_steps(eul, 1)
+    fv.fv_enqueue_steps(swe, CHUNK)
+    fv.fv_enqueue_steps(eul, CHUNK)
+    fv.fv_sync(swe)
+    fv.fv_sync(eul)
+
+    K = args.steps
+    chunks = [CHUNK] * (K // CHUNK) + ([K % CHUNK] if K % CHUNK else [])
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in chunks]
+    clocks = Clocks(local)
+    clocks.start()
+    barrier()
+    for c, k in enumerate(chunks):
+        ev[c][0].record(bs)
+        fv.fv_enqueue_steps(swe, k)
+        ev[c][1].record(bs)
+        fv.fv_enqueue_steps(eul, k)
+        ev[c][2].record(bs)
+    barrier()
+    clk = clocks.stop()
+    total_ms = ev[0][0].elapsed_time(ev[-1][2])
+    swe_ms = sum(e[0].elapsed_time(e[1]) for e in ev)
+    eul_ms = sum(e[1].elapsed_time(e[2]) for e in ev)
+    fv.fv_sync(swe)
+    fv.fv_sync(eul)
+    if ws > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    cells_per_step = N_SWE * N_SWE + N_EULER * N_EULER
+    value = ws * cells_per_step * K / (total_ms * 1e-3)
+
+    # roofline of the dominant kernel pair (SWE stage 1 + stage 2)
+    peak, peak_kind = measured_peaks()
+    swe_step_s = swe_ms * 1e-3 / K
+    achieved = SWE_BYTES_PER_CELL_UPDATE * N_SWE * N_SWE / swe_step_s / 1e9
+    eul_achieved = EULER_BYTES_PER_CELL_UPDATE * N_EULER * N_EULER / (eul_ms * 1e-3 / K) / 1e9
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(prof):
+        with open(prof) as f:
+            traffic = json.load(f).get("swe_stage_pair_4096")
+
+    # end to end through the public API with host buffers: upload the initial
+    # states from pinned memory, advance them by K steps, read the results back
+    h_swe = q_swe.pin_memory()
+    h_eul = q_eul.pin_memory()
+    o_swe = torch.empty_like(h_swe).pin_memory()
+    o_eul = torch.empty_like(h_eul).pin_memory()
+    e2e_runs = []
+    for rep in range(2):
+        barrier()
+        t0 = time.perf_counter()
+        fv.fv_set_state(swe, h_swe)
+        fv.fv_set_state(eul, h_eul)
+        fv.fv_enqueue_steps(swe, K)
+        fv.fv_enqueue_steps(eul, K)
+        fv.fv_get_state(swe, out=o_swe)
+        fv.fv_get_state(eul, out=o_eul)
+        barrier()
+        e2e_runs.append(time.perf_counter() - t0)
+    e2e_s = min(e2e_runs[1:]) if len(e2e_runs) > 1 else e2e_runs[0]
+    if ws > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    state_bytes = (h_swe.numel() + h_eul.numel()) * 4
+    assert bool(torch.isfinite(o_swe).all()) and bool(torch.isfinite(o_eul).all())
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K,
+        "warmup": args.warmup, "ms_per_step": total_ms / K, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD,
+                   "swe": f"{N_SWE}x{N_SWE} Gaussian bump h=1+0.1exp(-r^2/0.005)",
+                   "euler": f"{N_EULER}x{N_EULER} Kelvin-Helmholtz, seed 0",
+                   "per_rank": "each rank runs its own copy (independent problems)",
+                   "l2": "inputs larger than L2 (SWE state buffer 201 MB > 129 MB L2)",
+                   "swe_cell_updates_per_s": N_SWE * N_SWE * K / (swe_ms * 1e-3),
+                   "euler_cell_updates_per_s": N_EULER * N_EULER * K / (eul_ms * 1e-3),
+                   "euler_stage_pair_gbs": eul_achieved},
+        "roofline": {"bound": "hbm", "kernel": "stage_minmod_kernel<SWE> (stage 1 + stage 2)",
+                     "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "algorithmic_bytes": f"{SWE_BYTES_PER_CELL_UPDATE} B/cell-update x {N_SWE}^2 cells per step"},
+        "e2e": {"value": ws * cells_per_step * K / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": state_bytes / K, "d2h_bytes_per_step": state_bytes / K,
+                "call": "fv_set_state(host) + fv_enqueue_steps(K) + fv_get_state(host) per state"},
+        "gpu_launches": 4 * K,
+        "clocks": clk,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        rate, secs, threads = oracle_sample(4, 512, 256)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+                                "sample": f"4 SSP-RK2 steps of SWE bump 512^2 + Euler KH 256^2, "
+                                          f"FP64 oracle, {secs:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,169 @@
+/*
+ * fv.h — C ABI of the GB300 finite-volume library (libfv.so).
+ *
+ * Explicit finite-volume time stepping of the 2D shallow-water equations
+ * (Eq. 2.3, flat bed) and the 2D Euler equations (Section 4.2, ideal gas,
+ * Eq. 2.4) on periodic Cartesian grids: MUSCL reconstruction with the MINMOD
+ * limiter (Eq. 2.18), the HLL numerical flux (Eq. 2.15) in the face-normal
+ * frame (Eq. 2.24), the conservative update (Eqs. 2.9, 2.23) and Heun /
+ * SSP-RK2 time integration (Eq. 2.19) with the CFL rule (Eq. 2.10).  The
+ * learned variant (Section 2.5.3, fourth approach) replaces MINMOD by
+ * CNN-predicted, sum-to-one stencil coefficients.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Every call returns an int status: FV_OK (0), FV_PENDING (1), or a
+ *    negative fv_status error.  fv_last_error() gives a thread-local message
+ *    for the last failing call of the calling thread.
+ *  - State layout: q[B][C][ny][nx], FP32, x fastest, contiguous.  SWE: C = 3,
+ *    (h, hu, hv).  Euler: C = 4, (rho, rho u, rho v, E).
+ *  - Pointer location tags: FV_HOST (pageable or pinned host memory) or
+ *    FV_DEVICE (device memory of the current CUDA device).  Caller buffers are
+ *    borrowed for the duration of the call only.
+ *  - Handles (fv_state, fv_net, fv_server) are opaque; the library owns every
+ *    device allocation it makes and frees it in the matching fv_destroy_*.
+ *  - stream: a cudaStream_t passed as void* (e.g. PyTorch's current stream).
+ *    A created (non-default) stream is used directly: every kernel of the
+ *    handle runs on it.  NULL, cudaStreamLegacy or cudaStreamPerThread make
+ *    the library create its own stream for the handle, ordered after work
+ *    already queued on the given default stream at each call, and before work
+ *    queued there afterwards.  Calls that return host data synchronise.
+ *  - Device-side failures (NaN/Inf, h <= 0, rho <= 0, p <= 0, Courant number
+ *    above 1 in FIXED/REPLAY mode) are recorded in a per-member health word and
+ *    reported as FV_EUNSTABLE by the next synchronising call.
+ */
+#ifndef FV_H_
+#define FV_H_
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FV_OK = 0,
+  FV_PENDING = 1,      /* poll(): the request is not finished yet            */
+  FV_EINVAL = -1,      /* bad argument (null pointer, size, mode, ...)       */
+  FV_ENOMEM = -2,      /* a device or host allocation failed                  */
+  FV_EUNSTABLE = -3,   /* health word set on the device (see above)           */
+  FV_ETIMEOUT = -4,    /* a bounded wait gave up                              */
+  FV_EBUSY = -5,       /* submit(): the request can never fit the budget      */
+  FV_ECUDA = -6,       /* a CUDA runtime call failed                          */
+  FV_ENOTFOUND = -7    /* unknown ticket                                      */
+} fv_status;
+
+enum { FV_HOST = 0, FV_DEVICE = 1 };
+enum { FV_EQ_SWE = 0, FV_EQ_EULER = 1 };
+enum { FV_DT_ADAPTIVE = 0, FV_DT_FIXED = 1, FV_DT_REPLAY = 2 };
+
+/* Health bits (fv_health). */
+enum {
+  FV_HEALTH_NONFINITE = 1u,   /* NaN or Inf in a stage output               */
+  FV_HEALTH_NONPOSITIVE = 2u, /* h <= 0 (SWE), rho <= 0 or p <= 0 (Euler)    */
+  FV_HEALTH_CFL = 4u,         /* Courant number > 1 with a FIXED/REPLAY dt   */
+  FV_HEALTH_REPLAY_END = 8u   /* REPLAY ran past the supplied dt sequence    */
+};
+
+/* Periodic grid [0, lx) x [0, ly) with nx x ny cells of size lx/nx x ly/ny
+ * (Section 2.3.1, "The grid": N cells per direction, centres (i + 1/2) dx),
+ * and `batch` independent members that share the grid. */
+typedef struct { int nx, ny, batch; double lx, ly; } fv_grid;
+
+/* Time-step control (Eq. 2.10 with the Courant number of the unsplit 2D
+ * update, C = dt * max_cells((|u| + c)/dx + (|v| + c)/dy)).  ADAPTIVE:
+ * dt = cfl / max_cells((|u| + c)/dx + (|v| + c)/dy), per member, evaluated
+ * on q^n.  FIXED: dt = dt_fixed.  REPLAY: step n uses the n-th value given to
+ * fv_set_replay_dt() for every member.  FIXED and REPLAY raise
+ * FV_HEALTH_CFL when C exceeds 1. */
+typedef struct { double g; double cfl; int dt_mode; double dt_fixed; } fv_swe_params;
+typedef struct { double gamma; double cfl; int dt_mode; double dt_fixed; } fv_euler_params;
+
+typedef struct fv_state fv_state;
+typedef struct fv_net fv_net;
+typedef struct fv_server fv_server;
+
+/* Thread-local message of the last failing call ("" if none). */
+const char* fv_last_error(void);
+
+/* ---------------------------------------------------------------------------
+ * States
+ * ------------------------------------------------------------------------- */
+
+/* Create a shallow-water state (Eq. 2.3, S = 0).  q0: [batch][3][ny][nx] FP32
+ * at location q0_loc; copied into library-owned device memory.  The initial
+ * dt is computed on the device.  Requires nx, ny >= 1, batch >= 1, g > 0,
+ * h > 0 everywhere (else FV_EUNSTABLE at the first synchronising call).
+ * Errors: FV_EINVAL, FV_ENOMEM, FV_ECUDA. */
+int swe_init(const fv_grid* grid, const fv_swe_params* params, const float* q0,
+             int q0_loc, void* stream, fv_state** out);
+
+/* Create a 2D Euler state (Section 4.2, ideal gas Eq. 2.4 with gamma > 1).
+ * q0: [batch][4][ny][nx] conserved variables (rho, rho u, rho v, E). */
+int euler_init(const fv_grid* grid, const fv_euler_params* params, const float* q0,
+               int q0_loc, void* stream, fv_state** out);
+
+/* Free a state and everything it owns (NULL is accepted). */
+int fv_destroy_state(fv_state* s);
+
+/* REPLAY mode: the dt of step k (k = 0..n-1, counted from the state's
+ * creation) for every member.  dts is a host array of n doubles, copied. */
+int fv_set_replay_dt(fv_state* s, const double* dts, long n);
+
+/* Enqueue one SSP-RK2 step (Eq. 2.19) of every member on the state's
+ * stream; asynchronous.  net == NULL: MUSCL-minmod reconstruction.  net !=
+ * NULL (SWE only): learned reconstruction with minmod fallback. */
+int fv_step(fv_state* s, const fv_net* net);
+
+/* Enqueue up to nsteps steps as replays of a captured CUDA graph and wait
+ * for them.  t_end > 0 stops every member at simulated time t_end exactly
+ * (its last step shortened, later steps skipped on the device); t_end <= 0
+ * ignores it.  If snaps != NULL and snap_every > 0, the state after every
+ * snap_every-th step is written to snaps (location snaps_loc) as
+ * [nsteps/snap_every][batch][C][ny][nx].  t_out (host, [batch], may be NULL)
+ * receives each member's simulated time.  Returns FV_EUNSTABLE if a health
+ * bit was raised. */
+int fv_rollout(fv_state* s, const fv_net* net, long nsteps, double t_end,
+               float* snaps, int snaps_loc, int snap_every, double* t_out);
+
+/* Enqueue nsteps steps (graph replays of 32-step chunks plus a direct tail)
+ * and return without waiting; the state's t_end setting is left as it is.
+ * Health is reported by the next synchronising call. */
+int fv_enqueue_steps(fv_state* s, const fv_net* net, long nsteps);
+
+/* Wait for the state's stream and report health (FV_OK or FV_EUNSTABLE). */
+int fv_sync(fv_state* s);
+
+/* Copy the current state to dst ([batch][C][ny][nx], location dst_loc). */
+int fv_get_state(const fv_state* s, float* dst, int dst_loc);
+
+/* Overwrite the current state from src (same shape); time and step count are
+ * kept, the dt of the next step is recomputed (ADAPTIVE). */
+int fv_set_state(fv_state* s, const float* src, int src_loc);
+
+/* Device pointer of the state buffer (owned by the state; valid until the
+ * next fv_destroy_state).  For zero-copy binding layers. */
+int fv_state_device_ptr(const fv_state* s, float** dptr);
+
+/* The CUDA stream (cudaStream_t as void*) on which the state's kernels run,
+ * owned by the state; for callers that time or order work against it. */
+int fv_state_stream(const fv_state* s, void** stream);
+
+/* Per member: simulated time t (host [batch]), the dt the next step will use
+ * (host [batch]) and the number of completed steps (host [batch]); any
+ * pointer may be NULL. */
+int fv_get_time(const fv_state* s, double* t, double* next_dt, long long* steps);
+
+/* Per member health bits (host [batch]). */
+int fv_health(const fv_state* s, unsigned* flags);
+
+/* FP64 global sums per member, host [batch][C+1]: the integral of each
+ * conserved variable (sum of cell values times dx dy), then SWE: total energy
+ * of Eq. 5.1, integral of g h^2/2 + (u^2+v^2) h/2; Euler: kinetic energy,
+ * integral of rho (u^2+v^2)/2.  Deterministic (fixed reduction order). */
+int fv_diagnostics(const fv_state* s, double* sums);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FV_H_ */

@@ -1,0 +1,46 @@
+// fv_internal.h — the state object behind the opaque fv_state handle and the
+// internal functions shared by the API translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "fv_common.cuh"
+#include "fv_kernels.h"
+
+struct fv_learned_ws;   // per-state workspace of the learned step (fv_learned.cu)
+
+struct fv_state {
+  fvk::Geom g{};
+  double lx = 1.0, ly = 1.0;
+  int dt_mode = FV_DT_ADAPTIVE;
+  cudaStream_t stream = nullptr;       // all work of the state runs here
+  cudaStream_t user_stream = nullptr;  // caller's stream, or null
+  bool own_stream = false;             // stream created by the library
+  cudaEvent_t ev = nullptr;
+  float* qA = nullptr;                 // q^n, and q^{n+1} after stage 2
+  float* qB = nullptr;                 // q^(1), the stage-1 output
+  fvk::Ctrl* ctrl = nullptr;           // device [B]
+  fvk::DtParams* dp = nullptr;         // device
+  fvk::DtParams dp_host{};
+  double* replay = nullptr;            // device REPLAY dt sequence
+  double* diag_partials = nullptr;
+  double* diag_out = nullptr;
+  cudaGraphExec_t graph = nullptr;     // captured chunk of steps
+  long graph_steps = 0;
+  const fv_net* graph_net = nullptr;
+  fv_learned_ws* lws = nullptr;        // learned-step workspace (lazily created)
+  float h_min = 0.f;                   // positivity threshold of learned faces
+};
+
+namespace fvs {
+int state_alloc(fv_state* s);
+void state_free(fv_state* s);
+cudaError_t enter(fv_state* s);
+cudaError_t leave(fv_state* s);
+cudaError_t enqueue_plain_step(fv_state* s);
+cudaError_t enqueue_step(fv_state* s, const fv_net* net);
+int check_health(fv_state* s);
+// learned path (fv_learned.cu)
+cudaError_t enqueue_learned_step(fv_state* s, const fv_net* net);
+void learned_workspace_free(fv_state* s);
+}  // namespace fvs

@@ -1,0 +1,42 @@
+// fv_kernels.h — host-side launchers of the finite-volume kernels (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "fv_common.cuh"
+
+namespace fvk {
+
+// Grid geometry and physical constant of one state.
+struct Geom {
+  int nx, ny, B, C, eq;   // eq: SWE or EULER
+  double dx, dy;
+  float phys;             // g (SWE) or gamma (Euler), as used by the FP32 kernels
+  double phys_d;          // the same constant in FP64 (diagnostics)
+  long long plane() const { return (long long)nx * ny; }
+  long long member() const { return plane() * C; }
+};
+
+// One SSP-RK2 stage (Eq. 2.19) with MUSCL-minmod faces (Eq. 2.18) and HLL
+// fluxes (Eq. 2.15):
+//   stage 1: qout = qin + dt L(qin)
+//   stage 2: qout = qn/2 + qin/2 + dt L(qin)/2, then the CFL reduction of qout
+// qout may alias qn (each cell of qn is read only by the thread writing it).
+cudaError_t launch_stage_minmod(const Geom& g, int stage, const float* qin, const float* qn,
+                                float* qout, Ctrl* ctrl, const DtParams* dp, cudaStream_t s);
+
+// Wave-speed reduction of q that sets each member's dt without advancing
+// time (state creation, fv_set_state).
+cudaError_t launch_wavespeed_init(const Geom& g, const float* q, Ctrl* ctrl, const DtParams* dp,
+                                  cudaStream_t s);
+
+// FP64 sums [B][C+1] into device memory `out` (deterministic order).
+// `partials` must hold diag_partials_size(g) doubles.
+long long diag_partials_size(const Geom& g);
+cudaError_t launch_diagnostics(const Geom& g, const float* q, double* partials, double* out,
+                               cudaStream_t s);
+
+// Set t_end on every member, clamp the pending dt to it and set `done`.
+cudaError_t launch_set_t_end(Ctrl* ctrl, int B, double t_end, cudaStream_t s);
+
+}  // namespace fvk

@@ -1,0 +1,244 @@
+"""Python binding of libfv (include/fv.h): argument marshalling only.
+
+Every numerical step runs in the CUDA library; this module converts torch
+tensors to pointers, picks the location tag, and turns negative status codes
+into ``FvError``.  Functions carry the C names.  Loading fails loudly when
+``libfv.so`` has not been built: there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+from .build import LIB
+
+c_int, c_long, c_double, c_void_p = ctypes.c_int, ctypes.c_long, ctypes.c_double, ctypes.c_void_p
+
+FV_OK, FV_PENDING = 0, 1
+FV_EINVAL, FV_ENOMEM, FV_EUNSTABLE, FV_ETIMEOUT, FV_EBUSY, FV_ECUDA, FV_ENOTFOUND = range(-1, -8, -1)
+FV_HOST, FV_DEVICE = 0, 1
+DT_MODES = {"adaptive": 0, "fixed": 1, "replay": 2}
+STATUS_NAMES = {0: "FV_OK", 1: "FV_PENDING", -1: "FV_EINVAL", -2: "FV_ENOMEM", -3: "FV_EUNSTABLE",
+                -4: "FV_ETIMEOUT", -5: "FV_EBUSY", -6: "FV_ECUDA", -7: "FV_ENOTFOUND"}
+CUDA_STREAM_LEGACY = 1
+
+
+class FvError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class fv_grid(ctypes.Structure):
+    _fields_ = [("nx", c_int), ("ny", c_int), ("batch", c_int), ("lx", c_double), ("ly", c_double)]
+
+
+class fv_swe_params(ctypes.Structure):
+    _fields_ = [("g", c_double), ("cfl", c_double), ("dt_mode", c_int), ("dt_fixed", c_double)]
+
+
+class fv_euler_params(ctypes.Structure):
+    _fields_ = [("gamma", c_double), ("cfl", c_double), ("dt_mode", c_int), ("dt_fixed", c_double)]
+
+
+_lib = None
+
+# name -> argtypes (all functions return int unless listed in _RESTYPES)
+_SIGS = {
+    "fv_last_error": [],
+    "swe_init": [ctypes.POINTER(fv_grid), ctypes.POINTER(fv_swe_params), c_void_p, c_int, c_void_p,
+                 ctypes.POINTER(c_void_p)],
+    "euler_init": [ctypes.POINTER(fv_grid), ctypes.POINTER(fv_euler_params), c_void_p, c_int,
+                   c_void_p, ctypes.POINTER(c_void_p)],
+    "fv_destroy_state": [c_void_p],
+    "fv_set_replay_dt": [c_void_p, c_void_p, c_long],
+    "fv_step": [c_void_p, c_void_p],
+    "fv_rollout": [c_void_p, c_void_p, c_long, c_double, c_void_p, c_int, c_int, c_void_p],
+    "fv_enqueue_steps": [c_void_p, c_void_p, c_long],
+    "fv_sync": [c_void_p],
+    "fv_get_state": [c_void_p, c_void_p, c_int],
+    "fv_set_state": [c_void_p, c_void_p, c_int],
+    "fv_state_device_ptr": [c_void_p, ctypes.POINTER(c_void_p)],
+    "fv_state_stream": [c_void_p, ctypes.POINTER(c_void_p)],
+    "fv_get_time": [c_void_p, c_void_p, c_void_p, c_void_p],
+    "fv_health": [c_void_p, c_void_p],
+    "fv_diagnostics": [c_void_p, c_void_p],
+}
+_RESTYPES = {"fv_last_error": ctypes.c_char_p}
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded CUDA library; raises if it was never built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB):
+            raise RuntimeError(f"{LIB} is missing: build it with __graft_entry__.build() "
+                               "(the CUDA library is required; there is no CPU fallback)")
+        L = ctypes.CDLL(LIB)
+        for name, args in _SIGS.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = _RESTYPES.get(name, c_int)
+        _lib = L
+    return _lib
+
+
+def exported_symbols() -> list[str]:
+    return list(_SIGS)
+
+
+def _check(rc: int) -> int:
+    if rc < 0:
+        raise FvError(rc, lib().fv_last_error().decode())
+    return rc
+
+
+def _torch_stream() -> int:
+    h = torch.cuda.current_stream().cuda_stream
+    return h if h else CUDA_STREAM_LEGACY
+
+
+def _ptr_loc(t: torch.Tensor):
+    if t.dtype != torch.float32 or not t.is_contiguous():
+        raise ValueError("state tensors must be contiguous float32")
+    return ctypes.c_void_p(t.data_ptr()), (FV_DEVICE if t.is_cuda else FV_HOST)
+
+
+class State:
+    """Owner of an ``fv_state*`` handle."""
+
+    def __init__(self, handle: int, eq: str, shape):
+        self.handle = ctypes.c_void_p(handle)
+        self.eq = eq
+        self.shape = tuple(shape)   # (B, C, ny, nx)
+
+    def __del__(self):
+        if getattr(self, "handle", None) and self.handle.value and _lib is not None:
+            _lib.fv_destroy_state(self.handle)
+            self.handle = ctypes.c_void_p(0)
+
+    @property
+    def stream(self) -> int:
+        out = c_void_p()
+        _check(lib().fv_state_stream(self.handle, ctypes.byref(out)))
+        return out.value or 0
+
+    @property
+    def device_ptr(self) -> int:
+        out = c_void_p()
+        _check(lib().fv_state_device_ptr(self.handle, ctypes.byref(out)))
+        return out.value
+
+
+def _grid(q: torch.Tensor, lx: float, ly: float) -> fv_grid:
+    if q.dim() != 4:
+        raise ValueError("q0 must be [B][C][ny][nx]")
+    B, _, ny, nx = q.shape
+    return fv_grid(nx, ny, B, lx, ly)
+
+
+def swe_init(q0: torch.Tensor, g: float = 9.81, cfl: float = 0.5, dt_mode: str = "adaptive",
+             dt_fixed: float = 0.0, lx: float = 1.0, ly: float = 1.0) -> State:
+    q0 = q0.contiguous()
+    if q0.shape[1] != 3:
+        raise ValueError("SWE state has 3 variables")
+    ptr, loc = _ptr_loc(q0)
+    out = c_void_p()
+    stream = c_void_p(_torch_stream()) if torch.cuda.is_available() else None
+    _check(lib().swe_init(ctypes.byref(_grid(q0, lx, ly)),
+                          ctypes.byref(fv_swe_params(g, cfl, DT_MODES[dt_mode], dt_fixed)),
+                          ptr, loc, stream, ctypes.byref(out)))
+    return State(out.value, "swe", q0.shape)
+
+
+def euler_init(q0: torch.Tensor, gamma: float = 1.4, cfl: float = 0.5, dt_mode: str = "adaptive",
+               dt_fixed: float = 0.0, lx: float = 1.0, ly: float = 1.0) -> State:
+    q0 = q0.contiguous()
+    if q0.shape[1] != 4:
+        raise ValueError("Euler state has 4 variables")
+    ptr, loc = _ptr_loc(q0)
+    out = c_void_p()
+    stream = c_void_p(_torch_stream()) if torch.cuda.is_available() else None
+    _check(lib().euler_init(ctypes.byref(_grid(q0, lx, ly)),
+                            ctypes.byref(fv_euler_params(gamma, cfl, DT_MODES[dt_mode], dt_fixed)),
+                            ptr, loc, stream, ctypes.byref(out)))
+    return State(out.value, "euler", q0.shape)
+
+
+def fv_set_replay_dt(s: State, dts) -> None:
+    a = np.ascontiguousarray(np.asarray(dts, dtype=np.float64))
+    _check(lib().fv_set_replay_dt(s.handle, a.ctypes.data_as(c_void_p), a.size))
+
+
+def _net_handle(net):
+    return None if net is None else net.handle
+
+
+def fv_step(s: State, net=None) -> None:
+    _check(lib().fv_step(s.handle, _net_handle(net)))
+
+
+def fv_enqueue_steps(s: State, nsteps: int, net=None) -> None:
+    _check(lib().fv_enqueue_steps(s.handle, _net_handle(net), int(nsteps)))
+
+
+def fv_sync(s: State) -> None:
+    _check(lib().fv_sync(s.handle))
+
+
+def fv_rollout(s: State, nsteps: int, net=None, t_end: float = 0.0, snap_every: int = 0,
+               snaps_on_device: bool = True):
+    """Run ``nsteps`` steps; returns ``(snaps or None, t_out[B])``."""
+    B = s.shape[0]
+    t_out = np.zeros(B, dtype=np.float64)
+    snaps = None
+    sptr, sloc = None, FV_DEVICE
+    if snap_every:
+        n = nsteps // snap_every
+        dev = "cuda" if snaps_on_device else "cpu"
+        snaps = torch.empty((n,) + s.shape, dtype=torch.float32, device=dev,
+                            pin_memory=(not snaps_on_device))
+        sptr, sloc = _ptr_loc(snaps)
+    _check(lib().fv_rollout(s.handle, _net_handle(net), int(nsteps), float(t_end), sptr, sloc,
+                            int(snap_every), t_out.ctypes.data_as(c_void_p)))
+    return snaps, t_out
+
+
+def fv_get_state(s: State, out: torch.Tensor | None = None, device: bool = True) -> torch.Tensor:
+    if out is None:
+        out = torch.empty(s.shape, dtype=torch.float32, device="cuda" if device else "cpu")
+    ptr, loc = _ptr_loc(out)
+    _check(lib().fv_get_state(s.handle, ptr, loc))
+    return out
+
+
+def fv_set_state(s: State, q: torch.Tensor) -> None:
+    q = q.contiguous()
+    ptr, loc = _ptr_loc(q)
+    _check(lib().fv_set_state(s.handle, ptr, loc))
+
+
+def fv_get_time(s: State):
+    B = s.shape[0]
+    t = np.zeros(B)
+    dt = np.zeros(B)
+    steps = np.zeros(B, dtype=np.int64)
+    _check(lib().fv_get_time(s.handle, t.ctypes.data_as(c_void_p), dt.ctypes.data_as(c_void_p),
+                             steps.ctypes.data_as(c_void_p)))
+    return t, dt, steps
+
+
+def fv_health(s: State) -> np.ndarray:
+    f = np.zeros(s.shape[0], dtype=np.uint32)
+    _check(lib().fv_health(s.handle, f.ctypes.data_as(c_void_p)))
+    return f
+
+
+def fv_diagnostics(s: State) -> np.ndarray:
+    B, C = s.shape[:2]
+    out = np.zeros((B, C + 1), dtype=np.float64)
+    _check(lib().fv_diagnostics(s.handle, out.ctypes.data_as(c_void_p)))
+    return out
