@@ -145,6 +145,13 @@ int fv_set_state(fv_state* s, const float* src, int src_loc);
  * next fv_destroy_state).  For zero-copy binding layers. */
 int fv_state_device_ptr(const fv_state* s, float** dptr);
 
+/* Stage-kernel implementation of the plain step: 0 = automatic (row-march
+ * kernel when nx is a multiple of 4 and >= 8, else the shared-memory tile
+ * kernel), 1 = tile kernel, 2 = row-march kernel (FV_EINVAL if nx does not
+ * allow it).  Both evaluate the same arithmetic per face and per cell, so the
+ * results are bitwise identical; the choice only changes speed. */
+int fv_set_stage_variant(fv_state* s, int variant);
+
 /* The CUDA stream (cudaStream_t as void*) on which the state's kernels run,
  * owned by the state; for callers that time or order work against it. */
 int fv_state_stream(const fv_state* s, void** stream);

@@ -27,6 +27,7 @@ def nvcc() -> str:
 
 def _flags(debug: bool) -> list[str]:
     f = [ARCH, "-std=c++17", "-Xcompiler", "-fPIC", "-lineinfo", "--expt-relaxed-constexpr",
+         "-fmad=false",
          "-I", os.path.join(HERE, "..", "include")]
     f += ["-O0", "-G"] if debug else ["-O3"]
     return f

@@ -30,6 +30,7 @@ struct fv_state {
   const fv_net* graph_net = nullptr;
   fv_learned_ws* lws = nullptr;        // learned-step workspace (lazily created)
   float h_min = 0.f;                   // positivity threshold of learned faces
+  int variant = 0;                     // stage kernel choice (fvk::STAGE_*)
 };
 
 namespace fvs {

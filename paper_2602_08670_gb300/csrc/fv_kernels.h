@@ -22,8 +22,14 @@ struct Geom {
 //   stage 1: qout = qin + dt L(qin)
 //   stage 2: qout = qn/2 + qin/2 + dt L(qin)/2, then the CFL reduction of qout
 // qout may alias qn (each cell of qn is read only by the thread writing it).
+// variant: STAGE_AUTO (row-march kernel when nx % 4 == 0 and nx >= 8, else
+// the shared-memory tile kernel), STAGE_TILE or STAGE_MARCH.  Both kernels
+// evaluate the same per-face and per-cell arithmetic, so their results are
+// bitwise identical.
+enum { STAGE_AUTO = 0, STAGE_TILE = 1, STAGE_MARCH = 2 };
 cudaError_t launch_stage_minmod(const Geom& g, int stage, const float* qin, const float* qn,
-                                float* qout, Ctrl* ctrl, const DtParams* dp, cudaStream_t s);
+                                float* qout, Ctrl* ctrl, const DtParams* dp, cudaStream_t s,
+                                int variant);
 
 // Wave-speed reduction of q that sets each member's dt without advancing
 // time (state creation, fv_set_state).

@@ -50,17 +50,17 @@ __device__ __forceinline__ void stencil_flux(const float (&m)[C], const float (&
   float L[C], R[C];
 #pragma unroll
   for (int c = 0; c < C; ++c) {
-    L[c] = a[c] + 0.5f * minmod(a[c] - m[c], b[c] - a[c]);
-    R[c] = b[c] - 0.5f * minmod(b[c] - a[c], p[c] - b[c]);
+    L[c] = face_left(a[c], minmod(vsub(a[c], m[c]), vsub(b[c], a[c])));
+    R[c] = face_right(b[c], minmod(vsub(b[c], a[c]), vsub(p[c], b[c])));
   }
   if (rot) {
     float t = L[1]; L[1] = L[2]; L[2] = t;
     t = R[1]; R[1] = R[2]; R[2] = t;
   }
   if constexpr (EQ == SWE) {
-    hll_swe(L[0], L[1], L[2], R[0], R[1], R[2], phys, F[0], F[1], F[2]);
+    hll_swe<float>(L[0], L[1], L[2], R[0], R[1], R[2], phys, F[0], F[1], F[2]);
   } else {
-    hll_euler(L, R, phys, F);
+    hll_euler<float>(L, R, phys, F);
   }
   if (rot) {
     float t = F[1]; F[1] = F[2]; F[2] = t;
@@ -140,14 +140,12 @@ __global__ void __launch_bounds__(NT) stage_minmod_kernel(StageArgs a) {
       const float Fe = sF[(c * TY + r) * (TX + 1) + i + 1];
       const float Gs = sG[(c * (TY + 1) + r) * TX + i];
       const float Gn = sG[(c * (TY + 1) + r + 1) * TX + i];
-      // products rounded separately (no FMA contraction) so that x and y
-      // enter symmetrically: a transposed state gives the transposed result
-      const float L = -__fadd_rn(__fmul_rn(Fe - Fw, a.rdx), __fmul_rn(Gn - Gs, a.rdy));
+      const float L = divergence<float>(Fw, Fe, Gs, Gn, a.rdx, a.rdy);
       const float q = sq[(c * SY + r + 2) * SX + i + 2];
       if (STAGE == 1) {
-        out[c] = q + dt * L;
+        out[c] = rk_stage1<float>(q, dt, L);
       } else {
-        out[c] = 0.5f * qn[c * a.plane + off] + 0.5f * q + 0.5f * dt * L;
+        out[c] = rk_stage2<float>(qn[c * a.plane + off], q, 0.5f * dt, L);
       }
       qout[c * a.plane + off] = out[c];
     }
@@ -164,6 +162,287 @@ __global__ void __launch_bounds__(NT) stage_minmod_kernel(StageArgs a) {
   if (STAGE == 2) {
     block_reduce_max_or(amax, bad, red);
     if (tid == 0) publish_and_close(ctrl, a.dp, amax, bad, gridDim.x * gridDim.y, true);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Row-march stage kernel (nx a multiple of 4).
+//
+// A block owns a strip of MW = 512 columns (4 per thread, float4 loads) and
+// TY rows.  It walks down its rows; the rows it needs (its own plus a 2-row
+// periodic halo above and below) arrive through a ring of MS shared-memory
+// rows filled by cp.async MPF rows ahead, each with a 2-cell halo on both
+// sides.  Per row step a thread
+//   - computes the y slopes of its 4 cells at the previous row, the y faces
+//     between the two previous rows (rotated HLL) and keeps the lower face
+//     state and the last y flux in registers (sliding window down the strip);
+//   - computes the x slopes, x faces and x flux divergence of the row being
+//     finished from the ring row (its 4 cells plus 2 neighbours each side);
+//   - combines and stores that row (float4 stores).
+// One __syncthreads per row publishes the ring row.  The y faces are computed
+// once; each thread recomputes the x face shared with its right neighbour
+// (5 x faces for 4 cells), which removes any per-row flux exchange.
+// ---------------------------------------------------------------------------
+constexpr int MT = 128;           // threads per block
+constexpr int MW = 4 * MT;        // strip width
+constexpr int MS = 8;             // ring rows
+constexpr int MPF = 3;            // rows prefetched ahead (MS >= MPF + 4)
+constexpr int RS = MW + 8;        // ring row stride: 4 left pad (2 used) + MW + 4 right
+static_assert(MS >= MPF + 4, "ring too shallow for the prefetch depth");
+
+template <int C>
+constexpr int march_smem_bytes() { return MS * C * RS * 4; }
+
+__device__ __forceinline__ void cp_async16(float* smem, const float* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(float* smem, const float* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Face flux in the x frame / in the rotated y frame (normal momentum =
+// component 2), for scalars or packed pairs.
+template <int C, int EQ, class V>
+__device__ __forceinline__ void face_flux_x(const V (&L)[C], const V (&R)[C], float phys, V (&F)[C]) {
+  if constexpr (EQ == SWE) {
+    hll_swe<V>(L[0], L[1], L[2], R[0], R[1], R[2], phys, F[0], F[1], F[2]);
+  } else {
+    hll_euler<V>(L, R, phys, F);
+  }
+}
+
+template <int C, int EQ, class V>
+__device__ __forceinline__ void face_flux_y(const V (&L)[C], const V (&R)[C], float phys, V (&F)[C]) {
+  V l[C], r[C], f[C];
+#pragma unroll
+  for (int c = 0; c < C; ++c) { l[c] = L[c]; r[c] = R[c]; }
+  l[1] = L[2]; l[2] = L[1];
+  r[1] = R[2]; r[2] = R[1];
+  if constexpr (EQ == SWE) {
+    hll_swe<V>(l[0], l[1], l[2], r[0], r[1], r[2], phys, f[0], f[1], f[2]);
+  } else {
+    hll_euler<V>(l, r, phys, f);
+  }
+#pragma unroll
+  for (int c = 0; c < C; ++c) F[c] = f[c];
+  F[1] = f[2]; F[2] = f[1];
+}
+
+__device__ __forceinline__ float2 lo(float4 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi(float4 v) { return make_float2(v.z, v.w); }
+
+template <int C, int EQ, int STAGE>
+__global__ void __launch_bounds__(MT) stage_march_kernel(StageArgs a, int TY) {
+  extern __shared__ __align__(16) float ring[];   // [MS][C][RS]
+  __shared__ unsigned red[2 * MT / 32];
+  const int b = blockIdx.z;
+  Ctrl* ctrl = a.ctrl + b;
+  if (skip_if_done(ctrl)) return;
+  const float dt = (float)ctrl->dt;
+  const int t = threadIdx.x;
+  const int X0 = blockIdx.x * MW;
+  const int wact = min(MW, a.nx - X0);        // active columns of the strip (multiple of 4)
+  const bool active = 4 * t < wact;
+  const int Y0 = blockIdx.y * TY;
+  const int rows = min(TY, a.ny - Y0);
+  const int NL = rows + 4;                    // rows Y0-2 .. Y0+rows+1
+  const float* qin = a.qin + b * a.member;
+  const int xl = X0 == 0 ? a.nx - 2 : X0 - 2;           // left halo cells xl, xl+1
+  const int xr = X0 + wact == a.nx ? 0 : X0 + wact;     // right halo cells xr, xr+1
+  const int plane = (int)a.plane;                       // < 2^31 floats per variable plane
+  int gy_next = Y0 - 2;                                 // next row to fetch (periodic)
+  while (gy_next < 0) gy_next += a.ny;
+  int i_next = 0;
+
+  auto issue_next = [&]() {
+    float* slot = ring + (i_next & (MS - 1)) * C * RS;
+    const float* src = qin + gy_next * a.nx;
+    if (active) {
+#pragma unroll
+      for (int c = 0; c < C; ++c) cp_async16(slot + c * RS + 4 + 4 * t, src + c * plane + X0 + 4 * t);
+    }
+    if (t == 0) {
+#pragma unroll
+      for (int c = 0; c < C; ++c) cp_async8(slot + c * RS + 2, src + c * plane + xl);
+    } else if (t == 1) {
+#pragma unroll
+      for (int c = 0; c < C; ++c) cp_async8(slot + c * RS + 4 + wact, src + c * plane + xr);
+    }
+    ++i_next;
+    if (++gy_next == a.ny) gy_next = 0;
+  };
+
+#pragma unroll
+  for (int p = 0; p < MPF; ++p) {
+    if (p < NL) issue_next();
+    cp_async_commit();
+  }
+
+  float2 PL[C][2];   // lower state of the next y face (row r-1 extrapolated up), cell pairs
+  float2 Gp[C][2];   // y flux on the south face of the row being finished
+  float amax = 0.f;
+  unsigned bad = 0u;
+  const float* qnb = a.qn + b * a.member;
+  float* qout = a.qout + b * a.member;
+  const int col = 4 + 4 * t;
+
+  for (int i = 0; i < NL; ++i) {
+    if (i + MPF < NL) issue_next();
+    cp_async_commit();
+    const int orow = Y0 + i - 4;                // output row at this step (valid for i >= 4)
+    float2 qn2[C][2];
+    if (STAGE == 2 && i >= 4 && active) {
+      const int off = orow * a.nx + X0 + 4 * t;
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(qnb + c * plane + off));
+        qn2[c][0] = lo(v);
+        qn2[c][1] = hi(v);
+      }
+    }
+    cp_async_wait<MPF>();
+    __syncthreads();
+    if (i < 2 || !active) continue;
+
+    const float* s0 = ring + ((i - 2) & (MS - 1)) * C * RS;   // row r-2
+    const float* s1 = ring + ((i - 1) & (MS - 1)) * C * RS;   // row r-1
+    const float* s2 = ring + (i & (MS - 1)) * C * RS;         // row r
+    float2 q0[C][2], q1[C][2], sy[C][2];
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      const float4 v0 = *reinterpret_cast<const float4*>(s0 + c * RS + col);
+      const float4 v1 = *reinterpret_cast<const float4*>(s1 + c * RS + col);
+      const float4 v2 = *reinterpret_cast<const float4*>(s2 + c * RS + col);
+      q0[c][0] = lo(v0); q0[c][1] = hi(v0);
+      q1[c][0] = lo(v1); q1[c][1] = hi(v1);
+      // y slope at row r-1
+      sy[c][0] = minmod(vsub(q1[c][0], q0[c][0]), vsub(lo(v2), q1[c][0]));
+      sy[c][1] = minmod(vsub(q1[c][1], q0[c][1]), vsub(hi(v2), q1[c][1]));
+    }
+
+    if (i >= 3) {
+      // y faces between rows r-2 and r-1 (two packed cell pairs)
+      float2 Gn[C][2];
+#pragma unroll
+      for (int p = 0; p < 2; ++p) {
+        float2 Lf[C], Rf[C], F[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          Lf[c] = PL[c][p];
+          Rf[c] = face_right(q1[c][p], sy[c][p]);
+        }
+        face_flux_y<C, EQ, float2>(Lf, Rf, a.phys, F);
+#pragma unroll
+        for (int c = 0; c < C; ++c) Gn[c][p] = F[c];
+      }
+      if (i >= 4) {
+        // finish row r-2: cells 4t-2 .. 4t+5 of the ring row, slopes at
+        // 4t-1 .. 4t+4, faces 4t-1/2 .. 4t+7/2 (pairs f0 f1, f2 f3; f4 alone)
+        float e[C][8];
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          const float2 lft = *reinterpret_cast<const float2*>(s0 + c * RS + col - 2);
+          const float2 rgt = *reinterpret_cast<const float2*>(s0 + c * RS + col + 4);
+          e[c][0] = lft.x; e[c][1] = lft.y;
+          e[c][2] = q0[c][0].x; e[c][3] = q0[c][0].y; e[c][4] = q0[c][1].x; e[c][5] = q0[c][1].y;
+          e[c][6] = rgt.x; e[c][7] = rgt.y;
+        }
+        float sx[C][6];
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          float d[7];
+#pragma unroll
+          for (int j = 0; j < 7; ++j) d[j] = vsub(e[c][j + 1], e[c][j]);
+#pragma unroll
+          for (int j = 0; j < 6; ++j) sx[c][j] = minmod(d[j], d[j + 1]);
+        }
+        float2 Fx2[C][2];
+        float Fx4[C];
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+          float2 Lf[C], Rf[C], F[C];
+#pragma unroll
+          for (int c = 0; c < C; ++c) {
+            Lf[c] = face_left(make_float2(e[c][1 + 2 * p], e[c][2 + 2 * p]),
+                              make_float2(sx[c][2 * p], sx[c][2 * p + 1]));
+            Rf[c] = face_right(make_float2(e[c][2 + 2 * p], e[c][3 + 2 * p]),
+                               make_float2(sx[c][2 * p + 1], sx[c][2 * p + 2]));
+          }
+          face_flux_x<C, EQ, float2>(Lf, Rf, a.phys, F);
+#pragma unroll
+          for (int c = 0; c < C; ++c) Fx2[c][p] = F[c];
+        }
+        {
+          float Lf[C], Rf[C];
+#pragma unroll
+          for (int c = 0; c < C; ++c) {
+            Lf[c] = face_left(e[c][5], sx[c][4]);
+            Rf[c] = face_right(e[c][6], sx[c][5]);
+          }
+          face_flux_x<C, EQ, float>(Lf, Rf, a.phys, Fx4);
+        }
+        // faces f0..f4 = Fx2[.][0].x, Fx2[.][0].y, Fx2[.][1].x, Fx2[.][1].y, Fx4
+        float2 out[C][2];
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          const float2 Fw0 = Fx2[c][0];
+          const float2 Fe0 = make_float2(Fx2[c][0].y, Fx2[c][1].x);
+          const float2 Fw1 = Fx2[c][1];
+          const float2 Fe1 = make_float2(Fx2[c][1].y, Fx4[c]);
+          const float2 L0 = divergence(Fw0, Fe0, Gp[c][0], Gn[c][0], a.rdx, a.rdy);
+          const float2 L1 = divergence(Fw1, Fe1, Gp[c][1], Gn[c][1], a.rdx, a.rdy);
+          if (STAGE == 1) {
+            out[c][0] = rk_stage1(q0[c][0], dt, L0);
+            out[c][1] = rk_stage1(q0[c][1], dt, L1);
+          } else {
+            out[c][0] = rk_stage2(qn2[c][0], q0[c][0], 0.5f * dt, L0);
+            out[c][1] = rk_stage2(qn2[c][1], q0[c][1], 0.5f * dt, L1);
+          }
+        }
+        const int off = orow * a.nx + X0 + 4 * t;
+#pragma unroll
+        for (int c = 0; c < C; ++c)
+          *reinterpret_cast<float4*>(qout + c * plane + off) =
+              make_float4(out[c][0].x, out[c][0].y, out[c][1].x, out[c][1].y);
+        if (STAGE == 2) {
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            float v[C];
+#pragma unroll
+            for (int c = 0; c < C; ++c) v[c] = (k & 1) ? out[c][k >> 1].y : out[c][k >> 1].x;
+            float sp;
+            if constexpr (EQ == SWE) {
+              sp = cell_rate_swe(v[0], v[1], v[2], a.phys, a.rdx, a.rdy, bad);
+            } else {
+              sp = cell_rate_euler(v, a.phys, a.rdx, a.rdy, bad);
+            }
+            amax = fmaxf(amax, sp);
+          }
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        Gp[c][0] = Gn[c][0];
+        Gp[c][1] = Gn[c][1];
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      PL[c][0] = face_left(q1[c][0], sy[c][0]);
+      PL[c][1] = face_left(q1[c][1], sy[c][1]);
+    }
+  }
+  cp_async_wait<0>();
+  if (STAGE == 2) {
+    block_reduce_max_or(amax, bad, red);
+    if (t == 0) publish_and_close(ctrl, a.dp, amax, bad, gridDim.x * gridDim.y, true);
   }
 }
 
@@ -265,19 +544,66 @@ __global__ void set_t_end_kernel(Ctrl* ctrl, int B, double t_end) {
   }
 }
 
+// Rows per march block: long strips amortise the 4 halo rows, but the grid
+// must fill the GPU in whole waves.  Among TY in [8, 128] pick the one whose
+// last wave is fullest (ties: larger TY).
+int march_rows_per_block(int ny, int columns_x_members, int per_sm) {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms < 1) sms = 1;
+  }
+  const long long slots = (long long)sms * per_sm;
+  int best = ny < 8 ? ny : 8;
+  double best_eff = -1.0;
+  for (int ty = 8; ty <= 128; ++ty) {
+    if (ty > ny && ty != 8) break;
+    const long long blocks = (long long)columns_x_members * ((ny + ty - 1) / ty);
+    const long long waves = (blocks + slots - 1) / slots;
+    // useful fraction: block work over wave slots, discounting the halo rows
+    const double eff = (double)blocks / (double)(waves * slots) * (double)ty / (ty + 4.0);
+    if (eff >= best_eff) {
+      best_eff = eff;
+      best = ty;
+    }
+  }
+  return best;
+}
+
 template <int C, int EQ, int STAGE>
 cudaError_t launch_stage_t(const Geom& g, const float* qin, const float* qn, float* qout,
-                           Ctrl* ctrl, const DtParams* dp, cudaStream_t s) {
+                           Ctrl* ctrl, const DtParams* dp, cudaStream_t s, int variant) {
+  StageArgs a{qin, qn, qout, ctrl, dp, g.nx, g.ny, g.plane(), g.member(),
+              (float)(1.0 / g.dx), (float)(1.0 / g.dy), g.phys};
+  const bool march_ok = (g.nx % 4 == 0) && g.nx >= 8;
+  if (variant == STAGE_MARCH && !march_ok) return cudaErrorInvalidValue;
+  if (variant != STAGE_TILE && march_ok) {
+    constexpr int smem = march_smem_bytes<C>();
+    auto kern = stage_march_kernel<C, EQ, STAGE>;
+    static int per_sm = 0;   // resident blocks per SM, queried once per instance
+    if (!per_sm) {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      if (e != cudaSuccess) return e;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, MT, smem);
+      if (e != cudaSuccess) return e;
+      if (per_sm < 1) per_sm = 1;
+    }
+    const int nsx = (g.nx + MW - 1) / MW;
+    const int TY = march_rows_per_block(g.ny, nsx * g.B, per_sm);
+    dim3 grid(nsx, (g.ny + TY - 1) / TY, g.B);
+    kern<<<grid, MT, smem, s>>>(a, TY);
+    return cudaGetLastError();
+  }
   constexpr int smem = stage_smem_bytes<C>();
   auto kern = stage_minmod_kernel<C, EQ, STAGE>;
-  static bool attr_set = false;   // set once per process (per template instance)
+  static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  StageArgs a{qin, qn, qout, ctrl, dp, g.nx, g.ny, g.plane(), g.member(),
-              (float)(1.0 / g.dx), (float)(1.0 / g.dy), g.phys};
   dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, g.B);
   kern<<<grid, NT, smem, s>>>(a);
   return cudaGetLastError();
@@ -286,13 +612,14 @@ cudaError_t launch_stage_t(const Geom& g, const float* qin, const float* qn, flo
 }  // namespace
 
 cudaError_t launch_stage_minmod(const Geom& g, int stage, const float* qin, const float* qn,
-                                float* qout, Ctrl* ctrl, const DtParams* dp, cudaStream_t s) {
+                                float* qout, Ctrl* ctrl, const DtParams* dp, cudaStream_t s,
+                                int variant) {
   if (g.eq == SWE) {
-    return stage == 1 ? launch_stage_t<3, SWE, 1>(g, qin, qn, qout, ctrl, dp, s)
-                      : launch_stage_t<3, SWE, 2>(g, qin, qn, qout, ctrl, dp, s);
+    return stage == 1 ? launch_stage_t<3, SWE, 1>(g, qin, qn, qout, ctrl, dp, s, variant)
+                      : launch_stage_t<3, SWE, 2>(g, qin, qn, qout, ctrl, dp, s, variant);
   }
-  return stage == 1 ? launch_stage_t<4, EULER, 1>(g, qin, qn, qout, ctrl, dp, s)
-                    : launch_stage_t<4, EULER, 2>(g, qin, qn, qout, ctrl, dp, s);
+  return stage == 1 ? launch_stage_t<4, EULER, 1>(g, qin, qn, qout, ctrl, dp, s, variant)
+                    : launch_stage_t<4, EULER, 2>(g, qin, qn, qout, ctrl, dp, s, variant);
 }
 
 cudaError_t launch_wavespeed_init(const Geom& g, const float* q, Ctrl* ctrl, const DtParams* dp,

@@ -177,9 +177,11 @@ cudaError_t leave(fv_state* s) {
 }
 
 cudaError_t enqueue_plain_step(fv_state* s) {
-  cudaError_t e = fvk::launch_stage_minmod(s->g, 1, s->qA, nullptr, s->qB, s->ctrl, s->dp, s->stream);
+  cudaError_t e = fvk::launch_stage_minmod(s->g, 1, s->qA, nullptr, s->qB, s->ctrl, s->dp,
+                                           s->stream, s->variant);
   if (e != cudaSuccess) return e;
-  return fvk::launch_stage_minmod(s->g, 2, s->qB, s->qA, s->qA, s->ctrl, s->dp, s->stream);
+  return fvk::launch_stage_minmod(s->g, 2, s->qB, s->qA, s->qA, s->ctrl, s->dp, s->stream,
+                                  s->variant);
 }
 
 cudaError_t enqueue_step(fv_state* s, const fv_net* net) {
@@ -396,6 +398,19 @@ extern "C" int fv_diagnostics(const fv_state* cs, double* sums) {
                               cudaMemcpyDeviceToHost, s->stream));
   FV_CUDA_TRY(fvs::leave(s));
   FV_CUDA_TRY(cudaStreamSynchronize(s->stream));
+  return FV_OK;
+}
+
+extern "C" int fv_set_stage_variant(fv_state* s, int variant) {
+  if (!s) return fvh::fail(FV_EINVAL, "null state");
+  if (variant < fvk::STAGE_AUTO || variant > fvk::STAGE_MARCH)
+    return fvh::fail(FV_EINVAL, "unknown stage variant");
+  if (variant == fvk::STAGE_MARCH && (s->g.nx % 4 != 0 || s->g.nx < 8))
+    return fvh::fail(FV_EINVAL, "the row-march kernel needs nx % 4 == 0 and nx >= 8");
+  FV_CUDA_TRY(cudaStreamSynchronize(s->stream));
+  s->variant = variant;
+  if (s->graph) cudaGraphExecDestroy(s->graph);
+  s->graph = nullptr;
   return FV_OK;
 }
 

@@ -63,6 +63,7 @@ _SIGS = {
     "fv_set_state": [c_void_p, c_void_p, c_int],
     "fv_state_device_ptr": [c_void_p, ctypes.POINTER(c_void_p)],
     "fv_state_stream": [c_void_p, ctypes.POINTER(c_void_p)],
+    "fv_set_stage_variant": [c_void_p, c_int],
     "fv_get_time": [c_void_p, c_void_p, c_void_p, c_void_p],
     "fv_health": [c_void_p, c_void_p],
     "fv_diagnostics": [c_void_p, c_void_p],
@@ -219,6 +220,13 @@ def fv_set_state(s: State, q: torch.Tensor) -> None:
     q = q.contiguous()
     ptr, loc = _ptr_loc(q)
     _check(lib().fv_set_state(s.handle, ptr, loc))
+
+
+STAGE_VARIANTS = {"auto": 0, "tile": 1, "march": 2}
+
+
+def fv_set_stage_variant(s: State, variant: str) -> None:
+    _check(lib().fv_set_stage_variant(s.handle, STAGE_VARIANTS[variant]))
 
 
 def fv_get_time(s: State):
