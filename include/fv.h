@@ -170,6 +170,49 @@ int fv_health(const fv_state* s, unsigned* flags);
  * integral of rho (u^2+v^2)/2.  Deterministic (fixed reduction order). */
 int fv_diagnostics(const fv_state* s, double* sums);
 
+/* Learned step: the positivity threshold h_min = hmin_frac * (mean depth of
+ * each member when its first learned step is taken; the mean depth is
+ * conserved).  Learned face states with a depth below h_min fall back to the
+ * MUSCL-minmod states.  Default 1e-3.  Must be set before the first learned
+ * step (FV_EINVAL after). */
+int fv_set_learned_hmin(fv_state* s, double hmin_frac);
+
+/* ---------------------------------------------------------------------------
+ * Learned stencil network (Section 2.5.3, fourth approach)
+ *
+ * x = (q - mean) / std per channel; four 3x3 convolutions with periodic
+ * padding, 3 -> 32 -> 32 -> 32 -> 36 channels, ReLU after the first three;
+ * BF16 operands, FP32 accumulation on the tensor cores.  The 36 outputs of
+ * cell i are r[((dir * 3 + var) * 2 + side) * 3 + tap] (dir 0 = x, 1 = y;
+ * side 0 = Q^L of face i+1/2 on cells {i-1, i, i+1}, side 1 = Q^R on
+ * {i, i+1, i+2}); each 3-tap stencil is normalised to w = e_centre + r -
+ * mean(r), so the weights sum to one and r = 0 gives the first-order scheme.
+ * ------------------------------------------------------------------------- */
+
+/* Number of parameters: W1[32][3][3][3] b1[32] W2[32][32][3][3] b2[32]
+ * W3[32][32][3][3] b3[32] W4[36][32][3][3] b4[36], concatenated in that
+ * order (PyTorch Conv2d layout). */
+#define FV_NET_PARAMS 29796
+
+/* Create a network.  params: host [FV_NET_PARAMS] FP32 (NULL = all zeros:
+ * the first-order scheme); norm: host [6] = mean[3], std[3] of (h, hu, hv)
+ * (NULL = 0 and 1).  Errors: FV_EINVAL, FV_ENOMEM, FV_ECUDA. */
+int stencil_net_create(const float* params, const float* norm, fv_net** out);
+int stencil_net_destroy(fv_net* n);
+
+/* Replace / read the FP32 parameters ([FV_NET_PARAMS], location loc). */
+int stencil_net_set_params(fv_net* n, const float* params, int loc);
+int stencil_net_get_params(const fv_net* n, float* params, int loc);
+
+/* Forward on q (device [B][3][ny][nx] FP32): coeffs (device [B][36][ny][nx]
+ * FP32) receives the normalised stencil weights, or the raw network outputs
+ * r if raw != 0.  nx must be 8, 16, 32, 64 or a multiple of 128 and nx*ny a
+ * multiple of 128 (FV_EINVAL otherwise).  stream: cudaStream_t or NULL (the
+ * network's own stream); the call waits for completion.  FV_ETIMEOUT if a
+ * bounded tensor-core wait gave up. */
+int stencil_net_forward(const fv_net* n, const float* q, int B, int ny, int nx, float* coeffs,
+                        int raw, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -7,6 +7,12 @@
 #include "fv_common.cuh"
 #include "fv_kernels.h"
 
+namespace fvk {
+cudaError_t launch_stage_learned(const Geom& g, int stage, const float* qin, const float* qn,
+                                 float* qout, const float* w, const float* hmin, Ctrl* ctrl,
+                                 const DtParams* dp, cudaStream_t s);
+}
+
 struct fv_learned_ws;   // per-state workspace of the learned step (fv_learned.cu)
 
 struct fv_state {
@@ -29,7 +35,7 @@ struct fv_state {
   long graph_steps = 0;
   const fv_net* graph_net = nullptr;
   fv_learned_ws* lws = nullptr;        // learned-step workspace (lazily created)
-  float h_min = 0.f;                   // positivity threshold of learned faces
+  float hmin_frac = 1e-3f;             // learned faces: h_min = hmin_frac * mean depth
   int variant = 0;                     // stage kernel choice (fvk::STAGE_*)
 };
 
@@ -42,6 +48,8 @@ cudaError_t enqueue_plain_step(fv_state* s);
 cudaError_t enqueue_step(fv_state* s, const fv_net* net);
 int check_health(fv_state* s);
 // learned path (fv_learned.cu)
+int learned_prepare(fv_state* s);                    // host side, before enqueueing
 cudaError_t enqueue_learned_step(fv_state* s, const fv_net* net);
 void learned_workspace_free(fv_state* s);
+int net_check(const fv_net* n);                      // device error word of a network
 }  // namespace fvs

@@ -1,7 +1,257 @@
-// fv_learned.cu — learned-stencil step (placeholder until the CNN kernels land).
+// fv_learned.cu — the learned-stencil SSP-RK2 step (shallow water).
+//
+// Each Runge-Kutta stage (Eq. 2.19) runs the CNN on the stage input to get the
+// 36 normalised coefficients per cell (Section 2.5.3, fourth approach), then
+// one fused stage kernel: face states from the coefficients of the face's
+// owner cell (cell i owns faces i+1/2 in x and j+1/2 in y),
+//   Q^L = wL0 Q_{i-1} + wL1 Q_i + wL2 Q_{i+1},  Q^R = wR0 Q_i + wR1 Q_{i+1} + wR2 Q_{i+2},
+// replaced by the MUSCL-minmod states (Eq. 2.18) wherever a learned depth
+// falls below h_min (positivity fallback); then the same HLL flux, flux
+// divergence and RK combine as the plain step.
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "fv_common.cuh"
 #include "fv_internal.h"
+#include "stencil_net.cuh"
+
+struct fv_learned_ws {
+  float* w = nullptr;          // coefficients [B][36][plane]
+  float* hmin = nullptr;       // per member positivity threshold (device)
+  snk::Acts acts;
+};
+
+namespace fvk {
+namespace {
+
+constexpr int TX = 64, TY = 16, SX = TX + 4, SY = TY + 4, NT = 256;
+constexpr int C = 3;
+
+constexpr int learned_smem_bytes() {
+  return (C * (SY * SX + TY * (TX + 1) + (TY + 1) * TX) + 4 * (NT / 32)) * 4;
+}
+
+struct LArgs {
+  const float* qin;
+  const float* qn;
+  float* qout;
+  const float* w;      // [B][36][plane]
+  const float* hmin;   // [B]
+  Ctrl* ctrl;
+  const DtParams* dp;
+  int nx, ny;
+  long long plane, member;
+  float rdx, rdy, g;
+};
+
+// Learned (or, below h_min, minmod) face states of one face from its 4-cell
+// stencil m = Q_{i-1}, a = Q_i, b = Q_{i+1}, p = Q_{i+2} and the owner's 18
+// coefficients of this direction, wd[(var * 2 + side) * 3 + tap].
+__device__ __forceinline__ void learned_face(const float (&m)[C], const float (&a)[C],
+                                             const float (&b)[C], const float (&p)[C],
+                                             const float (&wd)[18], float hmin, float (&L)[C],
+                                             float (&R)[C]) {
+#pragma unroll
+  for (int c = 0; c < C; ++c) {
+    const float* wl = wd + (c * 2 + 0) * 3;
+    const float* wr = wd + (c * 2 + 1) * 3;
+    L[c] = vfma(wl[2], b[c], vfma(wl[1], a[c], vmul(wl[0], m[c])));
+    R[c] = vfma(wr[2], p[c], vfma(wr[1], b[c], vmul(wr[0], a[c])));
+  }
+  if (!(L[0] >= hmin) || !(R[0] >= hmin)) {
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      L[c] = face_left(a[c], minmod(vsub(a[c], m[c]), vsub(b[c], a[c])));
+      R[c] = face_right(b[c], minmod(vsub(b[c], a[c]), vsub(p[c], b[c])));
+    }
+  }
+}
+
+template <int STAGE>
+__global__ void __launch_bounds__(NT) stage_learned_kernel(LArgs a) {
+  extern __shared__ float smem[];
+  float* sq = smem;
+  float* sF = sq + C * SY * SX;
+  float* sG = sF + C * TY * (TX + 1);
+  unsigned* red = reinterpret_cast<unsigned*>(sG + C * (TY + 1) * TX);
+  const int b = blockIdx.z;
+  Ctrl* ctrl = a.ctrl + b;
+  if (skip_if_done(ctrl)) return;
+  const float dt = (float)ctrl->dt;
+  const float hmin = a.hmin[b];
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const float* qin = a.qin + b * a.member;
+  const float* wb = a.w + (long long)b * 36 * a.plane;
+  const int tid = threadIdx.x;
+
+  for (int idx = tid; idx < C * SY * SX; idx += NT) {
+    const int c = idx / (SY * SX);
+    const int r = idx - c * (SY * SX);
+    const int sy = r / SX, sx = r - sy * SX;
+    const int gx = wrap(x0 - 2 + sx, a.nx), gy = wrap(y0 - 2 + sy, a.ny);
+    sq[idx] = qin[c * a.plane + (long long)gy * a.nx + gx];
+  }
+  __syncthreads();
+
+  for (int idx = tid; idx < TY * (TX + 1); idx += NT) {
+    const int r = idx / (TX + 1), k = idx - r * (TX + 1);
+    const int gy = y0 + r;
+    if (gy >= a.ny) continue;
+    const long long owner = (long long)gy * a.nx + wrap(x0 - 1 + k, a.nx);
+    const float* row = sq + (r + 2) * SX + k;
+    float m[C], s0[C], s1[C], p[C], wd[18], L[C], R[C], F[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      const float* rc = row + c * SY * SX;
+      m[c] = rc[0]; s0[c] = rc[1]; s1[c] = rc[2]; p[c] = rc[3];
+    }
+#pragma unroll
+    for (int j = 0; j < 18; ++j) wd[j] = wb[j * a.plane + owner];
+    learned_face(m, s0, s1, p, wd, hmin, L, R);
+    hll_swe<float>(L[0], L[1], L[2], R[0], R[1], R[2], a.g, F[0], F[1], F[2]);
+#pragma unroll
+    for (int c = 0; c < C; ++c) sF[(c * TY + r) * (TX + 1) + k] = F[c];
+  }
+  for (int idx = tid; idx < (TY + 1) * TX; idx += NT) {
+    const int k = idx / TX, i = idx - k * TX;
+    const int gx = x0 + i;
+    if (gx >= a.nx) continue;
+    const long long owner = (long long)wrap(y0 - 1 + k, a.ny) * a.nx + gx;
+    const float* col = sq + k * SX + (i + 2);
+    float m[C], s0[C], s1[C], p[C], wd[18], L[C], R[C], F[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      const float* cc = col + c * SY * SX;
+      m[c] = cc[0]; s0[c] = cc[SX]; s1[c] = cc[2 * SX]; p[c] = cc[3 * SX];
+    }
+#pragma unroll
+    for (int j = 0; j < 18; ++j) wd[j] = wb[(18 + j) * a.plane + owner];
+    learned_face(m, s0, s1, p, wd, hmin, L, R);
+    // rotated frame: normal momentum = hv
+    hll_swe<float>(L[0], L[2], L[1], R[0], R[2], R[1], a.g, F[0], F[2], F[1]);
+#pragma unroll
+    for (int c = 0; c < C; ++c) sG[(c * (TY + 1) + k) * TX + i] = F[c];
+  }
+  __syncthreads();
+
+  float amax = 0.f;
+  unsigned bad = 0u;
+  const float* qn = a.qn + b * a.member;
+  float* qout = a.qout + b * a.member;
+  for (int idx = tid; idx < TY * TX; idx += NT) {
+    const int r = idx / TX, i = idx - r * TX;
+    const int gx = x0 + i, gy = y0 + r;
+    if (gx >= a.nx || gy >= a.ny) continue;
+    const long long off = (long long)gy * a.nx + gx;
+    float out[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      const float L = divergence<float>(sF[(c * TY + r) * (TX + 1) + i], sF[(c * TY + r) * (TX + 1) + i + 1],
+                                        sG[(c * (TY + 1) + r) * TX + i], sG[(c * (TY + 1) + r + 1) * TX + i],
+                                        a.rdx, a.rdy);
+      const float q = sq[(c * SY + r + 2) * SX + i + 2];
+      out[c] = STAGE == 1 ? rk_stage1<float>(q, dt, L) : rk_stage2<float>(qn[c * a.plane + off], q, 0.5f * dt, L);
+      qout[c * a.plane + off] = out[c];
+    }
+    if (STAGE == 2) amax = fmaxf(amax, cell_rate_swe(out[0], out[1], out[2], a.g, a.rdx, a.rdy, bad));
+  }
+  if (STAGE == 2) {
+    block_reduce_max_or(amax, bad, red);
+    if (tid == 0) publish_and_close(ctrl, a.dp, amax, bad, gridDim.x * gridDim.y, true);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_stage_learned(const Geom& g, int stage, const float* qin, const float* qn,
+                                 float* qout, const float* w, const float* hmin, Ctrl* ctrl,
+                                 const DtParams* dp, cudaStream_t s) {
+  constexpr int smem = learned_smem_bytes();
+  LArgs a{qin, qn, qout, w, hmin, ctrl, dp, g.nx, g.ny, g.plane(), g.member(),
+          (float)(1.0 / g.dx), (float)(1.0 / g.dy), g.phys};
+  dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, g.B);
+  if (stage == 1) {
+    static bool attr = false;
+    if (!attr) {
+      cudaError_t e = cudaFuncSetAttribute(stage_learned_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      if (e != cudaSuccess) return e;
+      attr = true;
+    }
+    stage_learned_kernel<1><<<grid, NT, smem, s>>>(a);
+  } else {
+    static bool attr = false;
+    if (!attr) {
+      cudaError_t e = cudaFuncSetAttribute(stage_learned_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      if (e != cudaSuccess) return e;
+      attr = true;
+    }
+    stage_learned_kernel<2><<<grid, NT, smem, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace fvk
 
 namespace fvs {
-cudaError_t enqueue_learned_step(fv_state*, const fv_net*) { return cudaErrorNotSupported; }
-void learned_workspace_free(fv_state*) {}
+
+// Lazily create the learned workspace of a state: coefficient buffer,
+// activations, and h_min = frac * (mean depth of the current state) per member
+// (the mean depth is conserved by the scheme).
+static int learned_ws_ready(fv_state* s, float hmin_frac) {
+  if (s->lws) return FV_OK;
+  if (!snk::grid_supported(s->g.nx) || s->g.plane() % snk::TILE != 0)
+    return fvh::fail(FV_EINVAL, "learned step: nx must be 8, 16, 32, 64 or a multiple of 128, "
+                                "and nx*ny a multiple of 128");
+  fv_learned_ws* w = new fv_learned_ws();
+  const long long cells = (long long)s->g.B * s->g.plane();
+  cudaError_t e = cudaMalloc(&w->w, sizeof(float) * 36 * cells);
+  if (e == cudaSuccess) e = cudaMalloc(&w->hmin, sizeof(float) * s->g.B);
+  if (e == cudaSuccess) e = snk::acts_reserve(w->acts, cells);
+  if (e == cudaSuccess) e = fvk::launch_diagnostics(s->g, s->qA, s->diag_partials, s->diag_out, s->stream);
+  std::vector<double> sums((size_t)s->g.B * (s->g.C + 1));
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(sums.data(), s->diag_out, sizeof(double) * sums.size(), cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e == cudaSuccess) {
+    std::vector<float> hm(s->g.B);
+    const double area = s->lx * s->ly;
+    for (int b = 0; b < s->g.B; ++b) hm[b] = (float)(hmin_frac * sums[(size_t)b * (s->g.C + 1)] / area);
+    e = cudaMemcpy(w->hmin, hm.data(), sizeof(float) * s->g.B, cudaMemcpyHostToDevice);
+  }
+  if (e != cudaSuccess) {
+    cudaFree(w->w);
+    cudaFree(w->hmin);
+    snk::acts_free(w->acts);
+    delete w;
+    return fvh::cuda_fail(e, "learned workspace");
+  }
+  s->lws = w;
+  return FV_OK;
+}
+
+int learned_prepare(fv_state* s) { return learned_ws_ready(s, s->hmin_frac); }
+
+cudaError_t enqueue_learned_step(fv_state* s, const fv_net* net) {
+  if (!s->lws) return cudaErrorNotReady;   // learned_prepare() must run first (host side)
+  fv_learned_ws* w = s->lws;
+  const int B = s->g.B, ny = s->g.ny, nx = s->g.nx;
+  cudaError_t e = snk::forward(net->n, s->qA, B, ny, nx, w->acts, w->w, nullptr, s->stream);
+  if (e != cudaSuccess) return e;
+  e = fvk::launch_stage_learned(s->g, 1, s->qA, nullptr, s->qB, w->w, w->hmin, s->ctrl, s->dp, s->stream);
+  if (e != cudaSuccess) return e;
+  e = snk::forward(net->n, s->qB, B, ny, nx, w->acts, w->w, nullptr, s->stream);
+  if (e != cudaSuccess) return e;
+  return fvk::launch_stage_learned(s->g, 2, s->qB, s->qA, s->qA, w->w, w->hmin, s->ctrl, s->dp, s->stream);
+}
+
+void learned_workspace_free(fv_state* s) {
+  if (!s->lws) return;
+  cudaFree(s->lws->w);
+  cudaFree(s->lws->hmin);
+  snk::acts_free(s->lws->acts);
+  delete s->lws;
+  s->lws = nullptr;
+}
+
 }  // namespace fvs

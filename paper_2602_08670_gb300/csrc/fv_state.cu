@@ -10,6 +10,7 @@
 #include "fv_common.cuh"
 #include "fv_internal.h"
 #include "fv_kernels.h"
+#include "stencil_net.cuh"
 
 // ---------------------------------------------------------------------------
 // Error reporting
@@ -248,6 +249,10 @@ extern "C" int fv_set_replay_dt(fv_state* s, const double* dts, long n) {
 extern "C" int fv_step(fv_state* s, const fv_net* net) {
   if (!s) return fvh::fail(FV_EINVAL, "null state");
   if (net && s->g.eq != fvk::SWE) return fvh::fail(FV_EINVAL, "learned step is SWE only");
+  if (net) {
+    int rc = fvs::learned_prepare(s);
+    if (rc != FV_OK) return rc;
+  }
   FV_CUDA_TRY(fvs::enter(s));
   FV_CUDA_TRY(fvs::enqueue_step(s, net));
   FV_CUDA_TRY(fvs::leave(s));
@@ -308,6 +313,10 @@ extern "C" int fv_enqueue_steps(fv_state* s, const fv_net* net, long nsteps) {
   if (!s) return fvh::fail(FV_EINVAL, "null state");
   if (nsteps < 0) return fvh::fail(FV_EINVAL, "nsteps < 0");
   if (net && s->g.eq != fvk::SWE) return fvh::fail(FV_EINVAL, "learned step is SWE only");
+  if (net) {
+    int rc = fvs::learned_prepare(s);
+    if (rc != FV_OK) return rc;
+  }
   FV_CUDA_TRY(fvs::enter(s));
   const long chunk = nsteps < 32 ? (nsteps > 0 ? nsteps : 1) : 32;
   int rc = enqueue_steps(s, net, nsteps, chunk, nullptr, FV_DEVICE);
@@ -322,6 +331,10 @@ extern "C" int fv_rollout(fv_state* s, const fv_net* net, long nsteps, double t_
   if (nsteps < 0) return fvh::fail(FV_EINVAL, "nsteps < 0");
   if (net && s->g.eq != fvk::SWE) return fvh::fail(FV_EINVAL, "learned step is SWE only");
   if (snaps && snap_every <= 0) return fvh::fail(FV_EINVAL, "snap_every must be > 0 with snaps");
+  if (net) {
+    int rc = fvs::learned_prepare(s);
+    if (rc != FV_OK) return rc;
+  }
   FV_CUDA_TRY(fvs::enter(s));
   FV_CUDA_TRY(fvk::launch_set_t_end(s->ctrl, s->g.B, t_end, s->stream));
   const long chunk = snaps ? snap_every : (nsteps < 32 ? (nsteps > 0 ? nsteps : 1) : 32);
@@ -333,6 +346,10 @@ extern "C" int fv_rollout(fv_state* s, const fv_net* net, long nsteps, double t_
     std::vector<fvk::Ctrl> c(s->g.B);
     FV_CUDA_TRY(cudaMemcpy(c.data(), s->ctrl, sizeof(fvk::Ctrl) * s->g.B, cudaMemcpyDeviceToHost));
     for (int b = 0; b < s->g.B; ++b) t_out[b] = c[b].t;
+  }
+  if (net) {
+    int rc = fvs::net_check(net);
+    if (rc != FV_OK) return rc;
   }
   return fvs::check_health(s);
 }
@@ -411,6 +428,14 @@ extern "C" int fv_set_stage_variant(fv_state* s, int variant) {
   s->variant = variant;
   if (s->graph) cudaGraphExecDestroy(s->graph);
   s->graph = nullptr;
+  return FV_OK;
+}
+
+extern "C" int fv_set_learned_hmin(fv_state* s, double hmin_frac) {
+  if (!s) return fvh::fail(FV_EINVAL, "null state");
+  if (!(hmin_frac >= 0.0) || hmin_frac >= 1.0) return fvh::fail(FV_EINVAL, "hmin_frac must be in [0, 1)");
+  if (s->lws) return fvh::fail(FV_EINVAL, "h_min is fixed once the state has taken a learned step");
+  s->hmin_frac = (float)hmin_frac;
   return FV_OK;
 }
 

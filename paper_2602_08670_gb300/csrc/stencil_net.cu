@@ -1,0 +1,484 @@
+// stencil_net.cu — the learned-stencil CNN on tcgen05 tensor cores.
+//
+// Each 3x3 periodic convolution is an implicit GEMM: M = 128 consecutive
+// cells of one member, N = output channels, K = 9 taps x input channels.  A
+// CTA stages the input cells its tile needs (with periodic wrap) in shared
+// memory in the K-major canonical layout [channel group][position][8 BF16],
+// arranged so that for every tap the 128 shifted input rows are contiguous
+// positions: one shared-memory descriptor per (tap, 16-channel step) then
+// addresses them directly, and 9 x (C_in / 16) tcgen05.mma instructions
+// accumulate the tile in TMEM (FP32).  The epilogue reads TMEM, adds the
+// bias and either applies ReLU and stores BF16 activations, or normalises
+// each 3-tap stencil (w = e_centre + r - mean(r)) and stores the FP32
+// coefficients.  The first layer reads the FP32 state and normalises it
+// (x = (q - mean) / std) while staging.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "fv_common.cuh"
+#include "stencil_net.cuh"
+#include "tc_common.cuh"
+
+namespace snk {
+
+ParamLayout param_layout() {
+  ParamLayout L{};
+  const int cout[4] = {HID, HID, HID, N_OUT};
+  const int cin[4] = {C_IN, HID, HID, HID};
+  int off = 0;
+  for (int l = 0; l < 4; ++l) {
+    L.cout[l] = cout[l];
+    L.cin[l] = cin[l];
+    L.w[l] = off;
+    off += cout[l] * cin[l] * 9;
+    L.b[l] = off;
+    off += cout[l];
+  }
+  return L;
+}
+
+bool grid_supported(int nx) { return nx % TILE == 0 || nx == 8 || nx == 16 || nx == 32 || nx == 64; }
+
+namespace {
+
+constexpr int NT = 128;                 // threads per CTA (4 warps = 128 TMEM lanes)
+constexpr int RW = TILE + 2;            // row mode: staged row width (1-cell halo each side)
+constexpr int NPOS_ROW = 3 * RW;        // row mode: 3 rows
+constexpr int NPOS_MAX = 3 * (TILE + 2 * 64);   // flat mode with nx <= 64
+constexpr uint32_t WAIT_ITERS = 1u << 22;
+
+enum { IN_STATE = 0, IN_ACT = 1 };
+enum { OUT_RELU = 0, OUT_W = 1, OUT_RAW = 2 };
+
+struct ConvArgs {
+  const float* q;          // IN_STATE: [B][3][plane]
+  const uint16_t* x;       // IN_ACT: [B][4][plane][8]
+  const uint16_t* wpk;     // [9][CG][N][8]
+  const float* bias;
+  uint16_t* y;             // OUT_RELU: [B][4][plane][8]
+  float* w;                // OUT_W / OUT_RAW: [B][36][plane]
+  float mean0, mean1, mean2, rstd0, rstd1, rstd2;
+  int nx, ny;
+  long long plane;
+  unsigned* err;
+};
+
+__device__ __forceinline__ int wrapi(int i, int n) {
+  i %= n;
+  return i < 0 ? i + n : i;
+}
+
+__device__ __forceinline__ int floordiv(int a, int b) {
+  const int q = a / b;
+  return (a % b != 0 && (a < 0) != (b < 0)) ? q - 1 : q;
+}
+
+template <int CG, int N>
+constexpr int conv_smem_bytes() {
+  return CG * NPOS_MAX * 16 + 9 * CG * N * 16 + 64;
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(tc::smem_u32(smem)), "l"(gmem)
+               : "memory");
+}
+
+template <int CG, int N, int IN, int OUT>
+__global__ void __launch_bounds__(NT) conv_kernel(ConvArgs a) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint8_t* sA = smem;                                   // [CG][NPOS_MAX][16 B]
+  uint8_t* sB = smem + CG * NPOS_MAX * 16;              // [9][CG][N][16 B]
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sB + 9 * CG * N * 16);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+
+  const int tid = threadIdx.x;
+  const long long tiles_per_member = a.plane / TILE;
+  const int b = (int)(blockIdx.x / tiles_per_member);
+  const int p0 = (int)(blockIdx.x - (long long)b * tiles_per_member) * TILE;
+  const int nx = a.nx, ny = a.ny;
+  const bool rowmode = nx % TILE == 0;
+  const int y0 = p0 / nx, x0 = p0 - (p0 / nx) * nx;
+  const int Lf = TILE + 2 * nx;
+  const int npos = rowmode ? NPOS_ROW : 3 * Lf;
+
+  if (tid < 32) tc::tmem_alloc(tslot, 64);
+  if (tid == 0) tc::mbar_init(mbar, 1);
+
+  // weights: 9 * CG * N chunks of 16 bytes
+  for (int i = tid; i < 9 * CG * N; i += NT) cp_async16(sB + i * 16, a.wpk + i * 8);
+
+  // input positions
+  for (int n = tid; n < npos; n += NT) {
+    int yy, xx;
+    if (rowmode) {
+      const int dyi = n / RW, xi = n - dyi * RW;
+      yy = wrapi(y0 - 1 + dyi, ny);
+      xx = wrapi(x0 - 1 + xi, nx);
+    } else {
+      const int dxi = n / Lf;
+      const int c = p0 + (n - dxi * Lf) - nx;
+      const int r = floordiv(c, nx);
+      yy = wrapi(r, ny);
+      xx = wrapi(c - r * nx + dxi - 1, nx);
+    }
+    const long long cell = (long long)yy * nx + xx;
+    if constexpr (IN == IN_ACT) {
+#pragma unroll
+      for (int g = 0; g < CG; ++g)
+        cp_async16(sA + (g * NPOS_MAX + n) * 16, a.x + (((long long)b * CG + g) * a.plane + cell) * 8);
+    } else {
+      const float* qb = a.q + (long long)b * 3 * a.plane;
+      const float h0 = (qb[cell] - a.mean0) * a.rstd0;
+      const float h1 = (qb[a.plane + cell] - a.mean1) * a.rstd1;
+      const float h2 = (qb[2 * a.plane + cell] - a.mean2) * a.rstd2;
+      uint4 v0 = make_uint4(pack_bf16x2(h0, h1), pack_bf16x2(h2, 0.f), 0u, 0u);
+      *reinterpret_cast<uint4*>(sA + n * 16) = v0;
+#pragma unroll
+      for (int g = 1; g < CG; ++g) *reinterpret_cast<uint4*>(sA + (g * NPOS_MAX + n) * 16) = make_uint4(0, 0, 0, 0);
+    }
+  }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+  tc::fence_proxy_async_smem();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tslot;
+
+  if (tid == 0) {
+    constexpr uint32_t idesc = tc::idesc_bf16_f32(TILE, N);
+    const uint32_t a0 = tc::smem_u32(sA), b0 = tc::smem_u32(sB);
+    bool acc = false;
+#pragma unroll 1
+    for (int tap = 0; tap < 9; ++tap) {
+      const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+      const int start = rowmode ? (1 + dy) * RW + (1 + dx) : (1 + dx) * Lf + nx + dy * nx;
+#pragma unroll
+      for (int ks = 0; ks < CG / 2; ++ks) {
+        const uint64_t ad = tc::sdesc(a0 + (uint32_t)((2 * ks * NPOS_MAX + start) * 16), NPOS_MAX * 16, 128);
+        const uint64_t bd = tc::sdesc(b0 + (uint32_t)(((tap * CG + 2 * ks) * N) * 16), N * 16, 128);
+        tc::mma_bf16(tmem, ad, bd, idesc, acc);
+        acc = true;
+      }
+    }
+    tc::mma_commit(mbar);
+  }
+  const bool ok = tc::mbar_wait_bounded(mbar, 0, WAIT_ITERS);
+  if (!ok && tid == 0) atomicOr(a.err, 1u);
+  tc::fence_after_sync();
+
+  if (ok) {
+    const int w = tid >> 5;
+    const int m = tid;                                   // TMEM lane = tile row
+    const long long cell = p0 + m;
+    const uint32_t lane_addr = tmem + ((uint32_t)(32 * w) << 16);
+    if constexpr (OUT == OUT_RELU) {
+      float v[32];
+      tc::tmem_ld32(lane_addr, v);
+#pragma unroll
+      for (int g = 0; g < 4; ++g) {
+        uint32_t pk[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int c0 = 8 * g + 2 * j;
+          pk[j] = pack_bf16x2(fmaxf(v[c0] + a.bias[c0], 0.f), fmaxf(v[c0 + 1] + a.bias[c0 + 1], 0.f));
+        }
+        *reinterpret_cast<uint4*>(a.y + (((long long)b * 4 + g) * a.plane + cell) * 8) =
+            make_uint4(pk[0], pk[1], pk[2], pk[3]);
+      }
+    } else {
+      float v[32], v2[16];
+      tc::tmem_ld32(lane_addr, v);
+      tc::tmem_ld16(lane_addr + 32, v2);
+      float r[N_OUT];
+#pragma unroll
+      for (int k = 0; k < 32; ++k) r[k] = v[k] + a.bias[k];
+#pragma unroll
+      for (int k = 32; k < N_OUT; ++k) r[k] = v2[k - 32] + a.bias[k];
+      float* wb = a.w + (long long)b * N_OUT * a.plane + cell;
+      if constexpr (OUT == OUT_RAW) {
+#pragma unroll
+        for (int k = 0; k < N_OUT; ++k) wb[k * a.plane] = r[k];
+      } else {
+#pragma unroll
+        for (int s = 0; s < N_OUT / 3; ++s) {
+          const float mean = (r[3 * s] + r[3 * s + 1] + r[3 * s + 2]) * (1.f / 3.f);
+          wb[(3 * s) * a.plane] = r[3 * s] - mean;
+          wb[(3 * s + 1) * a.plane] = 1.f + (r[3 * s + 1] - mean);
+          wb[(3 * s + 2) * a.plane] = r[3 * s + 2] - mean;
+        }
+      }
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (tid < 32) tc::tmem_dealloc(tmem, 64);
+}
+
+// FP32 master parameters -> BF16 operand layouts.
+//   forward  wf[l][tap][g][n][k8] = W_l[n][8g + k8][ky][kx]
+//   backward wb[l][tap][g][n][k8] = W_l[8g + k8][n][2 - ky][2 - kx]   (l >= 1)
+__global__ void repack_kernel(const float* params, ParamLayout L, uint16_t* wf0, uint16_t* wf1,
+                              uint16_t* wf2, uint16_t* wf3, uint16_t* wb1, uint16_t* wb2,
+                              uint16_t* wb3) {
+  uint16_t* wf[4] = {wf0, wf1, wf2, wf3};
+  uint16_t* wb[4] = {nullptr, wb1, wb2, wb3};
+  const int cgs[4] = {CG_IN0, CG_HID, CG_HID, CG_HID};
+  const int ns[4] = {HID, HID, HID, N_OUT_PAD};
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  for (int l = 0; l < 4; ++l) {
+    const int CG = cgs[l], N = ns[l];
+    const int total = 9 * CG * N * 8;
+    if (i < total) {
+      const int k8 = i % 8, n = (i / 8) % N, g = (i / (8 * N)) % CG, tap = i / (8 * N * CG);
+      const int ci = 8 * g + k8, co = n;
+      float v = 0.f;
+      if (ci < L.cin[l] && co < L.cout[l]) v = params[L.w[l] + ((co * L.cin[l] + ci) * 3 + tap / 3) * 3 + tap % 3];
+      const __nv_bfloat16 h = __float2bfloat16_rn(v);
+      wf[l][i] = *reinterpret_cast<const uint16_t*>(&h);
+    }
+    if (l >= 1) {
+      // dX of layer l: K = its output channels (groups of 8), N = its inputs (32)
+      const int CGo = (L.cout[l] + 7) / 8 + ((L.cout[l] + 7) / 8) % 2;   // even number of groups
+      const int Nb = HID;
+      const int totb = 9 * CGo * Nb * 8;
+      if (i < totb) {
+        const int k8 = i % 8, n = (i / 8) % Nb, g = (i / (8 * Nb)) % CGo, tap = i / (8 * Nb * CGo);
+        const int co = 8 * g + k8, ci = n;
+        const int fy = 2 - tap / 3, fx = 2 - tap % 3;
+        float v = 0.f;
+        if (co < L.cout[l] && ci < L.cin[l]) v = params[L.w[l] + ((co * L.cin[l] + ci) * 3 + fy) * 3 + fx];
+        const __nv_bfloat16 h = __float2bfloat16_rn(v);
+        wb[l][i] = *reinterpret_cast<const uint16_t*>(&h);
+      }
+    }
+  }
+}
+
+template <int CG, int N, int IN, int OUT>
+cudaError_t launch_conv(const ConvArgs& a, int B, cudaStream_t s) {
+  constexpr int smem = conv_smem_bytes<CG, N>();
+  auto kern = conv_kernel<CG, N, IN, OUT>;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const long long tiles = (long long)B * (a.plane / TILE);
+  kern<<<(unsigned)tiles, NT, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int backward_groups(int cout) {
+  const int g = (cout + 7) / 8;
+  return g + (g % 2);
+}
+
+cudaError_t repack(Net& net, cudaStream_t s) {
+  const ParamLayout L = param_layout();
+  const int maxn = 9 * CG_HID * N_OUT_PAD * 8 > 9 * 6 * HID * 8 ? 9 * CG_HID * N_OUT_PAD * 8 : 9 * 6 * HID * 8;
+  repack_kernel<<<(maxn + 255) / 256, 256, 0, s>>>(net.params, L, net.wf[0], net.wf[1], net.wf[2],
+                                                   net.wf[3], net.wb[1], net.wb[2], net.wb[3]);
+  return cudaGetLastError();
+}
+
+cudaError_t acts_reserve(Acts& acts, long long cells) {
+  if (acts.cells >= cells) return cudaSuccess;
+  acts_free(acts);
+  for (int l = 0; l < 3; ++l) {
+    cudaError_t e = cudaMalloc(&acts.a[l], (size_t)cells * CG_HID * 16);
+    if (e != cudaSuccess) {
+      acts_free(acts);
+      return e;
+    }
+  }
+  acts.cells = cells;
+  return cudaSuccess;
+}
+
+void acts_free(Acts& acts) {
+  for (int l = 0; l < 3; ++l) {
+    cudaFree(acts.a[l]);
+    acts.a[l] = nullptr;
+  }
+  acts.cells = 0;
+}
+
+cudaError_t forward(const Net& net, const float* q, int B, int ny, int nx, Acts& acts, float* w,
+                    float* raw, cudaStream_t s) {
+  const ParamLayout L = param_layout();
+  ConvArgs a{};
+  a.nx = nx;
+  a.ny = ny;
+  a.plane = (long long)nx * ny;
+  a.err = net.err;
+  a.mean0 = net.mean[0];
+  a.mean1 = net.mean[1];
+  a.mean2 = net.mean[2];
+  a.rstd0 = 1.f / net.std_[0];
+  a.rstd1 = 1.f / net.std_[1];
+  a.rstd2 = 1.f / net.std_[2];
+  // layer 1: state -> a0
+  a.q = q;
+  a.wpk = net.wf[0];
+  a.bias = net.params + L.b[0];
+  a.y = acts.a[0];
+  cudaError_t e = launch_conv<CG_IN0, HID, IN_STATE, OUT_RELU>(a, B, s);
+  if (e != cudaSuccess) return e;
+  // layers 2, 3
+  for (int l = 1; l < 3; ++l) {
+    a.x = acts.a[l - 1];
+    a.wpk = net.wf[l];
+    a.bias = net.params + L.b[l];
+    a.y = acts.a[l];
+    e = launch_conv<CG_HID, HID, IN_ACT, OUT_RELU>(a, B, s);
+    if (e != cudaSuccess) return e;
+  }
+  // layer 4: a2 -> coefficients
+  a.x = acts.a[2];
+  a.wpk = net.wf[3];
+  a.bias = net.params + L.b[3];
+  if (raw) {
+    a.w = raw;
+    return launch_conv<CG_HID, N_OUT_PAD, IN_ACT, OUT_RAW>(a, B, s);
+  }
+  a.w = w;
+  return launch_conv<CG_HID, N_OUT_PAD, IN_ACT, OUT_W>(a, B, s);
+}
+
+}  // namespace snk
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+namespace {
+
+int net_alloc(fv_net* n) {
+  snk::Net& N = n->n;
+  cudaError_t e;
+  if ((e = cudaMalloc(&N.params, sizeof(float) * snk::N_PARAMS)) != cudaSuccess) return fvh::cuda_fail(e, "cudaMalloc(params)");
+  const int fsz[4] = {9 * snk::CG_IN0 * snk::HID * 8, 9 * snk::CG_HID * snk::HID * 8,
+                      9 * snk::CG_HID * snk::HID * 8, 9 * snk::CG_HID * snk::N_OUT_PAD * 8};
+  for (int l = 0; l < 4; ++l)
+    if ((e = cudaMalloc(&N.wf[l], 2 * fsz[l])) != cudaSuccess) return fvh::cuda_fail(e, "cudaMalloc(wf)");
+  for (int l = 1; l < 4; ++l) {
+    const int cg = snk::backward_groups(snk::param_layout().cout[l]);
+    if ((e = cudaMalloc(&N.wb[l], 2 * 9 * cg * snk::HID * 8)) != cudaSuccess)
+      return fvh::cuda_fail(e, "cudaMalloc(wb)");
+  }
+  if ((e = cudaMalloc(&N.err, sizeof(unsigned))) != cudaSuccess) return fvh::cuda_fail(e, "cudaMalloc(err)");
+  if ((e = cudaMemset(N.err, 0, sizeof(unsigned))) != cudaSuccess) return fvh::cuda_fail(e, "cudaMemset");
+  if ((e = cudaStreamCreateWithFlags(&n->stream, cudaStreamNonBlocking)) != cudaSuccess)
+    return fvh::cuda_fail(e, "cudaStreamCreate");
+  return FV_OK;
+}
+
+void net_free(fv_net* n) {
+  if (!n) return;
+  if (n->stream) cudaStreamSynchronize(n->stream);
+  cudaFree(n->n.params);
+  for (int l = 0; l < 4; ++l) {
+    cudaFree(n->n.wf[l]);
+    cudaFree(n->n.wb[l]);
+  }
+  cudaFree(n->n.err);
+  snk::acts_free(n->ws);
+  if (n->stream) cudaStreamDestroy(n->stream);
+  delete n;
+}
+
+int net_check_err(const fv_net* n) {
+  unsigned h = 0;
+  cudaError_t e = cudaMemcpy(&h, n->n.err, sizeof h, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return fvh::cuda_fail(e, "reading the network error word");
+  if (h) return fvh::fail(FV_ETIMEOUT, "a tensor-core wait gave up (bounded mbarrier wait)");
+  return FV_OK;
+}
+
+}  // namespace
+
+namespace fvs {
+int net_check(const fv_net* n) { return net_check_err(n); }
+}  // namespace fvs
+
+extern "C" int stencil_net_create(const float* params, const float* norm, fv_net** out) {
+  if (!out) return fvh::fail(FV_EINVAL, "null output");
+  *out = nullptr;
+  fv_net* n = new fv_net();
+  int rc = net_alloc(n);
+  if (rc != FV_OK) {
+    net_free(n);
+    return rc;
+  }
+  if (norm) {
+    for (int c = 0; c < 3; ++c) {
+      n->n.mean[c] = norm[c];
+      n->n.std_[c] = norm[3 + c];
+      if (!(norm[3 + c] > 0.f)) {
+        net_free(n);
+        return fvh::fail(FV_EINVAL, "normalisation std must be > 0");
+      }
+    }
+  }
+  cudaError_t e;
+  if (params) {
+    e = cudaMemcpy(n->n.params, params, sizeof(float) * snk::N_PARAMS, cudaMemcpyHostToDevice);
+  } else {
+    e = cudaMemset(n->n.params, 0, sizeof(float) * snk::N_PARAMS);
+  }
+  if (e == cudaSuccess) e = snk::repack(n->n, n->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(n->stream);
+  if (e != cudaSuccess) {
+    net_free(n);
+    return fvh::cuda_fail(e, "stencil_net_create");
+  }
+  *out = n;
+  return FV_OK;
+}
+
+extern "C" int stencil_net_destroy(fv_net* n) {
+  net_free(n);
+  return FV_OK;
+}
+
+extern "C" int stencil_net_set_params(fv_net* n, const float* params, int loc) {
+  if (!n || !params) return fvh::fail(FV_EINVAL, "null argument");
+  FV_CUDA_TRY(cudaMemcpyAsync(n->n.params, params, sizeof(float) * snk::N_PARAMS,
+                              loc == FV_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                              n->stream));
+  FV_CUDA_TRY(snk::repack(n->n, n->stream));
+  FV_CUDA_TRY(cudaStreamSynchronize(n->stream));
+  return FV_OK;
+}
+
+extern "C" int stencil_net_get_params(const fv_net* n, float* params, int loc) {
+  if (!n || !params) return fvh::fail(FV_EINVAL, "null argument");
+  FV_CUDA_TRY(cudaStreamSynchronize(n->stream));
+  FV_CUDA_TRY(cudaMemcpy(params, n->n.params, sizeof(float) * snk::N_PARAMS,
+                         loc == FV_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost));
+  return FV_OK;
+}
+
+extern "C" int stencil_net_forward(const fv_net* cn, const float* q, int B, int ny, int nx,
+                                   float* coeffs, int raw, void* stream) {
+  fv_net* n = const_cast<fv_net*>(cn);
+  if (!n || !q || !coeffs) return fvh::fail(FV_EINVAL, "null argument");
+  if (B < 1 || ny < 1 || !snk::grid_supported(nx) || ((long long)nx * ny) % snk::TILE != 0)
+    return fvh::fail(FV_EINVAL, "unsupported grid: nx must be 8, 16, 32, 64 or a multiple of 128, "
+                                "and nx*ny a multiple of 128");
+  cudaStream_t s = stream ? (cudaStream_t)stream : n->stream;
+  FV_CUDA_TRY(snk::acts_reserve(n->ws, (long long)B * nx * ny));
+  FV_CUDA_TRY(snk::forward(n->n, q, B, ny, nx, n->ws, raw ? nullptr : coeffs, raw ? coeffs : nullptr, s));
+  FV_CUDA_TRY(cudaStreamSynchronize(s));
+  return net_check_err(n);
+}

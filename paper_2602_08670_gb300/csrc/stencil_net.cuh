@@ -1,0 +1,71 @@
+// stencil_net.cuh — the learned-stencil CNN (internal interface).
+//
+// Section 2.5.3, fourth approach: a CNN maps the cell-average state to
+// constrained reconstruction coefficients.  Architecture: x = (q - mean)/std
+// per channel; four 3x3 convolutions with periodic padding, 3 -> 32 -> 32 ->
+// 32 -> 36 channels, ReLU after the first three.  The 36 outputs of a cell are
+// 2 directions x 3 variables x 2 sides x 3 taps; each 3-tap stencil is
+// normalised to w = e_centre + r - mean(r) (weights sum to one; r = 0 is the
+// first-order scheme).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/fv.h"
+
+namespace snk {
+
+constexpr int C_IN = 3;
+constexpr int HID = 32;
+constexpr int N_OUT = 36;
+constexpr int N_OUT_PAD = 48;        // MMA N must be a multiple of 16
+constexpr int N_PARAMS = 29796;      // W1 b1 W2 b2 W3 b3 W4 b4 (PyTorch order)
+constexpr int CG_IN0 = 2;            // layer-1 input: 3 channels padded to 16 (2 groups of 8)
+constexpr int CG_HID = 4;            // 32 channels = 4 groups of 8
+constexpr int TILE = 128;            // cells per MMA tile (M)
+
+// Offsets of each layer's weight and bias in the flat parameter vector.
+struct ParamLayout {
+  int w[4], b[4], cout[4], cin[4];
+};
+ParamLayout param_layout();
+
+// Device buffers of one network.
+struct Net {
+  float* params = nullptr;     // FP32 master parameters [N_PARAMS]
+  uint16_t* wf[4] = {};        // forward B operands, BF16 [9][CG_in][N][8]
+  uint16_t* wb[4] = {};        // backward (dX) B operands, BF16 [9][CG_out][N_in][8], layers 1..3
+  float mean[3] = {0, 0, 0};
+  float std_[3] = {1, 1, 1};
+  unsigned* err = nullptr;     // device error word (bounded waits that gave up)
+};
+
+// Per-call activation workspace for `cells` = B * plane cells.
+struct Acts {
+  uint16_t* a[3] = {};         // post-ReLU activations of layers 1..3, BF16 [B][4][plane][8]
+  long long cells = 0;
+};
+
+bool grid_supported(int nx);   // nx % 128 == 0, or nx in {8, 16, 32, 64}
+
+// Pack the FP32 master parameters into the BF16 MMA operand layouts.
+cudaError_t repack(Net& net, cudaStream_t s);
+
+// Forward of the whole network on q [B][3][ny][nx] (FP32, device).  Writes
+// the normalised weights w [B][36][ny][nx] (FP32) and keeps the hidden
+// activations in `acts` (which must hold B*ny*nx cells).  If raw != nullptr
+// the un-normalised outputs r [B][36][ny][nx] are written instead of w.
+cudaError_t forward(const Net& net, const float* q, int B, int ny, int nx, Acts& acts, float* w,
+                    float* raw, cudaStream_t s);
+
+cudaError_t acts_reserve(Acts& acts, long long cells);
+void acts_free(Acts& acts);
+
+}  // namespace snk
+
+struct fv_net {
+  snk::Net n;
+  snk::Acts ws;                 // workspace of stencil_net_forward / backward
+  cudaStream_t stream = nullptr;
+};

@@ -64,6 +64,12 @@ _SIGS = {
     "fv_state_device_ptr": [c_void_p, ctypes.POINTER(c_void_p)],
     "fv_state_stream": [c_void_p, ctypes.POINTER(c_void_p)],
     "fv_set_stage_variant": [c_void_p, c_int],
+    "fv_set_learned_hmin": [c_void_p, c_double],
+    "stencil_net_create": [c_void_p, c_void_p, ctypes.POINTER(c_void_p)],
+    "stencil_net_destroy": [c_void_p],
+    "stencil_net_set_params": [c_void_p, c_void_p, c_int],
+    "stencil_net_get_params": [c_void_p, c_void_p, c_int],
+    "stencil_net_forward": [c_void_p, c_void_p, c_int, c_int, c_int, c_void_p, c_int, c_void_p],
     "fv_get_time": [c_void_p, c_void_p, c_void_p, c_void_p],
     "fv_health": [c_void_p, c_void_p],
     "fv_diagnostics": [c_void_p, c_void_p],
@@ -250,3 +256,72 @@ def fv_diagnostics(s: State) -> np.ndarray:
     out = np.zeros((B, C + 1), dtype=np.float64)
     _check(lib().fv_diagnostics(s.handle, out.ctypes.data_as(c_void_p)))
     return out
+
+
+# ---------------------------------------------------------------------------
+# Learned stencil network
+# ---------------------------------------------------------------------------
+
+FV_NET_PARAMS = 29796
+
+
+class Net:
+    """Owner of an ``fv_net*`` handle."""
+
+    def __init__(self, handle: int):
+        self.handle = ctypes.c_void_p(handle)
+
+    def __del__(self):
+        if getattr(self, "handle", None) and self.handle.value and _lib is not None:
+            _lib.stencil_net_destroy(self.handle)
+            self.handle = ctypes.c_void_p(0)
+
+
+def _host_params(params):
+    a = np.ascontiguousarray(np.asarray(params, dtype=np.float32).reshape(-1))
+    if a.size != FV_NET_PARAMS:
+        raise ValueError(f"expected {FV_NET_PARAMS} parameters, got {a.size}")
+    return a
+
+
+def stencil_net_create(params=None, mean=(0.0, 0.0, 0.0), std=(1.0, 1.0, 1.0)) -> Net:
+    norm = np.ascontiguousarray(np.asarray(list(mean) + list(std), dtype=np.float32))
+    out = c_void_p()
+    p = None
+    if params is not None:
+        hp = _host_params(params)
+        p = hp.ctypes.data_as(c_void_p)
+    _check(lib().stencil_net_create(p, norm.ctypes.data_as(c_void_p), ctypes.byref(out)))
+    return Net(out.value)
+
+
+def stencil_net_set_params(net: Net, params) -> None:
+    if isinstance(params, torch.Tensor) and params.is_cuda:
+        t = params.contiguous().float()
+        _check(lib().stencil_net_set_params(net.handle, c_void_p(t.data_ptr()), FV_DEVICE))
+        return
+    hp = _host_params(params)
+    _check(lib().stencil_net_set_params(net.handle, hp.ctypes.data_as(c_void_p), FV_HOST))
+
+
+def stencil_net_get_params(net: Net) -> np.ndarray:
+    out = np.zeros(FV_NET_PARAMS, dtype=np.float32)
+    _check(lib().stencil_net_get_params(net.handle, out.ctypes.data_as(c_void_p), FV_HOST))
+    return out
+
+
+def stencil_net_forward(net: Net, q: torch.Tensor, raw: bool = False) -> torch.Tensor:
+    """Normalised coefficients (or raw outputs) [B][36][ny][nx] for q on the GPU."""
+    q = q.contiguous()
+    if not q.is_cuda or q.dtype != torch.float32 or q.dim() != 4 or q.shape[1] != 3:
+        raise ValueError("q must be a CUDA float32 tensor [B][3][ny][nx]")
+    B, _, ny, nx = q.shape
+    out = torch.empty((B, 36, ny, nx), dtype=torch.float32, device=q.device)
+    _check(lib().stencil_net_forward(net.handle, c_void_p(q.data_ptr()), B, ny, nx,
+                                     c_void_p(out.data_ptr()), int(raw),
+                                     c_void_p(_torch_stream())))
+    return out
+
+
+def fv_set_learned_hmin(s: State, hmin_frac: float) -> None:
+    _check(lib().fv_set_learned_hmin(s.handle, float(hmin_frac)))
