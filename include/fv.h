@@ -213,6 +213,46 @@ int stencil_net_get_params(const fv_net* n, float* params, int loc);
 int stencil_net_forward(const fv_net* n, const float* q, int B, int ny, int nx, float* coeffs,
                         int raw, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Training: taped learned rollout, rollout loss (Eq. 2.28), backward, Adam
+ * ------------------------------------------------------------------------- */
+typedef struct fv_tape fv_tape;
+
+/* A tape for T learned SSP-RK2 steps of B shallow-water members on an
+ * nx x ny periodic unit square with a fixed dt, gravity g and positivity
+ * threshold h_min = hmin_frac * (mean depth of each member's q0).  The tape
+ * owns device buffers for every stage input, the CNN activations and the
+ * coefficients.  net is borrowed and must outlive the tape. */
+int fv_tape_create(fv_net* net, int B, int ny, int nx, int T, double dt, double g, double hmin_frac,
+                   fv_tape** out);
+int fv_tape_destroy(fv_tape* t);
+
+/* Run the T steps from q0 (device [B][3][ny][nx]) with the network's current
+ * parameters, recording the tape; snaps (device [T][B][3][ny][nx], may be
+ * NULL) receives q_1 .. q_T.  Synchronous; FV_EUNSTABLE if a state went
+ * non-physical. */
+int fv_tape_forward(fv_tape* t, const float* q0, float* snaps);
+
+/* Eq. 2.28 over the recorded rollout: loss = sum_{t=1..T} sum_c
+ * mean_{members, cells} ((q_t - target_t) / scale_c)^2 with targets (device
+ * [T][B][3][ny][nx]) and scale3 (host [3]).  Keeps d loss / d q_t on the
+ * tape for fv_tape_backward. */
+int fv_tape_loss(fv_tape* t, const float* targets, const float* scale3, double* loss);
+
+/* Reverse pass through the recorded rollout.  dsnaps: device [T][B][3][ny][nx]
+ * cotangents of q_1 .. q_T, or NULL for the gradient of the last
+ * fv_tape_loss.  Adds the parameter gradient to dparams (device
+ * [FV_NET_PARAMS]); dq0 (device [B][3][ny][nx], may be NULL) receives the
+ * cotangent of q0.  Cotangents between CNN layers are BF16 (tensor-core
+ * operands); everything else is FP32. */
+int fv_tape_backward(fv_tape* t, const float* dsnaps, float* dparams, float* dq0);
+
+/* One Adam step (bias-corrected; moments kept in the network) with the
+ * gradient grad (device [FV_NET_PARAMS]); step counts from 1.  Repacks the
+ * tensor-core weights. */
+int stencil_net_adam_step(fv_net* n, const float* grad, int step, double lr, double b1, double b2,
+                          double eps);
+
 #ifdef __cplusplus
 }
 #endif

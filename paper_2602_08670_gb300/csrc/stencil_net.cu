@@ -51,7 +51,7 @@ constexpr int NPOS_MAX = 3 * (TILE + 2 * 64);   // flat mode with nx <= 64
 constexpr uint32_t WAIT_ITERS = 1u << 22;
 
 enum { IN_STATE = 0, IN_ACT = 1 };
-enum { OUT_RELU = 0, OUT_W = 1, OUT_RAW = 2 };
+enum { OUT_RELU = 0, OUT_W = 1, OUT_RAW = 2, OUT_MASK = 3 };
 
 struct ConvArgs {
   const float* q;          // IN_STATE: [B][3][plane]
@@ -60,6 +60,7 @@ struct ConvArgs {
   const float* bias;
   uint16_t* y;             // OUT_RELU: [B][4][plane][8]
   float* w;                // OUT_W / OUT_RAW: [B][36][plane]
+  const uint16_t* mask;    // OUT_MASK: activation [B][4][plane][8]; output kept where it is > 0
   float mean0, mean1, mean2, rstd0, rstd1, rstd2;
   int nx, ny;
   long long plane;
@@ -179,7 +180,27 @@ __global__ void __launch_bounds__(NT) conv_kernel(ConvArgs a) {
     const int m = tid;                                   // TMEM lane = tile row
     const long long cell = p0 + m;
     const uint32_t lane_addr = tmem + ((uint32_t)(32 * w) << 16);
-    if constexpr (OUT == OUT_RELU) {
+    if constexpr (OUT == OUT_MASK) {
+      // backward through ReLU: cotangent of the layer input, zero where the
+      // stored activation is zero (BF16 out, 32 channels)
+      float v[32];
+      tc::tmem_ld32(lane_addr, v);
+#pragma unroll
+      for (int g = 0; g < 4; ++g) {
+        const uint4 mk = *reinterpret_cast<const uint4*>(a.mask + (((long long)b * 4 + g) * a.plane + cell) * 8);
+        const uint32_t mw[4] = {mk.x, mk.y, mk.z, mk.w};
+        uint32_t pk[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int c0 = 8 * g + 2 * j;
+          const bool p0 = (mw[j] & 0x7FFFu) != 0 && !(mw[j] & 0x8000u);
+          const bool p1 = ((mw[j] >> 16) & 0x7FFFu) != 0 && !((mw[j] >> 16) & 0x8000u);
+          pk[j] = pack_bf16x2(p0 ? v[c0] : 0.f, p1 ? v[c0 + 1] : 0.f);
+        }
+        *reinterpret_cast<uint4*>(a.y + (((long long)b * 4 + g) * a.plane + cell) * 8) =
+            make_uint4(pk[0], pk[1], pk[2], pk[3]);
+      }
+    } else if constexpr (OUT == OUT_RELU) {
       float v[32];
       tc::tmem_ld32(lane_addr, v);
 #pragma unroll
@@ -356,6 +377,317 @@ cudaError_t forward(const Net& net, const float* q, int B, int ny, int nx, Acts&
   return launch_conv<CG_HID, N_OUT_PAD, IN_ACT, OUT_W>(a, B, s);
 }
 
+// ---------------------------------------------------------------------------
+// Backward
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int DW_TILES = 16;         // 128-cell tiles per CTA of the weight-gradient kernel
+
+// Cotangent of the normalised coefficients -> cotangent of the raw outputs
+// (w = e + r - mean(r) per 3-tap stencil: dr_k = dw_k - mean(dw)), stored as
+// BF16 in 6 channel groups (channels 36..47 zero).
+__global__ void coeff_to_raw_kernel(const float* dw, uint16_t* dr, long long plane, long long cells) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= cells) return;
+  const long long b = t / plane, cell = t - b * plane;
+  const float* src = dw + b * N_OUT * plane + cell;
+  float r[48];
+#pragma unroll
+  for (int s = 0; s < N_OUT / 3; ++s) {
+    const float g0 = src[(3 * s) * plane], g1 = src[(3 * s + 1) * plane], g2 = src[(3 * s + 2) * plane];
+    const float m = (g0 + g1 + g2) * (1.f / 3.f);
+    r[3 * s] = g0 - m;
+    r[3 * s + 1] = g1 - m;
+    r[3 * s + 2] = g2 - m;
+  }
+#pragma unroll
+  for (int k = N_OUT; k < 48; ++k) r[k] = 0.f;
+#pragma unroll
+  for (int g = 0; g < 6; ++g) {
+    uint32_t pk[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) pk[j] = pack_bf16x2(r[8 * g + 2 * j], r[8 * g + 2 * j + 1]);
+    *reinterpret_cast<uint4*>(dr + ((b * 6 + g) * plane + cell) * 8) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+  }
+}
+
+__device__ __forceinline__ float bf16_lo(uint32_t v) { return __uint_as_float(v << 16); }
+__device__ __forceinline__ float bf16_hi(uint32_t v) { return __uint_as_float(v & 0xFFFF0000u); }
+
+// Weight and bias gradients of one layer as a deterministic reduction:
+//   dW[co][ci][tap] = sum_cells dy[cell][co] * x[cell + off(tap)][ci],  db[co] = sum dy[cell][co].
+// Each CTA handles DW_TILES tiles of 128 cells (staged like the forward:
+// x in the tap-shifted position layout, FP32) and writes its partial sums;
+// dw_reduce_kernel adds the partials in CTA order.  CI: input channels (3 for
+// the first layer, read from the state and normalised), CO: output channels.
+template <int CI, int CO, int CGO>
+__global__ void __launch_bounds__(288) dw_partial_kernel(const uint16_t* x, const float* q,
+                                                         const uint16_t* dy, float* part, int nx,
+                                                         int ny, long long plane, long long ntiles,
+                                                         float m0, float m1, float m2, float r0,
+                                                         float r1, float r2) {
+  extern __shared__ __align__(16) float dsm[];
+  float* xs = dsm;                            // [NPOS_MAX][CI]
+  float* ys = xs + NPOS_MAX * CI;             // [TILE][CO]
+  const int tid = threadIdx.x;
+  const bool rowmode = nx % TILE == 0;
+  const int Lf = TILE + 2 * nx;
+  const int npos = rowmode ? NPOS_ROW : 3 * Lf;
+  constexpr int NE = 9 * CO;                  // (tap, co) pairs
+  float acc[2][CI];
+  float accb[2];
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    accb[u] = 0.f;
+#pragma unroll
+    for (int c = 0; c < CI; ++c) acc[u][c] = 0.f;
+  }
+  const long long tiles_per_member = plane / TILE;
+  for (int it = 0; it < DW_TILES; ++it) {
+    const long long tile = (long long)blockIdx.x * DW_TILES + it;
+    if (tile >= ntiles) break;
+    const int b = (int)(tile / tiles_per_member);
+    const int p0 = (int)(tile - (long long)b * tiles_per_member) * TILE;
+    const int y0 = p0 / nx, x0 = p0 - (p0 / nx) * nx;
+    __syncthreads();
+    for (int n = tid; n < npos; n += blockDim.x) {
+      int yy, xx;
+      if (rowmode) {
+        const int dyi = n / RW, xi = n - dyi * RW;
+        yy = wrapi(y0 - 1 + dyi, ny);
+        xx = wrapi(x0 - 1 + xi, nx);
+      } else {
+        const int dxi = n / Lf;
+        const int c = p0 + (n - dxi * Lf) - nx;
+        const int r = floordiv(c, nx);
+        yy = wrapi(r, ny);
+        xx = wrapi(c - r * nx + dxi - 1, nx);
+      }
+      const long long cell = (long long)yy * nx + xx;
+      if constexpr (CI == 3) {
+        const float* qb = q + (long long)b * 3 * plane;
+        xs[n * 3 + 0] = __bfloat162float(__float2bfloat16_rn((qb[cell] - m0) * r0));
+        xs[n * 3 + 1] = __bfloat162float(__float2bfloat16_rn((qb[plane + cell] - m1) * r1));
+        xs[n * 3 + 2] = __bfloat162float(__float2bfloat16_rn((qb[2 * plane + cell] - m2) * r2));
+      } else {
+#pragma unroll
+        for (int g = 0; g < CI / 8; ++g) {
+          const uint4 v = *reinterpret_cast<const uint4*>(x + (((long long)b * (CI / 8) + g) * plane + cell) * 8);
+          float* d = xs + n * CI + 8 * g;
+          d[0] = bf16_lo(v.x); d[1] = bf16_hi(v.x); d[2] = bf16_lo(v.y); d[3] = bf16_hi(v.y);
+          d[4] = bf16_lo(v.z); d[5] = bf16_hi(v.z); d[6] = bf16_lo(v.w); d[7] = bf16_hi(v.w);
+        }
+      }
+    }
+    for (int n = tid; n < TILE * CGO; n += blockDim.x) {
+      const int m = n / CGO, g = n - (n / CGO) * CGO;
+      const uint4 v = *reinterpret_cast<const uint4*>(dy + (((long long)b * CGO + g) * plane + p0 + m) * 8);
+      const float vv[8] = {bf16_lo(v.x), bf16_hi(v.x), bf16_lo(v.y), bf16_hi(v.y),
+                           bf16_lo(v.z), bf16_hi(v.z), bf16_lo(v.w), bf16_hi(v.w)};
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        if (8 * g + j < CO) ys[m * CO + 8 * g + j] = vv[j];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int e = tid + u * 288;
+      if (e >= NE) break;
+      const int tap = e / CO, co = e - tap * CO;
+      const int dy_ = tap / 3 - 1, dx_ = tap % 3 - 1;
+      const int start = rowmode ? (1 + dy_) * RW + (1 + dx_) : (1 + dx_) * Lf + nx + dy_ * nx;
+      for (int m = 0; m < TILE; ++m) {
+        const float g = ys[m * CO + co];
+        const float* xr = xs + (start + m) * CI;
+#pragma unroll
+        for (int c = 0; c < CI; ++c) acc[u][c] = fmaf(g, xr[c], acc[u][c]);
+        accb[u] += g;
+      }
+    }
+  }
+  // partials: [cta][tap][co][ci] then [cta][9*CO*CI + co] for the bias
+  float* pp = part + (long long)blockIdx.x * (NE * CI + CO);
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    const int e = tid + u * 288;
+    if (e >= NE) break;
+#pragma unroll
+    for (int c = 0; c < CI; ++c) pp[e * CI + c] = acc[u][c];
+    if (e < CO) pp[NE * CI + e] = accb[u];   // tap 0 threads carry the bias sums
+  }
+}
+
+// Sum the partials in CTA order and add them to dparams (PyTorch layout).
+template <int CI, int CO>
+__global__ void dw_reduce_kernel(const float* part, int nparts, float* dW, float* db, float scale) {
+  constexpr int NE = 9 * CO * CI;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= NE + CO) return;
+  float s = 0.f;
+  for (int k = 0; k < nparts; ++k) s += part[(long long)k * (NE + CO) + i];
+  if (i < NE) {
+    const int c = i % CI, co = (i / CI) % CO, tap = i / (CI * CO);
+    dW[(co * CI + c) * 9 + tap] += scale * s;
+  } else {
+    db[i - NE] += scale * s;
+  }
+}
+
+// Cotangent of the normalised state from the first layer's output cotangent
+// (3 input channels: a small dot product per cell, CUDA cores):
+//   dx[ci](p) = sum_tap sum_co W1[co][ci][tap] dy[co](p - off(tap));  dq += dx / std.
+__global__ void dx_first_kernel(const uint16_t* dy, const float* W1, float* dq, int nx, int ny,
+                                long long plane, long long cells, float r0, float r1, float r2) {
+  __shared__ float w[HID * 3 * 9];
+  for (int i = threadIdx.x; i < HID * 3 * 9; i += blockDim.x) w[i] = W1[i];
+  __syncthreads();
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= cells) return;
+  const long long b = t / plane, cell = t - b * plane;
+  const int y = (int)(cell / nx), x = (int)(cell - (long long)(cell / nx) * nx);
+  float acc[3] = {0.f, 0.f, 0.f};
+  for (int tap = 0; tap < 9; ++tap) {
+    const int ky = tap / 3, kx = tap % 3;
+    const int yy = wrapi(y - (ky - 1), ny), xx = wrapi(x - (kx - 1), nx);
+    const long long c2 = (long long)yy * nx + xx;
+    for (int g = 0; g < 4; ++g) {
+      const uint4 v = *reinterpret_cast<const uint4*>(dy + ((b * 4 + g) * plane + c2) * 8);
+      const float vv[8] = {bf16_lo(v.x), bf16_hi(v.x), bf16_lo(v.y), bf16_hi(v.y),
+                           bf16_lo(v.z), bf16_hi(v.z), bf16_lo(v.w), bf16_hi(v.w)};
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int co = 8 * g + j;
+#pragma unroll
+        for (int ci = 0; ci < 3; ++ci) acc[ci] = fmaf(w[(co * 3 + ci) * 9 + tap], vv[j], acc[ci]);
+      }
+    }
+  }
+  float* d = dq + b * 3 * plane + cell;
+  d[0] += acc[0] * r0;
+  d[plane] += acc[1] * r1;
+  d[2 * plane] += acc[2] * r2;
+}
+
+template <int CI, int CO, int CGO>
+cudaError_t weight_grad(const uint16_t* x, const float* q, const uint16_t* dy, float* dW, float* db,
+                        float* part, int B, int ny, int nx, const Net& net, float scale,
+                        cudaStream_t s) {
+  const long long plane = (long long)nx * ny;
+  const long long ntiles = (long long)B * (plane / TILE);
+  const int nctas = (int)((ntiles + DW_TILES - 1) / DW_TILES);
+  const int smem = (NPOS_MAX * CI + TILE * CO) * 4;
+  auto kern = dw_partial_kernel<CI, CO, CGO>;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  kern<<<nctas, 288, smem, s>>>(x, q, dy, part, nx, ny, plane, ntiles, net.mean[0], net.mean[1],
+                                net.mean[2], 1.f / net.std_[0], 1.f / net.std_[1], 1.f / net.std_[2]);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int ne = 9 * CO * CI + CO;
+  dw_reduce_kernel<CI, CO><<<(ne + 255) / 256, 256, 0, s>>>(part, nctas, dW, db, scale);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+long long backward_partials_floats(int B, int ny, int nx) {
+  const long long ntiles = (long long)B * ((long long)nx * ny / TILE);
+  const long long nctas = (ntiles + DW_TILES - 1) / DW_TILES;
+  return nctas * (9 * N_OUT * HID + N_OUT);
+}
+
+cudaError_t backward_reserve(Grads& g, long long cells, long long partial_floats) {
+  if (g.cells < cells) {
+    cudaFree(g.dr);
+    cudaFree(g.da[0]);
+    cudaFree(g.da[1]);
+    g.dr = nullptr;
+    g.da[0] = g.da[1] = nullptr;
+    g.cells = 0;
+    cudaError_t e = cudaMalloc(&g.dr, (size_t)cells * 6 * 16);
+    if (e == cudaSuccess) e = cudaMalloc(&g.da[0], (size_t)cells * CG_HID * 16);
+    if (e == cudaSuccess) e = cudaMalloc(&g.da[1], (size_t)cells * CG_HID * 16);
+    if (e != cudaSuccess) return e;
+    g.cells = cells;
+  }
+  if (g.part_floats < partial_floats) {
+    cudaFree(g.part);
+    g.part = nullptr;
+    g.part_floats = 0;
+    cudaError_t e = cudaMalloc(&g.part, sizeof(float) * partial_floats);
+    if (e != cudaSuccess) return e;
+    g.part_floats = partial_floats;
+  }
+  return cudaSuccess;
+}
+
+void backward_free(Grads& g) {
+  cudaFree(g.dr);
+  cudaFree(g.da[0]);
+  cudaFree(g.da[1]);
+  cudaFree(g.part);
+  g = Grads{};
+}
+
+cudaError_t backward(const Net& net, const float* q, int B, int ny, int nx, const Acts& acts,
+                     const float* dw, float* dq, float* dparams, float scale, Grads& g,
+                     cudaStream_t s) {
+  const ParamLayout L = param_layout();
+  const long long plane = (long long)nx * ny, cells = (long long)B * plane;
+  cudaError_t e;
+  coeff_to_raw_kernel<<<(unsigned)((cells + 255) / 256), 256, 0, s>>>(dw, g.dr, plane, cells);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+
+  ConvArgs a{};
+  a.nx = nx;
+  a.ny = ny;
+  a.plane = plane;
+  a.err = net.err;
+  // layer 4: dW4, db4 from (dr, a3); dX -> da[0] masked by a3
+  if ((e = weight_grad<HID, N_OUT, 6>(acts.a[2], nullptr, g.dr, dparams + L.w[3], dparams + L.b[3],
+                                      g.part, B, ny, nx, net, scale, s)) != cudaSuccess)
+    return e;
+  a.x = g.dr;
+  a.wpk = net.wb[3];
+  a.mask = acts.a[2];
+  a.y = g.da[0];
+  if ((e = launch_conv<6, HID, IN_ACT, OUT_MASK>(a, B, s)) != cudaSuccess) return e;
+  // layer 3: dW3 from (da0, a2); dX -> da[1] masked by a2
+  if ((e = weight_grad<HID, HID, 4>(acts.a[1], nullptr, g.da[0], dparams + L.w[2], dparams + L.b[2],
+                                    g.part, B, ny, nx, net, scale, s)) != cudaSuccess)
+    return e;
+  a.x = g.da[0];
+  a.wpk = net.wb[2];
+  a.mask = acts.a[1];
+  a.y = g.da[1];
+  if ((e = launch_conv<CG_HID, HID, IN_ACT, OUT_MASK>(a, B, s)) != cudaSuccess) return e;
+  // layer 2: dW2 from (da1, a1); dX -> da[0] masked by a1
+  if ((e = weight_grad<HID, HID, 4>(acts.a[0], nullptr, g.da[1], dparams + L.w[1], dparams + L.b[1],
+                                    g.part, B, ny, nx, net, scale, s)) != cudaSuccess)
+    return e;
+  a.x = g.da[1];
+  a.wpk = net.wb[1];
+  a.mask = acts.a[0];
+  a.y = g.da[0];
+  if ((e = launch_conv<CG_HID, HID, IN_ACT, OUT_MASK>(a, B, s)) != cudaSuccess) return e;
+  // layer 1: dW1 from (da0, normalised state); dq += dX / std
+  if ((e = weight_grad<3, HID, 4>(nullptr, q, g.da[0], dparams + L.w[0], dparams + L.b[0], g.part,
+                                  B, ny, nx, net, scale, s)) != cudaSuccess)
+    return e;
+  if (dq) {
+    dx_first_kernel<<<(unsigned)((cells + 127) / 128), 128, 0, s>>>(
+        g.da[0], net.params + L.w[0], dq, nx, ny, plane, cells, 1.f / net.std_[0],
+        1.f / net.std_[1], 1.f / net.std_[2]);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 }  // namespace snk
 
 // ---------------------------------------------------------------------------
@@ -392,6 +724,8 @@ void net_free(fv_net* n) {
     cudaFree(n->n.wb[l]);
   }
   cudaFree(n->n.err);
+  cudaFree(n->adam_m);
+  cudaFree(n->adam_v);
   snk::acts_free(n->ws);
   if (n->stream) cudaStreamDestroy(n->stream);
   delete n;

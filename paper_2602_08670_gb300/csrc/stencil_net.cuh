@@ -62,10 +62,33 @@ cudaError_t forward(const Net& net, const float* q, int B, int ny, int nx, Acts&
 cudaError_t acts_reserve(Acts& acts, long long cells);
 void acts_free(Acts& acts);
 
+// Backward workspace.
+struct Grads {
+  uint16_t* dr = nullptr;       // cotangent of the raw outputs, BF16 [B][6][plane][8]
+  uint16_t* da[2] = {};         // cotangents of hidden pre-activations, BF16 [B][4][plane][8]
+  float* part = nullptr;        // weight-gradient partial sums
+  long long cells = 0, part_floats = 0;
+};
+long long backward_partials_floats(int B, int ny, int nx);
+cudaError_t backward_reserve(Grads& g, long long cells, long long partial_floats);
+void backward_free(Grads& g);
+
+// Vector-Jacobian product of forward() at q given the cotangent dw of the
+// normalised coefficients [B][36][ny][nx]: adds scale * (d params) to
+// dparams [N_PARAMS] and, if dq != nullptr, the cotangent of q to dq
+// [B][3][ny][nx] (scale applies to dparams only).  `acts` must hold the
+// activations forward() produced for this q.  Cotangents between layers are
+// BF16 (tensor-core operands); weight gradients accumulate in FP32.
+cudaError_t backward(const Net& net, const float* q, int B, int ny, int nx, const Acts& acts,
+                     const float* dw, float* dq, float* dparams, float scale, Grads& g,
+                     cudaStream_t s);
+
 }  // namespace snk
 
 struct fv_net {
   snk::Net n;
-  snk::Acts ws;                 // workspace of stencil_net_forward / backward
+  snk::Acts ws;                 // workspace of stencil_net_forward
+  float* adam_m = nullptr;      // Adam moments (stencil_net_adam_step)
+  float* adam_v = nullptr;
   cudaStream_t stream = nullptr;
 };

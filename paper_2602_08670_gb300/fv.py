@@ -70,6 +70,13 @@ _SIGS = {
     "stencil_net_set_params": [c_void_p, c_void_p, c_int],
     "stencil_net_get_params": [c_void_p, c_void_p, c_int],
     "stencil_net_forward": [c_void_p, c_void_p, c_int, c_int, c_int, c_void_p, c_int, c_void_p],
+    "fv_tape_create": [c_void_p, c_int, c_int, c_int, c_int, c_double, c_double, c_double,
+                       ctypes.POINTER(c_void_p)],
+    "fv_tape_destroy": [c_void_p],
+    "fv_tape_forward": [c_void_p, c_void_p, c_void_p],
+    "fv_tape_loss": [c_void_p, c_void_p, c_void_p, ctypes.POINTER(c_double)],
+    "fv_tape_backward": [c_void_p, c_void_p, c_void_p, c_void_p],
+    "stencil_net_adam_step": [c_void_p, c_void_p, c_int, c_double, c_double, c_double, c_double],
     "fv_get_time": [c_void_p, c_void_p, c_void_p, c_void_p],
     "fv_health": [c_void_p, c_void_p],
     "fv_diagnostics": [c_void_p, c_void_p],
@@ -325,3 +332,66 @@ def stencil_net_forward(net: Net, q: torch.Tensor, raw: bool = False) -> torch.T
 
 def fv_set_learned_hmin(s: State, hmin_frac: float) -> None:
     _check(lib().fv_set_learned_hmin(s.handle, float(hmin_frac)))
+
+
+# ---------------------------------------------------------------------------
+# Training
+# ---------------------------------------------------------------------------
+
+class Tape:
+    """Owner of an ``fv_tape*`` (keeps its network alive)."""
+
+    def __init__(self, handle: int, net: Net, shape, T: int):
+        self.handle = ctypes.c_void_p(handle)
+        self.net = net
+        self.shape = tuple(shape)   # (B, 3, ny, nx)
+        self.T = T
+
+    def __del__(self):
+        if getattr(self, "handle", None) and self.handle.value and _lib is not None:
+            _lib.fv_tape_destroy(self.handle)
+            self.handle = ctypes.c_void_p(0)
+
+
+def fv_tape_create(net: Net, B: int, ny: int, nx: int, T: int, dt: float, g: float = 9.81,
+                   hmin_frac: float = 1e-3) -> Tape:
+    out = c_void_p()
+    _check(lib().fv_tape_create(net.handle, B, ny, nx, T, dt, g, hmin_frac, ctypes.byref(out)))
+    return Tape(out.value, net, (B, 3, ny, nx), T)
+
+
+def _dev(t: torch.Tensor) -> c_void_p:
+    if not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA float32 tensor")
+    return c_void_p(t.data_ptr())
+
+
+def fv_tape_forward(tape: Tape, q0: torch.Tensor, want_snaps: bool = True):
+    torch.cuda.current_stream().synchronize()
+    snaps = torch.empty((tape.T,) + tape.shape, dtype=torch.float32, device="cuda") if want_snaps else None
+    _check(lib().fv_tape_forward(tape.handle, _dev(q0.contiguous()), _dev(snaps) if want_snaps else None))
+    return snaps
+
+
+def fv_tape_loss(tape: Tape, targets: torch.Tensor, scale) -> float:
+    torch.cuda.current_stream().synchronize()
+    sc = np.ascontiguousarray(np.asarray(scale, dtype=np.float32))
+    out = c_double()
+    _check(lib().fv_tape_loss(tape.handle, _dev(targets.contiguous()), sc.ctypes.data_as(c_void_p),
+                              ctypes.byref(out)))
+    return out.value
+
+
+def fv_tape_backward(tape: Tape, dparams: torch.Tensor, dsnaps: torch.Tensor | None = None,
+                     want_dq0: bool = False):
+    torch.cuda.current_stream().synchronize()
+    dq0 = torch.empty(tape.shape, dtype=torch.float32, device="cuda") if want_dq0 else None
+    _check(lib().fv_tape_backward(tape.handle, _dev(dsnaps.contiguous()) if dsnaps is not None else None,
+                                  _dev(dparams), _dev(dq0) if want_dq0 else None))
+    return dq0
+
+
+def stencil_net_adam_step(net: Net, grad: torch.Tensor, step: int, lr: float = 1e-3,
+                          b1: float = 0.9, b2: float = 0.999, eps: float = 1e-8) -> None:
+    torch.cuda.current_stream().synchronize()
+    _check(lib().stencil_net_adam_step(net.handle, _dev(grad), int(step), lr, b1, b2, eps))

@@ -155,3 +155,53 @@ def test_unsupported_grid_rejected(fv):
     with pytest.raises(fv.FvError) as ei:
         fv.stencil_net_forward(net, torch.ones(1, 3, 100, 100, device="cuda"))
     assert ei.value.code == fv.FV_EINVAL
+
+
+def _cos_rel(a, b):
+    a = torch.as_tensor(a, dtype=torch.float64).reshape(-1)
+    b = torch.as_tensor(b, dtype=torch.float64).reshape(-1)
+    cos = float(a @ b / (a.norm() * b.norm()))
+    rel = float((a - b).norm() / b.norm())
+    return cos, rel
+
+
+@pytest.mark.parametrize("n,T,B,zero", [(16, 2, 2, True), (16, 2, 2, False), (64, 3, 2, False)])
+def test_rollout_gradients_match_oracle(fv, n, T, B, zero):
+    """Loss (Eq. 2.28) and its gradient w.r.t. the parameters and the initial
+    state through a T-step learned rollout: GPU hand-written backward against
+    the oracle's FP64 reverse-mode gradient of the same (BF16-mirrored)
+    forward.  zero=True: all-zero network (first-order faces; only b4 has a
+    gradient), which isolates the finite-volume adjoint."""
+    if zero:
+        p = osn.init_params(0, MEAN, STD, zero_last=True)
+        for l in range(4):
+            p.W[l] = torch.zeros_like(p.W[l])
+            p.b[l] = torch.zeros_like(p.b[l])
+    else:
+        p = rand_params(6, last_scale=0.1)
+    dt = 1e-3 if n == 64 else 2e-3
+    q0 = swe_state(n, 21, members=B)
+    g = torch.Generator().manual_seed(3)
+    targets = [torch.tensor(q0) * (1 + 0.01 * torch.randn(q0.shape, generator=g, dtype=torch.float64))
+               for _ in range(T)]
+    targets = [W.as_f32_exact(t.numpy()) for t in targets]
+    scale = [0.05, 0.02, 0.02]
+    hmin = torch.tensor(1e-3 * q0[:, 0].mean(axis=(1, 2)))
+    loss_ref, g_ref, dq_ref = osn.loss_and_grads(q0, [torch.tensor(t) for t in targets], p, dt, hmin,
+                                                 scale, round_bf16=True, want_dq0=True)
+    net = gpu_net(fv, p)
+    tape = fv.fv_tape_create(net, B, n, n, T, dt)
+    fv.fv_tape_forward(tape, f32(q0).cuda())
+    loss = fv.fv_tape_loss(tape, f32(np.stack(targets)).cuda(), scale)
+    assert abs(loss - loss_ref) <= 1e-4 * abs(loss_ref), (loss, loss_ref)
+    dparams = torch.zeros(fv.FV_NET_PARAMS, device="cuda")
+    dq0 = fv.fv_tape_backward(tape, dparams, want_dq0=True)
+    cos, rel = _cos_rel(dq0.cpu(), dq_ref)
+    assert cos >= 0.9999 and rel <= 1e-2, ("dq0", cos, rel)
+    gp = dparams.cpu().double()
+    cos, rel = _cos_rel(gp, g_ref)
+    assert cos >= 0.999 and rel <= 2e-2, ("dparams", cos, rel)
+    if zero:
+        nz = torch.nonzero(g_ref).reshape(-1)
+        lo = 29796 - 36
+        assert int(nz.min()) >= lo   # only b4
