@@ -213,6 +213,12 @@ int stencil_net_get_params(const fv_net* n, float* params, int loc);
 int stencil_net_forward(const fv_net* n, const float* q, int B, int ny, int nx, float* coeffs,
                         int raw, void* stream);
 
+/* Coarse graining (Section 2.5.1): coarse[p][j][i] = mean of the factor x
+ * factor block of fine[p][.][.] (FP64 sum), for `planes` planes of ny x nx
+ * (device pointers; nx, ny multiples of factor).  Synchronous on `stream`
+ * (cudaStream_t or NULL). */
+int fv_coarsen(const float* fine, int planes, int ny, int nx, int factor, float* coarse, void* stream);
+
 /* ---------------------------------------------------------------------------
  * Training: taped learned rollout, rollout loss (Eq. 2.28), backward, Adam
  * ------------------------------------------------------------------------- */

@@ -77,6 +77,7 @@ _SIGS = {
     "fv_tape_loss": [c_void_p, c_void_p, c_void_p, ctypes.POINTER(c_double)],
     "fv_tape_backward": [c_void_p, c_void_p, c_void_p, c_void_p],
     "stencil_net_adam_step": [c_void_p, c_void_p, c_int, c_double, c_double, c_double, c_double],
+    "fv_coarsen": [c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_void_p],
     "fv_get_time": [c_void_p, c_void_p, c_void_p, c_void_p],
     "fv_health": [c_void_p, c_void_p],
     "fv_diagnostics": [c_void_p, c_void_p],
@@ -311,10 +312,14 @@ def stencil_net_set_params(net: Net, params) -> None:
     _check(lib().stencil_net_set_params(net.handle, hp.ctypes.data_as(c_void_p), FV_HOST))
 
 
-def stencil_net_get_params(net: Net) -> np.ndarray:
-    out = np.zeros(FV_NET_PARAMS, dtype=np.float32)
-    _check(lib().stencil_net_get_params(net.handle, out.ctypes.data_as(c_void_p), FV_HOST))
-    return out
+def stencil_net_get_params(net: Net, out: torch.Tensor | None = None):
+    """Parameters as a numpy array, or into the given CUDA tensor."""
+    if out is not None:
+        _check(lib().stencil_net_get_params(net.handle, _dev(out), FV_DEVICE))
+        return out
+    host = np.zeros(FV_NET_PARAMS, dtype=np.float32)
+    _check(lib().stencil_net_get_params(net.handle, host.ctypes.data_as(c_void_p), FV_HOST))
+    return host
 
 
 def stencil_net_forward(net: Net, q: torch.Tensor, raw: bool = False) -> torch.Tensor:
@@ -395,3 +400,13 @@ def stencil_net_adam_step(net: Net, grad: torch.Tensor, step: int, lr: float = 1
                           b1: float = 0.9, b2: float = 0.999, eps: float = 1e-8) -> None:
     torch.cuda.current_stream().synchronize()
     _check(lib().stencil_net_adam_step(net.handle, _dev(grad), int(step), lr, b1, b2, eps))
+
+
+def fv_coarsen(q: torch.Tensor, factor: int) -> torch.Tensor:
+    """Block means of factor x factor cells of a CUDA tensor [..., ny, nx]."""
+    q = q.contiguous()
+    ny, nx = q.shape[-2:]
+    planes = int(np.prod(q.shape[:-2])) if q.dim() > 2 else 1
+    out = torch.empty(q.shape[:-2] + (ny // factor, nx // factor), dtype=torch.float32, device=q.device)
+    _check(lib().fv_coarsen(_dev(q), planes, ny, nx, factor, _dev(out), c_void_p(_torch_stream())))
+    return out

@@ -1,0 +1,203 @@
+"""Training and evaluation of the learned-stencil solver (GPU, via libfv).
+
+Data (Section 2.5.1 / 5.4 recipe, on this build's synthetic workload): the
+plain FP32 GPU solver runs seeded multi-bump shallow-water states at a fine
+resolution (256^2) with a fixed dt; every `factor` fine steps the state is
+block-averaged `factor` x `factor` down to the coarse grid (64^2), so one
+coarse step = `factor` fine steps.  Training windows are (q_k, q_{k+1} ..
+q_{k+T}) from those sequences; the loss is Eq. 2.28 on a T-step learned
+rollout at the coarse resolution, minimised with Adam.  All numerical work
+(solver, coarse graining, CNN forward / backward, loss, Adam) runs in the CUDA
+library; this module samples windows and calls it.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+import time
+
+import numpy as np
+import torch
+
+from . import fv, workloads
+
+G = 9.81
+LAYERS = [(32, 3), (32, 32), (32, 32), (36, 32)]
+
+
+@dataclasses.dataclass
+class Dataset:
+    coarse: torch.Tensor      # [S][B][3][nc][nc] (CUDA)
+    dt_coarse: float
+    dt_fine: float
+    n_fine: int
+    factor: int
+    seed: int
+
+    @property
+    def n_coarse(self) -> int:
+        return self.n_fine // self.factor
+
+
+def stable_fine_dt(n_fine: int, seed: int, members: int, cfl: float = 0.5, safety: float = 0.8) -> float:
+    """Fixed fine dt: the adaptive (CFL) dt the library computes for the
+    initial states, minimum over members, times a safety factor."""
+    q0 = torch.tensor(workloads.swe_random_bumps(n_fine, seed, members), dtype=torch.float32).cuda()
+    st = fv.swe_init(q0, cfl=cfl)
+    _, ndt, _ = fv.fv_get_time(st)
+    return float(safety * ndt.min())
+
+
+def generate(n_fine: int = 256, factor: int = 4, members: int = 64, seed: int = 0,
+             coarse_steps: int = 128, dt_fine: float | None = None) -> Dataset:
+    """Fine plain-solver trajectories coarse-grained to n_fine / factor."""
+    if dt_fine is None:
+        dt_fine = stable_fine_dt(n_fine, seed, members)
+    q0 = torch.tensor(workloads.swe_random_bumps(n_fine, seed, members), dtype=torch.float32).cuda()
+    st = fv.swe_init(q0, dt_mode="fixed", dt_fixed=dt_fine)
+    nc = n_fine // factor
+    coarse = torch.empty((coarse_steps + 1, members, 3, nc, nc), dtype=torch.float32, device="cuda")
+    coarse[0] = fv.fv_coarsen(q0, factor)
+    buf = torch.empty_like(q0)
+    for k in range(1, coarse_steps + 1):
+        fv.fv_rollout(st, factor)
+        fv.fv_get_state(st, out=buf)
+        coarse[k] = fv.fv_coarsen(buf, factor)
+    return Dataset(coarse, dt_fine * factor, dt_fine, n_fine, factor, seed)
+
+
+def init_params(seed: int, zero_last: bool = True) -> np.ndarray:
+    """He-normal weights, small biases; a zero last layer makes the network
+    start as the first-order scheme (the paper's initialisation)."""
+    g = torch.Generator().manual_seed(seed)
+    parts = []
+    for layer, (co, ci) in enumerate(LAYERS):
+        w = torch.randn(co, ci, 3, 3, generator=g) * math.sqrt(2.0 / (9 * ci))
+        b = torch.randn(co, generator=g) * 0.01
+        if layer == 3 and zero_last:
+            w.zero_()
+            b.zero_()
+        parts += [w.reshape(-1), b]
+    return torch.cat(parts).numpy().astype(np.float32)
+
+
+def data_stats(ds: Dataset):
+    """Per-variable mean and standard deviation of the coarse training states
+    (the loss scale of Eq. 2.28)."""
+    x = ds.coarse.transpose(0, 2).reshape(3, -1).double()
+    mean = x.mean(dim=1).cpu().numpy()
+    std = np.maximum(x.std(dim=1).cpu().numpy(), 1e-6)
+    return mean.astype(np.float32), std.astype(np.float32)
+
+
+def input_scale(ds: Dataset):
+    """Per-variable mean and largest absolute deviation from it: the CNN input
+    normalisation x = (q - mean) / scale maps the training states into
+    [-1, 1].  (The standard deviation is dominated by the flat background, so
+    dividing by it puts the bumps at 15-20 and makes every Adam step a large
+    change of the stencils.)"""
+    x = ds.coarse.transpose(0, 2).reshape(3, -1).double()
+    mean = x.mean(dim=1)
+    dev = (x - mean[:, None]).abs().amax(dim=1).cpu().numpy()
+    return mean.cpu().numpy().astype(np.float32), np.maximum(dev, 1e-6).astype(np.float32)
+
+
+@dataclasses.dataclass
+class TrainResult:
+    net: object
+    losses: list
+    seconds: float
+    iters: int
+    rejected: int
+    lr: float
+
+
+def train(ds: Dataset, iters: int = 500, batch: int = 64, T: int = 8, lr: float = 3e-4,
+          seed: int = 0, params=None, log_every: int = 0, net=None) -> TrainResult:
+    """Adam on the rollout loss.  An update after which a training rollout
+    leaves the physical states (the library reports FV_EUNSTABLE) is undone
+    and the learning rate halved."""
+    _, std = data_stats(ds)
+    if net is None:
+        in_mean, in_scale = input_scale(ds)
+        net = fv.stencil_net_create(init_params(seed) if params is None else params, in_mean, in_scale)
+    S, B = ds.coarse.shape[:2]
+    nc = ds.n_coarse
+    tape = fv.fv_tape_create(net, batch, nc, nc, T, ds.dt_coarse)
+    dparams = torch.zeros(fv.FV_NET_PARAMS, dtype=torch.float32, device="cuda")
+    prev = torch.empty_like(dparams)
+    fv.stencil_net_get_params(net, out=prev)
+    rng = np.random.Generator(np.random.Philox(seed))
+    scale = std
+    losses = []
+    rejected = 0
+    step = 0
+    t0 = time.perf_counter()
+    for it in range(iters):
+        traj = torch.tensor(rng.integers(0, B, size=batch), device="cuda")
+        start = torch.tensor(rng.integers(0, S - T, size=batch), device="cuda")
+        q0 = ds.coarse[start, traj].contiguous()
+        targets = torch.stack([ds.coarse[start + k, traj] for k in range(1, T + 1)]).contiguous()
+        try:
+            fv.fv_tape_forward(tape, q0, want_snaps=False)
+        except fv.FvError as e:
+            if e.code != fv.FV_EUNSTABLE:
+                raise
+            fv.stencil_net_set_params(net, prev)
+            lr *= 0.5
+            rejected += 1
+            continue
+        losses.append(fv.fv_tape_loss(tape, targets, scale))
+        dparams.zero_()
+        fv.fv_tape_backward(tape, dparams)
+        fv.stencil_net_get_params(net, out=prev)
+        step += 1
+        fv.stencil_net_adam_step(net, dparams, step, lr)
+        if log_every and (it + 1) % log_every == 0:
+            print(f"iter {it + 1}: loss {np.mean(losses[-log_every:]):.5g}", flush=True)
+    torch.cuda.synchronize()
+    return TrainResult(net, losses, time.perf_counter() - t0, iters, rejected, lr)
+
+
+def rel_l2(a: torch.Tensor, ref: torch.Tensor) -> list:
+    """Per-variable relative L2 error over all members and cells."""
+    return [float((a[:, c] - ref[:, c]).norm() / ref[:, c].norm()) for c in range(a.shape[1])]
+
+
+def state_error(a: torch.Tensor, ref: torch.Tensor, scale) -> float:
+    """RMS of the scaled state difference (the per-variable normalisation of
+    the training loss), over all members, cells and variables."""
+    s = torch.as_tensor(np.asarray(scale), dtype=torch.float64, device=a.device).view(1, -1, 1, 1)
+    d = (a.double() - ref.double()) / s
+    return float(torch.sqrt((d * d).mean()))
+
+
+def rollout_coarse(q0: torch.Tensor, dt: float, nsteps: int, net=None) -> torch.Tensor:
+    st = fv.swe_init(q0.contiguous(), dt_mode="fixed", dt_fixed=dt)
+    fv.fv_rollout(st, nsteps, net=net)
+    return fv.fv_get_state(st)
+
+
+def evaluate(net, ds: Dataset, nsteps: int, scale) -> dict:
+    """Learned and plain coarse solvers from ds.coarse[0], nsteps coarse steps,
+    against the coarse-grained fine reference ds.coarse[nsteps]."""
+    q0 = ds.coarse[0]
+    ref = ds.coarse[nsteps]
+    ql = rollout_coarse(q0, ds.dt_coarse, nsteps, net)
+    qp = rollout_coarse(q0, ds.dt_coarse, nsteps, None)
+    return {"learned": state_error(ql, ref, scale), "plain": state_error(qp, ref, scale),
+            "learned_rel_l2": rel_l2(ql, ref), "plain_rel_l2": rel_l2(qp, ref)}
+
+
+def plain_error_at(n: int, ds: Dataset, nsteps: int, scale) -> float:
+    """Error against the same reference of the plain solver run at n^2 (from
+    the same continuous initial field) and coarse-grained to the coarse grid."""
+    factor = n // ds.n_coarse
+    assert factor * ds.n_coarse == n
+    members = ds.coarse.shape[1]
+    q0 = torch.tensor(workloads.swe_random_bumps(n, ds.seed, members), dtype=torch.float32).cuda()
+    ratio = ds.n_fine / n
+    dt = ds.dt_fine * ratio
+    steps = int(round(nsteps * ds.factor / ratio))
+    q = rollout_coarse(q0, dt, steps)
+    return state_error(fv.fv_coarsen(q, factor), ds.coarse[nsteps], scale)
