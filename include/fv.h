@@ -177,6 +177,25 @@ int fv_diagnostics(const fv_state* s, double* sums);
  * step (FV_EINVAL after). */
 int fv_set_learned_hmin(fv_state* s, double hmin_frac);
 
+/* The sums of fv_diagnostics() for a state the caller holds (q: device
+ * [batch][C][ny][nx], C = 3 for FV_EQ_SWE with phys = g, 4 for FV_EQ_EULER
+ * with phys = gamma, periodic lx x ly domain), computed without allocating
+ * any device or host memory.  The paper has no counterpart: this entry point
+ * serves callers that cannot allocate once running (a fixed device-memory
+ * budget handed out up front, allocation-free real-time loops or host
+ * callbacks, frameworks that own all device memory through their own pool).
+ * The reduction scratch is a fixed array of 320 slots in the library that
+ * every GPU loading it keeps until the process exits: batch * (C + 1) must
+ * be at most 320 (80 shallow-water or 64 Euler members), else FV_EINVAL.
+ * sums: [batch][C+1] at sums_loc; FV_HOST returns after the result is
+ * copied, FV_DEVICE only enqueues on `stream` (cudaStream_t, NULL = default
+ * stream).  The first call on a device looks up the scratch address with
+ * that device current; make it before any stream capture.  All calls share
+ * the scratch, so calls that overlap on the GPU (other streams, other host
+ * threads) race; every slot a call reads is written by that call first. */
+int fv_diagnostics_noalloc(const float* q, int eq, int batch, int ny, int nx, double lx, double ly,
+                           double phys, double* sums, int sums_loc, void* stream);
+
 /* ---------------------------------------------------------------------------
  * Learned stencil network (Section 2.5.3, fourth approach)
  *

@@ -78,6 +78,8 @@ _SIGS = {
     "fv_tape_backward": [c_void_p, c_void_p, c_void_p, c_void_p],
     "stencil_net_adam_step": [c_void_p, c_void_p, c_int, c_double, c_double, c_double, c_double],
     "fv_coarsen": [c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_void_p],
+    "fv_diagnostics_noalloc": [c_void_p, c_int, c_int, c_int, c_int, c_double, c_double, c_double,
+                               c_void_p, c_int, c_void_p],
     "fv_get_time": [c_void_p, c_void_p, c_void_p, c_void_p],
     "fv_health": [c_void_p, c_void_p],
     "fv_diagnostics": [c_void_p, c_void_p],
