@@ -36,6 +36,7 @@ SWE_BYTES_PER_CELL_UPDATE = 60     # stage 1: 12 + 12; stage 2: 12 + 12 + 12 (FP
 EULER_BYTES_PER_CELL_UPDATE = 80   # C = 4
 CHUNK = 32                          # steps per enqueue between timing events
 WORKLOAD = "plain FV step: Euler KH 2048^2 + SWE Gaussian bump 4096^2, FP32, SSP-RK2, CFL 0.5"
+WEIGHTS = os.path.join(ROOT, "paper_2602_08670_gb300", "weights", "swe64_from256.npz")
 
 
 def measured_peaks():
@@ -279,6 +280,12 @@ def run_gpu(args):
         "gpu_launches": 4 * K,
         "clocks": clk,
     }
+    if not args.no_learned:
+        line["learned"] = learned_block(args)
+        plain_swe = N_SWE * N_SWE * K / (swe_ms * 1e-3)
+        line["learned"]["accuracy_matched"]["plain_rate"] = plain_swe
+        line["learned"]["accuracy_matched"]["learned_wins"] = \
+            line["learned"]["accuracy_matched"]["learned_rate_times_r3"] > plain_swe
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         rate, secs, threads = oracle_sample(4, 512, 256)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
@@ -291,6 +298,79 @@ def run_gpu(args):
     return 0
 
 
+def learned_block(args):
+    """The learned-stencil path: batched learned rollout throughput (256
+    members x 256^2, BF16 tensor-core CNN + FP32 flux, fixed dt, graph-captured
+    rollout), one training iteration (batch 64, 64^2, T = 8, forward + loss +
+    backward + Adam), and the accuracy-matched comparison with the plain
+    solver on held-out 64^2 trajectories coarse-grained from 256^2."""
+    import numpy as np
+    import torch
+
+    from paper_2602_08670_gb300 import fv
+    from paper_2602_08670_gb300 import train as TR
+    from paper_2602_08670_gb300 import workloads as W
+
+    out = {}
+    net, meta = TR.load_weights(WEIGHTS)
+    # -- batched learned rollout (C4 shape)
+    members, n = 256, 256
+    q0 = torch.tensor(W.swe_random_bumps(n, 3, members), dtype=torch.float32).cuda()
+    bs = torch.cuda.Stream()
+    dt = meta["dt_fine"]                       # stable at 256^2 (CFL 0.4)
+    with torch.cuda.stream(bs):
+        st = fv.swe_init(q0, dt_mode="fixed", dt_fixed=dt)
+    fv.fv_enqueue_steps(st, 2, net=net)
+    fv.fv_sync(st)
+    K = args.learned_steps
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(bs)
+    fv.fv_enqueue_steps(st, K, net=net)
+    e1.record(bs)
+    fv.fv_sync(st)
+    ms = e0.elapsed_time(e1)
+    learned_rate = members * n * n * K / (ms * 1e-3)
+    out["rollout"] = {"workload": f"{members} members x {n}^2 SWE, learned, fixed dt, {K} steps",
+                      "cell_updates_per_s": learned_rate, "ms_per_step": ms / K,
+                      "cnn_tflops": 2 * 59328 * 2 * members * n * n * K / (ms * 1e-3) / 1e12}
+    del st
+    # -- one training iteration (C3 shape)
+    tr = TR.generate(256, 4, members=64, seed=0, coarse_steps=32)
+    _, std = TR.data_stats(tr)
+    tnet = fv.stencil_net_create(TR.init_params(0), *TR.input_scale(tr))
+    res = TR.train(tr, iters=3, batch=64, T=8, net=tnet)       # warm-up
+    res = TR.train(tr, iters=10, batch=64, T=8, net=tnet)
+    out["training"] = {"workload": "batch 64 windows, 64^2, T = 8 steps (16 stages), forward + "
+                                   "Eq. 2.28 loss + backward + Adam",
+                       "ms_per_iteration": 1e3 * res.seconds / res.iters}
+    # -- accuracy-matched rate on held-out trajectories (seed 2)
+    te = TR.generate(256, 4, members=32, seed=2, coarse_steps=64, dt_fine=meta["dt_fine"])
+    ev = TR.evaluate(net, te, 64, std)
+    plain = {64: ev["plain"]}
+    for nn in (128, 192):
+        plain[nn] = TR.plain_error_at(nn, te, 64, std)
+    el = ev["learned"]
+    # resolution at which the plain solver reaches the learned error
+    # (log-log interpolation between the bracketing resolutions)
+    ns = sorted(plain)
+    n_eq = None
+    for a, b in zip(ns, ns[1:]):
+        if plain[a] >= el >= plain[b]:
+            t = (math.log(plain[a]) - math.log(el)) / (math.log(plain[a]) - math.log(plain[b]))
+            n_eq = math.exp(math.log(a) + t * (math.log(b) - math.log(a)))
+    if n_eq is None and el < plain[ns[-1]]:
+        n_eq = float(ns[-1])                   # at least this resolution
+    r = (n_eq or 64.0) / 64.0
+    out["accuracy"] = {"metric": "RMS of the per-variable-scaled state error vs the 4x-resolution "
+                                 "(256^2) run coarse-grained to 64^2, after 64 coarse steps, 32 held-out members",
+                       "learned_64": el, "plain": {str(k): v for k, v in plain.items()},
+                       "plain_resolution_matching_learned": n_eq,
+                       "note": "plain needs (N_eq/64)^2 more cells and N_eq/64 more steps"}
+    out["accuracy_matched"] = {"learned_rate_times_r3": learned_rate * r ** 3, "r": r}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -299,6 +379,8 @@ def main():
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end run")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-path measurements")
+    ap.add_argument("--learned-steps", type=int, default=20)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

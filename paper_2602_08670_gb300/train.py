@@ -201,3 +201,46 @@ def plain_error_at(n: int, ds: Dataset, nsteps: int, scale) -> float:
     steps = int(round(nsteps * ds.factor / ratio))
     q = rollout_coarse(q0, dt, steps)
     return state_error(fv.fv_coarsen(q, factor), ds.coarse[nsteps], scale)
+
+
+def save_weights(path: str, net, ds: Dataset, result: TrainResult, extra: dict | None = None) -> None:
+    """Parameters, input normalisation and the training recipe in one .npz."""
+    mean, scale = input_scale(ds)
+    meta = {"n_fine": ds.n_fine, "factor": ds.factor, "dt_coarse": ds.dt_coarse, "dt_fine": ds.dt_fine,
+            "seed": ds.seed, "iters": result.iters, "final_loss": float(np.mean(result.losses[-50:])),
+            "train_seconds": result.seconds}
+    meta.update(extra or {})
+    np.savez(path, params=fv.stencil_net_get_params(net), mean=mean, scale=scale,
+             meta=np.array(repr(meta)))
+
+
+def load_weights(path: str):
+    """(net, metadata) from a file written by save_weights."""
+    d = np.load(path, allow_pickle=False)
+    net = fv.stencil_net_create(d["params"], d["mean"], d["scale"])
+    import ast
+    return net, ast.literal_eval(str(d["meta"]))
+
+
+def main(argv=None):
+    import argparse
+    ap = argparse.ArgumentParser(description="train the learned-stencil network on GPU-generated data")
+    ap.add_argument("--members", type=int, default=256)
+    ap.add_argument("--coarse-steps", type=int, default=256)
+    ap.add_argument("--iters", type=int, default=2000)
+    ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--T", type=int, default=8)
+    ap.add_argument("--lr", type=float, default=3e-4)
+    ap.add_argument("--out", required=True)
+    a = ap.parse_args(argv)
+    ds = generate(256, 4, members=a.members, seed=0, coarse_steps=a.coarse_steps)
+    res = train(ds, iters=a.iters, batch=a.batch, T=a.T, lr=a.lr, seed=0, log_every=100)
+    te = generate(256, 4, members=32, seed=2, coarse_steps=128, dt_fine=ds.dt_fine)
+    _, std = data_stats(ds)
+    ev = {k: evaluate(res.net, te, k, std) for k in (16, 64, 128)}
+    print({k: (v["learned"], v["plain"]) for k, v in ev.items()})
+    save_weights(a.out, res.net, ds, res, {"test_errors": {k: (v["learned"], v["plain"]) for k, v in ev.items()}})
+
+
+if __name__ == "__main__":
+    main()
