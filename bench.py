@@ -286,6 +286,8 @@ def run_gpu(args):
         line["learned"]["accuracy_matched"]["plain_rate"] = plain_swe
         line["learned"]["accuracy_matched"]["learned_wins"] = \
             line["learned"]["accuracy_matched"]["learned_rate_times_r3"] > plain_swe
+    if not args.no_serving:
+        line["serving"] = serving_block(args)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         rate, secs, threads = oracle_sample(4, 512, 256)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
@@ -371,6 +373,38 @@ def learned_block(args):
     return out
 
 
+def serving_block(args):
+    """Continuous-batching server under Poisson load: requests of SWE (50 %
+    learned, 25 % plain) and Euler (25 %), grids uniform over {64, 128, 256,
+    512}^2, horizons uniform in [100, 1000] (a reduced version of the full
+    serving workload, which has grids to 2048^2 and horizons to 5000 steps;
+    paper_2602_08670_gb300.serve runs that).  Capacity = requests per second
+    with all requests queued at t = 0; the Poisson runs use 0.5 and 0.9 x
+    capacity."""
+    from paper_2602_08670_gb300 import fv, serve
+    from paper_2602_08670_gb300 import train as TR
+    from paper_2602_08670_gb300 import workloads as W
+
+    net, _ = TR.load_weights(WEIGHTS)
+    base = W.serving_requests(args.serve_requests, 1.0, seed=42, sizes=(64, 128, 256, 512),
+                              horizon=(100, 1000))
+    server = fv.fv_server_create(64 << 30, 16, net)
+    closed = serve.with_arrivals(base, 1e9, seed=42)
+    lat, span, fail = serve.run_load(server, closed)
+    cap = serve.summarize(closed, lat, span, fail)
+    out = {"workload": "requests: 50 % learned SWE, 25 % plain SWE, 25 % plain Euler; grids "
+                       "{64,128,256,512}^2; horizons U[100,1000]; seed 42; budget 64 GB, 16 slots",
+           "capacity": cap, "load": []}
+    for frac in (0.5, 0.9):
+        reqs = serve.with_arrivals(base, frac * cap["requests_per_s"], seed=int(frac * 100))
+        lat, span, fail = serve.run_load(server, reqs)
+        d = serve.summarize(reqs, lat, span, fail)
+        d["rate_fraction_of_capacity"] = frac
+        out["load"].append(d)
+    out["learned_fallbacks_to_plain"] = fv.fv_server_stats(server)[3]
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -381,6 +415,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end run")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-path measurements")
     ap.add_argument("--learned-steps", type=int, default=20)
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving measurements")
+    ap.add_argument("--serve-requests", type=int, default=48)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

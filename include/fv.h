@@ -239,6 +239,61 @@ int stencil_net_forward(const fv_net* n, const float* q, int B, int ny, int nx, 
 int fv_coarsen(const float* fine, int planes, int ny, int nx, int factor, float* coarse, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Serving: continuous batching of solve requests
+ *
+ * The request/response pair of the serving loop is named fv_submit /
+ * fv_poll (not submit / poll: a C symbol `poll` exported by a shared library
+ * would interpose the C library's poll(2) for the whole process).
+ * ------------------------------------------------------------------------- */
+
+/* One solve request: a single member on an nx x ny periodic unit square,
+ * advanced nsteps SSP-RK2 steps with the adaptive CFL time step at Courant
+ * number cfl.  eq: FV_EQ_SWE or FV_EQ_EULER; learned != 0 uses the server's
+ * network (shallow water only; nx must be 8, 16, 32, 64 or a multiple of
+ * 128).  q0: host [C][ny][nx], copied at submission. */
+typedef struct {
+  int eq;
+  int learned;
+  int nx, ny;
+  long nsteps;
+  double cfl;
+  const float* q0;
+} fv_request;
+
+/* A server with a device-memory budget for resident request states and at
+ * most max_slots requests on the device at once; net (may be NULL, borrowed)
+ * serves learned requests.  A worker thread admits requests in arrival order
+ * as slots and memory free up, keeps admitted states resident, and advances
+ * every admitted request by graph-replayed chunks on its own stream, so
+ * requests that arrive while others run overlap on the GPU. */
+int fv_server_create(size_t hbm_budget_bytes, int max_slots, const fv_net* net, fv_server** out);
+
+/* Stop the worker (requests still running end with FV_ETIMEOUT) and free
+ * everything, including results not yet polled. */
+int fv_server_destroy(fv_server* s);
+
+/* Queue a request; *ticket identifies it.  FV_EBUSY if its device-memory
+ * footprint exceeds the whole budget (it could never be admitted),
+ * FV_EINVAL for a malformed request. */
+int fv_submit(fv_server* s, const fv_request* r, unsigned long long* ticket);
+
+/* A learned request whose state becomes non-physical is rerun from its
+ * initial state with the plain MUSCL-minmod step (the learned step's
+ * fallback); fv_server_stats counts these. */
+
+/* FV_PENDING while the request waits or runs.  Once done: copies the final
+ * state to q_out (host [C][ny][nx], may be NULL), the submission-to-
+ * completion latency to *latency_s, forgets the ticket and returns FV_OK or
+ * the request's error (FV_EUNSTABLE, FV_ECUDA, ...).  FV_ENOTFOUND for an
+ * unknown or already collected ticket. */
+int fv_poll(fv_server* s, unsigned long long ticket, float* q_out, double* latency_s);
+
+/* Requests on the device, requests waiting, device bytes reserved, learned
+ * requests that fell back to the plain step so far (any pointer may be NULL). */
+int fv_server_stats(fv_server* s, int* active, int* pending, size_t* used_bytes,
+                    long long* fallbacks);
+
+/* ---------------------------------------------------------------------------
  * Training: taped learned rollout, rollout loss (Eq. 2.28), backward, Adam
  * ------------------------------------------------------------------------- */
 typedef struct fv_tape fv_tape;

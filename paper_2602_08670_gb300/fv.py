@@ -78,6 +78,12 @@ _SIGS = {
     "fv_tape_backward": [c_void_p, c_void_p, c_void_p, c_void_p],
     "stencil_net_adam_step": [c_void_p, c_void_p, c_int, c_double, c_double, c_double, c_double],
     "fv_coarsen": [c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_void_p],
+    "fv_server_create": [ctypes.c_size_t, c_int, c_void_p, ctypes.POINTER(c_void_p)],
+    "fv_server_destroy": [c_void_p],
+    "fv_submit": [c_void_p, c_void_p, ctypes.POINTER(ctypes.c_ulonglong)],
+    "fv_poll": [c_void_p, ctypes.c_ulonglong, c_void_p, ctypes.POINTER(c_double)],
+    "fv_server_stats": [c_void_p, ctypes.POINTER(c_int), ctypes.POINTER(c_int),
+                        ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_longlong)],
     "fv_diagnostics_noalloc": [c_void_p, c_int, c_int, c_int, c_int, c_double, c_double, c_double,
                                c_void_p, c_int, c_void_p],
     "fv_get_time": [c_void_p, c_void_p, c_void_p, c_void_p],
@@ -412,3 +418,68 @@ def fv_coarsen(q: torch.Tensor, factor: int) -> torch.Tensor:
     out = torch.empty(q.shape[:-2] + (ny // factor, nx // factor), dtype=torch.float32, device=q.device)
     _check(lib().fv_coarsen(_dev(q), planes, ny, nx, factor, _dev(out), c_void_p(_torch_stream())))
     return out
+
+
+# ---------------------------------------------------------------------------
+# Serving
+# ---------------------------------------------------------------------------
+
+class fv_request(ctypes.Structure):
+    _fields_ = [("eq", c_int), ("learned", c_int), ("nx", c_int), ("ny", c_int), ("nsteps", c_long),
+                ("cfl", c_double), ("q0", c_void_p)]
+
+
+class Server:
+    """Owner of an ``fv_server*`` (keeps its network alive)."""
+
+    def __init__(self, handle: int, net=None):
+        self.handle = ctypes.c_void_p(handle)
+        self.net = net
+        self.shapes = {}
+
+    def __del__(self):
+        if getattr(self, "handle", None) and self.handle.value and _lib is not None:
+            _lib.fv_server_destroy(self.handle)
+            self.handle = ctypes.c_void_p(0)
+
+
+def fv_server_create(hbm_budget_bytes: int, max_slots: int, net: Net | None = None) -> Server:
+    out = c_void_p()
+    _check(lib().fv_server_create(int(hbm_budget_bytes), int(max_slots),
+                                  net.handle if net is not None else None, ctypes.byref(out)))
+    return Server(out.value, net)
+
+
+def submit(server: Server, q0, eq: str = "swe", nsteps: int = 100, learned: bool = False,
+           cfl: float = 0.5) -> int:
+    """Queue a request for q0 (host [C][ny][nx]); returns its ticket."""
+    a = np.ascontiguousarray(np.asarray(q0, dtype=np.float32))
+    C, ny, nx = a.shape
+    r = fv_request(0 if eq == "swe" else 1, int(learned), nx, ny, int(nsteps), float(cfl),
+                   a.ctypes.data_as(c_void_p))
+    t = ctypes.c_ulonglong()
+    _check(lib().fv_submit(server.handle, ctypes.byref(r), ctypes.byref(t)))
+    server.shapes[t.value] = a.shape
+    return t.value
+
+
+def poll(server: Server, ticket: int):
+    """None while pending, else (final state [C][ny][nx], latency in s)."""
+    shape = server.shapes[ticket]
+    out = np.empty(shape, dtype=np.float32)
+    lat = c_double()
+    rc = lib().fv_poll(server.handle, ctypes.c_ulonglong(ticket), out.ctypes.data_as(c_void_p),
+                       ctypes.byref(lat))
+    if rc == FV_PENDING:
+        return None
+    del server.shapes[ticket]
+    _check(rc)
+    return out, lat.value
+
+
+def fv_server_stats(server: Server):
+    """(active, pending, device bytes reserved, learned requests that fell back)."""
+    a, p, u, f = c_int(), c_int(), ctypes.c_size_t(), ctypes.c_longlong()
+    _check(lib().fv_server_stats(server.handle, ctypes.byref(a), ctypes.byref(p), ctypes.byref(u),
+                                 ctypes.byref(f)))
+    return a.value, p.value, u.value, f.value
