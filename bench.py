@@ -16,6 +16,7 @@ only reference implementation there is), on a bounded sample per step.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -37,6 +38,23 @@ EULER_BYTES_PER_CELL_UPDATE = 80   # C = 4
 CHUNK = 32                          # steps per enqueue between timing events
 WORKLOAD = "plain FV step: Euler KH 2048^2 + SWE Gaussian bump 4096^2, FP32, SSP-RK2, CFL 0.5"
 WEIGHTS = os.path.join(ROOT, "paper_2602_08670_gb300", "weights", "swe64_from256.npz")
+
+
+def captured_traffic(key):
+    """DRAM bytes per launch pair from a committed ncu capture, or None when
+    the kernel sources have changed since the counters were taken."""
+    prof = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(prof):
+        return None
+    with open(prof) as f:
+        entry = json.load(f).get(key)
+    if not entry:
+        return None
+    h = hashlib.sha256()
+    for src in entry["sources"]:
+        with open(os.path.join(ROOT, src), "rb") as f:
+            h.update(f.read())
+    return entry["bytes"] if h.hexdigest() == entry["source_sha256"] else None
 
 
 def measured_peaks():
@@ -223,11 +241,7 @@ def run_gpu(args):
     swe_step_s = swe_ms * 1e-3 / K
     achieved = SWE_BYTES_PER_CELL_UPDATE * N_SWE * N_SWE / swe_step_s / 1e9
     eul_achieved = EULER_BYTES_PER_CELL_UPDATE * N_EULER * N_EULER / (eul_ms * 1e-3 / K) / 1e9
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(prof):
-        with open(prof) as f:
-            traffic = json.load(f).get("swe_stage_pair_4096")
+    traffic = captured_traffic("swe_stage_pair_4096")
 
     # end to end through the public API with host buffers: upload the initial
     # states from pinned memory, advance them by K steps, read the results back
@@ -275,6 +289,7 @@ def run_gpu(args):
         "roofline": {"bound": "hbm", "kernel": "stage_march_kernel<SWE> (stage 1 + stage 2)",
                      "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
+                     "traffic_unit": "DRAM bytes per stage pair (ncu capture)",
                      "algorithmic_bytes": f"{SWE_BYTES_PER_CELL_UPDATE} B/cell-update x {N_SWE}^2 cells per step"},
         "e2e": e2e,
         "gpu_launches": 4 * K,
