@@ -67,10 +67,8 @@ def measured_peaks():
 
 
 def dist_env():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+    from paper_2602_08670_gb300 import ranks
+    return ranks.env()
 
 
 class Clocks:
@@ -186,6 +184,7 @@ def run_gpu(args):
     import __graft_entry__
     __graft_entry__.build()
     from paper_2602_08670_gb300 import fv
+    from paper_2602_08670_gb300 import ranks
     from paper_2602_08670_gb300 import workloads as W
 
     bs = torch.cuda.Stream()
@@ -197,8 +196,7 @@ def run_gpu(args):
     assert swe.stream == bs.cuda_stream and eul.stream == bs.cuda_stream
 
     def barrier():
-        if ws > 1:
-            torch.distributed.barrier()
+        ranks.barrier()
         torch.cuda.synchronize()
 
     # warm-up (also captures the graphs)
@@ -229,12 +227,9 @@ def run_gpu(args):
     eul_ms = sum(e[1].elapsed_time(e[2]) for e in ev)
     fv.fv_sync(swe)
     fv.fv_sync(eul)
-    if ws > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
     cells_per_step = N_SWE * N_SWE + N_EULER * N_EULER
-    value = ws * cells_per_step * K / (total_ms * 1e-3)
+    value, secs = ranks.job_rate(cells_per_step * K, total_ms * 1e-3, device="cuda")
+    total_ms = secs * 1e3
 
     # roofline of the dominant kernel pair (SWE stage 1 + stage 2)
     peak, peak_kind = measured_peaks()
@@ -265,12 +260,9 @@ def run_gpu(args):
             barrier()
             e2e_runs.append(time.perf_counter() - t0)
         e2e_s = min(e2e_runs[1:]) if len(e2e_runs) > 1 else e2e_runs[0]
-        if ws > 1:
-            t = torch.tensor([e2e_s], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_rate, e2e_s = ranks.job_rate(cells_per_step * K, e2e_s, device="cuda")
         assert bool(torch.isfinite(o_swe).all()) and bool(torch.isfinite(o_eul).all())
-        e2e = {"value": ws * cells_per_step * K / e2e_s, "unit": UNIT,
+        e2e = {"value": e2e_rate, "unit": UNIT,
                "h2d_bytes_per_step": state_bytes / K, "d2h_bytes_per_step": state_bytes / K,
                "call": "fv_set_state(host) + fv_enqueue_steps(K) + fv_get_state(host) per state"}
 

@@ -66,7 +66,7 @@ enum {
 };
 
 /* Periodic grid [0, lx) x [0, ly) with nx x ny cells of size lx/nx x ly/ny
- * (Section 2.3.1, "The grid": N cells per direction, centres (i + 1/2) dx),
+ * (Section 2.3.1: N cells per direction, centres (i + 1/2) dx),
  * and `batch` independent members that share the grid. */
 typedef struct { int nx, ny, batch; double lx, ly; } fv_grid;
 

@@ -1,24 +1,25 @@
 """FP64 oracle of the learned-stencil variant (test infrastructure only).
 
-Section 2.5.3, "Calculate reconstruction slopes with CNN generated linear
-coefficients" (the fourth approach, Section 5.4): a CNN maps the cell-average
+Section 2.5.3, the fourth approach (reconstruction with CNN-generated linear
+coefficients; results in Section 5.4): a CNN maps the cell-average
 state to constrained coefficients; the face values are those coefficients
 applied to the neighbouring cell values; the same flux, divergence and
 SSP-RK2 as the plain scheme follow.  Training minimises the rollout loss of
-Eq. 2.28 with the solver inside the loss ("model consistent").
+Eq. 2.28 with the solver inside the loss (model-consistent training).
 
 Readings where the paper is silent (each one is listed with its reason in the
 design notes):
-  * Network: x = (q - mean) / std per channel; four 3x3 convolutions with
+  * Network: x = (q - mean) / scale per channel (the training set's mean and
+    largest absolute deviation); four 3x3 convolutions with
     circular padding, 3 -> 32 -> 32 -> 32 -> 36 channels, ReLU after the
     first three, the last one linear.
   * 36 outputs per cell = 2 directions x 3 variables x 2 sides x 3 taps.  Cell
     i owns face i+1/2 in x and face j+1/2 in y.  Side L uses cells
-    {i-1, i, i+1}, side R uses {i, i+1, i+2} ("three stencils", Section 6.2).
+    {i-1, i, i+1}, side R uses {i, i+1, i+2} (three stencils per face, Section 6.2).
   * Normalisation: w = e_centre + r - mean(r) over the three taps, so the
     weights sum to one and a zero raw output gives the first-order
-    (piecewise constant) scheme ("initialise ... to ensure first-order
-    accuracy", Section 2.5.3).
+    (piecewise constant) scheme, the first-order starting point that the
+    initialisation of Section 2.5.3 is meant to guarantee.
   * Positivity: where either reconstructed depth at a face is below h_min,
     that face uses the MUSCL-minmod states instead (the plain step is the
     fallback).
