@@ -340,9 +340,36 @@ def learned_block(args):
     fv.fv_sync(st)
     ms = e0.elapsed_time(e1)
     learned_rate = members * n * n * K / (ms * 1e-3)
+    cnn_tflops = 2 * 59328 * 2 * members * n * n * K / (ms * 1e-3) / 1e12
+    peaks = {}
+    pp = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pp):
+        with open(pp) as f:
+            peaks = json.load(f)
+    bf16_peak = peaks.get("bf16_tflops_sustained", 1700.0)
     out["rollout"] = {"workload": f"{members} members x {n}^2 SWE, learned, fixed dt, {K} steps",
+                      "kernel": "learned_fused_kernel (CNN on tcgen05 + learned faces + HLL + RK, "
+                                "one launch per stage)",
                       "cell_updates_per_s": learned_rate, "ms_per_step": ms / K,
-                      "cnn_tflops": 2 * 59328 * 2 * members * n * n * K / (ms * 1e-3) / 1e12}
+                      "cnn_tflops": cnn_tflops,
+                      "roofline": {"bound": "tensor", "achieved": cnn_tflops, "peak": bf16_peak,
+                                   "unit": "TFLOP/s", "frac": cnn_tflops / bf16_peak,
+                                   "peak_kind": "measured bf16 sustained",
+                                   "algorithmic": "118656 FLOP per cell-update (2 CNN passes of "
+                                                  "59328 FLOP)"},
+                      "hbm_gbs": 60 * learned_rate / 1e9}
+    # the same rollout through the two-pass path (CNN coefficients via HBM)
+    fv.fv_set_learned_variant(st, "two_pass")
+    fv.fv_enqueue_steps(st, 2, net=net)
+    fv.fv_sync(st)
+    K2 = max(2, K // 4)
+    torch.cuda.synchronize()
+    e0.record(bs)
+    fv.fv_enqueue_steps(st, K2, net=net)
+    e1.record(bs)
+    fv.fv_sync(st)
+    ms2 = e0.elapsed_time(e1)
+    out["rollout"]["two_pass_cell_updates_per_s"] = members * n * n * K2 / (ms2 * 1e-3)
     del st
     # -- one training iteration (C3 shape)
     tr = TR.generate(256, 4, members=64, seed=0, coarse_steps=32)

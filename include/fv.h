@@ -148,9 +148,26 @@ int fv_state_device_ptr(const fv_state* s, float** dptr);
 /* Stage-kernel implementation of the plain step: 0 = automatic (row-march
  * kernel when nx is a multiple of 4 and >= 8, else the shared-memory tile
  * kernel), 1 = tile kernel, 2 = row-march kernel (FV_EINVAL if nx does not
- * allow it).  Both evaluate the same arithmetic per face and per cell, so the
- * results are bitwise identical; the choice only changes speed. */
+ * allow it).  Both evaluate the same formulas per face and per cell; the
+ * approximate reciprocal and square root may be scheduled differently, so
+ * results agree to a few ulps, not bitwise.  The choice only changes speed. */
 int fv_set_stage_variant(fv_state* s, int variant);
+
+/* Implementation of the learned step (Section 2.5.3, fourth approach):
+ *  FV_LEARNED_AUTO (0): the fused kernel where the grid allows it, else the
+ *    two-pass path;
+ *  FV_LEARNED_FUSED (1): one persistent kernel per Runge-Kutta stage that
+ *    evaluates the CNN row by row on the tensor cores and uses the
+ *    coefficients straight from on-chip memory (nx a multiple of 128, at most
+ *    1024; FV_EINVAL otherwise);
+ *  FV_LEARNED_TWO_PASS (2): the CNN writes the coefficients of every cell to
+ *    device memory, then a stage kernel reads them (nx in {8, 16, 32, 64} or
+ *    a multiple of 128).
+ * Both use BF16 operands with FP32 accumulation and the same per-face
+ * arithmetic; the first layer sums its taps in a different order, so results
+ * agree to rounding, not bitwise. */
+enum { FV_LEARNED_AUTO = 0, FV_LEARNED_FUSED = 1, FV_LEARNED_TWO_PASS = 2 };
+int fv_set_learned_variant(fv_state* s, int variant);
 
 /* The CUDA stream (cudaStream_t as void*) on which the state's kernels run,
  * owned by the state; for callers that time or order work against it. */

@@ -1,0 +1,908 @@
+// fv_fused.cu — the learned-stencil SSP-RK2 stage as one persistent kernel.
+//
+// One launch = one Runge-Kutta stage (Eq. 2.19) of the learned step (Section
+// 2.5.3, fourth approach) over every member: CNN (four 3x3 periodic
+// convolutions on tcgen05, BF16 operands, FP32 accumulators in TMEM), the
+// sum-to-one normalisation of the 36 outputs, the learned face states with
+// their minmod fallback, the HLL fluxes (Eq. 2.15, rotated on y faces, Eq.
+// 2.24), the flux divergence (Eq. 2.23), the RK combine and, in stage 2, the
+// Courant-rate reduction for the next dt (Eq. 2.10).  Activations and
+// coefficients never leave the SM: HBM sees the stage input, q^n in stage 2
+// and the stage output, as in the plain step.
+//
+// Work decomposition.  A cluster of CS = nx / 128 CTAs (one per SM) owns whole
+// grid rows: CTA r of the cluster owns columns [128 r, 128 r + 128).  The
+// rows of all members, concatenated, are split into 2 x (number of clusters)
+// contiguous ranges, two per cluster ("streams").  A stream marches down its
+// rows; a tick processes one row at every layer of the pipeline:
+//   MMA(tick):  layer 1 output row t-1, and for layers 2, 3, 4 the completion
+//               of one output row and the start of the next (below);
+//   EPI(tick):  drain the finished accumulators (bias, ReLU, BF16) into the
+//               next layer's input rows; layer 4 gives the coefficients of row
+//               t-7 and, straight from registers, that row's x-face fluxes and
+//               its north y-face fluxes; update row t-8; build the layer-1
+//               input of row t+1 and stage the FP32 state row t-4.
+// The two streams alternate: in each phase the tensor core works on one
+// stream's tick while the CUDA cores drain the other's.
+//
+// Threads: warpgroups 0 and 1 drain TMEM (each thread one TMEM lane = one
+// column) and compute the faces; warpgroup 2 updates the finished row and
+// stages state rows, except its first warp, whose first lane issues the MMAs.
+//
+// Layers 2-4 keep two input rows and two adjacent accumulators each: slot 0
+// holds the row started at the previous tick (taps ky = 0 and 1 summed), slot
+// 1 the row started now.  When input row k arrives, six MMAs of the taps
+// ky = 0 on row k-1 start slot 1, and six MMAs with the taps ky = 2 and ky = 1
+// stacked along N (one read of row k, N = 64 or 96) complete slot 0 and add
+// to slot 1; after the drain, slot 1 moves to slot 0.  An output row thus sums
+// its taps in the order ky = 0, 1, 2 (kx and channel groups inner), the same
+// order as the two-pass CNN.  Layer 1 reads the three x taps of the state
+// gathered into one K = 16 operand (9 used channels) and sums three dy taps.
+// The 1-cell x halo of every hidden layer comes from the neighbouring CTA of
+// the cluster (distributed shared memory; the periodic wrap for CS = 1), and
+// so does the flux through the west face of column 0.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "fv_common.cuh"
+#include "fv_internal.h"
+#include "fv_learned.cuh"
+#include "stencil_net.cuh"
+#include "tc_common.cuh"
+
+namespace fvk {
+namespace fused {
+
+constexpr int EPI_THREADS = 256;        // 2 warpgroups that drain TMEM
+constexpr int NT = EPI_THREADS + 128;   // + the update / staging warpgroup
+constexpr int ISSUE_WARP = EPI_THREADS / 32;
+constexpr int W = 128;                  // columns per CTA = MMA M
+constexpr int FP = W + 2;               // hidden-layer input frame (1-cell halo)
+constexpr int QF = W + 4;               // FP32 state frame (2-cell halo)
+constexpr int MAX_CS = 8;               // portable cluster size
+constexpr int TICKS_AHEAD = 11;         // ticks before the first updated row
+constexpr uint32_t WAIT_ITERS = 1u << 22;
+
+// shared memory (bytes)
+constexpr int L1_SLOT = 2 * W * 16;                 // [2 groups][128][8 BF16]
+constexpr int HID_SLOT = 4 * FP * 16;               // [4 groups][130][8 BF16]
+constexpr int Q_SLOT = 3 * QF * 4;                  // [3 vars][132] FP32
+constexpr int F_SLOT = 1552;                        // [3 vars][129] FP32, padded
+constexpr int G_SLOT = 3 * W * 4;                   // [3 vars][128] FP32
+constexpr int OFF_L1 = 0;                           // 3 slots
+constexpr int OFF_IN = OFF_L1 + 3 * L1_SLOT;        // layers 2..4 inputs, 2 slots each
+constexpr int OFF_Q = OFF_IN + 3 * 2 * HID_SLOT;    // 5 slots
+constexpr int OFF_F = OFF_Q + 5 * Q_SLOT;           // 2 slots
+constexpr int OFF_G = OFF_F + 2 * F_SLOT;           // 3 slots
+constexpr int STREAM_BYTES = OFF_G + 3 * G_SLOT;
+
+constexpr int W1_BYTES = snk::W1G_ELEMS * 2;                       // 3072
+constexpr int WH_BYTES = 9 * snk::CG_HID * snk::HID * 16;          // 18432
+constexpr int W4_BYTES = 9 * snk::CG_HID * snk::N_OUT_PAD * 16;    // 27648
+constexpr int OFF_W1 = 0;
+constexpr int OFF_W2 = OFF_W1 + W1_BYTES;
+constexpr int OFF_W3 = OFF_W2 + WH_BYTES;
+constexpr int OFF_W4 = OFF_W3 + WH_BYTES;
+constexpr int OFF_STREAMS = OFF_W4 + W4_BYTES;
+constexpr int N_BIAS = 3 * snk::HID + snk::N_OUT;
+constexpr int OFF_BIAS = OFF_STREAMS + 2 * STREAM_BYTES;
+constexpr int OFF_MBAR = OFF_BIAS + ((N_BIAS * 4 + 15) / 16) * 16;
+constexpr int OFF_TSLOT = OFF_MBAR + 16;
+constexpr int OFF_RED = OFF_TSLOT + 16;
+constexpr int SMEM_BYTES = OFF_RED + 32 * 4;
+
+static_assert(STREAM_BYTES % 16 == 0 && OFF_STREAMS % 16 == 0, "16-byte aligned operands");
+static_assert(SMEM_BYTES <= 232448, "shared memory per CTA");
+
+// TMEM columns of one stream (two streams: 2 x 256 = 512)
+constexpr uint32_t TCOLS = 512;
+constexpr uint32_t ACC1 = 0;
+// layer 0..2 = layers 2..4; slot 0 and slot 1 are adjacent
+__host__ __device__ constexpr uint32_t acc_col(int layer, int slot) {
+  return layer < 2 ? 32u + 64u * layer + 32u * slot : 160u + 48u * slot;
+}
+
+struct Args {
+  const float* qin;
+  const float* qn;
+  float* qout;
+  const uint16_t* w1g;
+  const uint16_t* w2;
+  const uint16_t* w3;
+  const uint16_t* w4;
+  const float* params;
+  int bias_off[4];
+  float mean[3], rstd[3];
+  const float* hmin;
+  Ctrl* ctrl;
+  const DtParams* dp;
+  int nx, ny, cs;
+  long long plane, member;
+  long long rows;          // B * ny
+  long long nstreams;      // 2 x clusters
+  float rdx, rdy, g;
+  unsigned* err;
+};
+
+// ---------------------------------------------------------------------------
+// Cluster, TMEM and copy helpers (inline PTX)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t map_cta(uint32_t saddr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void st_cluster_v4(uint32_t addr, uint4 v) {
+  asm volatile("st.shared::cluster.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v.x), "r"(v.y),
+               "r"(v.z), "r"(v.w)
+               : "memory");
+}
+__device__ __forceinline__ void st_cluster_f32(uint32_t addr, float v) {
+  asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
+}
+__device__ __forceinline__ void cluster_arrive() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ void cluster_arrive_relaxed() {
+  asm volatile("barrier.cluster.arrive.relaxed.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() {
+  asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_cluster() {
+  asm volatile("fence.proxy.async.shared::cluster;\n" ::: "memory");
+}
+// Arrive on the mbarrier at the same shared-memory offset in every CTA of
+// `mask` once this thread's earlier tcgen05.mma have completed.
+__device__ __forceinline__ void commit_multicast(uint64_t* mbar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;\n"
+      ::"r"(tc::smem_u32(mbar)), "h"(mask)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_ld2(uint32_t taddr, float (&v)[2]) {
+  uint32_t r0, r1;
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];\n"
+               : "=r"(r0), "=r"(r1) : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+  v[0] = __uint_as_float(r0);
+  v[1] = __uint_as_float(r1);
+}
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float (&v)[4]) {
+  uint32_t r0, r1, r2, r3;
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];\n"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3) : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+  v[0] = __uint_as_float(r0);
+  v[1] = __uint_as_float(r1);
+  v[2] = __uint_as_float(r2);
+  v[3] = __uint_as_float(r3);
+}
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                 "=r"(r[7])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const float (&v)[8]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};\n"
+               ::"r"(taddr), "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])),
+                 "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])),
+                 "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7]))
+               : "memory");
+}
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+      "%12, %13, %14, %15, %16};\n"
+      ::"r"(taddr), "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+        "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+        "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])),
+        "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+        "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
+        "r"(__float_as_uint(v[15]))
+      : "memory");
+}
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(tc::smem_u32(smem)), "l"(gmem)
+               : "memory");
+}
+// Periodic index for rows (any offset: 32-bit remainder) and for columns
+// (offsets of at most one period: two compares).
+__device__ __forceinline__ int wrap_row(int i, int n) {
+  const int r = i % n;
+  return r < 0 ? r + n : r;
+}
+__device__ __forceinline__ int wrap_col(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
+// Index of the stream whose row range holds global row r (ranges are
+// [k R / S, (k + 1) R / S)).
+__device__ __forceinline__ long long stream_of_row(long long r, long long R, long long S) {
+  return ((r + 1) * S - 1) / R;
+}
+
+// Per-thread copy of a stream's position; every thread updates it the same way.
+struct Stream {
+  long long g, g_end;      // next row of the range (concatenated rows), end of range
+  int b, u0, u1;           // current segment: member and its rows [u0, u1)
+  int tau, ntau;           // tick within the segment
+  bool active, pending;    // has a segment; MMAs issued and not yet drained
+  uint32_t parity;         // next phase of the stream's mbarrier
+  float dt, hmin;
+  float amax;
+  unsigned bad;
+};
+
+// q^n of the row the next tick updates (stage 2), loaded one tick ahead of
+// its use, for the columns k and k + 96 of an updating thread.
+struct Pref {
+  float qn[2][3];
+};
+
+__device__ __forceinline__ void fetch_qn(Pref& P, const Args& a, int b, int u, int X0, int k) {
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const int m = k + 96 * r;
+    if (m < W) {
+      const long long off = (long long)b * a.member + (long long)u * a.nx + X0 + m;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) P.qn[r][c] = a.qn[off + c * a.plane];
+    }
+  }
+}
+
+// Layer-1 input at position m: the normalised state of the cells m-1, m,
+// m+1 as channel 3 kx + var (x = (q - mean) / scale, as in the two-pass CNN),
+// BF16, 9 of 16 channels used.
+__device__ __forceinline__ void prep_l1_pos(uint8_t* slot, const Args& a, const float (&q)[9], int m) {
+  float ch[9];
+#pragma unroll
+  for (int c = 0; c < 9; ++c) ch[c] = (q[c] - a.mean[c % 3]) * a.rstd[c % 3];
+  const uint4 g0 = make_uint4(pack_bf16x2(ch[0], ch[1]), pack_bf16x2(ch[2], ch[3]),
+                              pack_bf16x2(ch[4], ch[5]), pack_bf16x2(ch[6], ch[7]));
+  const uint4 g1 = make_uint4(pack_bf16x2(ch[8], 0.f), 0u, 0u, 0u);
+  *reinterpret_cast<uint4*>(slot + m * 16) = g0;
+  *reinterpret_cast<uint4*>(slot + (W + m) * 16) = g1;
+}
+
+// The layer-1 input row `row`, positions k and k + n (n >= 64): the loads of
+// both positions first, then the stores.
+__device__ __forceinline__ void load_l1_row(float (&q)[2][9], const Args& a, const float* qb, int row,
+                                            int X0, int k, int n) {
+  const float* base = qb + (long long)wrap_row(row, a.ny) * a.nx;
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const int m = k + r * n;
+    if (m < W) {
+#pragma unroll
+      for (int kx = 0; kx < 3; ++kx) {
+        const int col = wrap_col(X0 + m + kx - 1, a.nx);
+#pragma unroll
+        for (int v = 0; v < 3; ++v) q[r][3 * kx + v] = base[v * a.plane + col];
+      }
+    }
+  }
+}
+__device__ __forceinline__ void store_l1_row(uint8_t* slot, const Args& a, const float (&q)[2][9], int k,
+                                             int n) {
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const int m = k + r * n;
+    if (m < W) prep_l1_pos(slot, a, q[r], m);
+  }
+}
+
+// FP32 state row with a 2-cell periodic halo: frame position p is column
+// X0 - 2 + p; elements k, k + n, ... (n >= 96: at most five per thread, all
+// loads issued before the stores).
+__device__ __forceinline__ void load_q_row(float* slot, const Args& a, const float* qb, int row,
+                                           int X0, int k, int n) {
+  const float* base = qb + (long long)wrap_row(row, a.ny) * a.nx;
+  float v[5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    const int idx = k + i * n;
+    if (idx < 3 * QF) {
+      const int c = idx / QF, p = idx - c * QF;
+      v[i] = base[c * a.plane + wrap_col(X0 - 2 + p, a.nx)];
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    const int idx = k + i * n;
+    if (idx < 3 * QF) slot[idx] = v[i];
+  }
+}
+
+// Bring a state row (three variables, this CTA's columns) into L2 ahead of use.
+__device__ __forceinline__ void prefetch_row(const Args& a, const float* qb, int row, int X0, int k) {
+  if (k < 3 * 4) {
+    const int v = k / 4, seg = k % 4;    // 4 x 128-byte lines per variable and row
+    const float* p = qb + v * a.plane + (long long)wrap_row(row, a.ny) * a.nx + X0 + 32 * seg;
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+  }
+}
+
+// Bias, ReLU and BF16 of 16 accumulator columns (channel groups 2 wg, 2 wg + 1)
+// into position m + 1 of the next layer's input row; the CTA's edge columns
+// also go to the neighbours' halo positions.
+__device__ __forceinline__ void drain_hidden(uint32_t taddr, const float* bias, uint8_t* dst,
+                                             int m, int wg, uint32_t west, uint32_t east) {
+  float v[16];
+  tc::tmem_ld16(taddr + 16 * wg, v);
+#pragma unroll
+  for (int gg = 0; gg < 2; ++gg) {
+    const int g = 2 * wg + gg;
+    uint32_t pk[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int c = 8 * gg + 2 * j;
+      pk[j] = pack_bf16x2(fmaxf(v[c] + bias[8 * g + 2 * j], 0.f),
+                          fmaxf(v[c + 1] + bias[8 * g + 2 * j + 1], 0.f));
+    }
+    const uint4 val = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    uint8_t* row = dst + g * FP * 16;
+    *reinterpret_cast<uint4*>(row + (m + 1) * 16) = val;
+    if (m == 0) st_cluster_v4(map_cta(tc::smem_u32(row + (FP - 1) * 16), west), val);
+    if (m == W - 1) st_cluster_v4(map_cta(tc::smem_u32(row), east), val);
+  }
+}
+
+// The 18 normalised coefficients of one direction (dir 0: channels 0..17 = x,
+// dir 1: 18..35 = y) of this lane's cell: w = e_centre + r - mean(r) per
+// 3-tap stencil, as in the two-pass CNN's epilogue.
+__device__ __forceinline__ void drain_coeffs(uint32_t taddr, const float* bias, int dir,
+                                             float (&wd)[18]) {
+  float r[18];
+  if (dir == 0) {
+    float v16[16], v2[2];
+    tc::tmem_ld16(taddr, v16);
+    tmem_ld2(taddr + 16, v2);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) r[k] = v16[k] + bias[k];
+    r[16] = v2[0] + bias[16];
+    r[17] = v2[1] + bias[17];
+  } else {
+    // channels 18..35 from the 16-aligned loads of columns 16..31 and 32..35
+    float v16[16], v4[4];
+    tc::tmem_ld16(taddr + 16, v16);
+    tmem_ld4(taddr + 32, v4);
+#pragma unroll
+    for (int k = 0; k < 14; ++k) r[k] = v16[2 + k] + bias[18 + k];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) r[14 + k] = v4[k] + bias[32 + k];
+  }
+#pragma unroll
+  for (int s = 0; s < 6; ++s) {
+    const float mean = (r[3 * s] + r[3 * s + 1] + r[3 * s + 2]) * (1.f / 3.f);
+    wd[3 * s] = r[3 * s] - mean;
+    wd[3 * s + 1] = 1.f + (r[3 * s + 1] - mean);
+    wd[3 * s + 2] = r[3 * s + 2] - mean;
+  }
+}
+
+// Once every slot-0 read of the tick is done: the row started this tick
+// (slot 1) becomes the row to complete next tick (slot 0), for layers 2..4.
+// Warpgroup 0 moves columns 0-15 (and 32-39 of layer 4), warpgroup 1 columns
+// 16-31 (and 40-47), each thread its own TMEM lane.
+__device__ __forceinline__ void move_slots(uint32_t tm, int wg) {
+#pragma unroll
+  for (int l = 0; l < 3; ++l) {
+    float v[16];
+    tc::tmem_ld16(tm + acc_col(l, 1) + 16 * wg, v);
+    tmem_st16(tm + acc_col(l, 0) + 16 * wg, v);
+  }
+  float v8[8];
+  tmem_ld8(tm + acc_col(2, 1) + 32 + 8 * wg, v8);
+  tmem_st8(tm + acc_col(2, 0) + 32 + 8 * wg, v8);
+  asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
+}
+
+// Move a stream to its next segment whose member still has work; false when
+// the range is exhausted.  Every thread runs this with the same inputs.
+__device__ bool next_segment(Stream& S, const Args& a, uint32_t crank) {
+  while (S.g < S.g_end) {
+    const int b = (int)(S.g / a.ny);
+    const int u0 = (int)(S.g - (long long)b * a.ny);
+    const long long left = S.g_end - S.g;
+    const int u1 = (int)((long long)(a.ny - u0) < left ? a.ny : u0 + left);
+    S.g = (long long)b * a.ny + u1;
+    Ctrl* c = a.ctrl + b;
+    if (*reinterpret_cast<volatile unsigned*>(&c->done)) {
+      // a stage attempted after REPLAY ran out (flagged once per member)
+      if (c->exhausted && u0 == 0 && crank == 0 && threadIdx.x == 0)
+        atomicOr(&c->health, FV_HEALTH_REPLAY_END);
+      continue;
+    }
+    S.b = b;
+    S.u0 = u0;
+    S.u1 = u1;
+    S.tau = 0;
+    S.ntau = u1 - u0 + TICKS_AHEAD;
+    S.dt = (float)c->dt;
+    S.hmin = a.hmin[b];
+    S.amax = 0.f;
+    S.bad = 0u;
+    return true;
+  }
+  return false;
+}
+
+// Start of a segment: layer-1 inputs of rows u0-5, u0-4, u0-3 (slots 0, 1,
+// 2), one row per warpgroup.  (The issuing warp takes no part: it has not
+// waited for the MMAs that read these slots.)
+__device__ __forceinline__ void segment_prologue(const Stream& S, uint8_t* sbuf, const Args& a,
+                                                 int X0, int m, int wg) {
+  if (wg == 2 && m < 32) return;
+  const int k = wg == 2 ? m - 32 : m, n = wg == 2 ? W - 32 : W;
+  float q[2][9];
+  load_l1_row(q, a, a.qin + (long long)S.b * a.member, S.u0 - 5 + wg, X0, k, n);
+  store_l1_row(sbuf + OFF_L1 + wg * L1_SLOT, a, q, k, n);
+}
+
+// Shared-memory descriptors of the operands; a slot or tap offset is added to
+// the start-address field (bits 0-13, address / 16; shared addresses stay
+// below 256 KB, so the field never overflows).
+struct Descs {
+  uint64_t a_l1, a_in, b_w1;
+  uint64_t b_ky0[3], b_pair[3];   // layers 2..4: taps ky = 0, and ky = 2 | ky = 1 stacked
+};
+__device__ __forceinline__ uint64_t dplus(uint64_t d, uint32_t bytes) { return d + (bytes >> 4); }
+
+// All MMAs of one tick of one stream (issued by one thread), then a commit
+// to the stream's mbarrier in this CTA and its neighbours; `tm`: the
+// stream's first TMEM column.
+__device__ __forceinline__ void issue_tick(const Descs& D, uint32_t tm, int tau, uint64_t* mbar,
+                                           uint16_t mask) {
+  constexpr uint32_t id32 = tc::idesc_bf16_f32(W, snk::HID);
+  constexpr uint32_t id48 = tc::idesc_bf16_f32(W, snk::N_OUT_PAD);
+  constexpr uint32_t id64 = tc::idesc_bf16_f32(W, 2 * snk::HID);
+  constexpr uint32_t id96 = tc::idesc_bf16_f32(W, 2 * snk::N_OUT_PAD);
+  // layers 2..4: new input row in slot (tau+1)&1, previous one in slot tau&1
+  const uint32_t s_new = (uint32_t)((tau + 1) & 1), s_prev = (uint32_t)(tau & 1);
+  uint64_t a_new[3], a_prev[3];
+#pragma unroll
+  for (int l = 0; l < 3; ++l) {
+    a_new[l] = dplus(D.a_in, (uint32_t)(l * 2 * HID_SLOT) + s_new * HID_SLOT);
+    a_prev[l] = dplus(D.a_in, (uint32_t)(l * 2 * HID_SLOT) + s_prev * HID_SLOT);
+  }
+  // Steps 0-5: layer 1 (taps ky on input rows t-2, t-1, t) and the taps
+  // ky = 0 on the previous row into slot 1; steps 6-11: the stacked taps
+  // ky = 2 | ky = 1 on the new row into slot 0 | slot 1.  Layers are
+  // interleaved so that consecutive MMAs target different accumulators.
+#pragma unroll
+  for (int i = 0; i < 12; ++i) {
+    if (i < 3) {
+      const uint32_t slot = (uint32_t)((tau + i) % 3);
+      tc::mma_bf16(tm + ACC1, dplus(D.a_l1, slot * L1_SLOT), dplus(D.b_w1, i * 2 * snk::HID * 16), id32,
+                   i > 0);
+    }
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+      const uint32_t N = l == 2 ? snk::N_OUT_PAD : snk::HID;
+      const int j = i % 6, kx = j / 2, ks = j % 2;
+      const uint32_t aoff = (uint32_t)((2 * ks * FP + kx) * 16);
+      if (i < 6)
+        tc::mma_bf16(tm + acc_col(l, 1), dplus(a_prev[l], aoff),
+                     dplus(D.b_ky0[l], (uint32_t)((kx * 4 + 2 * ks) * N * 16)), l == 2 ? id48 : id32, i > 0);
+      else
+        tc::mma_bf16(tm + acc_col(l, 0), dplus(a_new[l], aoff),
+                     dplus(D.b_pair[l], (uint32_t)((kx * 4 + 2 * ks) * 2 * N * 16)), l == 2 ? id96 : id64,
+                     true);
+    }
+  }
+  // completion is signalled to this CTA and to its neighbours, which write
+  // into the rows these MMAs read only after it
+  commit_multicast(mbar, mask);
+}
+
+// Per-thread kernel context.
+struct Ctx {
+  uint8_t* smem;
+  const float* bias;
+  uint64_t* mbar;
+  unsigned* red;
+  uint32_t tmem;
+  Descs D[2];
+  int tid, m, wg, X0;
+  uint32_t lane_off, west, east, crank;
+  uint16_t commit_mask;
+  bool issuer, failed, arrived;
+};
+
+// Update of row u = t - 8 from the fluxes of the two previous ticks (columns
+// k and k + 96 of a staging thread: nothing here depends on this tick's
+// MMAs), and the load of q^n for the row the next tick updates.
+template <int STAGE>
+__device__ __forceinline__ void update_row(Stream& Q, Pref& P, uint8_t* sbuf, const Args& a,
+                                           const Ctx& X, int k) {
+  const int tau = Q.tau;
+  const int t = Q.u0 - 3 + tau;
+  const float* qring = reinterpret_cast<const float*>(sbuf + OFF_Q);
+  const float* Fb = reinterpret_cast<const float*>(sbuf + OFF_F);
+  const float* Gb = reinterpret_cast<const float*>(sbuf + OFF_G);
+  if (tau >= TICKS_AHEAD) {
+    const int u = t - 8;
+    const float* Fo = Fb + ((tau + 1) & 1) * (F_SLOT / 4);
+    const float* Gs = Gb + ((tau + 1) % 3) * (G_SLOT / 4);
+    const float* Gn = Gb + ((tau + 2) % 3) * (G_SLOT / 4);
+    const float* qu = qring + ((tau + 1) % 5) * (3 * QF);
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const int m = k + 96 * r;
+      if (m < W) {
+        const long long off = (long long)Q.b * a.member + (long long)u * a.nx + X.X0 + m;
+        float out[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const float Lc = divergence<float>(Fo[c * (W + 1) + m], Fo[c * (W + 1) + m + 1], Gs[c * W + m],
+                                             Gn[c * W + m], a.rdx, a.rdy);
+          const float q = qu[c * QF + m + 2];
+          out[c] = STAGE == 1 ? rk_stage1<float>(q, Q.dt, Lc)
+                              : rk_stage2<float>(P.qn[r][c], q, 0.5f * Q.dt, Lc);
+          a.qout[off + c * a.plane] = out[c];
+        }
+        if (STAGE == 2)
+          Q.amax = fmaxf(Q.amax, cell_rate_swe(out[0], out[1], out[2], a.g, a.rdx, a.rdy, Q.bad));
+      }
+    }
+  }
+  if (STAGE == 2 && tau + 1 >= TICKS_AHEAD && tau + 1 < Q.ntau) fetch_qn(P, a, Q.b, t - 7, X.X0, k);
+}
+
+// The TMEM-draining warpgroups' part of tick Q.tau (after its MMAs).
+__device__ __forceinline__ void epilogue(const Stream& Q, uint8_t* sbuf, uint32_t tm, const Args& a,
+                                         const Ctx& X) {
+  const int m = X.m, wg = X.wg;
+  const int tau = Q.tau;
+  const float* bias = X.bias;
+  float* qring = reinterpret_cast<float*>(sbuf + OFF_Q);
+  float* Fb = reinterpret_cast<float*>(sbuf + OFF_F);
+  float* Gb = reinterpret_cast<float*>(sbuf + OFF_G);
+  // hidden layers: finished accumulators -> next layer's input row (slot tau & 1)
+  drain_hidden(tm + ACC1, bias, sbuf + OFF_IN + (tau & 1) * HID_SLOT, m, wg, X.west, X.east);
+  drain_hidden(tm + acc_col(0, 0), bias + snk::HID, sbuf + OFF_IN + 2 * HID_SLOT + (tau & 1) * HID_SLOT,
+               m, wg, X.west, X.east);
+  drain_hidden(tm + acc_col(1, 0), bias + 2 * snk::HID,
+               sbuf + OFF_IN + 4 * HID_SLOT + (tau & 1) * HID_SLOT, m, wg, X.west, X.east);
+  // the next tick's MMAs read these rows through the async proxy
+  tc::fence_proxy_async_smem();
+  if (m == 0 || m == W - 1) fence_proxy_async_cluster();
+  // layer 4: coefficients of row j = t - 7 and the faces it owns
+  float wd[18];
+  drain_coeffs(tm + acc_col(2, 0), bias + 3 * snk::HID, wg, wd);
+  const float* qj = qring + ((tau + 2) % 5) * (3 * QF);
+  float qm[3], q0[3], q1[3], qp[3], L[3], R[3], F[3];
+  if (wg == 0) {
+    // x face j, i+1/2 from cells i-1 .. i+2 of row j
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      qm[c] = qj[c * QF + m + 1];
+      q0[c] = qj[c * QF + m + 2];
+      q1[c] = qj[c * QF + m + 3];
+      qp[c] = qj[c * QF + m + 4];
+    }
+    learned_face(qm, q0, q1, qp, wd, Q.hmin, L, R);
+    hll_swe<float>(L[0], L[1], L[2], R[0], R[1], R[2], a.g, F[0], F[1], F[2]);
+    float* Fs = Fb + (tau & 1) * (F_SLOT / 4);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      Fs[c * (W + 1) + m + 1] = F[c];
+      if (m == W - 1) st_cluster_f32(map_cta(tc::smem_u32(Fs + c * (W + 1)), X.east), F[c]);
+    }
+  } else {
+    // y face j+1/2 from rows j-1 .. j+2 of column i (rotated frame)
+    const float* r0 = qring + ((tau + 1) % 5) * (3 * QF);
+    const float* r2 = qring + ((tau + 3) % 5) * (3 * QF);
+    const float* r3 = qring + ((tau + 4) % 5) * (3 * QF);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      qm[c] = r0[c * QF + m + 2];
+      q0[c] = qj[c * QF + m + 2];
+      q1[c] = r2[c * QF + m + 2];
+      qp[c] = r3[c * QF + m + 2];
+    }
+    learned_face(qm, q0, q1, qp, wd, Q.hmin, L, R);
+    hll_swe<float>(L[0], L[2], L[1], R[0], R[2], R[1], a.g, F[0], F[2], F[1]);
+    float* Gs = Gb + (tau % 3) * (G_SLOT / 4);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) Gs[c * W + m] = F[c];
+  }
+}
+
+// The staging warps' part of tick Q.tau (warps 1-3 of warpgroup 2): the
+// update of row t-8, the FP32 state row t-4 into the ring, then (once the
+// tick's MMAs have read the slot) the layer-1 input of row t+1, and an L2
+// prefetch of the row the next tick stages.
+template <int STAGE>
+__device__ __forceinline__ bool staging(Stream& Q, Pref& P, uint8_t* sbuf, uint64_t* mbar,
+                                        const Args& a, const Ctx& X) {
+  const int tau = Q.tau, t = Q.u0 - 3 + tau;
+  const int k = X.m - 32, n = W - 32;
+  const float* qb = a.qin + (long long)Q.b * a.member;
+  const bool l1 = tau + 1 < Q.ntau;
+  float q[2][9];
+  if (l1) load_l1_row(q, a, qb, t + 1, X.X0, k, n);      // in flight during the update
+  update_row<STAGE>(Q, P, sbuf, a, X, k);
+  load_q_row(reinterpret_cast<float*>(sbuf + OFF_Q) + (tau % 5) * (3 * QF), a, qb, t - 4, X.X0, k, n);
+  if (!tc::mbar_wait_bounded(mbar, Q.parity, WAIT_ITERS)) return false;
+  if (l1) store_l1_row(sbuf + OFF_L1 + (tau % 3) * L1_SLOT, a, q, k, n);
+  tc::fence_proxy_async_smem();
+  if (tau + 2 < Q.ntau) prefetch_row(a, qb, t + 2, X.X0, k);
+  return true;
+}
+
+// One phase: the tick of stream M on the tensor core, the epilogue of stream
+// E (whose MMAs were issued in the previous phase) on the CUDA cores.
+template <int STAGE, int ms>
+__device__ __forceinline__ void phase(Stream& M, Stream& E, Pref& PE, const Args& a, Ctx& X) {
+  constexpr int es = ms ^ 1;
+  if (M.active) {
+    if (X.issuer && !X.failed) {
+      tc::fence_after_sync();
+      tc::fence_proxy_async_smem();
+      issue_tick(X.D[ms], X.tmem + 256u * ms, M.tau, &X.mbar[ms], X.commit_mask);
+    }
+    M.pending = true;
+  }
+  if (E.pending) {
+    uint8_t* sbuf = X.smem + OFF_STREAMS + es * STREAM_BYTES;
+    bool ok = !X.failed;
+    if (X.wg < 2) {
+      const uint32_t tm = X.tmem + 256u * es + X.lane_off;
+      if (ok) ok = tc::mbar_wait_bounded(&X.mbar[es], E.parity, WAIT_ITERS);
+      tc::fence_after_sync();
+      if (ok) epilogue(E, sbuf, tm, a, X);
+      asm volatile("bar.sync 1, %0;" ::"n"(EPI_THREADS) : "memory");   // slot-0 reads done
+      if (ok) move_slots(tm, X.wg);
+    } else if (X.m >= 32) {
+      if (ok) ok = staging<STAGE>(E, PE, sbuf, &X.mbar[es], a, X);
+    }
+    if (!ok && !X.failed) {
+      X.failed = true;
+      atomicOr(a.err, 1u);
+    }
+    E.parity ^= 1u;
+    E.pending = false;
+    if (++E.tau == E.ntau) {
+      // segment done: close the member's stage-2 reduction, start the next segment
+      if (STAGE == 2) {
+        float mx = E.amax;
+        unsigned bd = E.bad;
+        block_reduce_max_or(mx, bd, X.red);
+        if (X.tid == 0) {
+          const long long R = a.rows, Sn = a.nstreams;
+          const long long first = stream_of_row((long long)E.b * a.ny, R, Sn);
+          const long long last = stream_of_row((long long)(E.b + 1) * a.ny - 1, R, Sn);
+          publish_and_close(a.ctrl + E.b, a.dp, mx, bd, (unsigned)(a.cs * (last - first + 1)), true);
+        }
+      }
+      E.active = next_segment(E, a, X.crank);
+      if (E.active && !X.failed) {
+        segment_prologue(E, sbuf, a, X.X0, X.m, X.wg);
+        tc::fence_proxy_async_smem();
+      }
+    }
+  }
+  if (X.wg < 2) tc::fence_before_sync();
+  // The phase's cluster barrier.  The issuing warp waits for it at once: the
+  // next phase's MMAs read what every warp of every CTA wrote in this one.
+  // The other warps arrive and go on: the next phase's epilogue needs only
+  // its own stream's MMAs (an mbarrier) and data written two phases back, so
+  // they wait for this barrier after that epilogue, before arriving at the
+  // next one.  (The issuing warp writes nothing that others read: it
+  // arrives without a release, which would wait for its MMAs.)
+  if ((X.tid >> 5) == ISSUE_WARP) {
+    cluster_arrive_relaxed();
+    cluster_wait();
+  } else {
+    if (X.arrived) cluster_wait();
+    cluster_arrive();
+    X.arrived = true;
+  }
+}
+
+template <int STAGE>
+__global__ void __launch_bounds__(NT, 1) learned_fused_kernel(Args a) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  float* bias = reinterpret_cast<float*>(smem + OFF_BIAS);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + OFF_TSLOT);
+
+  Ctx X;
+  X.smem = smem;
+  X.bias = bias;
+  X.mbar = reinterpret_cast<uint64_t*>(smem + OFF_MBAR);
+  X.red = reinterpret_cast<unsigned*>(smem + OFF_RED);
+  X.tid = threadIdx.x;
+  X.m = X.tid & (W - 1);                  // TMEM lane = column within the CTA
+  X.wg = X.tid >> 7;                      // 0, 1: drain TMEM; 2: update and stage
+  X.issuer = X.tid == EPI_THREADS;        // first lane of warpgroup 2
+  X.failed = false;
+  X.arrived = false;
+  X.lane_off = (uint32_t)(32 * ((X.tid >> 5) & 3)) << 16;
+  X.crank = cluster_rank();
+  X.X0 = (int)X.crank * W;
+  X.west = (X.crank + a.cs - 1) % a.cs;
+  X.east = (X.crank + 1) % a.cs;
+  X.commit_mask = (uint16_t)((1u << X.crank) | (1u << X.west) | (1u << X.east));
+  const long long cluster = blockIdx.x / a.cs;
+
+  if ((X.tid >> 5) == ISSUE_WARP) {
+    tc::tmem_alloc(tslot, TCOLS);         // the issuing warp owns the TMEM allocation
+    if (X.issuer) {
+      // one arrival per tick from this CTA and from each distinct neighbour
+      const uint32_t arrivals = (uint32_t)__popc((unsigned)X.commit_mask);
+      tc::mbar_init(&X.mbar[0], arrivals);
+      tc::mbar_init(&X.mbar[1], arrivals);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+  }
+  // weights and biases
+  for (int i = X.tid; i < W1_BYTES / 16; i += NT) cp_async16(smem + OFF_W1 + i * 16, a.w1g + i * 8);
+  for (int i = X.tid; i < WH_BYTES / 16; i += NT) {
+    cp_async16(smem + OFF_W2 + i * 16, a.w2 + i * 8);
+    cp_async16(smem + OFF_W3 + i * 16, a.w3 + i * 8);
+  }
+  for (int i = X.tid; i < W4_BYTES / 16; i += NT) cp_async16(smem + OFF_W4 + i * 16, a.w4 + i * 8);
+  for (int i = X.tid; i < N_BIAS; i += NT) {
+    const int l = i / snk::HID < 3 ? i / snk::HID : 3;
+    bias[i] = a.params[a.bias_off[l] + (i - l * snk::HID)];
+  }
+
+  // the two streams of this cluster and their first segments
+  Stream S0, S1;
+  Pref P0 = {}, P1 = {};
+  S0.g = (2 * cluster) * a.rows / a.nstreams;
+  S0.g_end = (2 * cluster + 1) * a.rows / a.nstreams;
+  S1.g = S0.g_end;
+  S1.g_end = (2 * cluster + 2) * a.rows / a.nstreams;
+  S0.parity = S1.parity = 0u;
+  S0.pending = S1.pending = false;
+  S0.active = next_segment(S0, a, X.crank);
+  S1.active = next_segment(S1, a, X.crank);
+  if (S0.active) segment_prologue(S0, smem + OFF_STREAMS, a, X.X0, X.m, X.wg);
+  if (S1.active) segment_prologue(S1, smem + OFF_STREAMS + STREAM_BYTES, a, X.X0, X.m, X.wg);
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+  tc::fence_proxy_async_smem();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  X.tmem = *tslot;
+  const uint32_t sb = tc::smem_u32(smem);
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    const uint32_t base = sb + OFF_STREAMS + s * STREAM_BYTES;
+    X.D[s].a_l1 = tc::sdesc(base + OFF_L1, W * 16, 128);
+    X.D[s].a_in = tc::sdesc(base + OFF_IN, FP * 16, 128);
+    X.D[s].b_w1 = tc::sdesc(sb + OFF_W1, snk::HID * 16, 128);
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+      const uint32_t N = l == 2 ? snk::N_OUT_PAD : snk::HID;
+      const uint32_t wl = sb + (l == 0 ? OFF_W2 : l == 1 ? OFF_W3 : OFF_W4);
+      X.D[s].b_ky0[l] = tc::sdesc(wl, N * 16, 128);
+      X.D[s].b_pair[l] = tc::sdesc(wl + 3 * snk::CG_HID * N * 16, 2 * N * 16, 128);
+    }
+  }
+  // every CTA of the cluster is running (and its mbarriers initialised)
+  // before any remote store or multicast arrival
+  cluster_arrive();
+  cluster_wait();
+
+  for (;;) {
+    if (!(S0.active || S1.active || S0.pending || S1.pending)) break;
+    phase<STAGE, 0>(S0, S1, P1, a, X);
+    if (!(S0.active || S1.active || S0.pending || S1.pending)) break;
+    phase<STAGE, 1>(S1, S0, P0, a, X);
+  }
+
+  if (X.arrived) cluster_wait();   // the last phase's barrier (no remote store after it)
+  // no MMA is in flight unless a wait gave up; give those a bounded wait too
+  if (X.failed) {
+    tc::mbar_wait_bounded(&X.mbar[0], S0.parity, WAIT_ITERS);
+    tc::mbar_wait_bounded(&X.mbar[1], S1.parity, WAIT_ITERS);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if ((X.tid >> 5) == ISSUE_WARP) tc::tmem_dealloc(X.tmem, TCOLS);
+}
+
+}  // namespace fused
+
+bool learned_fused_supported(int nx, int ny) {
+  return nx % fused::W == 0 && nx / fused::W <= fused::MAX_CS && ny >= 1;
+}
+
+namespace {
+
+template <int STAGE>
+cudaError_t launch_fused_stage(const fused::Args& a, cudaStream_t s) {
+  using namespace fused;
+  auto kern = learned_fused_kernel<STAGE>;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  // clusters that fit on the device at once (one CTA per SM), cached per size
+  static int max_clusters[MAX_CS + 1] = {};
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)a.cs;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = SMEM_BYTES;
+  cfg.stream = s;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  if (!max_clusters[a.cs]) {
+    int n = 0;
+    cfg.gridDim = dim3((unsigned)a.cs);
+    cudaError_t e = cudaOccupancyMaxActiveClusters(&n, kern, &cfg);
+    if (e != cudaSuccess) return e;
+    if (n < 1) return cudaErrorInvalidConfiguration;
+    max_clusters[a.cs] = n;
+  }
+  // every stream gets at least one row (with a single row in total, the
+  // first stream of the only cluster stays empty)
+  long long clusters = max_clusters[a.cs];
+  if (clusters > a.rows / 2) clusters = a.rows / 2 > 0 ? a.rows / 2 : 1;
+  fused::Args args = a;
+  args.nstreams = 2 * clusters;
+  cfg.gridDim = dim3((unsigned)(clusters * a.cs));
+  return cudaLaunchKernelEx(&cfg, kern, args);
+}
+
+}  // namespace
+
+cudaError_t launch_learned_fused(const Geom& g, int stage, const float* qin, const float* qn,
+                                 float* qout, const snk::Net& net, const float* hmin, Ctrl* ctrl,
+                                 const DtParams* dp, cudaStream_t s) {
+  if (!learned_fused_supported(g.nx, g.ny)) return cudaErrorInvalidValue;
+  const snk::ParamLayout L = snk::param_layout();
+  fused::Args a{};
+  a.qin = qin;
+  a.qn = qn;
+  a.qout = qout;
+  a.w1g = net.w1g;
+  a.w2 = net.wpair[1];
+  a.w3 = net.wpair[2];
+  a.w4 = net.wpair[3];
+  a.params = net.params;
+  for (int l = 0; l < 4; ++l) a.bias_off[l] = L.b[l];
+  for (int c = 0; c < 3; ++c) {
+    a.mean[c] = net.mean[c];
+    a.rstd[c] = 1.f / net.std_[c];
+  }
+  a.hmin = hmin;
+  a.ctrl = ctrl;
+  a.dp = dp;
+  a.nx = g.nx;
+  a.ny = g.ny;
+  a.cs = g.nx / fused::W;
+  a.plane = g.plane();
+  a.member = g.member();
+  a.rows = (long long)g.B * g.ny;
+  a.rdx = (float)(1.0 / g.dx);
+  a.rdy = (float)(1.0 / g.dy);
+  a.g = g.phys;
+  a.err = net.err;
+  return stage == 1 ? launch_fused_stage<1>(a, s) : launch_fused_stage<2>(a, s);
+}
+
+}  // namespace fvk

@@ -7,7 +7,17 @@
 #include "fv_common.cuh"
 #include "fv_kernels.h"
 
+namespace snk {
+struct Net;
+}
+
 namespace fvk {
+// Learned stage as one persistent kernel (CNN + learned faces + HLL + RK),
+// for nx a multiple of 128 up to 1024.
+bool learned_fused_supported(int nx, int ny);
+cudaError_t launch_learned_fused(const Geom& g, int stage, const float* qin, const float* qn,
+                                 float* qout, const snk::Net& net, const float* hmin, Ctrl* ctrl,
+                                 const DtParams* dp, cudaStream_t s);
 cudaError_t launch_stage_learned(const Geom& g, int stage, const float* qin, const float* qn,
                                  float* qout, const float* w, const float* hmin, Ctrl* ctrl,
                                  const DtParams* dp, cudaStream_t s);
@@ -37,6 +47,7 @@ struct fv_state {
   fv_learned_ws* lws = nullptr;        // learned-step workspace (lazily created)
   float hmin_frac = 1e-3f;             // learned faces: h_min = hmin_frac * mean depth
   int variant = 0;                     // stage kernel choice (fvk::STAGE_*)
+  int learned_variant = 0;             // FV_LEARNED_AUTO / _FUSED / _TWO_PASS
 };
 
 namespace fvs {

@@ -14,6 +14,7 @@
 
 #include "fv_common.cuh"
 #include "fv_internal.h"
+#include "fv_learned.cuh"
 #include "stencil_net.cuh"
 
 struct fv_learned_ws {
@@ -44,29 +45,6 @@ struct LArgs {
   long long plane, member;
   float rdx, rdy, g;
 };
-
-// Learned (or, below h_min, minmod) face states of one face from its 4-cell
-// stencil m = Q_{i-1}, a = Q_i, b = Q_{i+1}, p = Q_{i+2} and the owner's 18
-// coefficients of this direction, wd[(var * 2 + side) * 3 + tap].
-__device__ __forceinline__ void learned_face(const float (&m)[C], const float (&a)[C],
-                                             const float (&b)[C], const float (&p)[C],
-                                             const float (&wd)[18], float hmin, float (&L)[C],
-                                             float (&R)[C]) {
-#pragma unroll
-  for (int c = 0; c < C; ++c) {
-    const float* wl = wd + (c * 2 + 0) * 3;
-    const float* wr = wd + (c * 2 + 1) * 3;
-    L[c] = vfma(wl[2], b[c], vfma(wl[1], a[c], vmul(wl[0], m[c])));
-    R[c] = vfma(wr[2], p[c], vfma(wr[1], b[c], vmul(wr[0], a[c])));
-  }
-  if (!(L[0] >= hmin) || !(R[0] >= hmin)) {
-#pragma unroll
-    for (int c = 0; c < C; ++c) {
-      L[c] = face_left(a[c], minmod(vsub(a[c], m[c]), vsub(b[c], a[c])));
-      R[c] = face_right(b[c], minmod(vsub(b[c], a[c]), vsub(p[c], b[c])));
-    }
-  }
-}
 
 template <int STAGE>
 __global__ void __launch_bounds__(NT) stage_learned_kernel(LArgs a) {
@@ -195,19 +173,31 @@ cudaError_t launch_stage_learned(const Geom& g, int stage, const float* qin, con
 
 namespace fvs {
 
-// Lazily create the learned workspace of a state: coefficient buffer,
-// activations, and h_min = frac * (mean depth of the current state) per member
-// (the mean depth is conserved by the scheme).
+static bool use_fused(const fv_state* s) {
+  return s->learned_variant != FV_LEARNED_TWO_PASS && fvk::learned_fused_supported(s->g.nx, s->g.ny);
+}
+
+// Lazily create the learned workspace of a state: h_min = frac * (mean depth
+// of the current state) per member (the mean depth is conserved by the
+// scheme), and, for the two-pass path only, the coefficient buffer and the
+// CNN activations.
 static int learned_ws_ready(fv_state* s, float hmin_frac) {
-  if (s->lws) return FV_OK;
-  if (!snk::grid_supported(s->g.nx) || s->g.plane() % snk::TILE != 0)
+  const bool fused = use_fused(s);
+  if (!fused && (!snk::grid_supported(s->g.nx) || s->g.plane() % snk::TILE != 0))
     return fvh::fail(FV_EINVAL, "learned step: nx must be 8, 16, 32, 64 or a multiple of 128, "
                                 "and nx*ny a multiple of 128");
-  fv_learned_ws* w = new fv_learned_ws();
   const long long cells = (long long)s->g.B * s->g.plane();
-  cudaError_t e = cudaMalloc(&w->w, sizeof(float) * 36 * cells);
-  if (e == cudaSuccess) e = cudaMalloc(&w->hmin, sizeof(float) * s->g.B);
-  if (e == cudaSuccess) e = snk::acts_reserve(w->acts, cells);
+  if (s->lws) {
+    if (fused || s->lws->w) return FV_OK;
+    // switched to the two-pass path after fused steps: add its buffers
+    cudaError_t e = cudaMalloc(&s->lws->w, sizeof(float) * 36 * cells);
+    if (e == cudaSuccess) e = snk::acts_reserve(s->lws->acts, cells);
+    return e == cudaSuccess ? FV_OK : fvh::cuda_fail(e, "learned workspace");
+  }
+  fv_learned_ws* w = new fv_learned_ws();
+  cudaError_t e = cudaMalloc(&w->hmin, sizeof(float) * s->g.B);
+  if (e == cudaSuccess && !fused) e = cudaMalloc(&w->w, sizeof(float) * 36 * cells);
+  if (e == cudaSuccess && !fused) e = snk::acts_reserve(w->acts, cells);
   if (e == cudaSuccess) e = fvk::launch_diagnostics(s->g, s->qA, s->diag_partials, s->diag_out, s->stream);
   std::vector<double> sums((size_t)s->g.B * (s->g.C + 1));
   if (e == cudaSuccess)
@@ -235,6 +225,14 @@ int learned_prepare(fv_state* s) { return learned_ws_ready(s, s->hmin_frac); }
 cudaError_t enqueue_learned_step(fv_state* s, const fv_net* net) {
   if (!s->lws) return cudaErrorNotReady;   // learned_prepare() must run first (host side)
   fv_learned_ws* w = s->lws;
+  if (use_fused(s)) {
+    cudaError_t e = fvk::launch_learned_fused(s->g, 1, s->qA, nullptr, s->qB, net->n, w->hmin, s->ctrl,
+                                              s->dp, s->stream);
+    if (e != cudaSuccess) return e;
+    return fvk::launch_learned_fused(s->g, 2, s->qB, s->qA, s->qA, net->n, w->hmin, s->ctrl, s->dp,
+                                     s->stream);
+  }
+  if (!w->w) return cudaErrorNotReady;
   const int B = s->g.B, ny = s->g.ny, nx = s->g.nx;
   cudaError_t e = snk::forward(net->n, s->qA, B, ny, nx, w->acts, w->w, nullptr, s->stream);
   if (e != cudaSuccess) return e;

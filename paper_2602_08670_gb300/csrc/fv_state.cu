@@ -431,6 +431,19 @@ extern "C" int fv_set_stage_variant(fv_state* s, int variant) {
   return FV_OK;
 }
 
+extern "C" int fv_set_learned_variant(fv_state* s, int variant) {
+  if (!s) return fvh::fail(FV_EINVAL, "null state");
+  if (variant < FV_LEARNED_AUTO || variant > FV_LEARNED_TWO_PASS)
+    return fvh::fail(FV_EINVAL, "unknown learned variant");
+  if (variant == FV_LEARNED_FUSED && !fvk::learned_fused_supported(s->g.nx, s->g.ny))
+    return fvh::fail(FV_EINVAL, "the fused learned kernel needs nx a multiple of 128, at most 1024");
+  FV_CUDA_TRY(cudaStreamSynchronize(s->stream));
+  s->learned_variant = variant;
+  if (s->graph) cudaGraphExecDestroy(s->graph);
+  s->graph = nullptr;
+  return FV_OK;
+}
+
 extern "C" int fv_set_learned_hmin(fv_state* s, double hmin_frac) {
   if (!s) return fvh::fail(FV_EINVAL, "null state");
   if (!(hmin_frac >= 0.0) || hmin_frac >= 1.0) return fvh::fail(FV_EINVAL, "hmin_frac must be in [0, 1)");

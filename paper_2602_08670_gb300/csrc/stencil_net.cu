@@ -248,12 +248,51 @@ __global__ void __launch_bounds__(NT) conv_kernel(ConvArgs a) {
 //   backward wb[l][tap][g][n][k8] = W_l[8g + k8][n][2 - ky][2 - kx]   (l >= 1)
 __global__ void repack_kernel(const float* params, ParamLayout L, uint16_t* wf0, uint16_t* wf1,
                               uint16_t* wf2, uint16_t* wf3, uint16_t* wb1, uint16_t* wb2,
-                              uint16_t* wb3) {
+                              uint16_t* wb3, uint16_t* w1g, uint16_t* wp1, uint16_t* wp2,
+                              uint16_t* wp3) {
   uint16_t* wf[4] = {wf0, wf1, wf2, wf3};
   uint16_t* wb[4] = {nullptr, wb1, wb2, wb3};
   const int cgs[4] = {CG_IN0, CG_HID, CG_HID, CG_HID};
   const int ns[4] = {HID, HID, HID, N_OUT_PAD};
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < W1G_ELEMS) {
+    // w1g[ky][g][n][k8] = W_1[n][var][ky][kx] with 8 g + k8 = 3 kx + var
+    const int k8 = i % 8, n = (i / 8) % HID, g = (i / (8 * HID)) % 2, ky = i / (16 * HID);
+    const int c = 8 * g + k8;
+    float v = 0.f;
+    if (c < 3 * C_IN) v = params[L.w[0] + ((n * C_IN + c % 3) * 3 + ky) * 3 + c / 3];
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    w1g[i] = *reinterpret_cast<const uint16_t*>(&h);
+  }
+  uint16_t* wp[4] = {nullptr, wp1, wp2, wp3};
+  for (int l = 1; l < 4; ++l) {
+    // [ky = 0: kx][g][n][k8], then [kx][g][ky = 2 | ky = 1][k8]
+    const int N = l == 3 ? N_OUT_PAD : HID;
+    const int part0 = 3 * CG_HID * N * 8;
+    if (i < 9 * CG_HID * N * 8) {
+      int kx, g, n, k8, ky;
+      if (i < part0) {
+        k8 = i % 8;
+        n = (i / 8) % N;
+        g = (i / (8 * N)) % CG_HID;
+        kx = i / (8 * N * CG_HID);
+        ky = 0;
+      } else {
+        const int j = i - part0;
+        k8 = j % 8;
+        const int n2 = (j / 8) % (2 * N);
+        g = (j / (16 * N)) % CG_HID;
+        kx = j / (16 * N * CG_HID);
+        ky = n2 < N ? 2 : 1;
+        n = n2 % N;
+      }
+      const int ci = 8 * g + k8, co = n;
+      float v = 0.f;
+      if (ci < L.cin[l] && co < L.cout[l]) v = params[L.w[l] + ((co * L.cin[l] + ci) * 3 + ky) * 3 + kx];
+      const __nv_bfloat16 h = __float2bfloat16_rn(v);
+      wp[l][i] = *reinterpret_cast<const uint16_t*>(&h);
+    }
+  }
   for (int l = 0; l < 4; ++l) {
     const int CG = cgs[l], N = ns[l];
     const int total = 9 * CG * N * 8;
@@ -309,7 +348,8 @@ cudaError_t repack(Net& net, cudaStream_t s) {
   const ParamLayout L = param_layout();
   const int maxn = 9 * CG_HID * N_OUT_PAD * 8 > 9 * 6 * HID * 8 ? 9 * CG_HID * N_OUT_PAD * 8 : 9 * 6 * HID * 8;
   repack_kernel<<<(maxn + 255) / 256, 256, 0, s>>>(net.params, L, net.wf[0], net.wf[1], net.wf[2],
-                                                   net.wf[3], net.wb[1], net.wb[2], net.wb[3]);
+                                                   net.wf[3], net.wb[1], net.wb[2], net.wb[3],
+                                                   net.w1g, net.wpair[1], net.wpair[2], net.wpair[3]);
   return cudaGetLastError();
 }
 
@@ -708,6 +748,9 @@ int net_alloc(fv_net* n) {
     if ((e = cudaMalloc(&N.wb[l], 2 * 9 * cg * snk::HID * 8)) != cudaSuccess)
       return fvh::cuda_fail(e, "cudaMalloc(wb)");
   }
+  if ((e = cudaMalloc(&N.w1g, 2 * snk::W1G_ELEMS)) != cudaSuccess) return fvh::cuda_fail(e, "cudaMalloc(w1g)");
+  for (int l = 1; l < 4; ++l)
+    if ((e = cudaMalloc(&N.wpair[l], 2 * fsz[l])) != cudaSuccess) return fvh::cuda_fail(e, "cudaMalloc(wpair)");
   if ((e = cudaMalloc(&N.err, sizeof(unsigned))) != cudaSuccess) return fvh::cuda_fail(e, "cudaMalloc(err)");
   if ((e = cudaMemset(N.err, 0, sizeof(unsigned))) != cudaSuccess) return fvh::cuda_fail(e, "cudaMemset");
   if ((e = cudaStreamCreateWithFlags(&n->stream, cudaStreamNonBlocking)) != cudaSuccess)
@@ -723,6 +766,8 @@ void net_free(fv_net* n) {
     cudaFree(n->n.wf[l]);
     cudaFree(n->n.wb[l]);
   }
+  cudaFree(n->n.w1g);
+  for (int l = 1; l < 4; ++l) cudaFree(n->n.wpair[l]);
   cudaFree(n->n.err);
   cudaFree(n->adam_m);
   cudaFree(n->adam_v);

@@ -36,6 +36,11 @@ struct Net {
   float* params = nullptr;     // FP32 master parameters [N_PARAMS]
   uint16_t* wf[4] = {};        // forward B operands, BF16 [9][CG_in][N][8]
   uint16_t* wb[4] = {};        // backward (dX) B operands, BF16 [9][CG_out][N_in][8], layers 1..3
+  uint16_t* w1g = nullptr;     // layer 1 with the three x taps gathered into K, BF16
+                               // [ky][2][HID][8]: channel c = 3 kx + var (c < 9, rest 0)
+  uint16_t* wpair[4] = {};     // layers 2..4 for the row-pipelined kernel, BF16: the taps
+                               // ky = 0 as [kx][4][N][8], then ky = 2 and ky = 1 stacked
+                               // along N as [kx][4][2N][8] (rows n < N: ky = 2)
   float mean[3] = {0, 0, 0};
   float std_[3] = {1, 1, 1};
   unsigned* err = nullptr;     // device error word (bounded waits that gave up)
@@ -48,6 +53,7 @@ struct Acts {
 };
 
 bool grid_supported(int nx);   // nx % 128 == 0, or nx in {8, 16, 32, 64}
+constexpr int W1G_ELEMS = 3 * 2 * HID * 8;
 
 // Pack the FP32 master parameters into the BF16 MMA operand layouts.
 cudaError_t repack(Net& net, cudaStream_t s);

@@ -64,6 +64,7 @@ _SIGS = {
     "fv_state_device_ptr": [c_void_p, ctypes.POINTER(c_void_p)],
     "fv_state_stream": [c_void_p, ctypes.POINTER(c_void_p)],
     "fv_set_stage_variant": [c_void_p, c_int],
+    "fv_set_learned_variant": [c_void_p, c_int],
     "fv_set_learned_hmin": [c_void_p, c_double],
     "stencil_net_create": [c_void_p, c_void_p, ctypes.POINTER(c_void_p)],
     "stencil_net_destroy": [c_void_p],
@@ -341,6 +342,16 @@ def stencil_net_forward(net: Net, q: torch.Tensor, raw: bool = False) -> torch.T
                                      c_void_p(out.data_ptr()), int(raw),
                                      c_void_p(_torch_stream())))
     return out
+
+
+LEARNED_VARIANTS = {"auto": 0, "fused": 1, "two_pass": 2}
+
+
+def fv_set_learned_variant(s: State, variant: str) -> None:
+    """Learned step implementation: "auto", "fused" (one persistent kernel
+    per stage, nx a multiple of 128 up to 1024) or "two_pass" (CNN to device
+    memory, then the stage kernel)."""
+    _check(lib().fv_set_learned_variant(s.handle, LEARNED_VARIANTS[variant]))
 
 
 def fv_set_learned_hmin(s: State, hmin_frac: float) -> None:
