@@ -1,0 +1,50 @@
+"""Time a batched rollout of the learned (or plain) shallow-water step.
+
+    python -m paper_2602_08670_gb300.rollout --members 64 --n 256 --steps 3 --variant fused
+
+Members are the random-bump initial states of `workloads.swe_random_bumps`
+(seed 3), the network the committed trained weights, dt the fine time step
+they were trained with.  Prints the wall-clock time per step and the rate in
+cell-updates per second.
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import time
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--members", type=int, default=64)
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--variant", choices=["auto", "fused", "two_pass", "plain"], default="fused")
+    args = ap.parse_args(argv)
+
+    import torch
+
+    from . import build, fv, train, workloads
+
+    build.build()
+    weights = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights", "swe64_from256.npz")
+    net, meta = train.load_weights(weights)
+    q0 = torch.tensor(workloads.swe_random_bumps(args.n, 3, args.members), dtype=torch.float32).cuda()
+    st = fv.swe_init(q0, dt_mode="fixed", dt_fixed=meta["dt_fine"])
+    use = None if args.variant == "plain" else net
+    if use is not None:
+        fv.fv_set_learned_variant(st, args.variant)
+    fv.fv_enqueue_steps(st, 2, net=use)
+    fv.fv_sync(st)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    fv.fv_enqueue_steps(st, args.steps, net=use)
+    fv.fv_sync(st)
+    dt = time.perf_counter() - t0
+    cells = args.members * args.n * args.n * args.steps
+    print(f"{args.variant} {args.members} x {args.n}^2, {args.steps} steps: {1e3 * dt / args.steps:.3f} ms/step, "
+          f"{cells / dt:.4g} cell-updates/s")
+
+
+if __name__ == "__main__":
+    main()
