@@ -153,6 +153,26 @@ int fv_state_device_ptr(const fv_state* s, float** dptr);
  * results agree to a few ulps, not bitwise.  The choice only changes speed. */
 int fv_set_stage_variant(fv_state* s, int variant);
 
+/* Numerical flux and time integrator of the plain step (Section 2.3.3):
+ *  flux: FV_FLUX_HLL (Eq. 2.15, default), FV_FLUX_RUSANOV (Eq. 2.12),
+ *        FV_FLUX_LF (Lax-Friedrichs, Eq. 2.11, with viscosity dx/(4 dt) on x
+ *        faces and dy/(4 dt) on y faces: the paper's one-dimensional dx/(2 dt)
+ *        in both directions of the unsplit update amplifies the grid-scale
+ *        checkerboard by -3 for every dt), FV_FLUX_ROE (Eqs. 2.13-2.14, Roe
+ *        averages, no entropy fix), FV_FLUX_HLLE (Eq. 2.16, speeds clamped by
+ *        the Roe state's and by 0), FV_FLUX_HLLC (Eq. 2.17, HLL outer speeds,
+ *        middle speed from the jump conditions);
+ *  rk:   2 = Heun / SSP-RK2 (Eq. 2.19, default), 3 = SSP-RK3 (Eq. 2.20,
+ *        printed as fourth order; it is the three-stage third-order scheme).
+ * Reconstruction (MUSCL-minmod), rotation, divergence and the CFL rule are
+ * unchanged.  The HLL / SSP-RK2 pair runs the row-march kernels; the others
+ * a shared-memory tile kernel with the flux chosen per launch.  rk = 3
+ * allocates one more state buffer on first use.  The learned step requires
+ * HLL and SSP-RK2 (FV_EINVAL otherwise).  Synchronises the state's stream. */
+enum { FV_FLUX_HLL = 0, FV_FLUX_RUSANOV = 1, FV_FLUX_LF = 2, FV_FLUX_ROE = 3, FV_FLUX_HLLE = 4,
+       FV_FLUX_HLLC = 5 };
+int fv_set_scheme(fv_state* s, int flux, int rk);
+
 /* Implementation of the learned step (Section 2.5.3, fourth approach):
  *  FV_LEARNED_AUTO (0): the fused kernel where the grid allows it, else the
  *    two-pass path;

@@ -18,6 +18,10 @@ bool learned_fused_supported(int nx, int ny);
 cudaError_t launch_learned_fused(const Geom& g, int stage, const float* qin, const float* qn,
                                  float* qout, const snk::Net& net, const float* hmin, Ctrl* ctrl,
                                  const DtParams* dp, cudaStream_t s);
+// One plain step with flux `flux` (fvk::Flux) and integrator `rk` (2: SSP-RK2,
+// 3: SSP-RK3); q^n in qa (updated in place), stages in qb and qc.
+cudaError_t enqueue_scheme_step(const Geom& g, int flux, int rk, float* qa, float* qb, float* qc,
+                                Ctrl* ctrl, const DtParams* dp, cudaStream_t s);
 cudaError_t launch_stage_learned(const Geom& g, int stage, const float* qin, const float* qn,
                                  float* qout, const float* w, const float* hmin, Ctrl* ctrl,
                                  const DtParams* dp, cudaStream_t s);
@@ -48,6 +52,9 @@ struct fv_state {
   float hmin_frac = 1e-3f;             // learned faces: h_min = hmin_frac * mean depth
   int variant = 0;                     // stage kernel choice (fvk::STAGE_*)
   int learned_variant = 0;             // FV_LEARNED_AUTO / _FUSED / _TWO_PASS
+  int flux = 0;                        // FV_FLUX_* of the plain step
+  int rk = 2;                          // 2: SSP-RK2, 3: SSP-RK3
+  float* qC = nullptr;                 // q^(2) of SSP-RK3 (allocated on first use)
 };
 
 namespace fvs {

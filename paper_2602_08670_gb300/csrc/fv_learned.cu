@@ -220,7 +220,11 @@ static int learned_ws_ready(fv_state* s, float hmin_frac) {
   return FV_OK;
 }
 
-int learned_prepare(fv_state* s) { return learned_ws_ready(s, s->hmin_frac); }
+int learned_prepare(fv_state* s) {
+  if (s->flux != FV_FLUX_HLL || s->rk != 2)
+    return fvh::fail(FV_EINVAL, "the learned step uses the HLL flux and SSP-RK2 (see fv_set_scheme)");
+  return learned_ws_ready(s, s->hmin_frac);
+}
 
 cudaError_t enqueue_learned_step(fv_state* s, const fv_net* net) {
   if (!s->lws) return cudaErrorNotReady;   // learned_prepare() must run first (host side)

@@ -150,6 +150,7 @@ void state_free(fv_state* s) {
   if (s->graph) cudaGraphExecDestroy(s->graph);
   cudaFree(s->qA);
   cudaFree(s->qB);
+  cudaFree(s->qC);
   cudaFree(s->ctrl);
   cudaFree(s->dp);
   cudaFree(s->replay);
@@ -178,6 +179,8 @@ cudaError_t leave(fv_state* s) {
 }
 
 cudaError_t enqueue_plain_step(fv_state* s) {
+  if (s->flux != FV_FLUX_HLL || s->rk != 2)
+    return fvk::enqueue_scheme_step(s->g, s->flux, s->rk, s->qA, s->qB, s->qC, s->ctrl, s->dp, s->stream);
   cudaError_t e = fvk::launch_stage_minmod(s->g, 1, s->qA, nullptr, s->qB, s->ctrl, s->dp,
                                            s->stream, s->variant);
   if (e != cudaSuccess) return e;
@@ -426,6 +429,22 @@ extern "C" int fv_set_stage_variant(fv_state* s, int variant) {
     return fvh::fail(FV_EINVAL, "the row-march kernel needs nx % 4 == 0 and nx >= 8");
   FV_CUDA_TRY(cudaStreamSynchronize(s->stream));
   s->variant = variant;
+  if (s->graph) cudaGraphExecDestroy(s->graph);
+  s->graph = nullptr;
+  return FV_OK;
+}
+
+extern "C" int fv_set_scheme(fv_state* s, int flux, int rk) {
+  if (!s) return fvh::fail(FV_EINVAL, "null state");
+  if (flux < FV_FLUX_HLL || flux > FV_FLUX_HLLC) return fvh::fail(FV_EINVAL, "unknown flux");
+  if (rk != 2 && rk != 3) return fvh::fail(FV_EINVAL, "rk must be 2 or 3");
+  FV_CUDA_TRY(cudaStreamSynchronize(s->stream));
+  if (rk == 3 && !s->qC) {
+    const size_t bytes = sizeof(float) * (size_t)s->g.B * (size_t)s->g.member();
+    FV_CUDA_TRY(cudaMalloc(&s->qC, bytes));
+  }
+  s->flux = flux;
+  s->rk = rk;
   if (s->graph) cudaGraphExecDestroy(s->graph);
   s->graph = nullptr;
   return FV_OK;

@@ -65,6 +65,7 @@ _SIGS = {
     "fv_state_stream": [c_void_p, ctypes.POINTER(c_void_p)],
     "fv_set_stage_variant": [c_void_p, c_int],
     "fv_set_learned_variant": [c_void_p, c_int],
+    "fv_set_scheme": [c_void_p, c_int, c_int],
     "fv_set_learned_hmin": [c_void_p, c_double],
     "stencil_net_create": [c_void_p, c_void_p, ctypes.POINTER(c_void_p)],
     "stencil_net_destroy": [c_void_p],
@@ -342,6 +343,15 @@ def stencil_net_forward(net: Net, q: torch.Tensor, raw: bool = False) -> torch.T
                                      c_void_p(out.data_ptr()), int(raw),
                                      c_void_p(_torch_stream())))
     return out
+
+
+FLUXES = {"hll": 0, "rusanov": 1, "lf": 2, "roe": 3, "hlle": 4, "hllc": 5}
+
+
+def fv_set_scheme(s: State, flux: str = "hll", rk: int = 2) -> None:
+    """Numerical flux ("hll", "rusanov", "lf", "roe", "hlle", "hllc") and
+    integrator (2: SSP-RK2, 3: SSP-RK3) of the plain step."""
+    _check(lib().fv_set_scheme(s.handle, FLUXES[flux], int(rk)))
 
 
 LEARNED_VARIANTS = {"auto": 0, "fused": 1, "two_pass": 2}

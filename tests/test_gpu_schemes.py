@@ -1,0 +1,101 @@
+"""Parity of the plain step with the other numerical fluxes (Lax-Friedrichs,
+Rusanov, Roe, HLLE, HLLC; Eqs. 2.11-2.17) and with SSP-RK3 (Eq. 2.20) against
+the FP64 oracle (``oracle.schemes``), through the C ABI, on both equations.
+Tolerances follow the plain-step parity tests: the oracle's own FP32-vs-FP64
+roundoff on these cases, with margin."""
+import numpy as np
+import pytest
+import torch
+
+from helpers import f32, rel_errors
+from oracle import fv as ofv
+from oracle import schemes as S
+from paper_2602_08670_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL_O1 = (1e-5, 1e-4)          # depth, density, energy, O(1) momenta
+TOL_SMALL = (1e-4, 2e-4)       # small momenta (O(1e-2)) after 100 steps
+STEPS = 100
+
+
+@pytest.fixture(scope="module")
+def fv():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2602_08670_gb300 import fv as binding
+    return binding
+
+
+def case(eq):
+    if eq == ofv.SWE:
+        q = W.swe_gaussian_bump(64, 48)
+        q[:, 1] = 0.05 * np.sin(2 * np.pi * W.cell_centres(64))[None, None, :]
+        q[:, 2] = 0.03 * np.cos(2 * np.pi * W.cell_centres(48))[None, :, None]
+        return W.as_f32_exact(q), [TOL_O1, TOL_SMALL, TOL_SMALL]
+    q = W.euler_kelvin_helmholtz(64, 64, seed=1)
+    return W.as_f32_exact(q), [TOL_O1, TOL_O1, (2e-4, 3e-4), TOL_O1]
+
+
+def gpu_replay(fv, q0, eq, dts, nsteps, flux, rk):
+    q0t = f32(q0).cuda()
+    s = fv.swe_init(q0t, dt_mode="replay") if eq == ofv.SWE else fv.euler_init(q0t, dt_mode="replay")
+    fv.fv_set_scheme(s, flux, rk)
+    fv.fv_set_replay_dt(s, dts)
+    fv.fv_rollout(s, nsteps)
+    return fv.fv_get_state(s).double().cpu(), s
+
+
+def check(err, tols):
+    for c, ((e2, ei), (l2, inf)) in enumerate(zip(err, tols)):
+        assert e2 <= l2 and ei <= inf, (c, e2, ei, err)
+
+
+CASES = [(f, 2) for f in ("rusanov", "lf", "roe", "hlle", "hllc")] + \
+        [(f, 3) for f in ("hll", "roe", "hllc")]
+
+
+@pytest.mark.parametrize("eq", [ofv.SWE, ofv.EULER])
+@pytest.mark.parametrize("flux,rk", CASES)
+def test_scheme_matches_oracle(fv, flux, rk, eq):
+    q0, tols = case(eq)
+    qr, tr, dts = S.run(torch.tensor(q0), eq, STEPS, flux=flux, rk=rk)
+    q, s = gpu_replay(fv, q0, eq, dts[:, 0].numpy(), STEPS, flux, rk)
+    check(rel_errors(q, qr), tols)
+    t, _, steps = fv.fv_get_time(s)
+    assert steps[0] == STEPS and abs(t[0] - float(tr[0])) < 1e-12
+
+
+def test_rk3_adaptive_dt_follows_the_oracle(fv):
+    """Adaptive dt: the CFL reduction runs in the third stage; the GPU's dt
+    sequence follows the oracle's to FP32 rounding of the wave speeds."""
+    q0, tols = case(ofv.SWE)
+    qr, tr, dts = S.run(torch.tensor(q0), ofv.SWE, 30, flux="hllc", rk=3)
+    s = fv.swe_init(f32(q0).cuda())
+    fv.fv_set_scheme(s, "hllc", 3)
+    _, t = fv.fv_rollout(s, 30)
+    assert abs(t[0] - float(tr[0])) <= 1e-5 * float(tr[0])
+    check(rel_errors(fv.fv_get_state(s).double().cpu(), qr), tols)
+
+
+def test_invalid_schemes_rejected(fv):
+    s = fv.swe_init(torch.ones(1, 3, 16, 16, device="cuda"))
+    with pytest.raises(fv.FvError):
+        fv.fv_set_scheme(s, "hll", 4)
+    fv.fv_set_scheme(s, "roe", 2)
+    net = fv.stencil_net_create(None, [1.0, 0.0, 0.0], [1.0, 1.0, 1.0])
+    with pytest.raises(fv.FvError) as ei:
+        fv.fv_step(s, net=net)
+    assert ei.value.code == fv.FV_EINVAL
+
+
+def test_lake_at_rest_every_flux(fv):
+    """A flat lake at rest is a fixed point of every flux and integrator."""
+    q0 = torch.zeros(1, 3, 24, 40)
+    q0[:, 0] = 1.25
+    for flux in ("rusanov", "lf", "roe", "hlle", "hllc"):
+        for rk in (2, 3):
+            s = fv.swe_init(q0.cuda(), dt_mode="fixed", dt_fixed=1e-3)
+            fv.fv_set_scheme(s, flux, rk)
+            fv.fv_rollout(s, 20)
+            assert torch.equal(fv.fv_get_state(s).cpu(), q0), (flux, rk)
