@@ -149,9 +149,10 @@ __global__ void __launch_bounds__(NT) stage_scheme_kernel(SchemeArgs a) {
       } else if (K == K_HEUN) {
         out[c] = rk_stage2<float>(qn[c * a.plane + off], q, 0.5f * dt, L);
       } else {
-        // w q^n + (1 - w) (q + dt L)
-        const float w = K == K_RK3_2 ? 0.75f : 1.f / 3.f;
-        out[c] = vfma(w, qn[c * a.plane + off], vmul(1.f - w, vfma(dt, L, q)));
+        // w q^n + (1 - w) (q + dt L), written as q^n + (1 - w) (q + dt L - q^n)
+        // so that a constant state stays bitwise constant
+        const float qnc = qn[c * a.plane + off];
+        out[c] = vfma(K == K_RK3_2 ? 0.25f : 2.f / 3.f, vsub(vfma(dt, L, q), qnc), qnc);
       }
       qout[c * a.plane + off] = out[c];
     }

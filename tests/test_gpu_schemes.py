@@ -1,8 +1,9 @@
 """Parity of the plain step with the other numerical fluxes (Lax-Friedrichs,
 Rusanov, Roe, HLLE, HLLC; Eqs. 2.11-2.17) and with SSP-RK3 (Eq. 2.20) against
 the FP64 oracle (``oracle.schemes``), through the C ABI, on both equations.
-Tolerances follow the plain-step parity tests: the oracle's own FP32-vs-FP64
-roundoff on these cases, with margin."""
+Tolerances follow the plain-step parity tests: max(fixed floor, 5 x the
+oracle's own FP32-vs-FP64 roundoff on the same case), the latter measured
+in the test."""
 import numpy as np
 import pytest
 import torch
@@ -51,6 +52,19 @@ def check(err, tols):
         assert e2 <= l2 and ei <= inf, (c, e2, ei, err)
 
 
+def fp32_yardstick(q0, eq, dts, flux, rk, qr):
+    """The oracle's own algorithm replayed in float32: its distance from the
+    FP64 result is the roundoff the scheme amplifies on this case (large for
+    Lax-Friedrichs, whose minmod faces and strong viscosity make it sensitive)."""
+    q = torch.tensor(q0, dtype=torch.float32)
+    dx, dy = ofv.grid_spacing(q)
+    step = ofv.ssp_rk2 if rk == 2 else S.ssp_rk3
+    for n in range(dts.shape[0]):
+        dt = torch.tensor([float(dts[n, 0])], dtype=torch.float32)
+        q = step(q, dt.view(1, 1, 1, 1), lambda s, dt=dt: S.rhs(s, eq, dx, dy, flux, dt))
+    return rel_errors(q.double(), qr)
+
+
 CASES = [(f, 2) for f in ("rusanov", "lf", "roe", "hlle", "hllc")] + \
         [(f, 3) for f in ("hll", "roe", "hllc")]
 
@@ -61,7 +75,8 @@ def test_scheme_matches_oracle(fv, flux, rk, eq):
     q0, tols = case(eq)
     qr, tr, dts = S.run(torch.tensor(q0), eq, STEPS, flux=flux, rk=rk)
     q, s = gpu_replay(fv, q0, eq, dts[:, 0].numpy(), STEPS, flux, rk)
-    check(rel_errors(q, qr), tols)
+    yard = fp32_yardstick(q0, eq, dts, flux, rk, qr)
+    check(rel_errors(q, qr), [(max(l2, 5 * y2), max(li, 5 * yi)) for (l2, li), (y2, yi) in zip(tols, yard)])
     t, _, steps = fv.fv_get_time(s)
     assert steps[0] == STEPS and abs(t[0] - float(tr[0])) < 1e-12
 
