@@ -295,6 +295,8 @@ def run_gpu(args):
             line["learned"]["accuracy_matched"]["learned_rate_times_r3"] > plain_swe
     if not args.no_serving:
         line["serving"] = serving_block(args)
+    if not args.no_schemes:
+        line["schemes"] = schemes_block(args)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         rate, secs, threads = oracle_sample(4, 512, 256)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
@@ -407,6 +409,43 @@ def learned_block(args):
     return out
 
 
+def schemes_block(args):
+    """The plain step with the other fluxes (Eqs. 2.11-2.17) and SSP-RK3
+    (Eq. 2.20) on the SWE 4096^2 bump: rate and HBM roofline of the tile
+    stage kernel (algorithmic bytes 60 per cell-update for SSP-RK2, 96 for
+    SSP-RK3: stage 1 reads q^n and writes q1, the others read their input and
+    q^n and write)."""
+    import torch
+
+    from paper_2602_08670_gb300 import fv
+    from paper_2602_08670_gb300 import workloads as W
+
+    peak, _ = measured_peaks()
+    q0 = torch.tensor(W.swe_gaussian_bump(N_SWE, N_SWE), dtype=torch.float32).cuda()
+    bs = torch.cuda.Stream()
+    out = {"workload": f"SWE Gaussian bump {N_SWE}^2, CFL 0.5 adaptive dt, 20 steps per scheme",
+           "kernel": "stage_scheme_kernel (shared-memory tile, flux chosen per launch)"}
+    K = 20
+    for flux, rk in (("rusanov", 2), ("lf", 2), ("roe", 2), ("hlle", 2), ("hllc", 2), ("hll", 3)):
+        with torch.cuda.stream(bs):
+            st = fv.swe_init(q0.clone(), cfl=0.5)
+        fv.fv_set_scheme(st, flux, rk)
+        fv.fv_enqueue_steps(st, 3)
+        fv.fv_sync(st)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(bs)
+        fv.fv_enqueue_steps(st, K)
+        e1.record(bs)
+        fv.fv_sync(st)
+        ms = e0.elapsed_time(e1)
+        rate = N_SWE * N_SWE * K / (ms * 1e-3)
+        gbs = (60 if rk == 2 else 96) * rate / 1e9
+        out[f"{flux}_rk{rk}"] = {"cell_updates_per_s": rate, "ms_per_step": ms / K,
+                                 "hbm_gbs": gbs, "frac_of_measured_hbm": gbs / peak}
+        del st
+    return out
+
+
 def serving_block(args):
     """Continuous-batching server under Poisson load: requests of SWE (50 %
     learned, 25 % plain) and Euler (25 %), grids uniform over {64, 128, 256,
@@ -450,6 +489,8 @@ def main():
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-path measurements")
     ap.add_argument("--learned-steps", type=int, default=20)
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurements")
+    ap.add_argument("--no-schemes", action="store_true",
+                    help="skip the other fluxes / SSP-RK3 measurements")
     ap.add_argument("--serve-requests", type=int, default=48)
     args = ap.parse_args()
     if args.impl == "reference":
