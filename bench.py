@@ -411,10 +411,11 @@ def learned_block(args):
 
 def schemes_block(args):
     """The plain step with the other fluxes (Eqs. 2.11-2.17) and SSP-RK3
-    (Eq. 2.20) on the SWE 4096^2 bump: rate and HBM roofline of the tile
-    stage kernel (algorithmic bytes 60 per cell-update for SSP-RK2, 96 for
-    SSP-RK3: stage 1 reads q^n and writes q1, the others read their input and
-    q^n and write)."""
+    (Eq. 2.20) on the SWE 4096^2 bump: rate and HBM roofline of the row-march
+    stage kernel with the flux chosen per launch, and of the shared-memory
+    tile kernel for one scheme (algorithmic bytes 60 per cell-update for
+    SSP-RK2, 96 for SSP-RK3: stage 1 reads q^n and writes q1, the others read
+    their input and q^n and write)."""
     import torch
 
     from paper_2602_08670_gb300 import fv
@@ -424,12 +425,16 @@ def schemes_block(args):
     q0 = torch.tensor(W.swe_gaussian_bump(N_SWE, N_SWE), dtype=torch.float32).cuda()
     bs = torch.cuda.Stream()
     out = {"workload": f"SWE Gaussian bump {N_SWE}^2, CFL 0.5 adaptive dt, 20 steps per scheme",
-           "kernel": "stage_scheme_kernel (shared-memory tile, flux chosen per launch)"}
+           "kernel": "stage_march_kernel (generic instances, flux chosen per launch); "
+                     "_tile: stage_scheme_kernel (shared-memory tile)"}
     K = 20
-    for flux, rk in (("rusanov", 2), ("lf", 2), ("roe", 2), ("hlle", 2), ("hllc", 2), ("hll", 3)):
+    runs = [(f, r, "march") for f, r in (("rusanov", 2), ("lf", 2), ("roe", 2), ("hlle", 2), ("hllc", 2),
+                                         ("hll", 3), ("hllc", 3))] + [("hllc", 2, "tile")]
+    for flux, rk, variant in runs:
         with torch.cuda.stream(bs):
             st = fv.swe_init(q0.clone(), cfl=0.5)
         fv.fv_set_scheme(st, flux, rk)
+        fv.fv_set_stage_variant(st, variant)
         fv.fv_enqueue_steps(st, 3)
         fv.fv_sync(st)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -440,7 +445,7 @@ def schemes_block(args):
         ms = e0.elapsed_time(e1)
         rate = N_SWE * N_SWE * K / (ms * 1e-3)
         gbs = (60 if rk == 2 else 96) * rate / 1e9
-        out[f"{flux}_rk{rk}"] = {"cell_updates_per_s": rate, "ms_per_step": ms / K,
+        out[f"{flux}_rk{rk}" + ("_tile" if variant == "tile" else "")] = {"cell_updates_per_s": rate, "ms_per_step": ms / K,
                                  "hbm_gbs": gbs, "frac_of_measured_hbm": gbs / peak}
         del st
     return out

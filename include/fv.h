@@ -145,10 +145,10 @@ int fv_set_state(fv_state* s, const float* src, int src_loc);
  * next fv_destroy_state).  For zero-copy binding layers. */
 int fv_state_device_ptr(const fv_state* s, float** dptr);
 
-/* Stage-kernel implementation of the plain step: 0 = automatic (row-march
- * kernel when nx is a multiple of 4 and >= 8, else the shared-memory tile
- * kernel), 1 = tile kernel, 2 = row-march kernel (FV_EINVAL if nx does not
- * allow it).  Both evaluate the same formulas per face and per cell; the
+/* Stage-kernel implementation of the plain step (every flux and integrator
+ * of fv_set_scheme): 0 = automatic (row-march kernel when nx is a multiple of
+ * 4 and >= 8, else the shared-memory tile kernel), 1 = tile kernel, 2 =
+ * row-march kernel (FV_EINVAL if nx does not allow it).  Both evaluate the same formulas per face and per cell; the
  * approximate reciprocal and square root may be scheduled differently, so
  * results agree to a few ulps, not bitwise.  The choice only changes speed. */
 int fv_set_stage_variant(fv_state* s, int variant);

@@ -19,9 +19,10 @@ cudaError_t launch_learned_fused(const Geom& g, int stage, const float* qin, con
                                  float* qout, const snk::Net& net, const float* hmin, Ctrl* ctrl,
                                  const DtParams* dp, cudaStream_t s);
 // One plain step with flux `flux` (fvk::Flux) and integrator `rk` (2: SSP-RK2,
-// 3: SSP-RK3); q^n in qa (updated in place), stages in qb and qc.
+// 3: SSP-RK3); q^n in qa (updated in place), stages in qb and qc.  `variant`
+// as for the HLL stages (STAGE_TILE forces the tile kernel).
 cudaError_t enqueue_scheme_step(const Geom& g, int flux, int rk, float* qa, float* qb, float* qc,
-                                Ctrl* ctrl, const DtParams* dp, cudaStream_t s);
+                                Ctrl* ctrl, const DtParams* dp, cudaStream_t s, int variant);
 cudaError_t launch_stage_learned(const Geom& g, int stage, const float* qin, const float* qn,
                                  float* qout, const float* w, const float* hmin, Ctrl* ctrl,
                                  const DtParams* dp, cudaStream_t s);

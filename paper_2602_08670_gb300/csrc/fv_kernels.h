@@ -31,6 +31,13 @@ cudaError_t launch_stage_minmod(const Geom& g, int stage, const float* qin, cons
                                 float* qout, Ctrl* ctrl, const DtParams* dp, cudaStream_t s,
                                 int variant);
 
+// Row-march stage with the flux chosen at run time (fvk::Flux) and stage
+// kind 1 (q1 = q^n + dt L), 2 (Heun), 3, 4 (SSP-RK3 stages 2 and 3; the
+// CFL reduction in 2 and 4).  Needs march_supported(g).
+bool march_supported(const Geom& g);
+cudaError_t launch_stage_general(const Geom& g, int stage, int flux, const float* qin, const float* qn,
+                                 float* qout, Ctrl* ctrl, const DtParams* dp, cudaStream_t s);
+
 // Wave-speed reduction of q that sets each member's dt without advancing
 // time (state creation, fv_set_state).
 cudaError_t launch_wavespeed_init(const Geom& g, const float* q, Ctrl* ctrl, const DtParams* dp,

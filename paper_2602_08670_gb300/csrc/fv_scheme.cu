@@ -4,9 +4,10 @@
 //
 // The MUSCL-minmod reconstruction (Eq. 2.18), the face-frame rotation (Eq.
 // 2.24), the divergence (Eq. 2.23) and the CFL reduction (Eq. 2.10) are those
-// of the HLL / SSP-RK2 stage kernels; this kernel is the shared-memory tile
-// variant with the flux chosen at run time (one uniform branch per face) and
-// four stage kinds:
+// of the HLL / SSP-RK2 stage kernels.  Grids with nx a multiple of 4 (>= 8)
+// run the row-march kernel of fv_stage.cu with the flux chosen at run time
+// (unless the tile variant is asked for); the others this shared-memory tile
+// kernel (one uniform branch per face), with four stage kinds:
 //   K_FIRST:   q1 = q^n + dt L(q^n)                          (both integrators)
 //   K_HEUN:    q^{n+1} = q^n/2 + (q1 + dt L(q1))/2, CFL     (SSP-RK2 stage 2)
 //   K_RK3_2:   q2 = 3/4 q^n + 1/4 (q1 + dt L(q1))           (SSP-RK3 stage 2)
@@ -209,7 +210,16 @@ cudaError_t launch_scheme_stage(const Geom& g, int kind, int flux, const float* 
 // One step of the plain scheme with the chosen flux and integrator.  q^n is
 // qa (updated in place); qb and (SSP-RK3) qc hold the intermediate stages.
 cudaError_t enqueue_scheme_step(const Geom& g, int flux, int rk, float* qa, float* qb, float* qc,
-                                Ctrl* ctrl, const DtParams* dp, cudaStream_t s) {
+                                Ctrl* ctrl, const DtParams* dp, cudaStream_t s, int variant) {
+  if (variant != STAGE_TILE && march_supported(g)) {
+    // row-march kernels (fv_stage.cu), stage kinds 1..4
+    cudaError_t e = launch_stage_general(g, 1, flux, qa, nullptr, qb, ctrl, dp, s);
+    if (e != cudaSuccess) return e;
+    if (rk == 2) return launch_stage_general(g, 2, flux, qb, qa, qa, ctrl, dp, s);
+    e = launch_stage_general(g, 3, flux, qb, qa, qc, ctrl, dp, s);
+    if (e != cudaSuccess) return e;
+    return launch_stage_general(g, 4, flux, qc, qa, qa, ctrl, dp, s);
+  }
   cudaError_t e = launch_scheme_stage(g, K_FIRST, flux, qa, nullptr, qb, ctrl, dp, s);
   if (e != cudaSuccess) return e;
   if (rk == 2) return launch_scheme_stage(g, K_HEUN, flux, qb, qa, qa, ctrl, dp, s);

@@ -14,6 +14,7 @@
 
 #include "fv_common.cuh"
 #include "fv_kernels.h"
+#include "fv_schemes.cuh"
 
 namespace fvk {
 
@@ -39,6 +40,7 @@ struct StageArgs {
   int nx, ny;
   long long plane, member;
   float rdx, rdy, phys;
+  int flux;            // fvk::Flux of the generic row-march stages
 };
 
 // Normal-frame flux of one face from its four-cell stencil.  `rot` selects the
@@ -208,28 +210,49 @@ __device__ __forceinline__ void cp_async_wait() {
 }
 
 // Face flux in the x frame / in the rotated y frame (normal momentum =
-// component 2), for scalars or packed pairs.
-template <int C, int EQ, class V>
-__device__ __forceinline__ void face_flux_x(const V (&L)[C], const V (&R)[C], float phys, V (&F)[C]) {
-  if constexpr (EQ == SWE) {
-    hll_swe<V>(L[0], L[1], L[2], R[0], R[1], R[2], phys, F[0], F[1], F[2]);
+// component 2), for scalars or packed pairs.  GEN: the flux is chosen at run
+// time (`flux`, fvk::Flux; `nu` the Lax-Friedrichs viscosity of the face's
+// direction); fluxes other than HLL are evaluated per cell.
+template <int C, int EQ, class V, bool GEN>
+__device__ __forceinline__ void normal_flux_any(const V (&L)[C], const V (&R)[C], float phys, int flux,
+                                                float nu, V (&F)[C]) {
+  if (!GEN || flux == FLUX_HLL) {
+    if constexpr (EQ == SWE) {
+      hll_swe<V>(L[0], L[1], L[2], R[0], R[1], R[2], phys, F[0], F[1], F[2]);
+    } else {
+      hll_euler<V>(L, R, phys, F);
+    }
+  } else if constexpr (sizeof(V) == sizeof(float)) {
+    scheme_flux<C, EQ>(flux, L, R, phys, nu, F);
   } else {
-    hll_euler<V>(L, R, phys, F);
+    float l0[C], r0[C], f0[C], l1[C], r1[C], f1[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      l0[c] = L[c].x; r0[c] = R[c].x;
+      l1[c] = L[c].y; r1[c] = R[c].y;
+    }
+    scheme_flux<C, EQ>(flux, l0, r0, phys, nu, f0);
+    scheme_flux<C, EQ>(flux, l1, r1, phys, nu, f1);
+#pragma unroll
+    for (int c = 0; c < C; ++c) F[c] = make_float2(f0[c], f1[c]);
   }
 }
 
-template <int C, int EQ, class V>
-__device__ __forceinline__ void face_flux_y(const V (&L)[C], const V (&R)[C], float phys, V (&F)[C]) {
+template <int C, int EQ, class V, bool GEN = false>
+__device__ __forceinline__ void face_flux_x(const V (&L)[C], const V (&R)[C], float phys, V (&F)[C],
+                                            int flux = 0, float nu = 0.f) {
+  normal_flux_any<C, EQ, V, GEN>(L, R, phys, flux, nu, F);
+}
+
+template <int C, int EQ, class V, bool GEN = false>
+__device__ __forceinline__ void face_flux_y(const V (&L)[C], const V (&R)[C], float phys, V (&F)[C],
+                                            int flux = 0, float nu = 0.f) {
   V l[C], r[C], f[C];
 #pragma unroll
   for (int c = 0; c < C; ++c) { l[c] = L[c]; r[c] = R[c]; }
   l[1] = L[2]; l[2] = L[1];
   r[1] = R[2]; r[2] = R[1];
-  if constexpr (EQ == SWE) {
-    hll_swe<V>(l[0], l[1], l[2], r[0], r[1], r[2], phys, f[0], f[1], f[2]);
-  } else {
-    hll_euler<V>(l, r, phys, f);
-  }
+  normal_flux_any<C, EQ, V, GEN>(l, r, phys, flux, nu, f);
 #pragma unroll
   for (int c = 0; c < C; ++c) F[c] = f[c];
   F[1] = f[2]; F[2] = f[1];
@@ -238,14 +261,21 @@ __device__ __forceinline__ void face_flux_y(const V (&L)[C], const V (&R)[C], fl
 __device__ __forceinline__ float2 lo(float4 v) { return make_float2(v.x, v.y); }
 __device__ __forceinline__ float2 hi(float4 v) { return make_float2(v.z, v.w); }
 
-template <int C, int EQ, int STAGE>
+// STAGE: 1 = q1 = q^n + dt L(q^n); 2 = Heun's second stage (Eq. 2.19) and
+// the CFL reduction; with GEN also 3 = SSP-RK3's second stage and 4 = its
+// third stage and the CFL reduction (Eq. 2.20).
+template <int C, int EQ, int STAGE, bool GEN = false>
 __global__ void __launch_bounds__(MT) stage_march_kernel(StageArgs a, int TY) {
+  constexpr bool CFL_STAGE = STAGE == 2 || STAGE == 4;
   extern __shared__ __align__(16) float ring[];   // [MS][C][RS]
   __shared__ unsigned red[2 * MT / 32];
   const int b = blockIdx.z;
   Ctrl* ctrl = a.ctrl + b;
   if (skip_if_done(ctrl)) return;
   const float dt = (float)ctrl->dt;
+  // Lax-Friedrichs viscosity per direction (generic stages): d / (4 dt)
+  const float nux = GEN ? vrcp(vmul(4.f, vmul(dt, a.rdx))) : 0.f;
+  const float nuy = GEN ? vrcp(vmul(4.f, vmul(dt, a.rdy))) : 0.f;
   const int t = threadIdx.x;
   const int X0 = blockIdx.x * MW;
   const int wact = min(MW, a.nx - X0);        // active columns of the strip (multiple of 4)
@@ -298,7 +328,7 @@ __global__ void __launch_bounds__(MT) stage_march_kernel(StageArgs a, int TY) {
     cp_async_commit();
     const int orow = Y0 + i - 4;                // output row at this step (valid for i >= 4)
     float2 qn2[C][2];
-    if (STAGE == 2 && i >= 4 && active) {
+    if (STAGE >= 2 && i >= 4 && active) {
       const int off = orow * a.nx + X0 + 4 * t;
 #pragma unroll
       for (int c = 0; c < C; ++c) {
@@ -338,7 +368,7 @@ __global__ void __launch_bounds__(MT) stage_march_kernel(StageArgs a, int TY) {
           Lf[c] = PL[c][p];
           Rf[c] = face_right(q1[c][p], sy[c][p]);
         }
-        face_flux_y<C, EQ, float2>(Lf, Rf, a.phys, F);
+        face_flux_y<C, EQ, float2, GEN>(Lf, Rf, a.phys, F, a.flux, nuy);
 #pragma unroll
         for (int c = 0; c < C; ++c) Gn[c][p] = F[c];
       }
@@ -375,7 +405,7 @@ __global__ void __launch_bounds__(MT) stage_march_kernel(StageArgs a, int TY) {
             Rf[c] = face_right(make_float2(e[c][2 + 2 * p], e[c][3 + 2 * p]),
                                make_float2(sx[c][2 * p + 1], sx[c][2 * p + 2]));
           }
-          face_flux_x<C, EQ, float2>(Lf, Rf, a.phys, F);
+          face_flux_x<C, EQ, float2, GEN>(Lf, Rf, a.phys, F, a.flux, nux);
 #pragma unroll
           for (int c = 0; c < C; ++c) Fx2[c][p] = F[c];
         }
@@ -386,7 +416,7 @@ __global__ void __launch_bounds__(MT) stage_march_kernel(StageArgs a, int TY) {
             Lf[c] = face_left(e[c][5], sx[c][4]);
             Rf[c] = face_right(e[c][6], sx[c][5]);
           }
-          face_flux_x<C, EQ, float>(Lf, Rf, a.phys, Fx4);
+          face_flux_x<C, EQ, float, GEN>(Lf, Rf, a.phys, Fx4, a.flux, nux);
         }
         // faces f0..f4 = Fx2[.][0].x, Fx2[.][0].y, Fx2[.][1].x, Fx2[.][1].y, Fx4
         float2 out[C][2];
@@ -401,9 +431,15 @@ __global__ void __launch_bounds__(MT) stage_march_kernel(StageArgs a, int TY) {
           if (STAGE == 1) {
             out[c][0] = rk_stage1(q0[c][0], dt, L0);
             out[c][1] = rk_stage1(q0[c][1], dt, L1);
-          } else {
+          } else if (STAGE == 2) {
             out[c][0] = rk_stage2(qn2[c][0], q0[c][0], 0.5f * dt, L0);
             out[c][1] = rk_stage2(qn2[c][1], q0[c][1], 0.5f * dt, L1);
+          } else {
+            // SSP-RK3: q^n + (1 - w)(q + dt L - q^n), 1 - w = 1/4 or 2/3
+            const float2 w = vsplat<float2>(STAGE == 3 ? 0.25f : 2.f / 3.f);
+            const float2 d = vsplat<float2>(dt);
+            out[c][0] = vfma(w, vsub(vfma(d, L0, q0[c][0]), qn2[c][0]), qn2[c][0]);
+            out[c][1] = vfma(w, vsub(vfma(d, L1, q0[c][1]), qn2[c][1]), qn2[c][1]);
           }
         }
         const int off = orow * a.nx + X0 + 4 * t;
@@ -411,7 +447,7 @@ __global__ void __launch_bounds__(MT) stage_march_kernel(StageArgs a, int TY) {
         for (int c = 0; c < C; ++c)
           *reinterpret_cast<float4*>(qout + c * plane + off) =
               make_float4(out[c][0].x, out[c][0].y, out[c][1].x, out[c][1].y);
-        if (STAGE == 2) {
+        if (CFL_STAGE) {
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
             float v[C];
@@ -440,7 +476,7 @@ __global__ void __launch_bounds__(MT) stage_march_kernel(StageArgs a, int TY) {
     }
   }
   cp_async_wait<0>();
-  if (STAGE == 2) {
+  if (CFL_STAGE) {
     block_reduce_max_or(amax, bad, red);
     if (t == 0) publish_and_close(ctrl, a.dp, amax, bad, gridDim.x * gridDim.y, true);
   }
@@ -572,30 +608,46 @@ int march_rows_per_block(int ny, int columns_x_members, int per_sm) {
   return best;
 }
 
+template <int C, int EQ, int STAGE, bool GEN>
+cudaError_t launch_march(const StageArgs& a, const Geom& g, cudaStream_t s) {
+  constexpr int smem = march_smem_bytes<C>();
+  auto kern = stage_march_kernel<C, EQ, STAGE, GEN>;
+  static int per_sm = 0;   // resident blocks per SM, queried once per instance
+  if (!per_sm) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, MT, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+  }
+  const int nsx = (g.nx + MW - 1) / MW;
+  const int TY = march_rows_per_block(g.ny, nsx * g.B, per_sm);
+  dim3 grid(nsx, (g.ny + TY - 1) / TY, g.B);
+  kern<<<grid, MT, smem, s>>>(a, TY);
+  return cudaGetLastError();
+}
+
+template <int C, int EQ>
+cudaError_t launch_general_t(const Geom& g, int stage, int flux, const float* qin, const float* qn,
+                             float* qout, Ctrl* ctrl, const DtParams* dp, cudaStream_t s) {
+  StageArgs a{qin, qn, qout, ctrl, dp, g.nx, g.ny, g.plane(), g.member(),
+              (float)(1.0 / g.dx), (float)(1.0 / g.dy), g.phys, flux};
+  switch (stage) {
+    case 1: return launch_march<C, EQ, 1, true>(a, g, s);
+    case 2: return launch_march<C, EQ, 2, true>(a, g, s);
+    case 3: return launch_march<C, EQ, 3, true>(a, g, s);
+    default: return launch_march<C, EQ, 4, true>(a, g, s);
+  }
+}
+
 template <int C, int EQ, int STAGE>
 cudaError_t launch_stage_t(const Geom& g, const float* qin, const float* qn, float* qout,
                            Ctrl* ctrl, const DtParams* dp, cudaStream_t s, int variant) {
   StageArgs a{qin, qn, qout, ctrl, dp, g.nx, g.ny, g.plane(), g.member(),
-              (float)(1.0 / g.dx), (float)(1.0 / g.dy), g.phys};
+              (float)(1.0 / g.dx), (float)(1.0 / g.dy), g.phys, 0};
   const bool march_ok = (g.nx % 4 == 0) && g.nx >= 8;
   if (variant == STAGE_MARCH && !march_ok) return cudaErrorInvalidValue;
-  if (variant != STAGE_TILE && march_ok) {
-    constexpr int smem = march_smem_bytes<C>();
-    auto kern = stage_march_kernel<C, EQ, STAGE>;
-    static int per_sm = 0;   // resident blocks per SM, queried once per instance
-    if (!per_sm) {
-      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-      if (e != cudaSuccess) return e;
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, MT, smem);
-      if (e != cudaSuccess) return e;
-      if (per_sm < 1) per_sm = 1;
-    }
-    const int nsx = (g.nx + MW - 1) / MW;
-    const int TY = march_rows_per_block(g.ny, nsx * g.B, per_sm);
-    dim3 grid(nsx, (g.ny + TY - 1) / TY, g.B);
-    kern<<<grid, MT, smem, s>>>(a, TY);
-    return cudaGetLastError();
-  }
+  if (variant != STAGE_TILE && march_ok) return launch_march<C, EQ, STAGE, false>(a, g, s);
   constexpr int smem = stage_smem_bytes<C>();
   auto kern = stage_minmod_kernel<C, EQ, STAGE>;
   static bool attr_set = false;
@@ -620,6 +672,15 @@ cudaError_t launch_stage_minmod(const Geom& g, int stage, const float* qin, cons
   }
   return stage == 1 ? launch_stage_t<4, EULER, 1>(g, qin, qn, qout, ctrl, dp, s, variant)
                     : launch_stage_t<4, EULER, 2>(g, qin, qn, qout, ctrl, dp, s, variant);
+}
+
+bool march_supported(const Geom& g) { return (g.nx % 4 == 0) && g.nx >= 8; }
+
+cudaError_t launch_stage_general(const Geom& g, int stage, int flux, const float* qin, const float* qn,
+                                 float* qout, Ctrl* ctrl, const DtParams* dp, cudaStream_t s) {
+  if (!march_supported(g)) return cudaErrorInvalidValue;
+  return g.eq == SWE ? launch_general_t<3, SWE>(g, stage, flux, qin, qn, qout, ctrl, dp, s)
+                     : launch_general_t<4, EULER>(g, stage, flux, qin, qn, qout, ctrl, dp, s);
 }
 
 cudaError_t launch_wavespeed_init(const Geom& g, const float* q, Ctrl* ctrl, const DtParams* dp,

@@ -180,7 +180,8 @@ cudaError_t leave(fv_state* s) {
 
 cudaError_t enqueue_plain_step(fv_state* s) {
   if (s->flux != FV_FLUX_HLL || s->rk != 2)
-    return fvk::enqueue_scheme_step(s->g, s->flux, s->rk, s->qA, s->qB, s->qC, s->ctrl, s->dp, s->stream);
+    return fvk::enqueue_scheme_step(s->g, s->flux, s->rk, s->qA, s->qB, s->qC, s->ctrl, s->dp, s->stream,
+                                    s->variant);
   cudaError_t e = fvk::launch_stage_minmod(s->g, 1, s->qA, nullptr, s->qB, s->ctrl, s->dp,
                                            s->stream, s->variant);
   if (e != cudaSuccess) return e;

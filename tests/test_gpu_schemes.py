@@ -38,10 +38,11 @@ def case(eq):
     return W.as_f32_exact(q), [TOL_O1, TOL_O1, (2e-4, 3e-4), TOL_O1]
 
 
-def gpu_replay(fv, q0, eq, dts, nsteps, flux, rk):
+def gpu_replay(fv, q0, eq, dts, nsteps, flux, rk, variant="auto"):
     q0t = f32(q0).cuda()
     s = fv.swe_init(q0t, dt_mode="replay") if eq == ofv.SWE else fv.euler_init(q0t, dt_mode="replay")
     fv.fv_set_scheme(s, flux, rk)
+    fv.fv_set_stage_variant(s, variant)
     fv.fv_set_replay_dt(s, dts)
     fv.fv_rollout(s, nsteps)
     return fv.fv_get_state(s).double().cpu(), s
@@ -72,13 +73,38 @@ CASES = [(f, 2) for f in ("rusanov", "lf", "roe", "hlle", "hllc")] + \
 @pytest.mark.parametrize("eq", [ofv.SWE, ofv.EULER])
 @pytest.mark.parametrize("flux,rk", CASES)
 def test_scheme_matches_oracle(fv, flux, rk, eq):
+    """Row-march kernels (nx = 64, a multiple of 4)."""
     q0, tols = case(eq)
     qr, tr, dts = S.run(torch.tensor(q0), eq, STEPS, flux=flux, rk=rk)
-    q, s = gpu_replay(fv, q0, eq, dts[:, 0].numpy(), STEPS, flux, rk)
+    q, s = gpu_replay(fv, q0, eq, dts[:, 0].numpy(), STEPS, flux, rk, "march")
     yard = fp32_yardstick(q0, eq, dts, flux, rk, qr)
     check(rel_errors(q, qr), [(max(l2, 5 * y2), max(li, 5 * yi)) for (l2, li), (y2, yi) in zip(tols, yard)])
     t, _, steps = fv.fv_get_time(s)
     assert steps[0] == STEPS and abs(t[0] - float(tr[0])) < 1e-12
+
+
+@pytest.mark.parametrize("eq", [ofv.SWE, ofv.EULER])
+@pytest.mark.parametrize("flux,rk", [("lf", 2), ("roe", 3), ("hllc", 3), ("hlle", 2)])
+def test_tile_kernel_matches_oracle(fv, flux, rk, eq):
+    """Shared-memory tile kernels: forced on nx = 64, and automatic on a
+    ragged nx = 62 (not a multiple of 4) whose tiles leave a partial column."""
+    q0, tols = case(eq)
+    for q0c, variant in ((q0, "tile"), (np.ascontiguousarray(q0[..., :62]), "auto")):
+        qr, tr, dts = S.run(torch.tensor(q0c), eq, 40, flux=flux, rk=rk)
+        q, s = gpu_replay(fv, q0c, eq, dts[:, 0].numpy(), 40, flux, rk, variant)
+        yard = fp32_yardstick(q0c, eq, dts, flux, rk, qr)
+        check(rel_errors(q, qr), [(max(l2, 5 * y2), max(li, 5 * yi)) for (l2, li), (y2, yi) in zip(tols, yard)])
+
+
+@pytest.mark.parametrize("flux", ["rusanov", "lf", "roe", "hlle", "hllc"])
+def test_tile_and_march_agree(fv, flux):
+    """Both kernels evaluate the same formulas per face and per cell: after
+    a few steps they agree to a few FP32 ulps of the state."""
+    q0, _ = case(ofv.EULER)
+    _, _, dts = S.run(torch.tensor(q0), ofv.EULER, 5, flux=flux, rk=3)
+    out = [gpu_replay(fv, q0, ofv.EULER, dts[:, 0].numpy(), 5, flux, 3, v)[0] for v in ("tile", "march")]
+    scale = out[0].abs().amax(dim=(0, 2, 3), keepdim=True)
+    assert ((out[0] - out[1]).abs() / scale).max() < 2e-5
 
 
 def test_rk3_adaptive_dt_follows_the_oracle(fv):
