@@ -69,12 +69,16 @@ constexpr int HID_SLOT = 4 * FP * 16;               // [4 groups][130][8 BF16]
 constexpr int Q_SLOT = 3 * QF * 4;                  // [3 vars][132] FP32
 constexpr int F_SLOT = 1552;                        // [3 vars][129] FP32, padded
 constexpr int G_SLOT = 3 * W * 4;                   // [3 vars][128] FP32
+constexpr int QN_SLOT = 3 * W * 4;                  // [3 vars][128] FP32: q^n of the next update
 constexpr int OFF_L1 = 0;                           // 3 slots
 constexpr int OFF_IN = OFF_L1 + 3 * L1_SLOT;        // layers 2..4 inputs, 2 slots each
 constexpr int OFF_Q = OFF_IN + 3 * 2 * HID_SLOT;    // 5 slots
 constexpr int OFF_F = OFF_Q + 5 * Q_SLOT;           // 2 slots
 constexpr int OFF_G = OFF_F + 2 * F_SLOT;           // 3 slots
-constexpr int STREAM_BYTES = OFF_G + 3 * G_SLOT;
+constexpr int OFF_QN = OFF_G + 3 * G_SLOT;          // 1 slot
+constexpr int OFF_FXO = OFF_QN + QN_SLOT;           // [2][4] FP32: east-face flux of column 127, sent east
+constexpr int OFF_FXI = OFF_FXO + 32;               // [2][4] FP32: west-face flux of column 0, received
+constexpr int STREAM_BYTES = OFF_FXI + 32;
 
 constexpr int W1_BYTES = snk::W1G_ELEMS * 2;                       // 3072
 constexpr int WH_BYTES = 9 * snk::CG_HID * snk::HID * 16;          // 18432
@@ -86,8 +90,10 @@ constexpr int OFF_W4 = OFF_W3 + WH_BYTES;
 constexpr int OFF_STREAMS = OFF_W4 + W4_BYTES;
 constexpr int N_BIAS = 3 * snk::HID + snk::N_OUT;
 constexpr int OFF_BIAS = OFF_STREAMS + 2 * STREAM_BYTES;
+// mbarriers: [0..1] MMAs of stream s done, [2..3] inputs of the next tick of
+// stream s ready, [4..7] tick n of stream s done (index 4 + 2 s + (n & 1))
 constexpr int OFF_MBAR = OFF_BIAS + ((N_BIAS * 4 + 15) / 16) * 16;
-constexpr int OFF_TSLOT = OFF_MBAR + 16;
+constexpr int OFF_TSLOT = OFF_MBAR + 8 * 8;
 constexpr int OFF_RED = OFF_TSLOT + 16;
 constexpr int SMEM_BYTES = OFF_RED + 32 * 4;
 
@@ -137,13 +143,34 @@ __device__ __forceinline__ uint32_t map_cta(uint32_t saddr, uint32_t rank) {
   asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
   return r;
 }
-__device__ __forceinline__ void st_cluster_v4(uint32_t addr, uint4 v) {
-  asm volatile("st.shared::cluster.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v.x), "r"(v.y),
-               "r"(v.z), "r"(v.w)
+// Arrive on a local mbarrier (release at CTA scope), optionally raising the
+// number of bytes its current phase still waits for.
+__device__ __forceinline__ void mbar_arrive(uint64_t* mbar) {
+  asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(mbar)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(tc::smem_u32(mbar)),
+               "r"(bytes)
                : "memory");
 }
-__device__ __forceinline__ void st_cluster_f32(uint32_t addr, float v) {
-  asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
+// Asynchronous 16-byte copy from this CTA's shared memory at `src` to the same
+// offset as `dst` in CTA `rank` of the cluster; completes (bytes) on that
+// CTA's mbarrier at the offset of `mbar`.  The source must have been made
+// visible to the async proxy (fence.proxy.async) by this thread.
+__device__ __forceinline__ void copy16_to_cta(const void* dst, const void* src, uint64_t* mbar,
+                                              uint32_t rank) {
+  asm volatile("cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], 16, [%2];" ::"r"(
+                   map_cta(tc::smem_u32(dst), rank)),
+               "r"(tc::smem_u32(src)), "r"(map_cta(tc::smem_u32(mbar), rank))
+               : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(tc::smem_u32(smem)), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 __device__ __forceinline__ void cluster_arrive() {
   asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
@@ -153,9 +180,6 @@ __device__ __forceinline__ void cluster_arrive_relaxed() {
 }
 __device__ __forceinline__ void cluster_wait() {
   asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
-}
-__device__ __forceinline__ void fence_proxy_async_cluster() {
-  asm volatile("fence.proxy.async.shared::cluster;\n" ::: "memory");
 }
 // Arrive on the mbarrier at the same shared-memory offset in every CTA of
 // `mask` once this thread's earlier tcgen05.mma have completed.
@@ -240,26 +264,27 @@ struct Stream {
   int b, u0, u1;           // current segment: member and its rows [u0, u1)
   int tau, ntau;           // tick within the segment
   bool active, pending;    // has a segment; MMAs issued and not yet drained
-  uint32_t parity;         // next phase of the stream's mbarrier
+  uint32_t parity;         // next phase of the stream's MMA mbarrier
+  uint32_t nt;             // ticks drained so far (all segments)
   float dt, hmin;
   float amax;
   unsigned bad;
 };
 
-// q^n of the row the next tick updates (stage 2), loaded one tick ahead of
-// its use, for the columns k and k + 96 of an updating thread.
-struct Pref {
-  float qn[2][3];
-};
-
-__device__ __forceinline__ void fetch_qn(Pref& P, const Args& a, int b, int u, int X0, int k) {
+// q^n of the row the next tick of this stream updates (stage 2), copied into
+// the stream's q^n slot one tick ahead of its use (cp.async: no registers
+// held across the phases), for the columns k and k + 96 of an updating thread.
+__device__ __forceinline__ void fetch_qn(float* qnb, const Args& a, int b, int u, int X0, int k) {
 #pragma unroll
   for (int r = 0; r < 2; ++r) {
     const int m = k + 96 * r;
     if (m < W) {
       const long long off = (long long)b * a.member + (long long)u * a.nx + X0 + m;
 #pragma unroll
-      for (int c = 0; c < 3; ++c) P.qn[r][c] = a.qn[off + c * a.plane];
+      for (int c = 0; c < 3; ++c)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(tc::smem_u32(qnb + c * W + m)),
+                     "l"(a.qn + off + c * a.plane)
+                     : "memory");
     }
   }
 }
@@ -306,24 +331,18 @@ __device__ __forceinline__ void store_l1_row(uint8_t* slot, const Args& a, const
 }
 
 // FP32 state row with a 2-cell periodic halo: frame position p is column
-// X0 - 2 + p; elements k, k + n, ... (n >= 96: at most five per thread, all
-// loads issued before the stores).
+// X0 - 2 + p; elements k, k + n, ... (n >= 96: at most five per thread),
+// copied with cp.async (the caller commits and waits).
 __device__ __forceinline__ void load_q_row(float* slot, const Args& a, const float* qb, int row,
                                            int X0, int k, int n) {
   const float* base = qb + (long long)wrap_row(row, a.ny) * a.nx;
-  float v[5];
 #pragma unroll
   for (int i = 0; i < 5; ++i) {
     const int idx = k + i * n;
     if (idx < 3 * QF) {
       const int c = idx / QF, p = idx - c * QF;
-      v[i] = base[c * a.plane + wrap_col(X0 - 2 + p, a.nx)];
+      cp_async4(slot + idx, base + c * a.plane + wrap_col(X0 - 2 + p, a.nx));
     }
-  }
-#pragma unroll
-  for (int i = 0; i < 5; ++i) {
-    const int idx = k + i * n;
-    if (idx < 3 * QF) slot[idx] = v[i];
   }
 }
 
@@ -337,10 +356,8 @@ __device__ __forceinline__ void prefetch_row(const Args& a, const float* qb, int
 }
 
 // Bias, ReLU and BF16 of 16 accumulator columns (channel groups 2 wg, 2 wg + 1)
-// into position m + 1 of the next layer's input row; the CTA's edge columns
-// also go to the neighbours' halo positions.
-__device__ __forceinline__ void drain_hidden(uint32_t taddr, const float* bias, uint8_t* dst,
-                                             int m, int wg, uint32_t west, uint32_t east) {
+// into position m + 1 of the next layer's input row.
+__device__ __forceinline__ void drain_hidden(uint32_t taddr, const float* bias, uint8_t* dst, int m, int wg) {
   float v[16];
   tc::tmem_ld16(taddr + 16 * wg, v);
 #pragma unroll
@@ -353,11 +370,7 @@ __device__ __forceinline__ void drain_hidden(uint32_t taddr, const float* bias, 
       pk[j] = pack_bf16x2(fmaxf(v[c] + bias[8 * g + 2 * j], 0.f),
                           fmaxf(v[c + 1] + bias[8 * g + 2 * j + 1], 0.f));
     }
-    const uint4 val = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-    uint8_t* row = dst + g * FP * 16;
-    *reinterpret_cast<uint4*>(row + (m + 1) * 16) = val;
-    if (m == 0) st_cluster_v4(map_cta(tc::smem_u32(row + (FP - 1) * 16), west), val);
-    if (m == W - 1) st_cluster_v4(map_cta(tc::smem_u32(row), east), val);
+    *reinterpret_cast<uint4*>(dst + g * FP * 16 + (m + 1) * 16) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
   }
 }
 
@@ -366,24 +379,16 @@ __device__ __forceinline__ void drain_hidden(uint32_t taddr, const float* bias, 
 // 3-tap stencil, as in the two-pass CNN's epilogue.
 __device__ __forceinline__ void drain_coeffs(uint32_t taddr, const float* bias, int dir,
                                              float (&wd)[18]) {
+  // columns 16 dir .. 16 dir + 19 hold the channels 18 dir .. 18 dir + 17
+  float v16[16], v4[4];
+  tc::tmem_ld16(taddr + 16 * dir, v16);
+  tmem_ld4(taddr + 16 + 16 * dir, v4);
   float r[18];
-  if (dir == 0) {
-    float v16[16], v2[2];
-    tc::tmem_ld16(taddr, v16);
-    tmem_ld2(taddr + 16, v2);
 #pragma unroll
-    for (int k = 0; k < 16; ++k) r[k] = v16[k] + bias[k];
-    r[16] = v2[0] + bias[16];
-    r[17] = v2[1] + bias[17];
-  } else {
-    // channels 18..35 from the 16-aligned loads of columns 16..31 and 32..35
-    float v16[16], v4[4];
-    tc::tmem_ld16(taddr + 16, v16);
-    tmem_ld4(taddr + 32, v4);
-#pragma unroll
-    for (int k = 0; k < 14; ++k) r[k] = v16[2 + k] + bias[18 + k];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) r[14 + k] = v4[k] + bias[32 + k];
+  for (int k = 0; k < 18; ++k) {
+    const float x = k < 16 ? v16[k] : v4[k - 16];
+    const float y = k < 14 ? v16[2 + k] : v4[k - 14];
+    r[k] = (dir ? y : x) + bias[18 * dir + k];
   }
 #pragma unroll
   for (int s = 0; s < 6; ++s) {
@@ -516,27 +521,33 @@ struct Ctx {
   uint64_t* mbar;
   unsigned* red;
   uint32_t tmem;
-  Descs D[2];
+  Descs D;                // operands of stream 0 (stream 1: + STREAM_BYTES)
   int tid, m, wg, X0;
   uint32_t lane_off, west, east, crank;
   uint16_t commit_mask;
-  bool issuer, failed, arrived;
+  bool issuer, failed;
+  uint32_t ph;            // phases run so far (selects the halo hand-off barrier)
 };
 
 // Update of row u = t - 8 from the fluxes of the two previous ticks (columns
 // k and k + 96 of a staging thread: nothing here depends on this tick's
 // MMAs), and the load of q^n for the row the next tick updates.
 template <int STAGE>
-__device__ __forceinline__ void update_row(Stream& Q, Pref& P, uint8_t* sbuf, const Args& a,
+__device__ __forceinline__ void update_row(Stream& Q, uint8_t* sbuf, const Args& a,
                                            const Ctx& X, int k) {
   const int tau = Q.tau;
   const int t = Q.u0 - 3 + tau;
   const float* qring = reinterpret_cast<const float*>(sbuf + OFF_Q);
   const float* Fb = reinterpret_cast<const float*>(sbuf + OFF_F);
   const float* Gb = reinterpret_cast<const float*>(sbuf + OFF_G);
+  float* qnb = reinterpret_cast<float*>(sbuf + OFF_QN);
   if (tau >= TICKS_AHEAD) {
+    // this thread's copies of q^n (issued one tick of this stream back; only
+    // the state row copies of this tick may still be in flight)
+    if (STAGE == 2) cp_async_wait_group<1>();
     const int u = t - 8;
     const float* Fo = Fb + ((tau + 1) & 1) * (F_SLOT / 4);
+    const float* Fw = reinterpret_cast<const float*>(sbuf + OFF_FXI) + ((Q.nt + 1) & 1) * 4;
     const float* Gs = Gb + ((tau + 1) % 3) * (G_SLOT / 4);
     const float* Gn = Gb + ((tau + 2) % 3) * (G_SLOT / 4);
     const float* qu = qring + ((tau + 1) % 5) * (3 * QF);
@@ -548,11 +559,13 @@ __device__ __forceinline__ void update_row(Stream& Q, Pref& P, uint8_t* sbuf, co
         float out[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          const float Lc = divergence<float>(Fo[c * (W + 1) + m], Fo[c * (W + 1) + m + 1], Gs[c * W + m],
-                                             Gn[c * W + m], a.rdx, a.rdy);
+          // the west face of column 0 is the west neighbour's east face
+          const float fw = m == 0 ? Fw[c] : Fo[c * (W + 1) + m];
+          const float Lc = divergence<float>(fw, Fo[c * (W + 1) + m + 1], Gs[c * W + m], Gn[c * W + m], a.rdx,
+                                             a.rdy);
           const float q = qu[c * QF + m + 2];
           out[c] = STAGE == 1 ? rk_stage1<float>(q, Q.dt, Lc)
-                              : rk_stage2<float>(P.qn[r][c], q, 0.5f * Q.dt, Lc);
+                              : rk_stage2<float>(qnb[c * W + m], q, 0.5f * Q.dt, Lc);
           a.qout[off + c * a.plane] = out[c];
         }
         if (STAGE == 2)
@@ -560,63 +573,83 @@ __device__ __forceinline__ void update_row(Stream& Q, Pref& P, uint8_t* sbuf, co
       }
     }
   }
-  if (STAGE == 2 && tau + 1 >= TICKS_AHEAD && tau + 1 < Q.ntau) fetch_qn(P, a, Q.b, t - 7, X.X0, k);
+  if (STAGE == 2 && tau + 1 >= TICKS_AHEAD && tau + 1 < Q.ntau) fetch_qn(qnb, a, Q.b, t - 7, X.X0, k);
 }
 
-// The TMEM-draining warpgroups' part of tick Q.tau (after its MMAs).
-__device__ __forceinline__ void epilogue(const Stream& Q, uint8_t* sbuf, uint32_t tm, const Args& a,
-                                         const Ctx& X) {
+// The TMEM-draining warpgroups' part of tick Q.tau (after its MMAs), first
+// half: the finished hidden accumulators into the next layer's input rows
+// (slot tau & 1), which the next tick's MMAs and the halo copies read through
+// the async proxy.  Then (in the caller) the layer-4 coefficients of row
+// j = t - 7 and the slot move; after those the next tick may be issued.
+__device__ __forceinline__ void drain_rows(const Stream& Q, uint8_t* sbuf, uint32_t tm, const Ctx& X) {
+  const int m = X.m, wg = X.wg;
+  const float* bias = X.bias;
+  uint8_t* in = sbuf + OFF_IN + (Q.tau & 1) * HID_SLOT;
+  drain_hidden(tm + ACC1, bias, in, m, wg);
+  drain_hidden(tm + acc_col(0, 0), bias + snk::HID, in + 2 * HID_SLOT, m, wg);
+  drain_hidden(tm + acc_col(1, 0), bias + 2 * snk::HID, in + 4 * HID_SLOT, m, wg);
+  tc::fence_proxy_async_smem();
+}
+
+// The edge columns of the rows just drained go to the neighbours' halo
+// positions (column 0 to the west neighbour's position W + 1, column W - 1 to
+// the east neighbour's position 0): 24 copies of 16 bytes (3 layers x 2 sides
+// x 4 channel groups), one per lane of a staging warp, completing on the
+// neighbours' "inputs ready" mbarrier of the stream.
+__device__ __forceinline__ void send_halos(const Stream& Q, uint8_t* sbuf, uint64_t* ready, const Ctx& X) {
+  const int lane = threadIdx.x & 31;
+  if (lane < 24) {
+    const int l = lane >> 3, east = (lane >> 2) & 1, g = lane & 3;
+    uint8_t* row = sbuf + OFF_IN + (Q.tau & 1) * HID_SLOT + 2 * l * HID_SLOT + g * FP * 16;
+    if (east) copy16_to_cta(row, row + W * 16, ready, X.east);
+    else copy16_to_cta(row + (FP - 1) * 16, row + 16, ready, X.west);
+  }
+}
+
+// Second half: the faces row j owns from the coefficients `wd` and the
+// staged state rows; x-face fluxes into F slot tau & 1 (the east face of
+// column W - 1 also to the east neighbour), y-face fluxes into G slot tau % 3.
+__device__ __forceinline__ void epilogue_faces(const Stream& Q, uint8_t* sbuf, const Args& a, const Ctx& X,
+                                               uint64_t* tick_done, const float (&wd)[18]) {
   const int m = X.m, wg = X.wg;
   const int tau = Q.tau;
-  const float* bias = X.bias;
   float* qring = reinterpret_cast<float*>(sbuf + OFF_Q);
   float* Fb = reinterpret_cast<float*>(sbuf + OFF_F);
   float* Gb = reinterpret_cast<float*>(sbuf + OFF_G);
-  // hidden layers: finished accumulators -> next layer's input row (slot tau & 1)
-  drain_hidden(tm + ACC1, bias, sbuf + OFF_IN + (tau & 1) * HID_SLOT, m, wg, X.west, X.east);
-  drain_hidden(tm + acc_col(0, 0), bias + snk::HID, sbuf + OFF_IN + 2 * HID_SLOT + (tau & 1) * HID_SLOT,
-               m, wg, X.west, X.east);
-  drain_hidden(tm + acc_col(1, 0), bias + 2 * snk::HID,
-               sbuf + OFF_IN + 4 * HID_SLOT + (tau & 1) * HID_SLOT, m, wg, X.west, X.east);
-  // the next tick's MMAs read these rows through the async proxy
-  tc::fence_proxy_async_smem();
-  if (m == 0 || m == W - 1) fence_proxy_async_cluster();
-  // layer 4: coefficients of row j = t - 7 and the faces it owns
-  float wd[18];
-  drain_coeffs(tm + acc_col(2, 0), bias + 3 * snk::HID, wg, wd);
   const float* qj = qring + ((tau + 2) % 5) * (3 * QF);
+  // warpgroup 0: x face j, i+1/2 from cells i-1 .. i+2 of row j; warpgroup
+  // 1: y face j+1/2 from rows j-1 .. j+2 of column i, in the rotated frame
+  // (one code path for both: the stencil pointers and the swap differ)
+  const bool yf = wg != 0;
+  const float* p0 = yf ? qring + ((tau + 1) % 5) * (3 * QF) + m + 2 : qj + m + 1;
+  const float* p1 = qj + m + 2;
+  const float* p2 = yf ? qring + ((tau + 3) % 5) * (3 * QF) + m + 2 : qj + m + 3;
+  const float* p3 = yf ? qring + ((tau + 4) % 5) * (3 * QF) + m + 2 : qj + m + 4;
   float qm[3], q0[3], q1[3], qp[3], L[3], R[3], F[3];
-  if (wg == 0) {
-    // x face j, i+1/2 from cells i-1 .. i+2 of row j
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      qm[c] = qj[c * QF + m + 1];
-      q0[c] = qj[c * QF + m + 2];
-      q1[c] = qj[c * QF + m + 3];
-      qp[c] = qj[c * QF + m + 4];
-    }
-    learned_face(qm, q0, q1, qp, wd, Q.hmin, L, R);
-    hll_swe<float>(L[0], L[1], L[2], R[0], R[1], R[2], a.g, F[0], F[1], F[2]);
+  for (int c = 0; c < 3; ++c) {
+    qm[c] = p0[c * QF];
+    q0[c] = p1[c * QF];
+    q1[c] = p2[c * QF];
+    qp[c] = p3[c * QF];
+  }
+  learned_face(qm, q0, q1, qp, wd, Q.hmin, L, R);
+  float f1, f2;
+  hll_swe<float>(L[0], yf ? L[2] : L[1], yf ? L[1] : L[2], R[0], yf ? R[2] : R[1], yf ? R[1] : R[2], a.g,
+                 F[0], f1, f2);
+  F[1] = yf ? f2 : f1;
+  F[2] = yf ? f1 : f2;
+  if (!yf) {
     float* Fs = Fb + (tau & 1) * (F_SLOT / 4);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      Fs[c * (W + 1) + m + 1] = F[c];
-      if (m == W - 1) st_cluster_f32(map_cta(tc::smem_u32(Fs + c * (W + 1)), X.east), F[c]);
+    for (int c = 0; c < 3; ++c) Fs[c * (W + 1) + m + 1] = F[c];
+    if (m == W - 1) {
+      float* fo = reinterpret_cast<float*>(sbuf + OFF_FXO) + (Q.nt & 1) * 4;
+      *reinterpret_cast<float4*>(fo) = make_float4(F[0], F[1], F[2], 0.f);
+      tc::fence_proxy_async_smem();
+      copy16_to_cta(sbuf + OFF_FXI + (Q.nt & 1) * 16, fo, tick_done, X.east);
     }
   } else {
-    // y face j+1/2 from rows j-1 .. j+2 of column i (rotated frame)
-    const float* r0 = qring + ((tau + 1) % 5) * (3 * QF);
-    const float* r2 = qring + ((tau + 3) % 5) * (3 * QF);
-    const float* r3 = qring + ((tau + 4) % 5) * (3 * QF);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      qm[c] = r0[c * QF + m + 2];
-      q0[c] = qj[c * QF + m + 2];
-      q1[c] = r2[c * QF + m + 2];
-      qp[c] = r3[c * QF + m + 2];
-    }
-    learned_face(qm, q0, q1, qp, wd, Q.hmin, L, R);
-    hll_swe<float>(L[0], L[2], L[1], R[0], R[2], R[1], a.g, F[0], F[2], F[1]);
     float* Gs = Gb + (tau % 3) * (G_SLOT / 4);
 #pragma unroll
     for (int c = 0; c < 3; ++c) Gs[c * W + m] = F[c];
@@ -624,52 +657,125 @@ __device__ __forceinline__ void epilogue(const Stream& Q, uint8_t* sbuf, uint32_
 }
 
 // The staging warps' part of tick Q.tau (warps 1-3 of warpgroup 2): the
-// update of row t-8, the FP32 state row t-4 into the ring, then (once the
-// tick's MMAs have read the slot) the layer-1 input of row t+1, and an L2
-// prefetch of the row the next tick stages.
+// FP32 state row t-4 into the ring (cp.async), the update of row t-8, then
+// (once the tick's MMAs have read the slot) the layer-1 input of row t+1,
+// and an L2 prefetch of the row the next tick stages.  `prev_done`: tick
+// nt - 1 of the stream done (null for the first tick).
 template <int STAGE>
-__device__ __forceinline__ bool staging(Stream& Q, Pref& P, uint8_t* sbuf, uint64_t* mbar,
-                                        const Args& a, const Ctx& X) {
+__device__ __forceinline__ bool staging(Stream& Q, uint8_t* sbuf, uint64_t* mma, uint64_t* ready,
+                                        uint64_t* prev_done, uint32_t prev_parity, const Args& a,
+                                        const Ctx& X) {
   const int tau = Q.tau, t = Q.u0 - 3 + tau;
   const int k = X.m - 32, n = W - 32;
   const float* qb = a.qin + (long long)Q.b * a.member;
   const bool l1 = tau + 1 < Q.ntau;
+  // every read of the previous tick is done, its fluxes are written
+  if (prev_done && !tc::mbar_wait_bounded(prev_done, prev_parity, WAIT_ITERS)) return false;
+  load_q_row(reinterpret_cast<float*>(sbuf + OFF_Q) + (tau % 5) * (3 * QF), a, qb, t - 4, X.X0, k, n);
+  cp_async_commit();
   float q[2][9];
   if (l1) load_l1_row(q, a, qb, t + 1, X.X0, k, n);      // in flight during the update
-  update_row<STAGE>(Q, P, sbuf, a, X, k);
-  load_q_row(reinterpret_cast<float*>(sbuf + OFF_Q) + (tau % 5) * (3 * QF), a, qb, t - 4, X.X0, k, n);
-  if (!tc::mbar_wait_bounded(mbar, Q.parity, WAIT_ITERS)) return false;
+  update_row<STAGE>(Q, sbuf, a, X, k);
+  cp_async_commit();                                     // the q^n copies (possibly none)
+  if (!tc::mbar_wait_bounded(mma, Q.parity, WAIT_ITERS)) return false;
   if (l1) store_l1_row(sbuf + OFF_L1 + (tau % 3) * L1_SLOT, a, q, k, n);
   tc::fence_proxy_async_smem();
   if (tau + 2 < Q.ntau) prefetch_row(a, qb, t + 2, X.X0, k);
+  cp_async_wait_group<1>();                              // the state row has landed
   return true;
 }
 
-// One phase: the tick of stream M on the tensor core, the epilogue of stream
-// E (whose MMAs were issued in the previous phase) on the CUDA cores.
-template <int STAGE, int ms>
-__device__ __forceinline__ void phase(Stream& M, Stream& E, Pref& PE, const Args& a, Ctx& X) {
-  constexpr int es = ms ^ 1;
-  if (M.active) {
-    if (X.issuer && !X.failed) {
-      tc::fence_after_sync();
-      tc::fence_proxy_async_smem();
-      issue_tick(X.D[ms], X.tmem + 256u * ms, M.tau, &X.mbar[ms], X.commit_mask);
-    }
-    M.pending = true;
+// Max / or over the three staging warps (named barrier 3); the result is in
+// the first staging thread.
+__device__ __forceinline__ void staging_reduce_max_or(float& m, unsigned& bad, unsigned* red) {
+  for (int o = 16; o > 0; o >>= 1) {
+    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    bad |= __shfl_xor_sync(0xffffffffu, bad, o);
   }
+  const int w = (threadIdx.x >> 5) - (ISSUE_WARP + 1), lane = threadIdx.x & 31;
+  if (lane == 0) {
+    red[w] = __float_as_uint(m);
+    red[3 + w] = bad;
+  }
+  asm volatile("bar.sync 3, 96;" ::: "memory");
+  if (w == 0 && lane == 0) {
+    for (int i = 1; i < 3; ++i) {
+      m = fmaxf(m, __uint_as_float(red[i]));
+      bad |= red[3 + i];
+    }
+  }
+}
+
+// Per-warp arrival on a local mbarrier: the warp's lanes first order their
+// shared-memory and TMEM accesses, then lane 0 arrives (release).
+__device__ __forceinline__ void warp_arrive(uint64_t* mbar, uint32_t tx, bool with_tx) {
+  tc::fence_before_sync();
+  __syncwarp();
+  if ((threadIdx.x & 31) == 0) {
+    if (with_tx) mbar_arrive_expect_tx(mbar, tx);
+    else mbar_arrive(mbar);
+  }
+}
+
+// One phase: the tick of stream M (index ms) on the tensor core, the
+// epilogue of stream E (index ms ^ 1, whose MMAs were issued in the previous
+// phase) on the CUDA cores.  The stream indices are run-time values so that
+// the kernel holds one copy of the phase code.
+//
+// Hand-offs (all mbarriers, per stream s):
+//  * mma[s]: the tick's MMAs have completed, in this CTA and in the
+//    neighbours whose halos they read (multicast commit);
+//  * ready[s]: the inputs of the stream's next tick are in place: the hidden
+//    rows and the slot move (8 draining warps), the layer-1 input row (3
+//    staging warps) and the neighbours' halo columns (384 bytes of copies);
+//  * done[s][n & 1]: tick n is complete (draining and staging warps, and the
+//    16-byte east-face flux from the west neighbour); tick n + 1 waits for it
+//    before it reads the staged rows and fluxes or overwrites their slots.
+// The issuing thread waits only for ready[M]; the other warps wait for
+// mma[E] and done[E] of the previous tick, both normally complete long before.
+template <int STAGE>
+__device__ __forceinline__ void phase(Stream& M, Stream& E, const Args& a, Ctx& X, int ms) {
+  const int es = ms ^ 1;
+  if (M.active) M.pending = true;      // its MMAs go to the tensor core in this phase
   if (E.pending) {
     uint8_t* sbuf = X.smem + OFF_STREAMS + es * STREAM_BYTES;
+    uint64_t* ready = &X.mbar[2 + es];
+    uint64_t* done = &X.mbar[4 + 2 * es + (E.nt & 1)];
+    uint64_t* prev_done = E.nt ? &X.mbar[4 + 2 * es + ((E.nt - 1) & 1)] : nullptr;
+    const uint32_t prev_parity = ((E.nt - 1) >> 1) & 1;
+    // at the end of a segment the next segment's first layer-1 rows are
+    // written below; the "inputs ready" arrivals wait for them
+    const bool seg_end = E.tau + 1 == E.ntau;
     bool ok = !X.failed;
     if (X.wg < 2) {
       const uint32_t tm = X.tmem + 256u * es + X.lane_off;
       if (ok) ok = tc::mbar_wait_bounded(&X.mbar[es], E.parity, WAIT_ITERS);
       tc::fence_after_sync();
-      if (ok) epilogue(E, sbuf, tm, a, X);
-      asm volatile("bar.sync 1, %0;" ::"n"(EPI_THREADS) : "memory");   // slot-0 reads done
+      float wd[18];
+      if (ok) drain_rows(E, sbuf, tm, X);
+      // the rows are written: the halo-sending warp may copy their edges
+      // (named barriers 2 and 4 alternate: the draining warps may run up to
+      // one phase ahead of the sending warp)
+      if (X.ph & 1) asm volatile("bar.arrive 4, %0;" ::"n"(EPI_THREADS + 32) : "memory");
+      else asm volatile("bar.arrive 2, %0;" ::"n"(EPI_THREADS + 32) : "memory");
+      if (ok) drain_coeffs(tm + acc_col(2, 0), X.bias + 3 * snk::HID, X.wg, wd);
+      asm volatile("bar.sync 1, %0;" ::"n"(EPI_THREADS) : "memory");   // slot-0 reads of both warpgroups done
       if (ok) move_slots(tm, X.wg);
+      if (!seg_end) warp_arrive(ready, 0, false);
+      if (ok && prev_done) ok = tc::mbar_wait_bounded(prev_done, prev_parity, WAIT_ITERS);
+      if (ok) epilogue_faces(E, sbuf, a, X, done, wd);
+      warp_arrive(done, 0, false);
     } else if (X.m >= 32) {
-      if (ok) ok = staging<STAGE>(E, PE, sbuf, &X.mbar[es], a, X);
+      if (ok) ok = staging<STAGE>(E, sbuf, &X.mbar[es], ready, prev_done, prev_parity, a, X);
+      if (X.m >= 96) {
+        // warp 11 sends the halo columns once the draining warps wrote them
+        if (X.ph & 1) asm volatile("bar.sync 4, %0;" ::"n"(EPI_THREADS + 32) : "memory");
+        else asm volatile("bar.sync 2, %0;" ::"n"(EPI_THREADS + 32) : "memory");
+        if (ok) send_halos(E, sbuf, ready, X);
+      }
+      // warp 9 also announces the bytes the neighbours send for this tick
+      if (!seg_end) warp_arrive(ready, 384, X.m < 64);
+      warp_arrive(done, 16, X.m < 64);
     }
     if (!ok && !X.failed) {
       X.failed = true;
@@ -677,13 +783,15 @@ __device__ __forceinline__ void phase(Stream& M, Stream& E, Pref& PE, const Args
     }
     E.parity ^= 1u;
     E.pending = false;
+    ++E.nt;
     if (++E.tau == E.ntau) {
       // segment done: close the member's stage-2 reduction, start the next segment
-      if (STAGE == 2) {
+      if (STAGE == 2 && X.wg == 2 && X.m >= 32) {
+        // the staging warps hold the Courant rates of the rows they updated
         float mx = E.amax;
         unsigned bd = E.bad;
-        block_reduce_max_or(mx, bd, X.red);
-        if (X.tid == 0) {
+        staging_reduce_max_or(mx, bd, X.red);
+        if (X.m == 32) {
           const long long R = a.rows, Sn = a.nstreams;
           const long long first = stream_of_row((long long)E.b * a.ny, R, Sn);
           const long long last = stream_of_row((long long)(E.b + 1) * a.ny - 1, R, Sn);
@@ -695,23 +803,48 @@ __device__ __forceinline__ void phase(Stream& M, Stream& E, Pref& PE, const Args
         segment_prologue(E, sbuf, a, X.X0, X.m, X.wg);
         tc::fence_proxy_async_smem();
       }
+      if (X.wg < 2) warp_arrive(ready, 0, false);
+      else if (X.m >= 32) warp_arrive(ready, 384, X.m < 64);
     }
   }
-  if (X.wg < 2) tc::fence_before_sync();
-  // The phase's cluster barrier.  The issuing warp waits for it at once: the
-  // next phase's MMAs read what every warp of every CTA wrote in this one.
-  // The other warps arrive and go on: the next phase's epilogue needs only
-  // its own stream's MMAs (an mbarrier) and data written two phases back, so
-  // they wait for this barrier after that epilogue, before arriving at the
-  // next one.  (The issuing warp writes nothing that others read: it
-  // arrives without a release, which would wait for its MMAs.)
-  if ((X.tid >> 5) == ISSUE_WARP) {
-    cluster_arrive_relaxed();
-    cluster_wait();
-  } else {
-    if (X.arrived) cluster_wait();
-    cluster_arrive();
-    X.arrived = true;
+}
+
+// The issuing thread's loop: the same sequence of phases and stream states
+// as the other warps, reduced to what the MMA issue needs (the tick's slots,
+// the "inputs ready" phase to wait for, segment changes).
+__device__ __forceinline__ void issuer_loop(Stream M, Stream E, const Args& a, Ctx& X) {
+  int ms = 0;
+#pragma unroll 1
+  for (;;) {
+    if (!(M.active || E.active || M.pending || E.pending)) break;
+    if (M.active) {
+      if (!X.failed) {
+        const bool ok = M.nt == 0 || tc::mbar_wait_bounded(&X.mbar[2 + ms], (M.nt - 1) & 1, WAIT_ITERS);
+        if (ok) {
+          tc::fence_after_sync();
+          tc::fence_proxy_async_smem();
+          Descs D = X.D;
+          if (ms) {
+            D.a_l1 = dplus(D.a_l1, STREAM_BYTES);
+            D.a_in = dplus(D.a_in, STREAM_BYTES);
+          }
+          issue_tick(D, X.tmem + 256u * ms, M.tau, &X.mbar[ms], X.commit_mask);
+        } else {
+          X.failed = true;
+          atomicOr(a.err, 1u);
+        }
+      }
+      M.pending = true;
+    }
+    if (E.pending) {
+      E.pending = false;
+      ++E.nt;
+      if (++E.tau == E.ntau) E.active = next_segment(E, a, X.crank);
+    }
+    const Stream T = M;
+    M = E;
+    E = T;
+    ms ^= 1;
   }
 }
 
@@ -731,7 +864,7 @@ __global__ void __launch_bounds__(NT, 1) learned_fused_kernel(Args a) {
   X.wg = X.tid >> 7;                      // 0, 1: drain TMEM; 2: update and stage
   X.issuer = X.tid == EPI_THREADS;        // first lane of warpgroup 2
   X.failed = false;
-  X.arrived = false;
+  X.ph = 0;
   X.lane_off = (uint32_t)(32 * ((X.tid >> 5) & 3)) << 16;
   X.crank = cluster_rank();
   X.X0 = (int)X.crank * W;
@@ -747,6 +880,8 @@ __global__ void __launch_bounds__(NT, 1) learned_fused_kernel(Args a) {
       const uint32_t arrivals = (uint32_t)__popc((unsigned)X.commit_mask);
       tc::mbar_init(&X.mbar[0], arrivals);
       tc::mbar_init(&X.mbar[1], arrivals);
+      // ready and done: one arrival per draining and per staging warp
+      for (int i = 2; i < 8; ++i) tc::mbar_init(&X.mbar[i], EPI_THREADS / 32 + 3);
       asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
   }
@@ -764,12 +899,12 @@ __global__ void __launch_bounds__(NT, 1) learned_fused_kernel(Args a) {
 
   // the two streams of this cluster and their first segments
   Stream S0, S1;
-  Pref P0 = {}, P1 = {};
   S0.g = (2 * cluster) * a.rows / a.nstreams;
   S0.g_end = (2 * cluster + 1) * a.rows / a.nstreams;
   S1.g = S0.g_end;
   S1.g_end = (2 * cluster + 2) * a.rows / a.nstreams;
   S0.parity = S1.parity = 0u;
+  S0.nt = S1.nt = 0u;
   S0.pending = S1.pending = false;
   S0.active = next_segment(S0, a, X.crank);
   S1.active = next_segment(S1, a, X.crank);
@@ -782,40 +917,61 @@ __global__ void __launch_bounds__(NT, 1) learned_fused_kernel(Args a) {
   tc::fence_after_sync();
   X.tmem = *tslot;
   const uint32_t sb = tc::smem_u32(smem);
+  X.D.a_l1 = tc::sdesc(sb + OFF_STREAMS + OFF_L1, W * 16, 128);
+  X.D.a_in = tc::sdesc(sb + OFF_STREAMS + OFF_IN, FP * 16, 128);
+  X.D.b_w1 = tc::sdesc(sb + OFF_W1, snk::HID * 16, 128);
 #pragma unroll
-  for (int s = 0; s < 2; ++s) {
-    const uint32_t base = sb + OFF_STREAMS + s * STREAM_BYTES;
-    X.D[s].a_l1 = tc::sdesc(base + OFF_L1, W * 16, 128);
-    X.D[s].a_in = tc::sdesc(base + OFF_IN, FP * 16, 128);
-    X.D[s].b_w1 = tc::sdesc(sb + OFF_W1, snk::HID * 16, 128);
-#pragma unroll
-    for (int l = 0; l < 3; ++l) {
-      const uint32_t N = l == 2 ? snk::N_OUT_PAD : snk::HID;
-      const uint32_t wl = sb + (l == 0 ? OFF_W2 : l == 1 ? OFF_W3 : OFF_W4);
-      X.D[s].b_ky0[l] = tc::sdesc(wl, N * 16, 128);
-      X.D[s].b_pair[l] = tc::sdesc(wl + 3 * snk::CG_HID * N * 16, 2 * N * 16, 128);
-    }
+  for (int l = 0; l < 3; ++l) {
+    const uint32_t N = l == 2 ? snk::N_OUT_PAD : snk::HID;
+    const uint32_t wl = sb + (l == 0 ? OFF_W2 : l == 1 ? OFF_W3 : OFF_W4);
+    X.D.b_ky0[l] = tc::sdesc(wl, N * 16, 128);
+    X.D.b_pair[l] = tc::sdesc(wl + 3 * snk::CG_HID * N * 16, 2 * N * 16, 128);
   }
   // every CTA of the cluster is running (and its mbarriers initialised)
   // before any remote store or multicast arrival
   cluster_arrive();
   cluster_wait();
 
-  for (;;) {
-    if (!(S0.active || S1.active || S0.pending || S1.pending)) break;
-    phase<STAGE, 0>(S0, S1, P1, a, X);
-    if (!(S0.active || S1.active || S0.pending || S1.pending)) break;
-    phase<STAGE, 1>(S1, S0, P0, a, X);
-  }
-
-  if (X.arrived) cluster_wait();   // the last phase's barrier (no remote store after it)
-  // no MMA is in flight unless a wait gave up; give those a bounded wait too
-  if (X.failed) {
-    tc::mbar_wait_bounded(&X.mbar[0], S0.parity, WAIT_ITERS);
-    tc::mbar_wait_bounded(&X.mbar[1], S1.parity, WAIT_ITERS);
+  if ((X.tid >> 5) == ISSUE_WARP) {
+    if (X.issuer) issuer_loop(S0, S1, a, X);
+  } else {
+    // M: the stream whose tick goes to the tensor core in this phase (index
+    // ms), E: the other one; they swap roles every phase
+    Stream M = S0, E = S1;
+    int ms = 0;
+#pragma unroll 1
+    for (;;) {
+      if (!(M.active || E.active || M.pending || E.pending)) break;
+      phase<STAGE>(M, E, a, X, ms);
+      ++X.ph;
+      const Stream T = M;
+      M = E;
+      E = T;
+      ms ^= 1;
+    }
+    // The last tick of each stream: its "inputs ready" and "done" phases
+    // still receive the neighbours' copies; wait until they have landed.  No
+    // MMA is in flight unless a wait gave up; give those a bounded wait too.
+    if (X.tid == 0) {
+      const uint32_t nts[2] = {ms ? E.nt : M.nt, ms ? M.nt : E.nt};
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        if (nts[s]) {
+          tc::mbar_wait_bounded(&X.mbar[2 + s], (nts[s] - 1) & 1, WAIT_ITERS);
+          tc::mbar_wait_bounded(&X.mbar[4 + 2 * s + ((nts[s] - 1) & 1)], ((nts[s] - 1) >> 1) & 1, WAIT_ITERS);
+        }
+      }
+    }
+    if (X.failed) {
+      tc::mbar_wait_bounded(&X.mbar[ms], M.parity, WAIT_ITERS);
+      tc::mbar_wait_bounded(&X.mbar[ms ^ 1], E.parity, WAIT_ITERS);
+    }
   }
   tc::fence_before_sync();
   __syncthreads();
+  // no CTA leaves while a neighbour may still address its shared memory
+  cluster_arrive();
+  cluster_wait();
   if ((X.tid >> 5) == ISSUE_WARP) tc::tmem_dealloc(X.tmem, TCOLS);
 }
 
