@@ -78,7 +78,18 @@ constexpr int OFF_G = OFF_F + 2 * F_SLOT;           // 3 slots
 constexpr int OFF_QN = OFF_G + 3 * G_SLOT;          // 1 slot
 constexpr int OFF_FXO = OFF_QN + QN_SLOT;           // [2][4] FP32: east-face flux of column 127, sent east
 constexpr int OFF_FXI = OFF_FXO + 32;               // [2][4] FP32: west-face flux of column 0, received
-constexpr int STREAM_BYTES = OFF_FXI + 32;
+// halo columns of the three hidden-layer input rows, [side][layer][group] x
+// 16 bytes: sent (side 0 = column 0, for the west neighbour; 1 = column
+// W - 1, for the east neighbour) and received (side 0 = from the west
+// neighbour, for position 0; 1 = from the east neighbour, for position W + 1)
+constexpr int HALO_SIDE = 3 * 4 * 16;
+constexpr int OFF_HOUT = OFF_FXI + 32;
+constexpr int OFF_HIN = OFF_HOUT + 2 * HALO_SIDE;
+// FP32 state row t+1 of the next tick's layer-1 input, [3 vars][W + 8], frame
+// position p = column - X0 + 4 (16-byte aligned interior)
+constexpr int RAWF = W + 8;
+constexpr int OFF_RAW = OFF_HIN + 2 * HALO_SIDE;
+constexpr int STREAM_BYTES = OFF_RAW + 3 * RAWF * 4;
 
 constexpr int W1_BYTES = snk::W1G_ELEMS * 2;                       // 3072
 constexpr int WH_BYTES = 9 * snk::CG_HID * snk::HID * 16;          // 18432
@@ -153,15 +164,15 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* mbar, uint32_t b
                "r"(bytes)
                : "memory");
 }
-// Asynchronous 16-byte copy from this CTA's shared memory at `src` to the same
-// offset as `dst` in CTA `rank` of the cluster; completes (bytes) on that
+// Asynchronous copy of `bytes` (a multiple of 16) from this CTA's shared
+// memory at `src` to the same offset as `dst` in CTA `rank` of the cluster; completes (bytes) on that
 // CTA's mbarrier at the offset of `mbar`.  The source must have been made
 // visible to the async proxy (fence.proxy.async) by this thread.
-__device__ __forceinline__ void copy16_to_cta(const void* dst, const void* src, uint64_t* mbar,
-                                              uint32_t rank) {
-  asm volatile("cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], 16, [%2];" ::"r"(
+__device__ __forceinline__ void copy_to_cta(const void* dst, const void* src, uint32_t bytes, uint64_t* mbar,
+                                            uint32_t rank) {
+  asm volatile("cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                    map_cta(tc::smem_u32(dst), rank)),
-               "r"(tc::smem_u32(src)), "r"(map_cta(tc::smem_u32(mbar), rank))
+               "r"(tc::smem_u32(src)), "r"(bytes), "r"(map_cta(tc::smem_u32(mbar), rank))
                : "memory");
 }
 __device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
@@ -271,22 +282,13 @@ struct Stream {
   unsigned bad;
 };
 
-// q^n of the row the next tick of this stream updates (stage 2), copied into
-// the stream's q^n slot one tick ahead of its use (cp.async: no registers
-// held across the phases), for the columns k and k + 96 of an updating thread.
-__device__ __forceinline__ void fetch_qn(float* qnb, const Args& a, int b, int u, int X0, int k) {
+// q^n of cell m of the row the next tick of this stream updates (stage 2),
+// copied into the stream's q^n slot one tick ahead of its use (cp.async: no
+// registers held across the phases).
+__device__ __forceinline__ void fetch_qn(float* qnb, const Args& a, int b, int u, int X0, int m) {
+  const long long off = (long long)b * a.member + (long long)u * a.nx + X0 + m;
 #pragma unroll
-  for (int r = 0; r < 2; ++r) {
-    const int m = k + 96 * r;
-    if (m < W) {
-      const long long off = (long long)b * a.member + (long long)u * a.nx + X0 + m;
-#pragma unroll
-      for (int c = 0; c < 3; ++c)
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(tc::smem_u32(qnb + c * W + m)),
-                     "l"(a.qn + off + c * a.plane)
-                     : "memory");
-    }
-  }
+  for (int c = 0; c < 3; ++c) cp_async4(qnb + c * W + m, a.qn + off + c * a.plane);
 }
 
 // Layer-1 input at position m: the normalised state of the cells m-1, m,
@@ -330,6 +332,38 @@ __device__ __forceinline__ void store_l1_row(uint8_t* slot, const Args& a, const
   }
 }
 
+// The raw state row `row` (three variables, columns X0 - 1 .. X0 + W) into
+// the stream's raw row, by the 96 staging threads (k = 0..95): one 16-byte
+// copy of the interior each, and the two halo cells of each variable.
+__device__ __forceinline__ void fetch_raw_row(float* raw, const Args& a, const float* qb, int row, int X0,
+                                              int k) {
+  const float* base = qb + (long long)wrap_row(row, a.ny) * a.nx;
+  const int v = k >> 5, j = k & 31;
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(tc::smem_u32(raw + v * RAWF + 4 + 4 * j)),
+               "l"(base + v * a.plane + X0 + 4 * j)
+               : "memory");
+  if (k < 6) {
+    const int hv = k >> 1, east = k & 1;
+    cp_async4(raw + hv * RAWF + (east ? 4 + W : 3), base + hv * a.plane + wrap_col(east ? X0 + W : X0 - 1, a.nx));
+  }
+}
+
+// The layer-1 input row from the raw row, positions k and k + n (n >= 64).
+__device__ __forceinline__ void build_l1_row(uint8_t* slot, const float* raw, const Args& a, int k, int n) {
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const int m = k + r * n;
+    if (m < W) {
+      float q[9];
+#pragma unroll
+      for (int kx = 0; kx < 3; ++kx)
+#pragma unroll
+        for (int v = 0; v < 3; ++v) q[3 * kx + v] = raw[v * RAWF + m + 3 + kx];
+      prep_l1_pos(slot, a, q, m);
+    }
+  }
+}
+
 // FP32 state row with a 2-cell periodic halo: frame position p is column
 // X0 - 2 + p; elements k, k + n, ... (n >= 96: at most five per thread),
 // copied with cp.async (the caller commits and waits).
@@ -356,8 +390,10 @@ __device__ __forceinline__ void prefetch_row(const Args& a, const float* qb, int
 }
 
 // Bias, ReLU and BF16 of 16 accumulator columns (channel groups 2 wg, 2 wg + 1)
-// into position m + 1 of the next layer's input row.
-__device__ __forceinline__ void drain_hidden(uint32_t taddr, const float* bias, uint8_t* dst, int m, int wg) {
+// into position m + 1 of the next layer's input row; the edge columns also
+// into the layer's part of the halo-out buffer.
+__device__ __forceinline__ void drain_hidden(uint32_t taddr, const float* bias, uint8_t* dst, uint8_t* hout,
+                                             int m, int wg) {
   float v[16];
   tc::tmem_ld16(taddr + 16 * wg, v);
 #pragma unroll
@@ -370,7 +406,9 @@ __device__ __forceinline__ void drain_hidden(uint32_t taddr, const float* bias, 
       pk[j] = pack_bf16x2(fmaxf(v[c] + bias[8 * g + 2 * j], 0.f),
                           fmaxf(v[c + 1] + bias[8 * g + 2 * j + 1], 0.f));
     }
-    *reinterpret_cast<uint4*>(dst + g * FP * 16 + (m + 1) * 16) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    const uint4 val = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    *reinterpret_cast<uint4*>(dst + g * FP * 16 + (m + 1) * 16) = val;
+    if (m == 0 || m == W - 1) *reinterpret_cast<uint4*>(hout + (m ? HALO_SIDE : 0) + g * 16) = val;
   }
 }
 
@@ -447,15 +485,28 @@ __device__ bool next_segment(Stream& S, const Args& a, uint32_t crank) {
 }
 
 // Start of a segment: layer-1 inputs of rows u0-5, u0-4, u0-3 (slots 0, 1,
-// 2), one row per warpgroup.  (The issuing warp takes no part: it has not
+// 2), one row per warpgroup, and the raw row u0-2.  (The issuing warp takes no part: it has not
 // waited for the MMAs that read these slots.)
+// (`work` false: only the staging threads' named barrier.)
 __device__ __forceinline__ void segment_prologue(const Stream& S, uint8_t* sbuf, const Args& a,
-                                                 int X0, int m, int wg) {
+                                                 int X0, int m, int wg, bool work) {
   if (wg == 2 && m < 32) return;
   const int k = wg == 2 ? m - 32 : m, n = wg == 2 ? W - 32 : W;
-  float q[2][9];
-  load_l1_row(q, a, a.qin + (long long)S.b * a.member, S.u0 - 5 + wg, X0, k, n);
-  store_l1_row(sbuf + OFF_L1 + wg * L1_SLOT, a, q, k, n);
+  const float* qb = a.qin + (long long)S.b * a.member;
+  if (work) {
+    float q[2][9];
+    load_l1_row(q, a, qb, S.u0 - 5 + wg, X0, k, n);
+    store_l1_row(sbuf + OFF_L1 + wg * L1_SLOT, a, q, k, n);
+  }
+  if (wg == 2) {
+    // the raw row of the first tick's layer-1 input, visible to all staging
+    // threads before they leave
+    if (work) {
+      fetch_raw_row(reinterpret_cast<float*>(sbuf + OFF_RAW), a, qb, S.u0 - 2, X0, k);
+      asm volatile("cp.async.wait_all;\n" ::: "memory");
+    }
+    asm volatile("bar.sync 5, 96;" ::: "memory");
+  }
 }
 
 // Shared-memory descriptors of the operands; a slot or tap offset is added to
@@ -526,15 +577,14 @@ struct Ctx {
   uint32_t lane_off, west, east, crank;
   uint16_t commit_mask;
   bool issuer, failed;
-  uint32_t ph;            // phases run so far (selects the halo hand-off barrier)
 };
 
-// Update of row u = t - 8 from the fluxes of the two previous ticks (columns
-// k and k + 96 of a staging thread: nothing here depends on this tick's
-// MMAs), and the load of q^n for the row the next tick updates.
+// Update of cell m of row u = t - 8 from the fluxes of the two previous
+// ticks (nothing here depends on this tick's MMAs; run by draining
+// warpgroup 0 while it waits for them), and the copy of q^n for the cell the
+// next tick updates.
 template <int STAGE>
-__device__ __forceinline__ void update_row(Stream& Q, uint8_t* sbuf, const Args& a,
-                                           const Ctx& X, int k) {
+__device__ __forceinline__ void update_cell(Stream& Q, uint8_t* sbuf, const Args& a, const Ctx& X, int m) {
   const int tau = Q.tau;
   const int t = Q.u0 - 3 + tau;
   const float* qring = reinterpret_cast<const float*>(sbuf + OFF_Q);
@@ -542,38 +592,32 @@ __device__ __forceinline__ void update_row(Stream& Q, uint8_t* sbuf, const Args&
   const float* Gb = reinterpret_cast<const float*>(sbuf + OFF_G);
   float* qnb = reinterpret_cast<float*>(sbuf + OFF_QN);
   if (tau >= TICKS_AHEAD) {
-    // this thread's copies of q^n (issued one tick of this stream back; only
-    // the state row copies of this tick may still be in flight)
-    if (STAGE == 2) cp_async_wait_group<1>();
+    // this thread's copies of q^n (issued one tick of this stream back)
+    if (STAGE == 2) asm volatile("cp.async.wait_all;\n" ::: "memory");
     const int u = t - 8;
     const float* Fo = Fb + ((tau + 1) & 1) * (F_SLOT / 4);
     const float* Fw = reinterpret_cast<const float*>(sbuf + OFF_FXI) + ((Q.nt + 1) & 1) * 4;
     const float* Gs = Gb + ((tau + 1) % 3) * (G_SLOT / 4);
     const float* Gn = Gb + ((tau + 2) % 3) * (G_SLOT / 4);
     const float* qu = qring + ((tau + 1) % 5) * (3 * QF);
+    const long long off = (long long)Q.b * a.member + (long long)u * a.nx + X.X0 + m;
+    float out[3];
 #pragma unroll
-    for (int r = 0; r < 2; ++r) {
-      const int m = k + 96 * r;
-      if (m < W) {
-        const long long off = (long long)Q.b * a.member + (long long)u * a.nx + X.X0 + m;
-        float out[3];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          // the west face of column 0 is the west neighbour's east face
-          const float fw = m == 0 ? Fw[c] : Fo[c * (W + 1) + m];
-          const float Lc = divergence<float>(fw, Fo[c * (W + 1) + m + 1], Gs[c * W + m], Gn[c * W + m], a.rdx,
-                                             a.rdy);
-          const float q = qu[c * QF + m + 2];
-          out[c] = STAGE == 1 ? rk_stage1<float>(q, Q.dt, Lc)
-                              : rk_stage2<float>(qnb[c * W + m], q, 0.5f * Q.dt, Lc);
-          a.qout[off + c * a.plane] = out[c];
-        }
-        if (STAGE == 2)
-          Q.amax = fmaxf(Q.amax, cell_rate_swe(out[0], out[1], out[2], a.g, a.rdx, a.rdy, Q.bad));
-      }
+    for (int c = 0; c < 3; ++c) {
+      // the west face of column 0 is the west neighbour's east face
+      const float fw = m == 0 ? Fw[c] : Fo[c * (W + 1) + m];
+      const float Lc = divergence<float>(fw, Fo[c * (W + 1) + m + 1], Gs[c * W + m], Gn[c * W + m], a.rdx,
+                                         a.rdy);
+      const float q = qu[c * QF + m + 2];
+      out[c] = STAGE == 1 ? rk_stage1<float>(q, Q.dt, Lc) : rk_stage2<float>(qnb[c * W + m], q, 0.5f * Q.dt, Lc);
+      a.qout[off + c * a.plane] = out[c];
     }
+    if (STAGE == 2) Q.amax = fmaxf(Q.amax, cell_rate_swe(out[0], out[1], out[2], a.g, a.rdx, a.rdy, Q.bad));
   }
-  if (STAGE == 2 && tau + 1 >= TICKS_AHEAD && tau + 1 < Q.ntau) fetch_qn(qnb, a, Q.b, t - 7, X.X0, k);
+  if (STAGE == 2 && tau + 1 >= TICKS_AHEAD && tau + 1 < Q.ntau) {
+    fetch_qn(qnb, a, Q.b, t - 7, X.X0, m);
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  }
 }
 
 // The TMEM-draining warpgroups' part of tick Q.tau (after its MMAs), first
@@ -585,25 +629,22 @@ __device__ __forceinline__ void drain_rows(const Stream& Q, uint8_t* sbuf, uint3
   const int m = X.m, wg = X.wg;
   const float* bias = X.bias;
   uint8_t* in = sbuf + OFF_IN + (Q.tau & 1) * HID_SLOT;
-  drain_hidden(tm + ACC1, bias, in, m, wg);
-  drain_hidden(tm + acc_col(0, 0), bias + snk::HID, in + 2 * HID_SLOT, m, wg);
-  drain_hidden(tm + acc_col(1, 0), bias + 2 * snk::HID, in + 4 * HID_SLOT, m, wg);
+  uint8_t* hout = sbuf + OFF_HOUT;
+  drain_hidden(tm + ACC1, bias, in, hout, m, wg);
+  drain_hidden(tm + acc_col(0, 0), bias + snk::HID, in + 2 * HID_SLOT, hout + 64, m, wg);
+  drain_hidden(tm + acc_col(1, 0), bias + 2 * snk::HID, in + 4 * HID_SLOT, hout + 128, m, wg);
   tc::fence_proxy_async_smem();
 }
 
-// The edge columns of the rows just drained go to the neighbours' halo
-// positions (column 0 to the west neighbour's position W + 1, column W - 1 to
-// the east neighbour's position 0): 24 copies of 16 bytes (3 layers x 2 sides
-// x 4 channel groups), one per lane of a staging warp, completing on the
-// neighbours' "inputs ready" mbarrier of the stream.
-__device__ __forceinline__ void send_halos(const Stream& Q, uint8_t* sbuf, uint64_t* ready, const Ctx& X) {
+// The edge columns of the rows just drained go to the neighbours: two copies
+// of 192 bytes (threads 0 and 1, after every draining warp wrote its rows)
+// into their halo-in buffers,
+// completing on their "inputs ready" mbarrier of the stream; the receiving
+// CTA's issuing warp places them at positions 0 and W + 1 of the rows.
+__device__ __forceinline__ void send_halos(uint8_t* sbuf, uint64_t* ready, const Ctx& X) {
   const int lane = threadIdx.x & 31;
-  if (lane < 24) {
-    const int l = lane >> 3, east = (lane >> 2) & 1, g = lane & 3;
-    uint8_t* row = sbuf + OFF_IN + (Q.tau & 1) * HID_SLOT + 2 * l * HID_SLOT + g * FP * 16;
-    if (east) copy16_to_cta(row, row + W * 16, ready, X.east);
-    else copy16_to_cta(row + (FP - 1) * 16, row + 16, ready, X.west);
-  }
+  if (lane == 0) copy_to_cta(sbuf + OFF_HIN + HALO_SIDE, sbuf + OFF_HOUT, HALO_SIDE, ready, X.west);
+  if (lane == 1) copy_to_cta(sbuf + OFF_HIN, sbuf + OFF_HOUT + HALO_SIDE, HALO_SIDE, ready, X.east);
 }
 
 // Second half: the faces row j owns from the coefficients `wd` and the
@@ -647,62 +688,12 @@ __device__ __forceinline__ void epilogue_faces(const Stream& Q, uint8_t* sbuf, c
       float* fo = reinterpret_cast<float*>(sbuf + OFF_FXO) + (Q.nt & 1) * 4;
       *reinterpret_cast<float4*>(fo) = make_float4(F[0], F[1], F[2], 0.f);
       tc::fence_proxy_async_smem();
-      copy16_to_cta(sbuf + OFF_FXI + (Q.nt & 1) * 16, fo, tick_done, X.east);
+      copy_to_cta(sbuf + OFF_FXI + (Q.nt & 1) * 16, fo, 16, tick_done, X.east);
     }
   } else {
     float* Gs = Gb + (tau % 3) * (G_SLOT / 4);
 #pragma unroll
     for (int c = 0; c < 3; ++c) Gs[c * W + m] = F[c];
-  }
-}
-
-// The staging warps' part of tick Q.tau (warps 1-3 of warpgroup 2): the
-// FP32 state row t-4 into the ring (cp.async), the update of row t-8, then
-// (once the tick's MMAs have read the slot) the layer-1 input of row t+1,
-// and an L2 prefetch of the row the next tick stages.  `prev_done`: tick
-// nt - 1 of the stream done (null for the first tick).
-template <int STAGE>
-__device__ __forceinline__ bool staging(Stream& Q, uint8_t* sbuf, uint64_t* mma, uint64_t* ready,
-                                        uint64_t* prev_done, uint32_t prev_parity, const Args& a,
-                                        const Ctx& X) {
-  const int tau = Q.tau, t = Q.u0 - 3 + tau;
-  const int k = X.m - 32, n = W - 32;
-  const float* qb = a.qin + (long long)Q.b * a.member;
-  const bool l1 = tau + 1 < Q.ntau;
-  // every read of the previous tick is done, its fluxes are written
-  if (prev_done && !tc::mbar_wait_bounded(prev_done, prev_parity, WAIT_ITERS)) return false;
-  load_q_row(reinterpret_cast<float*>(sbuf + OFF_Q) + (tau % 5) * (3 * QF), a, qb, t - 4, X.X0, k, n);
-  cp_async_commit();
-  float q[2][9];
-  if (l1) load_l1_row(q, a, qb, t + 1, X.X0, k, n);      // in flight during the update
-  update_row<STAGE>(Q, sbuf, a, X, k);
-  cp_async_commit();                                     // the q^n copies (possibly none)
-  if (!tc::mbar_wait_bounded(mma, Q.parity, WAIT_ITERS)) return false;
-  if (l1) store_l1_row(sbuf + OFF_L1 + (tau % 3) * L1_SLOT, a, q, k, n);
-  tc::fence_proxy_async_smem();
-  if (tau + 2 < Q.ntau) prefetch_row(a, qb, t + 2, X.X0, k);
-  cp_async_wait_group<1>();                              // the state row has landed
-  return true;
-}
-
-// Max / or over the three staging warps (named barrier 3); the result is in
-// the first staging thread.
-__device__ __forceinline__ void staging_reduce_max_or(float& m, unsigned& bad, unsigned* red) {
-  for (int o = 16; o > 0; o >>= 1) {
-    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    bad |= __shfl_xor_sync(0xffffffffu, bad, o);
-  }
-  const int w = (threadIdx.x >> 5) - (ISSUE_WARP + 1), lane = threadIdx.x & 31;
-  if (lane == 0) {
-    red[w] = __float_as_uint(m);
-    red[3 + w] = bad;
-  }
-  asm volatile("bar.sync 3, 96;" ::: "memory");
-  if (w == 0 && lane == 0) {
-    for (int i = 1; i < 3; ++i) {
-      m = fmaxf(m, __uint_as_float(red[i]));
-      bad |= red[3 + i];
-    }
   }
 }
 
@@ -714,6 +705,60 @@ __device__ __forceinline__ void warp_arrive(uint64_t* mbar, uint32_t tx, bool wi
   if ((threadIdx.x & 31) == 0) {
     if (with_tx) mbar_arrive_expect_tx(mbar, tx);
     else mbar_arrive(mbar);
+  }
+}
+
+// The staging warps' part of tick Q.tau (warps 1-3 of warpgroup 2): once
+// the tick's MMAs have read the slot, the layer-1 input of row t+1 from the
+// raw row and, if `early_ready`, the "inputs ready" arrival; then the FP32
+// state row t-4 into the ring and the raw row t+2 of the next tick
+// (cp.async, landed before the "done" arrival), and an L2 prefetch of row
+// t+3.  `prev_done`: tick nt - 1 of the stream done (null for the first tick).
+// Called by every staging thread each phase, `ok` or not (the named barrier
+// must see all 96); returns `ok` and the outcome of its waits.
+template <int STAGE>
+__device__ __forceinline__ bool staging(Stream& Q, uint8_t* sbuf, uint64_t* mma, uint64_t* ready,
+                                        uint64_t* prev_done, uint32_t prev_parity, const Args& a,
+                                        const Ctx& X, bool ok, bool early_ready) {
+  const int tau = Q.tau, t = Q.u0 - 3 + tau;
+  const int k = X.m - 32, n = W - 32;
+  const float* qb = a.qin + (long long)Q.b * a.member;
+  float* raw = reinterpret_cast<float*>(sbuf + OFF_RAW);
+  // every read of the previous tick is done, its rows are staged
+  if (ok && prev_done) ok = tc::mbar_wait_bounded(prev_done, prev_parity, WAIT_ITERS);
+  if (ok) ok = tc::mbar_wait_bounded(mma, Q.parity, WAIT_ITERS);
+  if (ok && tau + 1 < Q.ntau) build_l1_row(sbuf + OFF_L1 + (tau % 3) * L1_SLOT, raw, a, k, n);
+  tc::fence_proxy_async_smem();
+  // warp 9 also announces the bytes the neighbours send for this tick
+  if (early_ready) warp_arrive(ready, 2 * HALO_SIDE, X.m < 64);
+  asm volatile("bar.sync 5, 96;" ::: "memory");          // every read of the raw row is done
+  if (ok) {
+    load_q_row(reinterpret_cast<float*>(sbuf + OFF_Q) + (tau % 5) * (3 * QF), a, qb, t - 4, X.X0, k, n);
+    if (tau + 2 < Q.ntau) fetch_raw_row(raw, a, qb, t + 2, X.X0, k);
+    if (tau + 3 < Q.ntau) prefetch_row(a, qb, t + 3, X.X0, k);
+    asm volatile("cp.async.wait_all;\n" ::: "memory");  // the rows have landed
+  }
+  return ok;
+}
+
+// Max / or over the four warps of draining warpgroup 0 (named barrier 3);
+// the result is in thread 0.
+__device__ __forceinline__ void wg0_reduce_max_or(float& m, unsigned& bad, unsigned* red) {
+  for (int o = 16; o > 0; o >>= 1) {
+    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+  }
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    red[w] = __float_as_uint(m);
+    red[4 + w] = bad;
+  }
+  asm volatile("bar.sync 3, 128;" ::: "memory");
+  if (threadIdx.x == 0) {
+    for (int i = 1; i < 4; ++i) {
+      m = fmaxf(m, __uint_as_float(red[i]));
+      bad |= red[4 + i];
+    }
   }
 }
 
@@ -749,32 +794,26 @@ __device__ __forceinline__ void phase(Stream& M, Stream& E, const Args& a, Ctx& 
     bool ok = !X.failed;
     if (X.wg < 2) {
       const uint32_t tm = X.tmem + 256u * es + X.lane_off;
+      // the previous tick's fluxes and staged rows (normally long complete):
+      // warpgroup 0 updates row t-8 while the MMAs run
+      if (ok && prev_done) ok = tc::mbar_wait_bounded(prev_done, prev_parity, WAIT_ITERS);
+      if (ok && X.wg == 0) update_cell<STAGE>(E, sbuf, a, X, X.m);
       if (ok) ok = tc::mbar_wait_bounded(&X.mbar[es], E.parity, WAIT_ITERS);
       tc::fence_after_sync();
       float wd[18];
       if (ok) drain_rows(E, sbuf, tm, X);
-      // the rows are written: the halo-sending warp may copy their edges
-      // (named barriers 2 and 4 alternate: the draining warps may run up to
-      // one phase ahead of the sending warp)
-      if (X.ph & 1) asm volatile("bar.arrive 4, %0;" ::"n"(EPI_THREADS + 32) : "memory");
-      else asm volatile("bar.arrive 2, %0;" ::"n"(EPI_THREADS + 32) : "memory");
+      // every draining warp has written its rows and halo columns: lanes 0
+      // and 1 send the halos
+      asm volatile("bar.sync 2, %0;" ::"n"(EPI_THREADS) : "memory");
+      if (ok && X.tid < 2) send_halos(sbuf, ready, X);
       if (ok) drain_coeffs(tm + acc_col(2, 0), X.bias + 3 * snk::HID, X.wg, wd);
       asm volatile("bar.sync 1, %0;" ::"n"(EPI_THREADS) : "memory");   // slot-0 reads of both warpgroups done
       if (ok) move_slots(tm, X.wg);
       if (!seg_end) warp_arrive(ready, 0, false);
-      if (ok && prev_done) ok = tc::mbar_wait_bounded(prev_done, prev_parity, WAIT_ITERS);
       if (ok) epilogue_faces(E, sbuf, a, X, done, wd);
       warp_arrive(done, 0, false);
     } else if (X.m >= 32) {
-      if (ok) ok = staging<STAGE>(E, sbuf, &X.mbar[es], ready, prev_done, prev_parity, a, X);
-      if (X.m >= 96) {
-        // warp 11 sends the halo columns once the draining warps wrote them
-        if (X.ph & 1) asm volatile("bar.sync 4, %0;" ::"n"(EPI_THREADS + 32) : "memory");
-        else asm volatile("bar.sync 2, %0;" ::"n"(EPI_THREADS + 32) : "memory");
-        if (ok) send_halos(E, sbuf, ready, X);
-      }
-      // warp 9 also announces the bytes the neighbours send for this tick
-      if (!seg_end) warp_arrive(ready, 384, X.m < 64);
+      ok = staging<STAGE>(E, sbuf, &X.mbar[es], ready, prev_done, prev_parity, a, X, ok, !seg_end);
       warp_arrive(done, 16, X.m < 64);
     }
     if (!ok && !X.failed) {
@@ -786,12 +825,12 @@ __device__ __forceinline__ void phase(Stream& M, Stream& E, const Args& a, Ctx& 
     ++E.nt;
     if (++E.tau == E.ntau) {
       // segment done: close the member's stage-2 reduction, start the next segment
-      if (STAGE == 2 && X.wg == 2 && X.m >= 32) {
-        // the staging warps hold the Courant rates of the rows they updated
+      if (STAGE == 2 && X.wg == 0) {
+        // draining warpgroup 0 holds the Courant rates of the rows it updated
         float mx = E.amax;
         unsigned bd = E.bad;
-        staging_reduce_max_or(mx, bd, X.red);
-        if (X.m == 32) {
+        wg0_reduce_max_or(mx, bd, X.red);
+        if (X.tid == 0) {
           const long long R = a.rows, Sn = a.nstreams;
           const long long first = stream_of_row((long long)E.b * a.ny, R, Sn);
           const long long last = stream_of_row((long long)(E.b + 1) * a.ny - 1, R, Sn);
@@ -799,39 +838,54 @@ __device__ __forceinline__ void phase(Stream& M, Stream& E, const Args& a, Ctx& 
         }
       }
       E.active = next_segment(E, a, X.crank);
-      if (E.active && !X.failed) {
-        segment_prologue(E, sbuf, a, X.X0, X.m, X.wg);
+      if (E.active) {
+        segment_prologue(E, sbuf, a, X.X0, X.m, X.wg, !X.failed);
         tc::fence_proxy_async_smem();
       }
       if (X.wg < 2) warp_arrive(ready, 0, false);
-      else if (X.m >= 32) warp_arrive(ready, 384, X.m < 64);
+      else if (X.m >= 32) warp_arrive(ready, 2 * HALO_SIDE, X.m < 64);
     }
   }
 }
 
-// The issuing thread's loop: the same sequence of phases and stream states
-// as the other warps, reduced to what the MMA issue needs (the tick's slots,
-// the "inputs ready" phase to wait for, segment changes).
+// The issuing warp's loop: the same sequence of phases and stream states as
+// the other warps, reduced to what the MMA issue needs (the tick's slots, the
+// "inputs ready" phase to wait for, segment changes).  Before a tick its
+// lanes place the received halo columns into the new input rows; lane 0
+// issues the MMAs.
 __device__ __forceinline__ void issuer_loop(Stream M, Stream E, const Args& a, Ctx& X) {
+  const int lane = threadIdx.x & 31;
   int ms = 0;
 #pragma unroll 1
   for (;;) {
     if (!(M.active || E.active || M.pending || E.pending)) break;
     if (M.active) {
       if (!X.failed) {
-        const bool ok = M.nt == 0 || tc::mbar_wait_bounded(&X.mbar[2 + ms], (M.nt - 1) & 1, WAIT_ITERS);
+        bool ok = M.nt == 0 || tc::mbar_wait_bounded(&X.mbar[2 + ms], (M.nt - 1) & 1, WAIT_ITERS);
+        ok = __all_sync(0xffffffffu, ok);
         if (ok) {
-          tc::fence_after_sync();
-          tc::fence_proxy_async_smem();
-          Descs D = X.D;
-          if (ms) {
-            D.a_l1 = dplus(D.a_l1, STREAM_BYTES);
-            D.a_in = dplus(D.a_in, STREAM_BYTES);
+          uint8_t* sbuf = X.smem + OFF_STREAMS + ms * STREAM_BYTES;
+          if (M.nt && lane < 24) {
+            const int side = lane / 12, l = (lane >> 2) % 3, g = lane & 3;
+            uint8_t* row = sbuf + OFF_IN + 2 * l * HID_SLOT + ((M.tau + 1) & 1) * HID_SLOT + g * FP * 16;
+            *reinterpret_cast<uint4*>(row + (side ? FP - 1 : 0) * 16) =
+                *reinterpret_cast<const uint4*>(sbuf + OFF_HIN + lane * 16);
           }
-          issue_tick(D, X.tmem + 256u * ms, M.tau, &X.mbar[ms], X.commit_mask);
+          tc::fence_proxy_async_smem();
+          __syncwarp();
+          if (lane == 0) {
+            tc::fence_after_sync();
+            Descs D = X.D;
+            if (ms) {
+              D.a_l1 = dplus(D.a_l1, STREAM_BYTES);
+              D.a_in = dplus(D.a_in, STREAM_BYTES);
+            }
+            issue_tick(D, X.tmem + 256u * ms, M.tau, &X.mbar[ms], X.commit_mask);
+          }
+          __syncwarp();
         } else {
           X.failed = true;
-          atomicOr(a.err, 1u);
+          if (lane == 0) atomicOr(a.err, 1u);
         }
       }
       M.pending = true;
@@ -864,7 +918,6 @@ __global__ void __launch_bounds__(NT, 1) learned_fused_kernel(Args a) {
   X.wg = X.tid >> 7;                      // 0, 1: drain TMEM; 2: update and stage
   X.issuer = X.tid == EPI_THREADS;        // first lane of warpgroup 2
   X.failed = false;
-  X.ph = 0;
   X.lane_off = (uint32_t)(32 * ((X.tid >> 5) & 3)) << 16;
   X.crank = cluster_rank();
   X.X0 = (int)X.crank * W;
@@ -908,8 +961,8 @@ __global__ void __launch_bounds__(NT, 1) learned_fused_kernel(Args a) {
   S0.pending = S1.pending = false;
   S0.active = next_segment(S0, a, X.crank);
   S1.active = next_segment(S1, a, X.crank);
-  if (S0.active) segment_prologue(S0, smem + OFF_STREAMS, a, X.X0, X.m, X.wg);
-  if (S1.active) segment_prologue(S1, smem + OFF_STREAMS + STREAM_BYTES, a, X.X0, X.m, X.wg);
+  if (S0.active) segment_prologue(S0, smem + OFF_STREAMS, a, X.X0, X.m, X.wg, true);
+  if (S1.active) segment_prologue(S1, smem + OFF_STREAMS + STREAM_BYTES, a, X.X0, X.m, X.wg, true);
   asm volatile("cp.async.wait_all;\n" ::: "memory");
   tc::fence_proxy_async_smem();
   tc::fence_before_sync();
@@ -933,7 +986,7 @@ __global__ void __launch_bounds__(NT, 1) learned_fused_kernel(Args a) {
   cluster_wait();
 
   if ((X.tid >> 5) == ISSUE_WARP) {
-    if (X.issuer) issuer_loop(S0, S1, a, X);
+    issuer_loop(S0, S1, a, X);
   } else {
     // M: the stream whose tick goes to the tensor core in this phase (index
     // ms), E: the other one; they swap roles every phase
@@ -943,7 +996,6 @@ __global__ void __launch_bounds__(NT, 1) learned_fused_kernel(Args a) {
     for (;;) {
       if (!(M.active || E.active || M.pending || E.pending)) break;
       phase<STAGE>(M, E, a, X, ms);
-      ++X.ph;
       const Stream T = M;
       M = E;
       E = T;
