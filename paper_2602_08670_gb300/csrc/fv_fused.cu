@@ -518,6 +518,20 @@ struct Descs {
 };
 __device__ __forceinline__ uint64_t dplus(uint64_t d, uint32_t bytes) { return d + (bytes >> 4); }
 
+// tcgen05.mma with both shared-memory descriptors given by their low words:
+// every operand of this kernel has the same high word (stride between
+// 8-row core matrices 128 bytes, descriptor version 1), so only the start
+// address and leading-dimension fields vary; `acc` is a compile-time flag.
+template <bool ACC, uint32_t IDESC>
+__device__ __forceinline__ void mma_lo(uint32_t d_tmem, uint32_t a_lo, uint32_t b_lo) {
+  constexpr uint32_t hi = (128u >> 4) | (1u << 14);
+  asm volatile(
+      "{\n.reg .b64 da, db;\n.reg .pred p;\nmov.b64 da, {%1, %3};\nmov.b64 db, {%2, %3};\n"
+      "setp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], da, db, %5, p;\n}\n"
+      ::"r"(d_tmem), "r"(a_lo), "r"(b_lo), "n"(hi), "n"(ACC ? 1 : 0), "n"(IDESC)
+      : "memory");
+}
+
 // All MMAs of one tick of one stream (issued by one thread), then a commit
 // to the stream's mbarrier in this CTA and its neighbours; `tm`: the
 // stream's first TMEM column.
@@ -529,35 +543,56 @@ __device__ __forceinline__ void issue_tick(const Descs& D, uint32_t tm, int tau,
   constexpr uint32_t id96 = tc::idesc_bf16_f32(W, 2 * snk::N_OUT_PAD);
   // layers 2..4: new input row in slot (tau+1)&1, previous one in slot tau&1
   const uint32_t s_new = (uint32_t)((tau + 1) & 1), s_prev = (uint32_t)(tau & 1);
-  uint64_t a_new[3], a_prev[3];
+  // low descriptor words (start address in 16-byte units in bits 0-13)
+  const uint32_t in_lo = (uint32_t)D.a_in, l1_lo = (uint32_t)D.a_l1, w1_lo = (uint32_t)D.b_w1;
+  uint32_t a_new[3], a_prev[3], b0[3], bp[3];
 #pragma unroll
   for (int l = 0; l < 3; ++l) {
-    a_new[l] = dplus(D.a_in, (uint32_t)(l * 2 * HID_SLOT) + s_new * HID_SLOT);
-    a_prev[l] = dplus(D.a_in, (uint32_t)(l * 2 * HID_SLOT) + s_prev * HID_SLOT);
+    a_new[l] = in_lo + (((uint32_t)(l * 2 * HID_SLOT) + s_new * HID_SLOT) >> 4);
+    a_prev[l] = in_lo + (((uint32_t)(l * 2 * HID_SLOT) + s_prev * HID_SLOT) >> 4);
+    b0[l] = (uint32_t)D.b_ky0[l];
+    bp[l] = (uint32_t)D.b_pair[l];
   }
   // Steps 0-5: layer 1 (taps ky on input rows t-2, t-1, t) and the taps
   // ky = 0 on the previous row into slot 1; steps 6-11: the stacked taps
   // ky = 2 | ky = 1 on the new row into slot 0 | slot 1.  Layers are
   // interleaved so that consecutive MMAs target different accumulators.
+  // accumulator columns of this stream
+  const uint32_t d1 = tm + ACC1;
+  uint32_t dn[3], dc[3];
+#pragma unroll
+  for (int l = 0; l < 3; ++l) {
+    dn[l] = tm + acc_col(l, 1);
+    dc[l] = tm + acc_col(l, 0);
+  }
+  const uint32_t s0 = (uint32_t)(tau % 3);
+  const uint32_t l1s[3] = {s0, s0 == 2 ? 0u : s0 + 1, s0 == 0 ? 2u : s0 - 1};   // (tau + i) % 3
 #pragma unroll
   for (int i = 0; i < 12; ++i) {
     if (i < 3) {
-      const uint32_t slot = (uint32_t)((tau + i) % 3);
-      tc::mma_bf16(tm + ACC1, dplus(D.a_l1, slot * L1_SLOT), dplus(D.b_w1, i * 2 * snk::HID * 16), id32,
-                   i > 0);
+      const uint32_t a = l1_lo + l1s[i] * (L1_SLOT >> 4), b = w1_lo + (uint32_t)(i * 2 * snk::HID);
+      if (i == 0) mma_lo<false, id32>(d1, a, b);
+      else mma_lo<true, id32>(d1, a, b);
     }
 #pragma unroll
     for (int l = 0; l < 3; ++l) {
       const uint32_t N = l == 2 ? snk::N_OUT_PAD : snk::HID;
       const int j = i % 6, kx = j / 2, ks = j % 2;
-      const uint32_t aoff = (uint32_t)((2 * ks * FP + kx) * 16);
-      if (i < 6)
-        tc::mma_bf16(tm + acc_col(l, 1), dplus(a_prev[l], aoff),
-                     dplus(D.b_ky0[l], (uint32_t)((kx * 4 + 2 * ks) * N * 16)), l == 2 ? id48 : id32, i > 0);
-      else
-        tc::mma_bf16(tm + acc_col(l, 0), dplus(a_new[l], aoff),
-                     dplus(D.b_pair[l], (uint32_t)((kx * 4 + 2 * ks) * 2 * N * 16)), l == 2 ? id96 : id64,
-                     true);
+      const uint32_t aoff = (uint32_t)(2 * ks * FP + kx);   // 16-byte units
+      if (i < 6) {
+        const uint32_t b = b0[l] + (uint32_t)((kx * 4 + 2 * ks) * N);
+        if (l == 2) {
+          if (i == 0) mma_lo<false, id48>(dn[l], a_prev[l] + aoff, b);
+          else mma_lo<true, id48>(dn[l], a_prev[l] + aoff, b);
+        } else {
+          if (i == 0) mma_lo<false, id32>(dn[l], a_prev[l] + aoff, b);
+          else mma_lo<true, id32>(dn[l], a_prev[l] + aoff, b);
+        }
+      } else {
+        const uint32_t b = bp[l] + (uint32_t)((kx * 4 + 2 * ks) * 2 * N);
+        if (l == 2) mma_lo<true, id96>(dc[l], a_new[l] + aoff, b);
+        else mma_lo<true, id64>(dc[l], a_new[l] + aoff, b);
+      }
     }
   }
   // completion is signalled to this CTA and to its neighbours, which write
