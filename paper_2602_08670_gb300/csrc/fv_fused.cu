@@ -732,6 +732,22 @@ __device__ __forceinline__ void epilogue_faces(const Stream& Q, uint8_t* sbuf, c
   }
 }
 
+// Wait for phase `parity` of `mbar` by polling without suspending (for the
+// issuing warp, whose waits are short and on the critical path); gives up
+// after `max_iters` polls and returns false.
+__device__ __forceinline__ bool mbar_spin_bounded(uint64_t* mbar, uint32_t parity, uint32_t max_iters) {
+  for (uint32_t i = 0; i < max_iters; ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(tc::smem_u32(mbar)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
 // Per-warp arrival on a local mbarrier: the warp's lanes first order their
 // shared-memory and TMEM accesses, then lane 0 arrives (release).
 __device__ __forceinline__ void warp_arrive(uint64_t* mbar, uint32_t tx, bool with_tx) {
@@ -883,57 +899,60 @@ __device__ __forceinline__ void phase(Stream& M, Stream& E, const Args& a, Ctx& 
   }
 }
 
-// The issuing warp's loop: the same sequence of phases and stream states as
-// the other warps, reduced to what the MMA issue needs (the tick's slots, the
-// "inputs ready" phase to wait for, segment changes).  Before a tick its
-// lanes place the received halo columns into the new input rows; lane 0
-// issues the MMAs.
-__device__ __forceinline__ void issuer_loop(Stream M, Stream E, const Args& a, Ctx& X) {
+// One phase of the issuing warp: the same stream states as the other warps,
+// reduced to what the MMA issue needs (the tick's slots, the "inputs ready"
+// phase to wait for, segment changes).  Before a tick its lanes place the
+// received halo columns into the new input rows; lane 0 issues the MMAs.
+// Returns false once both streams are done.
+__device__ __forceinline__ bool issuer_phase(Stream& M, Stream& E, const Args& a, Ctx& X, int ms) {
+  if (!(M.active || E.active || M.pending || E.pending)) return false;
   const int lane = threadIdx.x & 31;
-  int ms = 0;
+  if (M.active) {
+    if (!X.failed) {
+      bool ok = M.nt == 0 || mbar_spin_bounded(&X.mbar[2 + ms], (M.nt - 1) & 1, 64u * WAIT_ITERS);
+      ok = __all_sync(0xffffffffu, ok);
+      if (ok) {
+        uint8_t* sbuf = X.smem + OFF_STREAMS + ms * STREAM_BYTES;
+        if (M.nt && lane < 24) {
+          const int side = lane / 12, l = (lane >> 2) % 3, g = lane & 3;
+          uint8_t* row = sbuf + OFF_IN + 2 * l * HID_SLOT + ((M.tau + 1) & 1) * HID_SLOT + g * FP * 16;
+          *reinterpret_cast<uint4*>(row + (side ? FP - 1 : 0) * 16) =
+              *reinterpret_cast<const uint4*>(sbuf + OFF_HIN + lane * 16);
+        }
+        tc::fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+          tc::fence_after_sync();
+          Descs D = X.D;
+          if (ms) {
+            D.a_l1 = dplus(D.a_l1, STREAM_BYTES);
+            D.a_in = dplus(D.a_in, STREAM_BYTES);
+          }
+          issue_tick(D, X.tmem + 256u * ms, M.tau, &X.mbar[ms], X.commit_mask);
+        }
+        __syncwarp();
+      } else {
+        X.failed = true;
+        if (lane == 0) atomicOr(a.err, 1u);
+      }
+    }
+    M.pending = true;
+  }
+  if (E.pending) {
+    E.pending = false;
+    ++E.nt;
+    if (++E.tau == E.ntau) E.active = next_segment(E, a, X.crank);
+  }
+  return true;
+}
+
+// The issuing warp's loop, two phases per iteration (the streams' roles
+// alternate without copying their states).
+__device__ __forceinline__ void issuer_loop(Stream S0, Stream S1, const Args& a, Ctx& X) {
 #pragma unroll 1
   for (;;) {
-    if (!(M.active || E.active || M.pending || E.pending)) break;
-    if (M.active) {
-      if (!X.failed) {
-        bool ok = M.nt == 0 || tc::mbar_wait_bounded(&X.mbar[2 + ms], (M.nt - 1) & 1, WAIT_ITERS);
-        ok = __all_sync(0xffffffffu, ok);
-        if (ok) {
-          uint8_t* sbuf = X.smem + OFF_STREAMS + ms * STREAM_BYTES;
-          if (M.nt && lane < 24) {
-            const int side = lane / 12, l = (lane >> 2) % 3, g = lane & 3;
-            uint8_t* row = sbuf + OFF_IN + 2 * l * HID_SLOT + ((M.tau + 1) & 1) * HID_SLOT + g * FP * 16;
-            *reinterpret_cast<uint4*>(row + (side ? FP - 1 : 0) * 16) =
-                *reinterpret_cast<const uint4*>(sbuf + OFF_HIN + lane * 16);
-          }
-          tc::fence_proxy_async_smem();
-          __syncwarp();
-          if (lane == 0) {
-            tc::fence_after_sync();
-            Descs D = X.D;
-            if (ms) {
-              D.a_l1 = dplus(D.a_l1, STREAM_BYTES);
-              D.a_in = dplus(D.a_in, STREAM_BYTES);
-            }
-            issue_tick(D, X.tmem + 256u * ms, M.tau, &X.mbar[ms], X.commit_mask);
-          }
-          __syncwarp();
-        } else {
-          X.failed = true;
-          if (lane == 0) atomicOr(a.err, 1u);
-        }
-      }
-      M.pending = true;
-    }
-    if (E.pending) {
-      E.pending = false;
-      ++E.nt;
-      if (++E.tau == E.ntau) E.active = next_segment(E, a, X.crank);
-    }
-    const Stream T = M;
-    M = E;
-    E = T;
-    ms ^= 1;
+    if (!issuer_phase(S0, S1, a, X, 0)) break;
+    if (!issuer_phase(S1, S0, a, X, 1)) break;
   }
 }
 
