@@ -102,9 +102,10 @@ constexpr int OFF_STREAMS = OFF_W4 + W4_BYTES;
 constexpr int N_BIAS = 3 * snk::HID + snk::N_OUT;
 constexpr int OFF_BIAS = OFF_STREAMS + 2 * STREAM_BYTES;
 // mbarriers: [0..1] MMAs of stream s done, [2..3] inputs of the next tick of
-// stream s ready, [4..7] tick n of stream s done (index 4 + 2 s + (n & 1))
+// stream s ready, [4..7] tick n of stream s done (index 4 + 2 s + (n & 1)),
+// [8..9] the neighbours' halo columns of stream s received
 constexpr int OFF_MBAR = OFF_BIAS + ((N_BIAS * 4 + 15) / 16) * 16;
-constexpr int OFF_TSLOT = OFF_MBAR + 8 * 8;
+constexpr int OFF_TSLOT = OFF_MBAR + 10 * 8;
 constexpr int OFF_RED = OFF_TSLOT + 16;
 constexpr int SMEM_BYTES = OFF_RED + 32 * 4;
 
@@ -673,13 +674,29 @@ __device__ __forceinline__ void drain_rows(const Stream& Q, uint8_t* sbuf, uint3
 
 // The edge columns of the rows just drained go to the neighbours: two copies
 // of 192 bytes (threads 0 and 1, after every draining warp wrote its rows)
-// into their halo-in buffers,
-// completing on their "inputs ready" mbarrier of the stream; the receiving
-// CTA's issuing warp places them at positions 0 and W + 1 of the rows.
-__device__ __forceinline__ void send_halos(uint8_t* sbuf, uint64_t* ready, const Ctx& X) {
+// into their halo-in buffers, completing on their "halos received" mbarrier
+// of the stream.
+__device__ __forceinline__ void send_halos(uint8_t* sbuf, uint64_t* halo_in, const Ctx& X) {
   const int lane = threadIdx.x & 31;
-  if (lane == 0) copy_to_cta(sbuf + OFF_HIN + HALO_SIDE, sbuf + OFF_HOUT, HALO_SIDE, ready, X.west);
-  if (lane == 1) copy_to_cta(sbuf + OFF_HIN, sbuf + OFF_HOUT + HALO_SIDE, HALO_SIDE, ready, X.east);
+  if (lane == 0) copy_to_cta(sbuf + OFF_HIN + HALO_SIDE, sbuf + OFF_HOUT, HALO_SIDE, halo_in, X.west);
+  if (lane == 1) copy_to_cta(sbuf + OFF_HIN, sbuf + OFF_HOUT + HALO_SIDE, HALO_SIDE, halo_in, X.east);
+}
+
+// Staging warp 10, every tick: once the neighbours' halo columns of tick
+// Q.tau have landed, place them at positions 0 and W + 1 of the rows drained
+// in this tick (slot tau & 1), where the next tick's MMAs read them.
+__device__ __forceinline__ bool place_halos(const Stream& Q, uint8_t* sbuf, uint64_t* halo_in, bool ok) {
+  const int lane = threadIdx.x & 31;
+  if (lane == 0) mbar_arrive_expect_tx(halo_in, 2 * HALO_SIDE);
+  if (ok) ok = tc::mbar_wait_bounded(halo_in, Q.nt & 1, WAIT_ITERS);
+  if (ok && lane < 24) {
+    const int side = lane / 12, l = (lane >> 2) % 3, g = lane & 3;
+    uint8_t* row = sbuf + OFF_IN + 2 * l * HID_SLOT + (Q.tau & 1) * HID_SLOT + g * FP * 16;
+    *reinterpret_cast<uint4*>(row + (side ? FP - 1 : 0) * 16) =
+        *reinterpret_cast<const uint4*>(sbuf + OFF_HIN + lane * 16);
+  }
+  tc::fence_proxy_async_smem();
+  return ok;
 }
 
 // Second half: the faces row j owns from the coefficients `wd` and the
@@ -780,8 +797,7 @@ __device__ __forceinline__ bool staging(Stream& Q, uint8_t* sbuf, uint64_t* mma,
   if (ok) ok = tc::mbar_wait_bounded(mma, Q.parity, WAIT_ITERS);
   if (ok && tau + 1 < Q.ntau) build_l1_row(sbuf + OFF_L1 + (tau % 3) * L1_SLOT, raw, a, k, n);
   tc::fence_proxy_async_smem();
-  // warp 9 also announces the bytes the neighbours send for this tick
-  if (early_ready) warp_arrive(ready, 2 * HALO_SIDE, X.m < 64);
+  if (early_ready) warp_arrive(ready, 0, false);
   asm volatile("bar.sync 5, 96;" ::: "memory");          // every read of the raw row is done
   if (ok) {
     load_q_row(reinterpret_cast<float*>(sbuf + OFF_Q) + (tau % 5) * (3 * QF), a, qb, t - 4, X.X0, k, n);
@@ -823,7 +839,8 @@ __device__ __forceinline__ void wg0_reduce_max_or(float& m, unsigned& bad, unsig
 //    neighbours whose halos they read (multicast commit);
 //  * ready[s]: the inputs of the stream's next tick are in place: the hidden
 //    rows and the slot move (8 draining warps), the layer-1 input row (3
-//    staging warps) and the neighbours' halo columns (384 bytes of copies);
+//    staging warps; warp 10 once it has also placed the neighbours' halo
+//    columns, which arrive on halo_in[s] as 384 bytes of copies);
 //  * done[s][n & 1]: tick n is complete (draining and staging warps, and the
 //    16-byte east-face flux from the west neighbour); tick n + 1 waits for it
 //    before it reads the staged rows and fluxes or overwrites their slots.
@@ -856,7 +873,7 @@ __device__ __forceinline__ void phase(Stream& M, Stream& E, const Args& a, Ctx& 
       // every draining warp has written its rows and halo columns: lanes 0
       // and 1 send the halos
       asm volatile("bar.sync 2, %0;" ::"n"(EPI_THREADS) : "memory");
-      if (ok && X.tid < 2) send_halos(sbuf, ready, X);
+      if (ok && X.tid < 2) send_halos(sbuf, &X.mbar[8 + es], X);
       if (ok) drain_coeffs(tm + acc_col(2, 0), X.bias + 3 * snk::HID, X.wg, wd);
       asm volatile("bar.sync 1, %0;" ::"n"(EPI_THREADS) : "memory");   // slot-0 reads of both warpgroups done
       if (ok) move_slots(tm, X.wg);
@@ -864,8 +881,15 @@ __device__ __forceinline__ void phase(Stream& M, Stream& E, const Args& a, Ctx& 
       if (ok) epilogue_faces(E, sbuf, a, X, done, wd);
       warp_arrive(done, 0, false);
     } else if (X.m >= 32) {
-      ok = staging<STAGE>(E, sbuf, &X.mbar[es], ready, prev_done, prev_parity, a, X, ok, !seg_end);
+      const bool halo_warp = X.m >= 64 && X.m < 96;   // warp 10
+      ok = staging<STAGE>(E, sbuf, &X.mbar[es], ready, prev_done, prev_parity, a, X, ok,
+                          !seg_end && !halo_warp);
       warp_arrive(done, 16, X.m < 64);
+      if (halo_warp) {
+        // every tick, so that the halo barrier's phases stay in step
+        ok = place_halos(E, sbuf, &X.mbar[8 + es], ok);
+        if (!seg_end) warp_arrive(ready, 0, false);
+      }
     }
     if (!ok && !X.failed) {
       X.failed = true;
@@ -894,15 +918,14 @@ __device__ __forceinline__ void phase(Stream& M, Stream& E, const Args& a, Ctx& 
         tc::fence_proxy_async_smem();
       }
       if (X.wg < 2) warp_arrive(ready, 0, false);
-      else if (X.m >= 32) warp_arrive(ready, 2 * HALO_SIDE, X.m < 64);
+      else if (X.m >= 32) warp_arrive(ready, 0, false);
     }
   }
 }
 
 // One phase of the issuing warp: the same stream states as the other warps,
 // reduced to what the MMA issue needs (the tick's slots, the "inputs ready"
-// phase to wait for, segment changes).  Before a tick its lanes place the
-// received halo columns into the new input rows; lane 0 issues the MMAs.
+// phase to wait for, segment changes); lane 0 issues the MMAs.
 // Returns false once both streams are done.
 __device__ __forceinline__ bool issuer_phase(Stream& M, Stream& E, const Args& a, Ctx& X, int ms) {
   if (!(M.active || E.active || M.pending || E.pending)) return false;
@@ -912,15 +935,6 @@ __device__ __forceinline__ bool issuer_phase(Stream& M, Stream& E, const Args& a
       bool ok = M.nt == 0 || mbar_spin_bounded(&X.mbar[2 + ms], (M.nt - 1) & 1, 64u * WAIT_ITERS);
       ok = __all_sync(0xffffffffu, ok);
       if (ok) {
-        uint8_t* sbuf = X.smem + OFF_STREAMS + ms * STREAM_BYTES;
-        if (M.nt && lane < 24) {
-          const int side = lane / 12, l = (lane >> 2) % 3, g = lane & 3;
-          uint8_t* row = sbuf + OFF_IN + 2 * l * HID_SLOT + ((M.tau + 1) & 1) * HID_SLOT + g * FP * 16;
-          *reinterpret_cast<uint4*>(row + (side ? FP - 1 : 0) * 16) =
-              *reinterpret_cast<const uint4*>(sbuf + OFF_HIN + lane * 16);
-        }
-        tc::fence_proxy_async_smem();
-        __syncwarp();
         if (lane == 0) {
           tc::fence_after_sync();
           Descs D = X.D;
@@ -989,6 +1003,9 @@ __global__ void __launch_bounds__(NT, 1) learned_fused_kernel(Args a) {
       tc::mbar_init(&X.mbar[1], arrivals);
       // ready and done: one arrival per draining and per staging warp
       for (int i = 2; i < 8; ++i) tc::mbar_init(&X.mbar[i], EPI_THREADS / 32 + 3);
+      // halos: one local arrival (with the expected bytes) per tick
+      tc::mbar_init(&X.mbar[8], 1);
+      tc::mbar_init(&X.mbar[9], 1);
       asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
   }
