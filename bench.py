@@ -342,7 +342,8 @@ def learned_block(args):
     fv.fv_sync(st)
     ms = e0.elapsed_time(e1)
     learned_rate = members * n * n * K / (ms * 1e-3)
-    cnn_tflops = 2 * 59328 * 2 * members * n * n * K / (ms * 1e-3) / 1e12
+    # 59 328 FLOP (two per multiply-add) per cell and CNN pass, two passes per step
+    cnn_tflops = 59328 * 2 * members * n * n * K / (ms * 1e-3) / 1e12
     peaks = {}
     pp = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(pp):
