@@ -63,7 +63,7 @@ __device__ __forceinline__ void face_flux_any(const float (&m)[C], const float (
       hll_euler<float>(L, R, phys, F);
     }
   } else {
-    scheme_flux<C, EQ>(flux, L, R, phys, nu, F);
+    scheme_flux<C, EQ, float>(flux, L, R, phys, nu, F);
   }
   if (rot) {
     float t = F[1]; F[1] = F[2]; F[2] = t;

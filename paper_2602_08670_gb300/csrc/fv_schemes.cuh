@@ -16,23 +16,33 @@ namespace fvk {
 
 enum Flux { FLUX_HLL = 0, FLUX_RUSANOV = 1, FLUX_LF = 2, FLUX_ROE = 3, FLUX_HLLE = 4, FLUX_HLLC = 5 };
 
-// Physical x flux, normal velocity and sound speed of one face-frame state.
-template <int C, int EQ>
-__device__ __forceinline__ void frame_state(const float (&q)[C], float phys, float (&F)[C], float& u,
-                                            float& c, float& p) {
-  const float r = vrcp(q[0]);
+// Per-lane select: c >= 0 ? a : b (packed pairs lane by lane).
+__device__ __forceinline__ float vsel_ge0(float c, float a, float b) { return c >= 0.f ? a : b; }
+__device__ __forceinline__ float2 vsel_ge0(float2 c, float2 a, float2 b) {
+  return make_float2(c.x >= 0.f ? a.x : b.x, c.y >= 0.f ? a.y : b.y);
+}
+__device__ __forceinline__ float vsel_gt0(float c, float a, float b) { return c > 0.f ? a : b; }
+__device__ __forceinline__ float2 vsel_gt0(float2 c, float2 a, float2 b) {
+  return make_float2(c.x > 0.f ? a.x : b.x, c.y > 0.f ? a.y : b.y);
+}
+
+// Physical x flux, normal velocity and sound speed of one face-frame state
+// (V = float, or float2 for two faces at once).
+template <int C, int EQ, class V>
+__device__ __forceinline__ void frame_state(const V (&q)[C], float phys, V (&F)[C], V& u, V& c, V& p) {
+  const V r = vrcp(q[0]);
   u = vmul(q[1], r);
   if constexpr (EQ == SWE) {
-    const float gh = vmul(phys, q[0]);
+    const V gh = vmul(vsplat<V>(phys), q[0]);
     c = vsqrt(gh);
-    p = vmul(vmul(0.5f, gh), q[0]);
+    p = vmul(vmul(vsplat<V>(0.5f), gh), q[0]);
     F[0] = q[1];
     F[1] = vfma(q[1], u, p);
     F[2] = vmul(q[2], u);
   } else {
-    const float v = vmul(q[2], r);
-    p = vmul(phys - 1.f, vfma(-0.5f, vfma(q[1], u, vmul(q[2], v)), q[3]));
-    c = vsqrt(vmul(vmul(phys, p), r));
+    const V v = vmul(q[2], r);
+    p = vmul(vsplat<V>(phys - 1.f), vfma(vsplat<V>(-0.5f), vfma(q[1], u, vmul(q[2], v)), q[3]));
+    c = vsqrt(vmul(vmul(vsplat<V>(phys), p), r));
     F[0] = q[1];
     F[1] = vfma(q[1], u, p);
     F[2] = vmul(q[2], u);
@@ -41,134 +51,122 @@ __device__ __forceinline__ void frame_state(const float (&q)[C], float phys, flo
 }
 
 // 1/2 (F_L + F_R) - nu (Q_R - Q_L)
-template <int C>
-__device__ __forceinline__ void central(const float (&FL)[C], const float (&FR)[C], const float (&L)[C],
-                                        const float (&R)[C], float nu, float (&F)[C]) {
+template <int C, class V>
+__device__ __forceinline__ void central(const V (&FL)[C], const V (&FR)[C], const V (&L)[C], const V (&R)[C],
+                                        V nu, V (&F)[C]) {
 #pragma unroll
-  for (int k = 0; k < C; ++k) F[k] = vsub(vmul(0.5f, vadd(FL[k], FR[k])), vmul(nu, vsub(R[k], L[k])));
+  for (int k = 0; k < C; ++k) F[k] = vsub(vmul(vsplat<V>(0.5f), vadd(FL[k], FR[k])), vmul(nu, vsub(R[k], L[k])));
 }
 
 // Roe-averaged u, v, c (and H for Euler) of two face-frame states.
-template <int C, int EQ>
-__device__ __forceinline__ void roe_state(const float (&L)[C], const float (&R)[C], float phys, float& u,
-                                          float& v, float& c, float& H, float pL, float pR) {
-  const float sL = vsqrt(L[0]), sR = vsqrt(R[0]);
-  const float w = vrcp(vadd(sL, sR));
+template <int C, int EQ, class V>
+__device__ __forceinline__ void roe_state(const V (&L)[C], const V (&R)[C], float phys, V& u, V& v, V& c, V& H,
+                                          V pL, V pR) {
+  const V sL = vsqrt(L[0]), sR = vsqrt(R[0]);
+  const V w = vrcp(vadd(sL, sR));
   u = vmul(vadd(vmul(L[1], vrcp(sL)), vmul(R[1], vrcp(sR))), w);
   v = vmul(vadd(vmul(L[2], vrcp(sL)), vmul(R[2], vrcp(sR))), w);
   if constexpr (EQ == SWE) {
-    c = vsqrt(vmul(phys, vmul(0.5f, vadd(L[0], R[0]))));
-    H = 0.f;
+    c = vsqrt(vmul(vsplat<V>(phys), vmul(vsplat<V>(0.5f), vadd(L[0], R[0]))));
+    H = vsplat<V>(0.f);
   } else {
-    const float HL = vmul(vadd(L[3], pL), vrcp(L[0]));
-    const float HR = vmul(vadd(R[3], pR), vrcp(R[0]));
+    const V HL = vmul(vadd(L[3], pL), vrcp(L[0]));
+    const V HR = vmul(vadd(R[3], pR), vrcp(R[0]));
     H = vmul(vadd(vmul(sL, HL), vmul(sR, HR)), w);
-    c = vsqrt(vmul(phys - 1.f, vsub(H, vmul(0.5f, vfma(u, u, vmul(v, v))))));
+    c = vsqrt(vmul(vsplat<V>(phys - 1.f), vsub(H, vmul(vsplat<V>(0.5f), vfma(u, u, vmul(v, v))))));
   }
 }
 
-template <int C, int EQ>
-__device__ __forceinline__ void roe_flux(const float (&L)[C], const float (&R)[C], const float (&FL)[C],
-                                         const float (&FR)[C], float pL, float pR, float phys,
-                                         float (&F)[C]) {
-  float u, v, c, H;
-  roe_state<C, EQ>(L, R, phys, u, v, c, H, pL, pR);
-  float d[C];
+template <int C, int EQ, class V>
+__device__ __forceinline__ void roe_flux(const V (&L)[C], const V (&R)[C], const V (&FL)[C], const V (&FR)[C],
+                                         V pL, V pR, float phys, V (&F)[C]) {
+  V u, v, c, H;
+  roe_state<C, EQ, V>(L, R, phys, u, v, c, H, pL, pR);
+  V d[C];
 #pragma unroll
   for (int k = 0; k < C; ++k) d[k] = vsub(R[k], L[k]);
-  const float l1 = fabsf(vsub(u, c)), l2 = fabsf(u), l3 = fabsf(vadd(u, c));
-  const float r2c = vrcp(vadd(c, c));
-  float D[C];
+  const V l1 = vabs(vsub(u, c)), l2 = vabs(u), l3 = vabs(vadd(u, c));
+  const V r2c = vrcp(vadd(c, c));
+  V D[C];
   if constexpr (EQ == SWE) {
-    const float a1 = vmul(vsub(vmul(vadd(u, c), d[0]), d[1]), r2c);
-    const float a3 = vmul(vsub(d[1], vmul(vsub(u, c), d[0])), r2c);
-    const float a2 = vsub(d[2], vmul(v, d[0]));
-    const float w1 = vmul(l1, a1), w2 = vmul(l2, a2), w3 = vmul(l3, a3);
+    const V a1 = vmul(vsub(vmul(vadd(u, c), d[0]), d[1]), r2c);
+    const V a3 = vmul(vsub(d[1], vmul(vsub(u, c), d[0])), r2c);
+    const V a2 = vsub(d[2], vmul(v, d[0]));
+    const V w1 = vmul(l1, a1), w2 = vmul(l2, a2), w3 = vmul(l3, a3);
     D[0] = vadd(w1, w3);
     D[1] = vadd(vmul(w1, vsub(u, c)), vmul(w3, vadd(u, c)));
     D[2] = vadd(vadd(vmul(w1, v), w2), vmul(w3, v));
   } else {
-    const float g1 = phys - 1.f;
-    const float a3 = vsub(d[2], vmul(v, d[0]));
-    const float dE = vsub(d[3], vmul(a3, v));
-    const float a2 = vmul(vmul(g1, vrcp(vmul(c, c))),
-                          vsub(vadd(vmul(d[0], vsub(H, vmul(u, u))), vmul(u, d[1])), dE));
-    const float a1 = vmul(vsub(vsub(vmul(d[0], vadd(u, c)), d[1]), vmul(c, a2)), r2c);
-    const float a4 = vsub(d[0], vadd(a1, a2));
-    const float w1 = vmul(l1, a1), w2 = vmul(l2, a2), w3 = vmul(l2, a3), w4 = vmul(l3, a4);
-    const float k2 = vmul(0.5f, vfma(u, u, vmul(v, v)));
+    const V g1 = vsplat<V>(phys - 1.f);
+    const V a3 = vsub(d[2], vmul(v, d[0]));
+    const V dE = vsub(d[3], vmul(a3, v));
+    const V a2 = vmul(vmul(g1, vrcp(vmul(c, c))), vsub(vadd(vmul(d[0], vsub(H, vmul(u, u))), vmul(u, d[1])), dE));
+    const V a1 = vmul(vsub(vsub(vmul(d[0], vadd(u, c)), d[1]), vmul(c, a2)), r2c);
+    const V a4 = vsub(d[0], vadd(a1, a2));
+    const V w1 = vmul(l1, a1), w2 = vmul(l2, a2), w3 = vmul(l2, a3), w4 = vmul(l3, a4);
+    const V k2 = vmul(vsplat<V>(0.5f), vfma(u, u, vmul(v, v)));
     D[0] = vadd(vadd(w1, w2), w4);
     D[1] = vadd(vadd(vmul(w1, vsub(u, c)), vmul(w2, u)), vmul(w4, vadd(u, c)));
     D[2] = vadd(vadd(vadd(vmul(w1, v), vmul(w2, v)), w3), vmul(w4, v));
-    D[3] = vadd(vadd(vadd(vmul(w1, vsub(H, vmul(u, c))), vmul(w2, k2)), vmul(w3, v)),
-                vmul(w4, vfma(u, c, H)));
+    D[3] = vadd(vadd(vadd(vmul(w1, vsub(H, vmul(u, c))), vmul(w2, k2)), vmul(w3, v)), vmul(w4, vfma(u, c, H)));
   }
 #pragma unroll
-  for (int k = 0; k < C; ++k) F[k] = vsub(vmul(0.5f, vadd(FL[k], FR[k])), vmul(0.5f, D[k]));
-}
-
-// HLL formula with given speeds, three branches (Eq. 2.15 form)
-template <int C>
-__device__ __forceinline__ void hll_branches(const float (&L)[C], const float (&R)[C], const float (&FL)[C],
-                                             const float (&FR)[C], float sL, float sR, float (&F)[C]) {
-  if (sL >= 0.f) {
-#pragma unroll
-    for (int k = 0; k < C; ++k) F[k] = FL[k];
-  } else if (sR < 0.f) {
-#pragma unroll
-    for (int k = 0; k < C; ++k) F[k] = FR[k];
-  } else {
-    const float r = vrcp(vsub(sR, sL));
-#pragma unroll
-    for (int k = 0; k < C; ++k)
-      F[k] = vmul(vadd(vsub(vmul(sR, FL[k]), vmul(sL, FR[k])), vmul(vmul(sL, sR), vsub(R[k], L[k]))), r);
-  }
+  for (int k = 0; k < C; ++k)
+    F[k] = vsub(vmul(vsplat<V>(0.5f), vadd(FL[k], FR[k])), vmul(vsplat<V>(0.5f), D[k]));
 }
 
 // Q_*K = rho_K (s_K - u_K) / (s_K - s_*) [1, s_*, v_K, E_*] (Euler, Toro) or
 // h_K (s_K - u_K) / (s_K - s_*) [1, s_*, v_K] (SWE); F_*K = F_K + s_K (Q_*K - Q_K).
-template <int C, int EQ>
-__device__ __forceinline__ void hllc_star(const float (&Q)[C], const float (&FK)[C], float uK, float pK,
-                                          float sK, float ss, float (&F)[C]) {
-  const float fac = vmul(vmul(Q[0], vsub(sK, uK)), vrcp(vsub(sK, ss)));
-  float S[C];
+template <int C, int EQ, class V>
+__device__ __forceinline__ void hllc_star(const V (&Q)[C], const V (&FK)[C], V uK, V pK, V sK, V ss, V (&F)[C]) {
+  const V fac = vmul(vmul(Q[0], vsub(sK, uK)), vrcp(vsub(sK, ss)));
+  V S[C];
   S[0] = fac;
   S[1] = vmul(fac, ss);
   S[2] = vmul(fac, vmul(Q[2], vrcp(Q[0])));
   if constexpr (EQ == EULER) {
-    const float e = vadd(vmul(Q[3], vrcp(Q[0])),
-                         vmul(vsub(ss, uK), vadd(ss, vmul(pK, vrcp(vmul(Q[0], vsub(sK, uK)))))));
+    const V e = vadd(vmul(Q[3], vrcp(Q[0])), vmul(vsub(ss, uK), vadd(ss, vmul(pK, vrcp(vmul(Q[0], vsub(sK, uK)))))));
     S[3] = vmul(fac, e);
   }
 #pragma unroll
   for (int k = 0; k < C; ++k) F[k] = vadd(FK[k], vmul(sK, vsub(S[k], Q[k])));
 }
 
-// Numerical flux `flux` (not HLL) of two face-frame states; `nu` is the
-// Lax-Friedrichs viscosity of this face's direction.
-template <int C, int EQ>
-__device__ __forceinline__ void scheme_flux(int flux, const float (&L)[C], const float (&R)[C], float phys,
-                                            float nu, float (&F)[C]) {
-  float FL[C], FR[C], uL, cL, pL, uR, cR, pR;
-  frame_state<C, EQ>(L, phys, FL, uL, cL, pL);
-  frame_state<C, EQ>(R, phys, FR, uR, cR, pR);
+// Numerical flux `flux` (not HLL) of two face-frame states, for one face
+// (V = float) or two faces at once (V = float2); `nu` is the Lax-Friedrichs
+// viscosity of this face's direction.  Branches on wave speeds are taken per
+// lane as selects, so both forms give the same value for each face.
+template <int C, int EQ, class V>
+__device__ __forceinline__ void scheme_flux(int flux, const V (&L)[C], const V (&R)[C], float phys, float nu,
+                                            V (&F)[C]) {
+  V FL[C], FR[C], uL, cL, pL, uR, cR, pR;
+  frame_state<C, EQ, V>(L, phys, FL, uL, cL, pL);
+  frame_state<C, EQ, V>(R, phys, FR, uR, cR, pR);
   if (flux == FLUX_LF) {
-    central<C>(FL, FR, L, R, nu, F);
+    central<C, V>(FL, FR, L, R, vsplat<V>(nu), F);
   } else if (flux == FLUX_RUSANOV) {
-    const float s = vmul(0.5f, fmaxf(vadd(fabsf(uL), cL), vadd(fabsf(uR), cR)));
-    central<C>(FL, FR, L, R, s, F);
+    const V s = vmul(vsplat<V>(0.5f), vmax(vadd(vabs(uL), cL), vadd(vabs(uR), cR)));
+    central<C, V>(FL, FR, L, R, s, F);
   } else if (flux == FLUX_ROE) {
-    roe_flux<C, EQ>(L, R, FL, FR, pL, pR, phys, F);
+    roe_flux<C, EQ, V>(L, R, FL, FR, pL, pR, phys, F);
   } else if (flux == FLUX_HLLE) {
-    float u, v, c, H;
-    roe_state<C, EQ>(L, R, phys, u, v, c, H, pL, pR);
-    const float sL = fminf(fminf(vsub(uL, cL), vsub(u, c)), 0.f);
-    const float sR = fmaxf(fmaxf(vadd(uR, cR), vadd(u, c)), 0.f);
-    hll_branches<C>(L, R, FL, FR, sL, sR, F);
+    V u, v, c, H;
+    roe_state<C, EQ, V>(L, R, phys, u, v, c, H, pL, pR);
+    const V zero = vsplat<V>(0.f);
+    const V sL = vmin(vmin(vsub(uL, cL), vsub(u, c)), zero);
+    const V sR = vmax(vmax(vadd(uR, cR), vadd(u, c)), zero);
+    // three branches of Eq. 2.15 with these speeds: F_L if s_L >= 0, F_R if
+    // s_R < 0 (never: s_R >= 0), else the HLL average
+    const V r = vrcp(vsub(sR, sL));
+#pragma unroll
+    for (int k = 0; k < C; ++k) {
+      const V mid = vmul(vadd(vsub(vmul(sR, FL[k]), vmul(sL, FR[k])), vmul(vmul(sL, sR), vsub(R[k], L[k]))), r);
+      F[k] = vsel_ge0(sL, FL[k], mid);
+    }
   } else {   // HLLC
-    const float sL = fminf(vsub(uL, cL), vsub(uR, cR));
-    const float sR = fmaxf(vadd(uL, cL), vadd(uR, cR));
-    float num, den;
+    const V sL = vmin(vsub(uL, cL), vsub(uR, cR));
+    const V sR = vmax(vadd(uL, cL), vadd(uR, cR));
+    V num, den;
     if constexpr (EQ == SWE) {
       num = vsub(vmul(vmul(sL, R[0]), vsub(uR, sR)), vmul(vmul(sR, L[0]), vsub(uL, sL)));
       den = vsub(vmul(R[0], vsub(uR, sR)), vmul(L[0], vsub(uL, sL)));
@@ -176,18 +174,14 @@ __device__ __forceinline__ void scheme_flux(int flux, const float (&L)[C], const
       num = vsub(vadd(vsub(pR, pL), vmul(vmul(L[0], uL), vsub(sL, uL))), vmul(vmul(R[0], uR), vsub(sR, uR)));
       den = vsub(vmul(L[0], vsub(sL, uL)), vmul(R[0], vsub(sR, uR)));
     }
-    const float ss = vmul(num, vrcp(den));
-    if (sL >= 0.f) {
+    const V ss = vmul(num, vrcp(den));
+    V FsL[C], FsR[C];
+    hllc_star<C, EQ, V>(L, FL, uL, pL, sL, ss, FsL);
+    hllc_star<C, EQ, V>(R, FR, uR, pR, sR, ss, FsR);
+    // F_L if s_L >= 0, F*_L if s_* >= 0, F*_R if s_R > 0, else F_R
 #pragma unroll
-      for (int k = 0; k < C; ++k) F[k] = FL[k];
-    } else if (ss >= 0.f) {
-      hllc_star<C, EQ>(L, FL, uL, pL, sL, ss, F);
-    } else if (sR > 0.f) {
-      hllc_star<C, EQ>(R, FR, uR, pR, sR, ss, F);
-    } else {
-#pragma unroll
-      for (int k = 0; k < C; ++k) F[k] = FR[k];
-    }
+    for (int k = 0; k < C; ++k)
+      F[k] = vsel_ge0(sL, FL[k], vsel_ge0(ss, FsL[k], vsel_gt0(sR, FsR[k], FR[k])));
   }
 }
 

@@ -212,7 +212,7 @@ __device__ __forceinline__ void cp_async_wait() {
 // Face flux in the x frame / in the rotated y frame (normal momentum =
 // component 2), for scalars or packed pairs.  GEN: the flux is chosen at run
 // time (`flux`, fvk::Flux; `nu` the Lax-Friedrichs viscosity of the face's
-// direction); fluxes other than HLL are evaluated per cell.
+// direction), packed like the HLL path.
 template <int C, int EQ, class V, bool GEN>
 __device__ __forceinline__ void normal_flux_any(const V (&L)[C], const V (&R)[C], float phys, int flux,
                                                 float nu, V (&F)[C]) {
@@ -222,19 +222,8 @@ __device__ __forceinline__ void normal_flux_any(const V (&L)[C], const V (&R)[C]
     } else {
       hll_euler<V>(L, R, phys, F);
     }
-  } else if constexpr (sizeof(V) == sizeof(float)) {
-    scheme_flux<C, EQ>(flux, L, R, phys, nu, F);
   } else {
-    float l0[C], r0[C], f0[C], l1[C], r1[C], f1[C];
-#pragma unroll
-    for (int c = 0; c < C; ++c) {
-      l0[c] = L[c].x; r0[c] = R[c].x;
-      l1[c] = L[c].y; r1[c] = R[c].y;
-    }
-    scheme_flux<C, EQ>(flux, l0, r0, phys, nu, f0);
-    scheme_flux<C, EQ>(flux, l1, r1, phys, nu, f1);
-#pragma unroll
-    for (int c = 0; c < C; ++c) F[c] = make_float2(f0[c], f1[c]);
+    scheme_flux<C, EQ, V>(flux, L, R, phys, nu, F);
   }
 }
 
