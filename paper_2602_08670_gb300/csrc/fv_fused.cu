@@ -26,8 +26,12 @@
 // stream's tick while the CUDA cores drain the other's.
 //
 // Threads: warpgroups 0 and 1 drain TMEM (each thread one TMEM lane = one
-// column) and compute the faces; warpgroup 2 updates the finished row and
-// stages state rows, except its first warp, whose first lane issues the MMAs.
+// column) and compute the faces, and warpgroup 0 updates the finished row
+// while it waits for the MMAs; warpgroup 2's first warp issues the MMAs (one
+// lane), its other three warps stage the state rows and the layer-1 input and
+// place the halo columns received from the neighbours.  They hand work to
+// each other through mbarriers (see `phase`), not through block or cluster
+// barriers.
 //
 // Layers 2-4 keep two input rows and two adjacent accumulators each: slot 0
 // holds the row started at the previous tick (taps ky = 0 and 1 summed), slot
@@ -39,8 +43,8 @@
 // order as the two-pass CNN.  Layer 1 reads the three x taps of the state
 // gathered into one K = 16 operand (9 used channels) and sums three dy taps.
 // The 1-cell x halo of every hidden layer comes from the neighbouring CTA of
-// the cluster (distributed shared memory; the periodic wrap for CS = 1), and
-// so does the flux through the west face of column 0.
+// the cluster (asynchronous distributed-shared-memory copies; the periodic
+// wrap for CS = 1), and so does the flux through the west face of column 0.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
