@@ -96,6 +96,35 @@ def test_tile_kernel_matches_oracle(fv, flux, rk, eq):
         check(rel_errors(q, qr), [(max(l2, 5 * y2), max(li, 5 * yi)) for (l2, li), (y2, yi) in zip(tols, yard)])
 
 
+@pytest.mark.parametrize("eq", [ofv.SWE, ofv.EULER])
+@pytest.mark.parametrize("ny,nx", [(12, 8), (6, 516)])
+def test_march_edges_match_oracle(fv, eq, ny, nx):
+    """Row-march kernels at the narrowest strip (nx = 8, wrap on both sides of
+    one strip) and with a ragged last strip (nx = 516 = 512 + 4 columns), for
+    Roe with SSP-RK2 and HLLC with SSP-RK3."""
+    rng = np.random.default_rng(nx + ny)
+    if eq == ofv.SWE:
+        q0 = np.zeros((2, 3, ny, nx))
+        q0[:, 0] = 1.0 + 0.1 * rng.random((2, ny, nx))
+        q0[:, 1:] = 0.05 * rng.standard_normal((2, 2, ny, nx))
+        tols = [TOL_O1, TOL_SMALL, TOL_SMALL]
+    else:
+        q0 = np.zeros((2, 4, ny, nx))
+        q0[:, 0] = 1.0 + 0.2 * rng.random((2, ny, nx))
+        q0[:, 1:3] = 0.1 * rng.standard_normal((2, 2, ny, nx))
+        q0[:, 3] = 2.5 + 0.5 * (q0[:, 1] ** 2 + q0[:, 2] ** 2) / q0[:, 0]
+        tols = [TOL_O1, TOL_SMALL, TOL_SMALL, TOL_O1]
+    q0 = W.as_f32_exact(q0)
+    for flux, rk in (("roe", 2), ("hllc", 3)):
+        # member 0's adaptive dt sequence, replayed for both members
+        _, _, dts = S.run(torch.tensor(q0[:1]), eq, 20, flux=flux, rk=rk)
+        qr, _, dts = S.run(torch.tensor(q0), eq, 20, flux=flux, rk=rk, dt_mode=ofv.DT_REPLAY,
+                           dts=dts[:, 0])
+        q, _ = gpu_replay(fv, q0, eq, dts[:, 0].numpy(), 20, flux, rk, "march")
+        yard = fp32_yardstick(q0, eq, dts, flux, rk, qr)
+        check(rel_errors(q, qr), [(max(l2, 5 * y2), max(li, 5 * yi)) for (l2, li), (y2, yi) in zip(tols, yard)])
+
+
 @pytest.mark.parametrize("flux", ["rusanov", "lf", "roe", "hlle", "hllc"])
 def test_tile_and_march_agree(fv, flux):
     """Both kernels evaluate the same formulas per face and per cell: after
