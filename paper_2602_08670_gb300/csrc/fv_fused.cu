@@ -97,13 +97,14 @@ constexpr int STREAM_BYTES = OFF_RAW + 3 * RAWF * 4;
 
 constexpr int W1_BYTES = snk::W1G_ELEMS * 2;                       // 3072
 constexpr int WH_BYTES = 9 * snk::CG_HID * snk::HID * 16;          // 18432
-constexpr int W4_BYTES = 9 * snk::CG_HID * snk::N_OUT_PAD * 16;    // 27648
+constexpr int W4_BYTES = snk::W4R_ELEMS * 2;                       // 24576
 constexpr int OFF_W1 = 0;
 constexpr int OFF_W2 = OFF_W1 + W1_BYTES;
 constexpr int OFF_W3 = OFF_W2 + WH_BYTES;
 constexpr int OFF_W4 = OFF_W3 + WH_BYTES;
 constexpr int OFF_STREAMS = OFF_W4 + W4_BYTES;
-constexpr int N_BIAS = 3 * snk::HID + snk::N_OUT;
+// biases of layers 1..3, then of layer 4's 24 differences (b[3 s + j] - b[3 s + 2])
+constexpr int N_BIAS = 3 * snk::HID + snk::W4R_BLOCK;
 constexpr int OFF_BIAS = OFF_STREAMS + 2 * STREAM_BYTES;
 // mbarriers: [0..1] MMAs of stream s done, [2..3] inputs of the next tick of
 // stream s ready, [4..7] tick n of stream s done (index 4 + 2 s + (n & 1)),
@@ -119,10 +120,14 @@ static_assert(SMEM_BYTES <= 232448, "shared memory per CTA");
 // TMEM columns of one stream (two streams: 2 x 256 = 512)
 constexpr uint32_t TCOLS = 512;
 constexpr uint32_t ACC1 = 0;
-// layer 0..2 = layers 2..4; slot 0 and slot 1 are adjacent
-__host__ __device__ constexpr uint32_t acc_col(int layer, int slot) {
-  return layer < 2 ? 32u + 64u * layer + 32u * slot : 160u + 48u * slot;
-}
+// layer 0..1 = layers 2..3; slot 0 and slot 1 are adjacent
+__host__ __device__ constexpr uint32_t acc_col(int layer, int slot) { return 32u + 64u * layer + 32u * slot; }
+// Layer 4: a ring of three 24-column slots (the 24 stencil differences of
+// one output row each), then 8 columns that the 80-wide MMAs also write and
+// nothing reads.  The row completed at tick n of a stream is in slot n % 3.
+constexpr uint32_t ACC4 = 160;
+constexpr uint32_t R4 = snk::W4R_BLOCK;                // 24
+constexpr uint32_t N4 = 3 * R4 + 8;                    // 80 (N multiple of 16)
 
 struct Args {
   const float* qin;
@@ -222,6 +227,12 @@ __device__ __forceinline__ void tmem_st8(uint32_t taddr, const float (&v)[8]) {
                ::"r"(taddr), "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])),
                  "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])),
                  "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7]))
+               : "memory");
+}
+__device__ __forceinline__ void tmem_st4(uint32_t taddr, const float (&v)[4]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};\n" ::"r"(taddr),
+               "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+               "r"(__float_as_uint(v[3]))
                : "memory");
 }
 __device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16]) {
@@ -401,45 +412,45 @@ __device__ __forceinline__ void drain_hidden(uint32_t taddr, const float* bias, 
   }
 }
 
-// The 18 normalised coefficients of one direction (dir 0: channels 0..17 = x,
-// dir 1: 18..35 = y) of this lane's cell: w = e_centre + r - mean(r) per
-// 3-tap stencil, as in the two-pass CNN's epilogue.
-__device__ __forceinline__ void drain_coeffs(uint32_t taddr, const float* bias, int dir,
-                                             float (&wd)[18]) {
-  // columns 16 dir .. 16 dir + 19 hold the channels 18 dir .. 18 dir + 17
-  float v16[16], v4[4];
-  tc::tmem_ld16(taddr + 16 * dir, v16);
-  tmem_ld4(taddr + 16 + 16 * dir, v4);
-  float r[18];
-#pragma unroll
-  for (int k = 0; k < 18; ++k) {
-    const float x = k < 16 ? v16[k] : v4[k - 16];
-    const float y = k < 14 ? v16[2 + k] : v4[k - 14];
-    r[k] = (dir ? y : x) + bias[18 * dir + k];
-  }
+// The 18 normalised coefficients of one direction (dir 0: stencils 0..5 =
+// x, dir 1: 6..11 = y) of this lane's cell from the layer-4 ring slot `taddr`:
+// per 3-tap stencil the raw outputs r enter only through r - mean(r), which
+// the differences s1 = r0 - r2, s2 = r1 - r2 (+ their biases) determine:
+//   r0 - m = (2 s1 - s2) / 3,  r1 - m = (2 s2 - s1) / 3,  r2 - m = -(s1 + s2) / 3,
+// and w = e_centre + r - mean(r) as in the two-pass CNN's epilogue.
+__device__ __forceinline__ void drain_coeffs(uint32_t taddr, const float* bias, int dir, float (&wd)[18]) {
+  // columns 8 dir .. 8 dir + 15 (differences 12 dir .. 12 dir + 11 used)
+  float v[16];
+  tc::tmem_ld16(taddr + 8 * dir, v);
+  const float third = 1.f / 3.f;
 #pragma unroll
   for (int s = 0; s < 6; ++s) {
-    const float mean = (r[3 * s] + r[3 * s + 1] + r[3 * s + 2]) * (1.f / 3.f);
-    wd[3 * s] = r[3 * s] - mean;
-    wd[3 * s + 1] = 1.f + (r[3 * s + 1] - mean);
-    wd[3 * s + 2] = r[3 * s + 2] - mean;
+    const float x1 = dir ? v[4 + 2 * s] : v[2 * s];
+    const float x2 = dir ? v[5 + 2 * s] : v[2 * s + 1];
+    const float s1 = x1 + bias[12 * dir + 2 * s];
+    const float s2 = x2 + bias[12 * dir + 2 * s + 1];
+    wd[3 * s] = (2.f * s1 - s2) * third;
+    wd[3 * s + 1] = 1.f + (2.f * s2 - s1) * third;
+    wd[3 * s + 2] = -(s1 + s2) * third;
   }
 }
 
 // Once every slot-0 read of the tick is done: the row started this tick
-// (slot 1) becomes the row to complete next tick (slot 0), for layers 2..4.
-// Warpgroup 0 moves columns 0-15 (and 32-39 of layer 4), warpgroup 1 columns
-// 16-31 (and 40-47), each thread its own TMEM lane.
-__device__ __forceinline__ void move_slots(uint32_t tm, int wg) {
+// (slot 1) becomes the row to complete next tick (slot 0), for layers 2 and
+// 3 (warpgroup 0 moves columns 0-15, warpgroup 1 columns 16-31, each thread
+// its own TMEM lane), and the layer-4 ring slot drained in this tick is
+// cleared (warpgroup 0 its columns 0-11, warpgroup 1 12-23): the next tick's
+// MMAs start a new row in it by accumulating.
+__device__ __forceinline__ void move_slots(uint32_t tm, uint32_t ring_slot, int wg) {
 #pragma unroll
-  for (int l = 0; l < 3; ++l) {
+  for (int l = 0; l < 2; ++l) {
     float v[16];
     tc::tmem_ld16(tm + acc_col(l, 1) + 16 * wg, v);
     tmem_st16(tm + acc_col(l, 0) + 16 * wg, v);
   }
-  float v8[8];
-  tmem_ld8(tm + acc_col(2, 1) + 32 + 8 * wg, v8);
-  tmem_st8(tm + acc_col(2, 0) + 32 + 8 * wg, v8);
+  const float z8[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, z4[4] = {0.f, 0.f, 0.f, 0.f};
+  tmem_st8(ring_slot + 12 * wg, z8);
+  tmem_st4(ring_slot + 12 * wg + 8, z4);
   asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
 }
 
@@ -503,7 +514,8 @@ __device__ __forceinline__ void segment_prologue(const Stream& S, uint8_t* sbuf,
 // below 256 KB, so the field never overflows).
 struct Descs {
   uint64_t a_l1, a_in, b_w1;
-  uint64_t b_ky0[3], b_pair[3];   // layers 2..4: taps ky = 0, and ky = 2 | ky = 1 stacked
+  uint64_t b_ky0[2], b_pair[2];   // layers 2..3: taps ky = 0, and ky = 2 | ky = 1 stacked
+  uint64_t b_ring;                // layer 4: tap blocks ky = 2, 1, 0, 2, 1
 };
 __device__ __forceinline__ uint64_t dplus(uint64_t d, uint32_t bytes) { return d + (bytes >> 4); }
 
@@ -524,33 +536,39 @@ __device__ __forceinline__ void mma_lo(uint32_t d_tmem, uint32_t a_lo, uint32_t 
 // All MMAs of one tick of one stream (issued by one thread), then a commit
 // to the stream's mbarrier in this CTA and its neighbours; `tm`: the
 // stream's first TMEM column.
-__device__ __forceinline__ void issue_tick(const Descs& D, uint32_t tm, int tau, uint64_t* mbar,
+__device__ __forceinline__ void issue_tick(const Descs& D, uint32_t tm, int tau, uint32_t nt, uint64_t* mbar,
                                            uint16_t mask) {
   constexpr uint32_t id32 = tc::idesc_bf16_f32(W, snk::HID);
-  constexpr uint32_t id48 = tc::idesc_bf16_f32(W, snk::N_OUT_PAD);
   constexpr uint32_t id64 = tc::idesc_bf16_f32(W, 2 * snk::HID);
-  constexpr uint32_t id96 = tc::idesc_bf16_f32(W, 2 * snk::N_OUT_PAD);
+  constexpr uint32_t id80 = tc::idesc_bf16_f32(W, N4);
   // layers 2..4: new input row in slot (tau+1)&1, previous one in slot tau&1
   const uint32_t s_new = (uint32_t)((tau + 1) & 1), s_prev = (uint32_t)(tau & 1);
   // low descriptor words (start address in 16-byte units in bits 0-13)
   const uint32_t in_lo = (uint32_t)D.a_in, l1_lo = (uint32_t)D.a_l1, w1_lo = (uint32_t)D.b_w1;
-  uint32_t a_new[3], a_prev[3], b0[3], bp[3];
+  uint32_t a_new[3], a_prev[2], b0[2], bp[2];
 #pragma unroll
-  for (int l = 0; l < 3; ++l) {
-    a_new[l] = in_lo + (((uint32_t)(l * 2 * HID_SLOT) + s_new * HID_SLOT) >> 4);
+  for (int l = 0; l < 3; ++l) a_new[l] = in_lo + (((uint32_t)(l * 2 * HID_SLOT) + s_new * HID_SLOT) >> 4);
+#pragma unroll
+  for (int l = 0; l < 2; ++l) {
     a_prev[l] = in_lo + (((uint32_t)(l * 2 * HID_SLOT) + s_prev * HID_SLOT) >> 4);
     b0[l] = (uint32_t)D.b_ky0[l];
     bp[l] = (uint32_t)D.b_pair[l];
   }
-  // Steps 0-5: layer 1 (taps ky on input rows t-2, t-1, t) and the taps
-  // ky = 0 on the previous row into slot 1; steps 6-11: the stacked taps
-  // ky = 2 | ky = 1 on the new row into slot 0 | slot 1.  Layers are
+  // Layer 4's window covers ring slots 0, 1, 2; slot nt % 3 completes its row
+  // (tap ky = 2), slot (nt + 1) % 3 adds ky = 1, slot (nt + 2) % 3 starts a
+  // row (ky = 0): tap blocks 2,1,0 / 0,2,1 / 1,0,2 start at block 0 / 2 / 1.
+  const uint32_t r3 = nt % 3u;
+  const uint32_t ring_lo = (uint32_t)D.b_ring + (r3 == 0 ? 0u : (r3 == 1 ? 2u : 1u)) * R4;
+  // Steps 0-5: layer 1 (taps ky on input rows t-2, t-1, t) and, for layers 2
+  // and 3, the taps ky = 0 on the previous row into slot 1; steps 6-11: the
+  // stacked taps ky = 2 | ky = 1 on the new row into slot 0 | slot 1, and
+  // layer 4's three stacked taps on its new row into the ring.  Layers are
   // interleaved so that consecutive MMAs target different accumulators.
   // accumulator columns of this stream
-  const uint32_t d1 = tm + ACC1;
-  uint32_t dn[3], dc[3];
+  const uint32_t d1 = tm + ACC1, d4 = tm + ACC4;
+  uint32_t dn[2], dc[2];
 #pragma unroll
-  for (int l = 0; l < 3; ++l) {
+  for (int l = 0; l < 2; ++l) {
     dn[l] = tm + acc_col(l, 1);
     dc[l] = tm + acc_col(l, 0);
   }
@@ -563,26 +581,20 @@ __device__ __forceinline__ void issue_tick(const Descs& D, uint32_t tm, int tau,
       if (i == 0) mma_lo<false, id32>(d1, a, b);
       else mma_lo<true, id32>(d1, a, b);
     }
+    const int j = i % 6, kx = j / 2, ks = j % 2;
+    const uint32_t aoff = (uint32_t)(2 * ks * FP + kx);   // 16-byte units
 #pragma unroll
-    for (int l = 0; l < 3; ++l) {
-      const uint32_t N = l == 2 ? snk::N_OUT_PAD : snk::HID;
-      const int j = i % 6, kx = j / 2, ks = j % 2;
-      const uint32_t aoff = (uint32_t)(2 * ks * FP + kx);   // 16-byte units
+    for (int l = 0; l < 2; ++l) {
+      constexpr uint32_t N = snk::HID;
       if (i < 6) {
         const uint32_t b = b0[l] + (uint32_t)((kx * 4 + 2 * ks) * N);
-        if (l == 2) {
-          if (i == 0) mma_lo<false, id48>(dn[l], a_prev[l] + aoff, b);
-          else mma_lo<true, id48>(dn[l], a_prev[l] + aoff, b);
-        } else {
-          if (i == 0) mma_lo<false, id32>(dn[l], a_prev[l] + aoff, b);
-          else mma_lo<true, id32>(dn[l], a_prev[l] + aoff, b);
-        }
+        if (i == 0) mma_lo<false, id32>(dn[l], a_prev[l] + aoff, b);
+        else mma_lo<true, id32>(dn[l], a_prev[l] + aoff, b);
       } else {
-        const uint32_t b = bp[l] + (uint32_t)((kx * 4 + 2 * ks) * 2 * N);
-        if (l == 2) mma_lo<true, id96>(dc[l], a_new[l] + aoff, b);
-        else mma_lo<true, id64>(dc[l], a_new[l] + aoff, b);
+        mma_lo<true, id64>(dc[l], a_new[l] + aoff, bp[l] + (uint32_t)((kx * 4 + 2 * ks) * 2 * N));
       }
     }
+    if (i >= 6) mma_lo<true, id80>(d4, a_new[2] + aoff, ring_lo + (uint32_t)((kx * 4 + 2 * ks) * snk::W4R_ROWS));
   }
   // completion is signalled to this CTA and to its neighbours, which write
   // into the rows these MMAs read only after it
@@ -862,9 +874,10 @@ __device__ __forceinline__ void phase(Stream& M, Stream& E, const Args& a, Ctx& 
       // and 1 send the halos
       asm volatile("bar.sync 2, %0;" ::"n"(EPI_THREADS) : "memory");
       if (ok && X.tid < 2) send_halos(sbuf, &X.mbar[8 + es], X);
-      if (ok) drain_coeffs(tm + acc_col(2, 0), X.bias + 3 * snk::HID, X.wg, wd);
+      const uint32_t ring_slot = tm + ACC4 + R4 * (E.nt % 3u);
+      if (ok) drain_coeffs(ring_slot, X.bias + 3 * snk::HID, X.wg, wd);
       asm volatile("bar.sync 1, %0;" ::"n"(EPI_THREADS) : "memory");   // slot-0 reads of both warpgroups done
-      if (ok) move_slots(tm, X.wg);
+      if (ok) move_slots(tm, ring_slot, X.wg);
       if (!seg_end) warp_arrive(ready, 0, false);
       if (ok) epilogue_faces(E, sbuf, a, X, done, wd);
       warp_arrive(done, 0, false);
@@ -930,7 +943,7 @@ __device__ __forceinline__ bool issuer_phase(Stream& M, Stream& E, const Args& a
             D.a_l1 = dplus(D.a_l1, STREAM_BYTES);
             D.a_in = dplus(D.a_in, STREAM_BYTES);
           }
-          issue_tick(D, X.tmem + 256u * ms, M.tau, &X.mbar[ms], X.commit_mask);
+          issue_tick(D, X.tmem + 256u * ms, M.tau, M.nt, &X.mbar[ms], X.commit_mask);
         }
         __syncwarp();
       } else {
@@ -1005,8 +1018,13 @@ __global__ void __launch_bounds__(NT, 1) learned_fused_kernel(Args a) {
   }
   for (int i = X.tid; i < W4_BYTES / 16; i += NT) cp_async16(smem + OFF_W4 + i * 16, a.w4 + i * 8);
   for (int i = X.tid; i < N_BIAS; i += NT) {
-    const int l = i / snk::HID < 3 ? i / snk::HID : 3;
-    bias[i] = a.params[a.bias_off[l] + (i - l * snk::HID)];
+    if (i < 3 * snk::HID) {
+      bias[i] = a.params[a.bias_off[i / snk::HID] + i % snk::HID];
+    } else {
+      // layer 4: b[3 s + j] - b[3 s + 2] for difference 2 s + j
+      const int d = i - 3 * snk::HID, st = d / 2, jj = d % 2;
+      bias[i] = a.params[a.bias_off[3] + 3 * st + jj] - a.params[a.bias_off[3] + 3 * st + 2];
+    }
   }
 
   // the two streams of this cluster and their first segments
@@ -1033,11 +1051,27 @@ __global__ void __launch_bounds__(NT, 1) learned_fused_kernel(Args a) {
   X.D.a_in = tc::sdesc(sb + OFF_STREAMS + OFF_IN, FP * 16, 128);
   X.D.b_w1 = tc::sdesc(sb + OFF_W1, snk::HID * 16, 128);
 #pragma unroll
-  for (int l = 0; l < 3; ++l) {
-    const uint32_t N = l == 2 ? snk::N_OUT_PAD : snk::HID;
-    const uint32_t wl = sb + (l == 0 ? OFF_W2 : l == 1 ? OFF_W3 : OFF_W4);
+  for (int l = 0; l < 2; ++l) {
+    constexpr uint32_t N = snk::HID;
+    const uint32_t wl = sb + (l == 0 ? OFF_W2 : OFF_W3);
     X.D.b_ky0[l] = tc::sdesc(wl, N * 16, 128);
     X.D.b_pair[l] = tc::sdesc(wl + 3 * snk::CG_HID * N * 16, 2 * N * 16, 128);
+  }
+  X.D.b_ring = tc::sdesc(sb + OFF_W4, snk::W4R_ROWS * 16, 128);
+  if (X.wg < 2) {
+    // layer 4's ring slots start cleared (its MMAs only accumulate):
+    // warpgroup 0 columns 0-39, warpgroup 1 40-79 of each stream's ring
+    const float z16[16] = {};
+    const float z8[8] = {};
+#pragma unroll
+    for (int st = 0; st < 2; ++st) {
+      const uint32_t base = X.tmem + 256u * st + X.lane_off + ACC4 + 40u * X.wg;
+      tmem_st16(base, z16);
+      tmem_st16(base + 16, z16);
+      tmem_st8(base + 32, z8);
+    }
+    asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
+    tc::fence_before_sync();
   }
   // every CTA of the cluster is running (and its mbarriers initialised)
   // before any remote store or multicast arrival
@@ -1149,7 +1183,7 @@ cudaError_t launch_learned_fused(const Geom& g, int stage, const float* qin, con
   a.w1g = net.w1g;
   a.w2 = net.wpair[1];
   a.w3 = net.wpair[2];
-  a.w4 = net.wpair[3];
+  a.w4 = net.w4ring;
   a.params = net.params;
   for (int l = 0; l < 4; ++l) a.bias_off[l] = L.b[l];
   for (int c = 0; c < 3; ++c) {

@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(NT) conv_kernel(ConvArgs a) {
 __global__ void repack_kernel(const float* params, ParamLayout L, uint16_t* wf0, uint16_t* wf1,
                               uint16_t* wf2, uint16_t* wf3, uint16_t* wb1, uint16_t* wb2,
                               uint16_t* wb3, uint16_t* w1g, uint16_t* wp1, uint16_t* wp2,
-                              uint16_t* wp3) {
+                              uint16_t* w4r) {
   uint16_t* wf[4] = {wf0, wf1, wf2, wf3};
   uint16_t* wb[4] = {nullptr, wb1, wb2, wb3};
   const int cgs[4] = {CG_IN0, CG_HID, CG_HID, CG_HID};
@@ -264,10 +264,28 @@ __global__ void repack_kernel(const float* params, ParamLayout L, uint16_t* wf0,
     const __nv_bfloat16 h = __float2bfloat16_rn(v);
     w1g[i] = *reinterpret_cast<const uint16_t*>(&h);
   }
-  uint16_t* wp[4] = {nullptr, wp1, wp2, wp3};
-  for (int l = 1; l < 4; ++l) {
+  if (i < W4R_ELEMS) {
+    // w4ring[kx][g][n][k8]: block n / 24 holds the tap ky = 2, 1, 0, 2, 1; row
+    // r = n % 24 = 2 s + j the difference W_4[3 s + j] - W_4[3 s + 2]
+    const int k8 = i % 8, n = (i / 8) % W4R_ROWS, g = (i / (8 * W4R_ROWS)) % CG_HID,
+              kx = i / (8 * W4R_ROWS * CG_HID);
+    const int ci = 8 * g + k8;
+    float v = 0.f;
+    if (n < 5 * W4R_BLOCK && ci < L.cin[3]) {
+      const int blk = n / W4R_BLOCK, r = n % W4R_BLOCK;
+      const int ky = blk == 2 ? 0 : (blk == 1 || blk == 4 ? 1 : 2);
+      const int s = r / 2, j = r % 2;
+      const int ca = 3 * s + j, cc = 3 * s + 2;
+      v = params[L.w[3] + ((ca * L.cin[3] + ci) * 3 + ky) * 3 + kx] -
+          params[L.w[3] + ((cc * L.cin[3] + ci) * 3 + ky) * 3 + kx];
+    }
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    w4r[i] = *reinterpret_cast<const uint16_t*>(&h);
+  }
+  uint16_t* wp[3] = {nullptr, wp1, wp2};
+  for (int l = 1; l < 3; ++l) {
     // [ky = 0: kx][g][n][k8], then [kx][g][ky = 2 | ky = 1][k8]
-    const int N = l == 3 ? N_OUT_PAD : HID;
+    const int N = HID;
     const int part0 = 3 * CG_HID * N * 8;
     if (i < 9 * CG_HID * N * 8) {
       int kx, g, n, k8, ky;
@@ -347,9 +365,10 @@ int backward_groups(int cout) {
 cudaError_t repack(Net& net, cudaStream_t s) {
   const ParamLayout L = param_layout();
   const int maxn = 9 * CG_HID * N_OUT_PAD * 8 > 9 * 6 * HID * 8 ? 9 * CG_HID * N_OUT_PAD * 8 : 9 * 6 * HID * 8;
+  static_assert(W4R_ELEMS <= 9 * CG_HID * N_OUT_PAD * 8, "repack grid covers the layer-4 ring weights");
   repack_kernel<<<(maxn + 255) / 256, 256, 0, s>>>(net.params, L, net.wf[0], net.wf[1], net.wf[2],
                                                    net.wf[3], net.wb[1], net.wb[2], net.wb[3],
-                                                   net.w1g, net.wpair[1], net.wpair[2], net.wpair[3]);
+                                                   net.w1g, net.wpair[1], net.wpair[2], net.w4ring);
   return cudaGetLastError();
 }
 
@@ -749,8 +768,9 @@ int net_alloc(fv_net* n) {
       return fvh::cuda_fail(e, "cudaMalloc(wb)");
   }
   if ((e = cudaMalloc(&N.w1g, 2 * snk::W1G_ELEMS)) != cudaSuccess) return fvh::cuda_fail(e, "cudaMalloc(w1g)");
-  for (int l = 1; l < 4; ++l)
+  for (int l = 1; l < 3; ++l)
     if ((e = cudaMalloc(&N.wpair[l], 2 * fsz[l])) != cudaSuccess) return fvh::cuda_fail(e, "cudaMalloc(wpair)");
+  if ((e = cudaMalloc(&N.w4ring, 2 * snk::W4R_ELEMS)) != cudaSuccess) return fvh::cuda_fail(e, "cudaMalloc(w4ring)");
   if ((e = cudaMalloc(&N.err, sizeof(unsigned))) != cudaSuccess) return fvh::cuda_fail(e, "cudaMalloc(err)");
   if ((e = cudaMemset(N.err, 0, sizeof(unsigned))) != cudaSuccess) return fvh::cuda_fail(e, "cudaMemset");
   if ((e = cudaStreamCreateWithFlags(&n->stream, cudaStreamNonBlocking)) != cudaSuccess)
@@ -767,7 +787,8 @@ void net_free(fv_net* n) {
     cudaFree(n->n.wb[l]);
   }
   cudaFree(n->n.w1g);
-  for (int l = 1; l < 4; ++l) cudaFree(n->n.wpair[l]);
+  for (int l = 1; l < 3; ++l) cudaFree(n->n.wpair[l]);
+  cudaFree(n->n.w4ring);
   cudaFree(n->n.err);
   cudaFree(n->adam_m);
   cudaFree(n->adam_v);

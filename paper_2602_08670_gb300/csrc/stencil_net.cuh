@@ -38,9 +38,14 @@ struct Net {
   uint16_t* wb[4] = {};        // backward (dX) B operands, BF16 [9][CG_out][N_in][8], layers 1..3
   uint16_t* w1g = nullptr;     // layer 1 with the three x taps gathered into K, BF16
                                // [ky][2][HID][8]: channel c = 3 kx + var (c < 9, rest 0)
-  uint16_t* wpair[4] = {};     // layers 2..4 for the row-pipelined kernel, BF16: the taps
+  uint16_t* wpair[3] = {};     // layers 2..3 for the row-pipelined kernel, BF16: the taps
                                // ky = 0 as [kx][4][N][8], then ky = 2 and ky = 1 stacked
                                // along N as [kx][4][2N][8] (rows n < N: ky = 2)
+  uint16_t* w4ring = nullptr;  // layer 4 for the row-pipelined kernel, BF16 [kx][4][128][8]:
+                               // per 3-tap stencil s (12 of them, output channels 3 s + j)
+                               // the differences W[3 s] - W[3 s + 2], W[3 s + 1] - W[3 s + 2]
+                               // (rows 2 s, 2 s + 1 of a 24-row block), blocks of the taps
+                               // ky = 2, 1, 0, 2, 1 (rows 0..119), rows 120..127 zero
   float mean[3] = {0, 0, 0};
   float std_[3] = {1, 1, 1};
   unsigned* err = nullptr;     // device error word (bounded waits that gave up)
@@ -54,6 +59,9 @@ struct Acts {
 
 bool grid_supported(int nx);   // nx % 128 == 0, or nx in {8, 16, 32, 64}
 constexpr int W1G_ELEMS = 3 * 2 * HID * 8;
+constexpr int W4R_BLOCK = 24;        // rows of one tap in w4ring: 12 stencils x 2 differences
+constexpr int W4R_ROWS = 128;        // 5 tap blocks + 8 zero rows
+constexpr int W4R_ELEMS = 3 * CG_HID * W4R_ROWS * 8;
 
 // Pack the FP32 master parameters into the BF16 MMA operand layouts.
 cudaError_t repack(Net& net, cudaStream_t s);

@@ -86,12 +86,18 @@ def test_fused_zero_network_is_first_order(fv):
 
 @pytest.mark.parametrize("ny,nx,B", [(128, 128, 3), (48, 256, 5), (16, 1024, 1), (3, 128, 1), (1, 256, 2)])
 def test_fused_matches_two_pass(fv, ny, nx, B):
+    """The two GPU paths agree to the BF16 rounding of the last layer's
+    weights: the fused kernel evaluates the last layer in difference form
+    (W[3s+j] - W[3s+2], rounded to BF16 once, Section 2.5.3's normalisation
+    depends on r only through these differences), the two-pass path the 36
+    raw outputs; each is as close to the oracle as the other (about 1e-5 in
+    the momenta after 12 steps), so they agree to a few times that."""
     p = rand_params(8)
     net = gpu_net(fv, p)
     q0 = swe_state(ny, nx, 17, B)
     _, qf = run_gpu(fv, q0, net, 12, "fused")
     _, qt = run_gpu(fv, q0, net, 12, "two_pass")
-    assert_close(qf, qt, 1e-5, 1e-4)
+    assert_close(qf, qt, 5e-5, 2e-4)
 
 
 def test_fused_adaptive_dt_closes_every_member(fv):
