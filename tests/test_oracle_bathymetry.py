@@ -1,0 +1,143 @@
+"""Pins of the FP64 oracle of the bed-slope source (Eq. 2.3) and reflecting
+walls (``oracle.bathymetry``): each would fail under a plausible mistake (a
+sign, a stencil offset, a wall that transmits instead of reflecting)."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import bathymetry as OB
+from oracle import fv as ofv
+from oracle import riemann
+from oracle import schemes as S
+
+G = 9.81
+
+
+def random_state(B, ny, nx, seed):
+    g = torch.Generator().manual_seed(seed)
+    q = torch.zeros(B, 3, ny, nx, dtype=torch.float64)
+    q[:, 0] = 1.0 + 0.2 * torch.rand(B, ny, nx, generator=g)
+    q[:, 1:] = 0.1 * torch.randn(B, 2, ny, nx, generator=g)
+    return q
+
+
+@pytest.mark.parametrize("flux", S.FLUXES)
+def test_flat_periodic_is_the_plain_scheme(flux):
+    """No bed, periodic: the padded formulation is the periodic oracle, bit
+    for bit, for every flux."""
+    q = random_state(2, 12, 16, 1)
+    dx, dy = ofv.grid_spacing(q)
+    dt = torch.tensor([1e-3, 2e-3], dtype=torch.float64)
+    a = OB.rhs(q, dx, dy, flux=flux, dt=dt)
+    b = S.rhs(q, ofv.SWE, dx, dy, flux, dt)
+    assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("flux", [S.HLL, S.ROE, S.LAX_FRIEDRICHS])
+@pytest.mark.parametrize("axis", ["x", "y"])
+def test_lake_at_rest_on_a_linear_bed_balances(flux, axis):
+    """A flat water surface over a bed that is linear along one axis: away
+    from the walls the pressure-flux difference and the centred bed slope
+    cancel exactly (MUSCL-minmod reconstructs linear data, equal face states
+    have no flux dissipation); a sign error in the source doubles it."""
+    n = 24
+    c = (np.arange(n) + 0.5) / n
+    z1 = 0.3 * c - 0.1
+    z = torch.tensor(np.tile(z1, (n, 1)) if axis == "x" else np.tile(z1[:, None], (1, n)))
+    q = torch.zeros(1, 3, n, n, dtype=torch.float64)
+    q[:, 0] = 1.0 - z
+    dx, dy = ofv.grid_spacing(q)
+    L = OB.rhs(q, dx, dy, flux=flux, z=z, bc=OB.WALL, dt=torch.tensor([1e-3]))
+    inner = L[..., 2:-2, 2:-2]
+    scale = G * 1.0 * 0.3    # g h |dz/dx|: each of the two cancelling terms
+    assert float(inner.abs().max()) < 1e-12 * scale
+    # the source is really there: without it the momentum tendency is g h z'
+    L0 = OB.rhs(q, dx, dy, flux=flux, bc=OB.WALL, dt=torch.tensor([1e-3]))
+    k = 1 if axis == "x" else 2
+    assert float(L0[:, k, 2:-2, 2:-2].abs().min()) > 0.5 * scale
+
+
+def test_walls_conserve_mass_with_a_bed():
+    """No mass crosses a wall: the total depth stays constant to rounding
+    over a rough bed and a random initial state."""
+    n = 20
+    rng = np.random.default_rng(4)
+    z = torch.tensor(0.05 * rng.standard_normal((n, n)))
+    q0 = random_state(1, n, n, 5)
+    m0 = float(q0[:, 0].sum())
+    q, _, _ = OB.run(q0, 25, flux=S.ROE, z=z, bc=OB.WALL)
+    assert abs(float(q[:, 0].sum()) - m0) < 1e-13 * m0
+
+
+def test_wall_mirror_symmetry():
+    """A state mirror-symmetric about x = 1/2 (hu odd, h and hv even) over a
+    symmetric bed stays symmetric: both walls reflect the same way."""
+    n = 16
+    rng = np.random.default_rng(6)
+    half = rng.random((n, n // 2))
+    zh = 0.05 * rng.random((n, n // 2))
+    q0 = torch.zeros(1, 3, n, n, dtype=torch.float64)
+    q0[0, 0] = torch.tensor(np.concatenate([1.0 + 0.1 * half, (1.0 + 0.1 * half)[:, ::-1]], axis=1))
+    mom = 0.05 * rng.standard_normal((n, n // 2))
+    q0[0, 1] = torch.tensor(np.concatenate([mom, -mom[:, ::-1]], axis=1))
+    vt = 0.05 * rng.standard_normal((n, n // 2))
+    q0[0, 2] = torch.tensor(np.concatenate([vt, vt[:, ::-1]], axis=1))
+    z = torch.tensor(np.concatenate([zh, zh[:, ::-1]], axis=1))
+    q, _, _ = OB.run(q0, 20, flux=S.HLL, z=z, bc=OB.WALL)
+    m = q.flip(-1)
+    assert torch.allclose(q[:, 0], m[:, 0], rtol=0, atol=1e-13)
+    assert torch.allclose(q[:, 1], -m[:, 1], rtol=0, atol=1e-13)
+    assert torch.allclose(q[:, 2], m[:, 2], rtol=0, atol=1e-13)
+
+
+def _wall_exact(n, t, u0, sub=16):
+    """Uniform flow h = 1, u = u0 between two walls: at x = 1 the wall is
+    the Riemann problem (1, u0) | (1, -u0) centred on it (a reflected shock),
+    at x = 0 the problem (1, -u0) | (1, u0) (two rarefactions); before the
+    waves meet, the exact depth is the one or the other."""
+    x = (np.arange(n * sub) + 0.5) / (n * sub)
+    hw, _ = riemann.swe_sample(x / t, 1.0, -u0, 1.0, u0, G)
+    he, _ = riemann.swe_sample((x - 1.0) / t, 1.0, u0, 1.0, -u0, G)
+    h = np.where(x < 0.5, hw, he)
+    return h.reshape(n, sub).mean(axis=1)
+
+
+def test_wall_reflection_converges_to_the_exact_solution():
+    """A uniform stream between two walls: the depth converges to the exact
+    reflected-shock / rarefaction solution; a wall that let the flow through
+    would leave the depth at 1 (error 0.3 at the wall)."""
+    u0, t = 0.6, 0.1
+    errs = []
+    for n in (64, 128, 256):
+        q0 = torch.zeros(1, 3, 4, n, dtype=torch.float64)
+        q0[:, 0] = 1.0
+        q0[:, 1] = u0
+        dx = 1.0 / n
+        dt = 0.2 * dx / (u0 + math.sqrt(G * 1.6))
+        steps = int(round(t / dt))
+        dt = t / steps
+        q, _, _ = OB.run(q0, steps, flux=S.HLL, bc=OB.WALL, dt_mode=ofv.DT_FIXED, dt_fixed=dt)
+        h = q[0, 0, 0].numpy()
+        errs.append(np.abs(h - _wall_exact(n, t, u0)).mean())
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert errs[-1] < 5e-3, errs
+    assert min(rates) > 0.8, (errs, rates)
+
+
+def test_bed_slope_is_second_order_on_a_smooth_bed():
+    """A lake at rest over a smooth periodic bed is not an exact discrete
+    steady state; the spurious momentum it develops shrinks as dx^2 (a
+    first-order or wrongly signed source would not)."""
+    out = []
+    for n in (32, 64, 128):
+        c = (np.arange(n) + 0.5) / n
+        z = torch.tensor(np.tile(0.1 * np.sin(2 * np.pi * c), (4, 1)))
+        q0 = torch.zeros(1, 3, 4, n, dtype=torch.float64)
+        q0[:, 0] = 1.0 - z
+        dt = 0.1 / n / math.sqrt(G)
+        steps = int(round(0.02 / dt))
+        q, _, _ = OB.run(q0, steps, flux=S.HLL, z=z, dt_mode=ofv.DT_FIXED, dt_fixed=0.02 / steps)
+        out.append(float(q[:, 1].abs().max()))
+    assert out[0] / out[1] > 3.0 and out[1] / out[2] > 3.0, out
