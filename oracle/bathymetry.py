@@ -1,5 +1,5 @@
 """FP64 oracle of the shallow-water bed-slope source term and of reflecting
-walls (test infrastructure only).
+walls (for both equations) (test infrastructure only).
 
 Eq. 2.3 (and Section 4.2) add the source S = (0, -g h dz/dx, -g h dz/dy) of
 a bed z(x, y) to the momentum equations; Section 4.2's bathymetry test runs
@@ -70,25 +70,26 @@ def muscl_faces(P: torch.Tensor, dim: int, delta: float):
 
 
 def rhs(q: torch.Tensor, dx: float, dy: float, *, flux: str = schemes.HLL, z: torch.Tensor | None = None,
-        bc: str = PERIODIC, dt=None, g: float = 9.81) -> torch.Tensor:
-    """L(q) of the shallow-water step on ``q`` [B][3][ny][nx] with the bed
-    ``z`` [ny][nx] (None: flat) and the boundary ``bc`` on all four sides."""
-    eq = fv.SWE
+        bc: str = PERIODIC, dt=None, g: float = 9.81, eq: str = fv.SWE, gamma: float = 1.4) -> torch.Tensor:
+    """L(q) on ``q`` [B][C][ny][nx] with the boundary ``bc`` on all four
+    sides and, for shallow water, the bed ``z`` [ny][nx] (None: flat).  The
+    momentum normal to a wall is component 1 (x) or 2 (y) for both
+    equations."""
     nu_x = nu_y = None
     if flux == schemes.LAX_FRIEDRICHS:
-        dt = torch.as_tensor(dt, dtype=torch.float64).reshape(-1)
+        dt = torch.as_tensor(dt, dtype=q.dtype).reshape(-1)
         nu_x, nu_y = dx / (4.0 * dt), dy / (4.0 * dt)
     Px = pad(q, -1, bc, normal=1)
     QLx, QRx = muscl_faces(Px, -1, dx)
-    Fx = schemes.face_flux(flux, QLx, QRx, *fv.X_FACE, eq, g, 1.4, nu_x)    # nx + 1 faces
+    Fx = schemes.face_flux(flux, QLx, QRx, *fv.X_FACE, eq, g, gamma, nu_x)   # nx + 1 faces
     Py = pad(q, -2, bc, normal=2)
     QLy, QRy = muscl_faces(Py, -2, dy)
-    Gy = schemes.face_flux(flux, QLy, QRy, *fv.Y_FACE, eq, g, 1.4, nu_y)    # ny + 1 faces
+    Gy = schemes.face_flux(flux, QLy, QRy, *fv.Y_FACE, eq, g, gamma, nu_y)   # ny + 1 faces
     F_w, F_e = Fx[..., :-1], Fx[..., 1:]
     G_s, G_n = Gy[..., :-1, :], Gy[..., 1:, :]
     L = -(dy * (F_e - F_w) + dx * (G_n - G_s)) / (dx * dy)
     if z is not None:
-        zz = torch.as_tensor(z, dtype=torch.float64)[None, None]
+        zz = torch.as_tensor(z, dtype=q.dtype)[None, None]
         zx = pad(zz, -1, bc, n=1)
         zy = pad(zz, -2, bc, n=1)
         dzdx = (zx[..., 2:] - zx[..., :-2]) / (2.0 * dx)
@@ -101,29 +102,32 @@ def rhs(q: torch.Tensor, dx: float, dy: float, *, flux: str = schemes.HLL, z: to
 
 
 def run(q0, nsteps: int, *, flux: str = schemes.HLL, rk: int = schemes.RK2, z=None, bc: str = PERIODIC,
-        cfl: float = 0.5, dt_mode: str = fv.DT_ADAPTIVE, dt_fixed=None, dts=None, g: float = 9.81):
-    """``nsteps`` steps of the shallow-water scheme with bed and walls; the
-    adaptive dt is the CFL rule of Eq. 2.10.  Returns (q, t, dt_history)."""
-    q = torch.as_tensor(q0, dtype=torch.float64).clone()
+        cfl: float = 0.5, dt_mode: str = fv.DT_ADAPTIVE, dt_fixed=None, dts=None, g: float = 9.81,
+        eq: str = fv.SWE, gamma: float = 1.4, dtype=torch.float64):
+    """``nsteps`` steps of the scheme with walls (and, for shallow water, a
+    bed); the adaptive dt is the CFL rule of Eq. 2.10.  Returns (q, t,
+    dt_history).  ``dtype`` float32 replays the same algorithm in single
+    precision (the roundoff yardstick of the GPU parity tests)."""
+    q = torch.as_tensor(q0).to(dtype).clone()
     B = q.shape[0]
     dx, dy = fv.grid_spacing(q)
-    t = torch.zeros(B, dtype=torch.float64)
+    t = torch.zeros(B, dtype=dtype)
     hist = []
     for n in range(nsteps):
         if dt_mode == fv.DT_ADAPTIVE:
-            dt = fv.cfl_dt(q, fv.SWE, cfl, dx, dy, g, 1.4)
+            dt = fv.cfl_dt(q, eq, cfl, dx, dy, g, gamma).to(dtype)
         elif dt_mode == fv.DT_FIXED:
-            dt = torch.full((B,), float(dt_fixed), dtype=torch.float64)
+            dt = torch.full((B,), float(dt_fixed), dtype=dtype)
         else:
-            d = torch.as_tensor(dts[n], dtype=torch.float64)
+            d = torch.as_tensor(dts[n]).to(dtype)
             dt = d.expand(B).clone() if d.dim() == 0 else d.clone()
 
         def L(s, dt=dt):
-            return rhs(s, dx, dy, flux=flux, z=z, bc=bc, dt=dt, g=g)
+            return rhs(s, dx, dy, flux=flux, z=z, bc=bc, dt=dt, g=g, eq=eq, gamma=gamma)
 
         step = fv.ssp_rk2 if rk == schemes.RK2 else schemes.ssp_rk3
         q = step(q, dt.view(B, 1, 1, 1), L)
         t = t + dt
         hist.append(dt)
-    dt_hist = torch.stack(hist) if hist else torch.zeros(0, B, dtype=torch.float64)
+    dt_hist = torch.stack(hist) if hist else torch.zeros(0, B, dtype=dtype)
     return q, t, dt_hist

@@ -141,3 +141,18 @@ def test_bed_slope_is_second_order_on_a_smooth_bed():
         q, _, _ = OB.run(q0, steps, flux=S.HLL, z=z, dt_mode=ofv.DT_FIXED, dt_fixed=0.02 / steps)
         out.append(float(q[:, 1].abs().max()))
     assert out[0] / out[1] > 3.0 and out[1] / out[2] > 3.0, out
+
+
+def test_euler_walls_conserve_mass_and_energy():
+    """For the Euler equations a wall passes no mass and no energy (the
+    normal velocity vanishes there): both totals stay constant to rounding."""
+    n = 16
+    g = torch.Generator().manual_seed(9)
+    q0 = torch.zeros(1, 4, n, n, dtype=torch.float64)
+    q0[:, 0] = 1.0 + 0.3 * torch.rand(1, n, n, generator=g)
+    q0[:, 1:3] = 0.2 * torch.randn(1, 2, n, n, generator=g)
+    q0[:, 3] = 2.5 + 0.5 * (q0[:, 1] ** 2 + q0[:, 2] ** 2) / q0[:, 0]
+    q, _, _ = OB.run(q0, 25, flux=S.HLLC, bc=OB.WALL, eq=ofv.EULER)
+    for c in (0, 3):
+        a, b = float(q[:, c].sum()), float(q0[:, c].sum())
+        assert abs(a - b) < 1e-13 * b, (c, a, b)
