@@ -20,9 +20,12 @@ cudaError_t launch_learned_fused(const Geom& g, int stage, const float* qin, con
                                  const DtParams* dp, cudaStream_t s);
 // One plain step with flux `flux` (fvk::Flux) and integrator `rk` (2: SSP-RK2,
 // 3: SSP-RK3); q^n in qa (updated in place), stages in qb and qc.  `variant`
-// as for the HLL stages (STAGE_TILE forces the tile kernel).
+// as for the HLL stages (STAGE_TILE forces the tile kernel); `bc` FV_BC_*,
+// `z` the shallow-water bed [ny][nx] on the device or null (walls and beds
+// run in the tile kernel).
 cudaError_t enqueue_scheme_step(const Geom& g, int flux, int rk, float* qa, float* qb, float* qc,
-                                Ctrl* ctrl, const DtParams* dp, cudaStream_t s, int variant);
+                                Ctrl* ctrl, const DtParams* dp, cudaStream_t s, int variant, int bc,
+                                const float* z);
 cudaError_t launch_stage_learned(const Geom& g, int stage, const float* qin, const float* qn,
                                  float* qout, const float* w, const float* hmin, Ctrl* ctrl,
                                  const DtParams* dp, cudaStream_t s);
@@ -56,6 +59,8 @@ struct fv_state {
   int flux = 0;                        // FV_FLUX_* of the plain step
   int rk = 2;                          // 2: SSP-RK2, 3: SSP-RK3
   float* qC = nullptr;                 // q^(2) of SSP-RK3 (allocated on first use)
+  int bc = 0;                          // FV_BC_PERIODIC or FV_BC_WALL
+  float* zbed = nullptr;               // shallow-water bed [ny][nx] (device), or null
 };
 
 namespace fvs {

@@ -223,6 +223,8 @@ static int learned_ws_ready(fv_state* s, float hmin_frac) {
 int learned_prepare(fv_state* s) {
   if (s->flux != FV_FLUX_HLL || s->rk != 2)
     return fvh::fail(FV_EINVAL, "the learned step uses the HLL flux and SSP-RK2 (see fv_set_scheme)");
+  if (s->bc != FV_BC_PERIODIC || s->zbed)
+    return fvh::fail(FV_EINVAL, "the learned step runs on periodic flat-bed grids");
   return learned_ws_ready(s, s->hmin_frac);
 }
 

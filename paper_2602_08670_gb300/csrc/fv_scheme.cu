@@ -12,6 +12,11 @@
 //   K_HEUN:    q^{n+1} = q^n/2 + (q1 + dt L(q1))/2, CFL     (SSP-RK2 stage 2)
 //   K_RK3_2:   q2 = 3/4 q^n + 1/4 (q1 + dt L(q1))           (SSP-RK3 stage 2)
 //   K_RK3_3:   q^{n+1} = 1/3 q^n + 2/3 (q2 + dt L(q2)), CFL (SSP-RK3 stage 3)
+// It also carries the two variants of the shallow-water step that leave the
+// periodic flat-bed path (Eq. 2.3, Section 4.2): reflecting walls (the tile's
+// halo cells mirror the interior, with the momentum normal to the wall
+// negated) and the bed-slope source -g h (dz/dx, dz/dy) with centred slopes of
+// the bed z given at the cell centres (mirrored at walls, no sign change).
 #include <cuda_runtime.h>
 
 #include "fv_common.cuh"
@@ -23,10 +28,11 @@ namespace fvk {
 namespace {
 
 constexpr int TX = 64, TY = 16, SX = TX + 4, SY = TY + 4, NT = 256;
+constexpr int ZX = TX + 2, ZY = TY + 2;   // bed tile with a 1-cell halo
 
 template <int C>
 constexpr int scheme_smem_bytes() {
-  return (C * (SY * SX + TY * (TX + 1) + (TY + 1) * TX) + 4 * (NT / 32)) * 4;
+  return (C * (SY * SX + TY * (TX + 1) + (TY + 1) * TX) + 4 * (NT / 32) + ZY * ZX) * 4;
 }
 
 struct SchemeArgs {
@@ -38,7 +44,22 @@ struct SchemeArgs {
   int nx, ny, flux;
   long long plane, member;
   float rdx, rdy, phys;
+  int bc;              // BC_PERIODIC or BC_WALL on all four sides
+  const float* z;      // bed [ny][nx] (shallow water), or null: flat
 };
+
+enum { BC_PERIODIC = 0, BC_WALL = 1 };
+
+// Halo index along one axis of length n: periodic wrap, or the mirror image
+// (cell -1 - i outside the low end, 2 n - 1 - i outside the high end);
+// `flip` is set when the mirror was taken.
+__device__ __forceinline__ int halo_index(int i, int n, int bc, bool& flip) {
+  flip = false;
+  if (i >= 0 && i < n) return i;
+  if (bc == BC_PERIODIC) return wrap(i, n);
+  flip = true;
+  return i < 0 ? -1 - i : 2 * n - 1 - i;
+}
 
 // Face flux from the four-cell stencil m, a, b, p: MUSCL-minmod face states,
 // rotation into the face frame for y faces, the chosen flux, rotation back.
@@ -79,6 +100,7 @@ __global__ void __launch_bounds__(NT) stage_scheme_kernel(SchemeArgs a) {
   float* sF = sq + C * SY * SX;              // [C][TY][TX+1]
   float* sG = sF + C * TY * (TX + 1);        // [C][TY+1][TX]
   unsigned* red = reinterpret_cast<unsigned*>(sG + C * (TY + 1) * TX);
+  float* zs = reinterpret_cast<float*>(red + 4 * (NT / 32));   // [ZY][ZX]
   constexpr bool last = K == K_HEUN || K == K_RK3_3;
 
   const int b = blockIdx.z;
@@ -96,8 +118,19 @@ __global__ void __launch_bounds__(NT) stage_scheme_kernel(SchemeArgs a) {
     const int c = idx / (SY * SX);
     const int r = idx - c * (SY * SX);
     const int sy = r / SX, sx = r - sy * SX;
-    const int gx = wrap(x0 - 2 + sx, a.nx), gy = wrap(y0 - 2 + sy, a.ny);
-    sq[idx] = qin[c * a.plane + (long long)gy * a.nx + gx];
+    bool fx, fy;
+    const int gx = halo_index(x0 - 2 + sx, a.nx, a.bc, fx), gy = halo_index(y0 - 2 + sy, a.ny, a.bc, fy);
+    const float v = qin[c * a.plane + (long long)gy * a.nx + gx];
+    // a wall reverses the momentum normal to it (component 1 = x, 2 = y)
+    sq[idx] = (c == 1 && fx) || (c == 2 && fy) ? -v : v;
+  }
+  if (a.z) {
+    for (int idx = tid; idx < ZY * ZX; idx += NT) {
+      const int sy = idx / ZX, sx = idx - sy * ZX;
+      bool fx, fy;
+      const int gx = halo_index(x0 - 1 + sx, a.nx, a.bc, fx), gy = halo_index(y0 - 1 + sy, a.ny, a.bc, fy);
+      zs[idx] = a.z[(long long)gy * a.nx + gx];
+    }
   }
   __syncthreads();
 
@@ -139,11 +172,23 @@ __global__ void __launch_bounds__(NT) stage_scheme_kernel(SchemeArgs a) {
     if (gx >= a.nx || gy >= a.ny) continue;
     const long long off = (long long)gy * a.nx + gx;
     float out[C];
+    // bed slope source: -g h (z_e - z_w) / (2 dx), -g h (z_n - z_s) / (2 dy)
+    float src1 = 0.f, src2 = 0.f;
+    if constexpr (EQ == SWE) {
+      if (a.z) {
+        const float gh = vmul(a.phys, sq[(r + 2) * SX + i + 2]);
+        const float* zc = zs + (r + 1) * ZX + i + 1;
+        src1 = vmul(gh, vmul(vsub(zc[1], zc[-1]), 0.5f * a.rdx));
+        src2 = vmul(gh, vmul(vsub(zc[ZX], zc[-ZX]), 0.5f * a.rdy));
+      }
+    }
 #pragma unroll
     for (int c = 0; c < C; ++c) {
-      const float L = divergence<float>(sF[(c * TY + r) * (TX + 1) + i], sF[(c * TY + r) * (TX + 1) + i + 1],
-                                        sG[(c * (TY + 1) + r) * TX + i], sG[(c * (TY + 1) + r + 1) * TX + i],
-                                        a.rdx, a.rdy);
+      float L = divergence<float>(sF[(c * TY + r) * (TX + 1) + i], sF[(c * TY + r) * (TX + 1) + i + 1],
+                                  sG[(c * (TY + 1) + r) * TX + i], sG[(c * (TY + 1) + r + 1) * TX + i],
+                                  a.rdx, a.rdy);
+      if (EQ == SWE && c == 1) L = vsub(L, src1);
+      if (EQ == SWE && c == 2) L = vsub(L, src2);
       const float q = sq[(c * SY + r + 2) * SX + i + 2];
       if (K == K_FIRST) {
         out[c] = rk_stage1<float>(q, dt, L);
@@ -199,9 +244,10 @@ cudaError_t launch_eq(int kind, const SchemeArgs& a, const Geom& g, cudaStream_t
 }
 
 cudaError_t launch_scheme_stage(const Geom& g, int kind, int flux, const float* qin, const float* qn,
-                                float* qout, Ctrl* ctrl, const DtParams* dp, cudaStream_t s) {
+                                float* qout, Ctrl* ctrl, const DtParams* dp, cudaStream_t s, int bc,
+                                const float* z) {
   SchemeArgs a{qin, qn, qout, ctrl, dp, g.nx, g.ny, flux, g.plane(), g.member(),
-               (float)(1.0 / g.dx), (float)(1.0 / g.dy), g.phys};
+               (float)(1.0 / g.dx), (float)(1.0 / g.dy), g.phys, bc, z};
   return g.eq == SWE ? launch_eq<3, SWE>(kind, a, g, s) : launch_eq<4, EULER>(kind, a, g, s);
 }
 
@@ -210,8 +256,10 @@ cudaError_t launch_scheme_stage(const Geom& g, int kind, int flux, const float* 
 // One step of the plain scheme with the chosen flux and integrator.  q^n is
 // qa (updated in place); qb and (SSP-RK3) qc hold the intermediate stages.
 cudaError_t enqueue_scheme_step(const Geom& g, int flux, int rk, float* qa, float* qb, float* qc,
-                                Ctrl* ctrl, const DtParams* dp, cudaStream_t s, int variant) {
-  if (variant != STAGE_TILE && march_supported(g)) {
+                                Ctrl* ctrl, const DtParams* dp, cudaStream_t s, int variant, int bc,
+                                const float* z) {
+  // walls and beds run in the tile kernel only
+  if (variant != STAGE_TILE && march_supported(g) && bc == BC_PERIODIC && !z) {
     // row-march kernels (fv_stage.cu), stage kinds 1..4
     cudaError_t e = launch_stage_general(g, 1, flux, qa, nullptr, qb, ctrl, dp, s);
     if (e != cudaSuccess) return e;
@@ -220,12 +268,12 @@ cudaError_t enqueue_scheme_step(const Geom& g, int flux, int rk, float* qa, floa
     if (e != cudaSuccess) return e;
     return launch_stage_general(g, 4, flux, qc, qa, qa, ctrl, dp, s);
   }
-  cudaError_t e = launch_scheme_stage(g, K_FIRST, flux, qa, nullptr, qb, ctrl, dp, s);
+  cudaError_t e = launch_scheme_stage(g, K_FIRST, flux, qa, nullptr, qb, ctrl, dp, s, bc, z);
   if (e != cudaSuccess) return e;
-  if (rk == 2) return launch_scheme_stage(g, K_HEUN, flux, qb, qa, qa, ctrl, dp, s);
-  e = launch_scheme_stage(g, K_RK3_2, flux, qb, qa, qc, ctrl, dp, s);
+  if (rk == 2) return launch_scheme_stage(g, K_HEUN, flux, qb, qa, qa, ctrl, dp, s, bc, z);
+  e = launch_scheme_stage(g, K_RK3_2, flux, qb, qa, qc, ctrl, dp, s, bc, z);
   if (e != cudaSuccess) return e;
-  return launch_scheme_stage(g, K_RK3_3, flux, qc, qa, qa, ctrl, dp, s);
+  return launch_scheme_stage(g, K_RK3_3, flux, qc, qa, qa, ctrl, dp, s, bc, z);
 }
 
 }  // namespace fvk

@@ -151,6 +151,7 @@ void state_free(fv_state* s) {
   cudaFree(s->qA);
   cudaFree(s->qB);
   cudaFree(s->qC);
+  cudaFree(s->zbed);
   cudaFree(s->ctrl);
   cudaFree(s->dp);
   cudaFree(s->replay);
@@ -179,9 +180,9 @@ cudaError_t leave(fv_state* s) {
 }
 
 cudaError_t enqueue_plain_step(fv_state* s) {
-  if (s->flux != FV_FLUX_HLL || s->rk != 2)
+  if (s->flux != FV_FLUX_HLL || s->rk != 2 || s->bc != FV_BC_PERIODIC || s->zbed)
     return fvk::enqueue_scheme_step(s->g, s->flux, s->rk, s->qA, s->qB, s->qC, s->ctrl, s->dp, s->stream,
-                                    s->variant);
+                                    s->variant, s->bc, s->zbed);
   cudaError_t e = fvk::launch_stage_minmod(s->g, 1, s->qA, nullptr, s->qB, s->ctrl, s->dp,
                                            s->stream, s->variant);
   if (e != cudaSuccess) return e;
@@ -446,6 +447,35 @@ extern "C" int fv_set_scheme(fv_state* s, int flux, int rk) {
   }
   s->flux = flux;
   s->rk = rk;
+  if (s->graph) cudaGraphExecDestroy(s->graph);
+  s->graph = nullptr;
+  return FV_OK;
+}
+
+extern "C" int fv_set_boundary(fv_state* s, int bc) {
+  if (!s) return fvh::fail(FV_EINVAL, "null state");
+  if (bc != FV_BC_PERIODIC && bc != FV_BC_WALL) return fvh::fail(FV_EINVAL, "unknown boundary condition");
+  if (bc == FV_BC_WALL && (s->g.nx < 2 || s->g.ny < 2)) return fvh::fail(FV_EINVAL, "walls need nx, ny >= 2");
+  FV_CUDA_TRY(cudaStreamSynchronize(s->stream));
+  s->bc = bc;
+  if (s->graph) cudaGraphExecDestroy(s->graph);
+  s->graph = nullptr;
+  return FV_OK;
+}
+
+extern "C" int fv_set_bathymetry(fv_state* s, const float* z, int z_loc) {
+  if (!s) return fvh::fail(FV_EINVAL, "null state");
+  if (s->g.eq != fvk::SWE) return fvh::fail(FV_EINVAL, "a bed applies to shallow-water states only");
+  if (z && z_loc != FV_HOST && z_loc != FV_DEVICE) return fvh::fail(FV_EINVAL, "z_loc must be FV_HOST or FV_DEVICE");
+  FV_CUDA_TRY(cudaStreamSynchronize(s->stream));
+  if (!z) {
+    cudaFree(s->zbed);
+    s->zbed = nullptr;
+  } else {
+    const size_t bytes = sizeof(float) * (size_t)s->g.nx * (size_t)s->g.ny;
+    if (!s->zbed) FV_CUDA_TRY(cudaMalloc(&s->zbed, bytes));
+    FV_CUDA_TRY(cudaMemcpy(s->zbed, z, bytes, z_loc == FV_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice));
+  }
   if (s->graph) cudaGraphExecDestroy(s->graph);
   s->graph = nullptr;
   return FV_OK;

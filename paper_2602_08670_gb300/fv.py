@@ -66,6 +66,8 @@ _SIGS = {
     "fv_set_stage_variant": [c_void_p, c_int],
     "fv_set_learned_variant": [c_void_p, c_int],
     "fv_set_scheme": [c_void_p, c_int, c_int],
+    "fv_set_boundary": [c_void_p, c_int],
+    "fv_set_bathymetry": [c_void_p, c_void_p, c_int],
     "fv_set_learned_hmin": [c_void_p, c_double],
     "stencil_net_create": [c_void_p, c_void_p, ctypes.POINTER(c_void_p)],
     "stencil_net_destroy": [c_void_p],
@@ -352,6 +354,27 @@ def fv_set_scheme(s: State, flux: str = "hll", rk: int = 2) -> None:
     """Numerical flux ("hll", "rusanov", "lf", "roe", "hlle", "hllc") and
     integrator (2: SSP-RK2, 3: SSP-RK3) of the plain step."""
     _check(lib().fv_set_scheme(s.handle, FLUXES[flux], int(rk)))
+
+
+BOUNDARIES = {"periodic": 0, "wall": 1}
+
+
+def fv_set_boundary(s: State, bc: str) -> None:
+    """"periodic" (default) or "wall" (reflecting) on all four sides."""
+    _check(lib().fv_set_boundary(s.handle, BOUNDARIES[bc]))
+
+
+def fv_set_bathymetry(s: State, z) -> None:
+    """Shallow-water bed z [ny][nx] at the cell centres (a torch tensor on
+    the host or the device, or None for a flat bed)."""
+    if z is None:
+        _check(lib().fv_set_bathymetry(s.handle, None, FV_HOST))
+        return
+    zt = z.detach().to(torch.float32).contiguous()
+    if tuple(zt.shape) != tuple(s.shape[-2:]):
+        raise ValueError(f"bed shape {tuple(zt.shape)} != grid {tuple(s.shape[-2:])}")
+    loc = FV_DEVICE if zt.is_cuda else FV_HOST
+    _check(lib().fv_set_bathymetry(s.handle, c_void_p(zt.data_ptr()), loc))
 
 
 LEARNED_VARIANTS = {"auto": 0, "fused": 1, "two_pass": 2}
