@@ -52,12 +52,15 @@ enum { BC_PERIODIC = 0, BC_WALL = 1 };
 
 // Halo index along one axis of length n: periodic wrap, or the mirror image
 // (cell -1 - i outside the low end, 2 n - 1 - i outside the high end);
-// `flip` is set when the mirror was taken.
+// `flip` is set when the mirror was taken.  A ragged tile also loads cells
+// past the two ghost layers the stencil reads; for walls those are clamped
+// to the second ghost first, so the mirror stays inside [0, n) for n >= 2.
 __device__ __forceinline__ int halo_index(int i, int n, int bc, bool& flip) {
   flip = false;
   if (i >= 0 && i < n) return i;
   if (bc == BC_PERIODIC) return wrap(i, n);
   flip = true;
+  i = max(-2, min(i, n + 1));
   return i < 0 ? -1 - i : 2 * n - 1 - i;
 }
 

@@ -203,6 +203,54 @@ def random_smooth_swe(n: int, seed: int, members: int = 1, amp: float = 0.05,
     return q
 
 
+def perlin_bed(nx: int, ny: int, seed: int, cells: int = 6, octaves: int = 3,
+               amp: float = 0.1) -> np.ndarray:
+    """Water bed z [ny][nx] from 2D gradient (Perlin) noise, as in Section
+    4.2's bathymetry test.
+
+    Octave k has a lattice of ``cells * 2^k`` squares over the unit square,
+    a seeded random unit gradient at each lattice node, and contributes the
+    quintic-faded blend of the four corner ramps g . (p - node) at weight
+    2^-k; the sum is shifted to mean 0 and scaled to max |z| = ``amp``.
+    With the default depth h0 = 1 the water stays at least 0.9 deep."""
+    rng = _rng(seed)
+    X, Y = _mesh(nx, ny)
+    z = np.zeros((ny, nx))
+    for k in range(octaves):
+        m = cells << k
+        ang = rng.uniform(0.0, 2 * math.pi, size=(m + 1, m + 1))
+        gx, gy = np.cos(ang), np.sin(ang)
+        u, v = X * m, Y * m
+        i0 = np.minimum(np.floor(u).astype(np.int64), m - 1)
+        j0 = np.minimum(np.floor(v).astype(np.int64), m - 1)
+        fu, fv = u - i0, v - j0
+
+        def ramp(di, dj):
+            return gx[j0 + dj, i0 + di] * (fu - di) + gy[j0 + dj, i0 + di] * (fv - dj)
+
+        def fade(t):
+            return t * t * t * (t * (6.0 * t - 15.0) + 10.0)
+
+        wu, wv = fade(fu), fade(fv)
+        bottom = ramp(0, 0) + wu * (ramp(1, 0) - ramp(0, 0))
+        top = ramp(0, 1) + wu * (ramp(1, 1) - ramp(0, 1))
+        z += (bottom + wv * (top - bottom)) / (1 << k)
+    z -= z.mean()
+    return amp * z / np.abs(z).max()
+
+
+def swe_bump_over_bed(z: np.ndarray, amp: float = 0.1, width2: float = 0.005,
+                      h0: float = 1.0) -> np.ndarray:
+    """The Gaussian-hump surface of ``swe_gaussian_bump`` over the bed ``z``
+    [ny][nx]: the free surface h + z is h0 plus the hump, at rest
+    (Section 4.2 reuses the flat-bed initial condition).  Returns
+    ``[1][3][ny][nx]``."""
+    ny, nx = z.shape
+    q = swe_gaussian_bump(nx, ny, amp, width2, h0)
+    q[0, 0] -= z
+    return q
+
+
 @dataclasses.dataclass
 class Request:
     """One solve request of the serving workload."""
