@@ -21,8 +21,7 @@ cudaError_t launch_learned_fused(const Geom& g, int stage, const float* qin, con
 // One plain step with flux `flux` (fvk::Flux) and integrator `rk` (2: SSP-RK2,
 // 3: SSP-RK3); q^n in qa (updated in place), stages in qb and qc.  `variant`
 // as for the HLL stages (STAGE_TILE forces the tile kernel); `bc` FV_BC_*,
-// `z` the shallow-water bed [ny][nx] on the device or null (walls and beds
-// run in the tile kernel).
+// `z` the shallow-water bed [ny][nx] on the device or null.
 cudaError_t enqueue_scheme_step(const Geom& g, int flux, int rk, float* qa, float* qb, float* qc,
                                 Ctrl* ctrl, const DtParams* dp, cudaStream_t s, int variant, int bc,
                                 const float* z);

@@ -31,12 +31,19 @@ cudaError_t launch_stage_minmod(const Geom& g, int stage, const float* qin, cons
                                 float* qout, Ctrl* ctrl, const DtParams* dp, cudaStream_t s,
                                 int variant);
 
+// Boundary on all four sides: periodic, or reflecting walls (mirror ghost
+// cells with the momentum normal to the wall negated).
+enum { BC_PERIODIC = 0, BC_WALL = 1 };
+
 // Row-march stage with the flux chosen at run time (fvk::Flux) and stage
 // kind 1 (q1 = q^n + dt L), 2 (Heun), 3, 4 (SSP-RK3 stages 2 and 3; the
-// CFL reduction in 2 and 4).  Needs march_supported(g).
+// CFL reduction in 2 and 4); `bc` BC_*, `z` the shallow-water bed [ny][nx]
+// on the device (bed-slope source of Eq. 2.3) or null.  Needs
+// march_supported(g) (and ny >= 2 with walls).
 bool march_supported(const Geom& g);
 cudaError_t launch_stage_general(const Geom& g, int stage, int flux, const float* qin, const float* qn,
-                                 float* qout, Ctrl* ctrl, const DtParams* dp, cudaStream_t s);
+                                 float* qout, Ctrl* ctrl, const DtParams* dp, cudaStream_t s,
+                                 int bc = BC_PERIODIC, const float* z = nullptr);
 
 // Wave-speed reduction of q that sets each member's dt without advancing
 // time (state creation, fv_set_state).

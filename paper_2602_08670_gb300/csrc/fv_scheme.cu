@@ -48,8 +48,6 @@ struct SchemeArgs {
   const float* z;      // bed [ny][nx] (shallow water), or null: flat
 };
 
-enum { BC_PERIODIC = 0, BC_WALL = 1 };
-
 // Halo index along one axis of length n: periodic wrap, or the mirror image
 // (cell -1 - i outside the low end, 2 n - 1 - i outside the high end);
 // `flip` is set when the mirror was taken.  A ragged tile also loads cells
@@ -261,15 +259,14 @@ cudaError_t launch_scheme_stage(const Geom& g, int kind, int flux, const float* 
 cudaError_t enqueue_scheme_step(const Geom& g, int flux, int rk, float* qa, float* qb, float* qc,
                                 Ctrl* ctrl, const DtParams* dp, cudaStream_t s, int variant, int bc,
                                 const float* z) {
-  // walls and beds run in the tile kernel only
-  if (variant != STAGE_TILE && march_supported(g) && bc == BC_PERIODIC && !z) {
+  if (variant != STAGE_TILE && march_supported(g)) {
     // row-march kernels (fv_stage.cu), stage kinds 1..4
-    cudaError_t e = launch_stage_general(g, 1, flux, qa, nullptr, qb, ctrl, dp, s);
+    cudaError_t e = launch_stage_general(g, 1, flux, qa, nullptr, qb, ctrl, dp, s, bc, z);
     if (e != cudaSuccess) return e;
-    if (rk == 2) return launch_stage_general(g, 2, flux, qb, qa, qa, ctrl, dp, s);
-    e = launch_stage_general(g, 3, flux, qb, qa, qc, ctrl, dp, s);
+    if (rk == 2) return launch_stage_general(g, 2, flux, qb, qa, qa, ctrl, dp, s, bc, z);
+    e = launch_stage_general(g, 3, flux, qb, qa, qc, ctrl, dp, s, bc, z);
     if (e != cudaSuccess) return e;
-    return launch_stage_general(g, 4, flux, qc, qa, qa, ctrl, dp, s);
+    return launch_stage_general(g, 4, flux, qc, qa, qa, ctrl, dp, s, bc, z);
   }
   cudaError_t e = launch_scheme_stage(g, K_FIRST, flux, qa, nullptr, qb, ctrl, dp, s, bc, z);
   if (e != cudaSuccess) return e;

@@ -41,6 +41,8 @@ struct StageArgs {
   long long plane, member;
   float rdx, rdy, phys;
   int flux;            // fvk::Flux of the generic row-march stages
+  int bc;              // BC_PERIODIC / BC_WALL (generic row-march stages)
+  const float* z;      // shallow-water bed [ny][nx] or null (generic row-march stages)
 };
 
 // Normal-frame flux of one face from its four-cell stencil.  `rot` selects the
@@ -184,6 +186,15 @@ __global__ void __launch_bounds__(NT) stage_minmod_kernel(StageArgs a) {
 // One __syncthreads per row publishes the ring row.  The y faces are computed
 // once; each thread recomputes the x face shared with its right neighbour
 // (5 x faces for 4 cells), which removes any per-row flux exchange.
+//
+// BND instances add reflecting walls and the bed-slope source (Eq. 2.3).
+// A wall's ghost cells are the mirror image of the first two interior cells
+// with the normal momentum negated: ghost rows are fetched from the mirrored
+// rows and their component 2 negated where the y stencil reads them; the
+// strip's outer halo pair is fetched in memory order and swapped (component
+// 1 negated) where the x stencil reads it.  The bed enters as
+// -g h (z_e - z_w) / (2 dx), -g h (z_n - z_s) / (2 dy) on the momenta, with
+// the bed mirrored (walls) or wrapped (periodic) across the boundary.
 // ---------------------------------------------------------------------------
 constexpr int MT = 128;           // threads per block
 constexpr int MW = 4 * MT;        // strip width
@@ -253,7 +264,7 @@ __device__ __forceinline__ float2 hi(float4 v) { return make_float2(v.z, v.w); }
 // STAGE: 1 = q1 = q^n + dt L(q^n); 2 = Heun's second stage (Eq. 2.19) and
 // the CFL reduction; with GEN also 3 = SSP-RK3's second stage and 4 = its
 // third stage and the CFL reduction (Eq. 2.20).
-template <int C, int EQ, int STAGE, bool GEN = false>
+template <int C, int EQ, int STAGE, bool GEN = false, bool BND = false>
 __global__ void __launch_bounds__(MT) stage_march_kernel(StageArgs a, int TY) {
   constexpr bool CFL_STAGE = STAGE == 2 || STAGE == 4;
   extern __shared__ __align__(16) float ring[];   // [MS][C][RS]
@@ -273,8 +284,13 @@ __global__ void __launch_bounds__(MT) stage_march_kernel(StageArgs a, int TY) {
   const int rows = min(TY, a.ny - Y0);
   const int NL = rows + 4;                    // rows Y0-2 .. Y0+rows+1
   const float* qin = a.qin + b * a.member;
-  const int xl = X0 == 0 ? a.nx - 2 : X0 - 2;           // left halo cells xl, xl+1
-  const int xr = X0 + wact == a.nx ? 0 : X0 + wact;     // right halo cells xr, xr+1
+  const bool wall = BND && a.bc == BC_WALL;
+  const bool wall_w = wall && X0 == 0;                  // the strip touches the west wall
+  const bool wall_e = wall && X0 + wact == a.nx;        // ... the east wall
+  // left / right halo cells xl, xl+1 and xr, xr+1 (at a wall: the two
+  // boundary cells in memory order, mirrored when read)
+  const int xl = X0 == 0 ? (wall ? 0 : a.nx - 2) : X0 - 2;
+  const int xr = X0 + wact == a.nx ? (wall ? a.nx - 2 : 0) : X0 + wact;
   const int plane = (int)a.plane;                       // < 2^31 floats per variable plane
   int gy_next = Y0 - 2;                                 // next row to fetch (periodic)
   while (gy_next < 0) gy_next += a.ny;
@@ -282,7 +298,13 @@ __global__ void __launch_bounds__(MT) stage_march_kernel(StageArgs a, int TY) {
 
   auto issue_next = [&]() {
     float* slot = ring + (i_next & (MS - 1)) * C * RS;
-    const float* src = qin + gy_next * a.nx;
+    int gy = gy_next;
+    if (wall) {
+      // virtual row Y0 - 2 + i_next lies in [-2, ny + 1]: mirror it inside
+      const int v = Y0 - 2 + i_next;
+      gy = v < 0 ? -1 - v : (v >= a.ny ? 2 * a.ny - 1 - v : v);
+    }
+    const float* src = qin + gy * a.nx;
     if (active) {
 #pragma unroll
       for (int c = 0; c < C; ++c) cp_async16(slot + c * RS + 4 + 4 * t, src + c * plane + X0 + 4 * t);
@@ -326,6 +348,26 @@ __global__ void __launch_bounds__(MT) stage_march_kernel(StageArgs a, int TY) {
         qn2[c][1] = hi(v);
       }
     }
+    // bed around the 4 cells of the output row: zr[0..5] = columns
+    // 4t-1 .. 4t+4 of the row, zs / zn the rows below / above
+    float zr[6], zs[4], zn[4];
+    if constexpr (BND && EQ == SWE) {
+      if (a.z && i >= 4 && active) {
+        const int x = X0 + 4 * t;
+        const int xw = x > 0 ? x - 1 : (wall ? 0 : a.nx - 1);
+        const int xe = x + 4 < a.nx ? x + 4 : (wall ? a.nx - 1 : 0);
+        const int ys = orow > 0 ? orow - 1 : (wall ? 0 : a.ny - 1);
+        const int yn = orow + 1 < a.ny ? orow + 1 : (wall ? a.ny - 1 : 0);
+        const float4 c4 = __ldg(reinterpret_cast<const float4*>(a.z + orow * a.nx + x));
+        const float4 s4 = __ldg(reinterpret_cast<const float4*>(a.z + ys * a.nx + x));
+        const float4 n4 = __ldg(reinterpret_cast<const float4*>(a.z + yn * a.nx + x));
+        zr[0] = __ldg(a.z + orow * a.nx + xw);
+        zr[1] = c4.x; zr[2] = c4.y; zr[3] = c4.z; zr[4] = c4.w;
+        zr[5] = __ldg(a.z + orow * a.nx + xe);
+        zs[0] = s4.x; zs[1] = s4.y; zs[2] = s4.z; zs[3] = s4.w;
+        zn[0] = n4.x; zn[1] = n4.y; zn[2] = n4.z; zn[3] = n4.w;
+      }
+    }
     cp_async_wait<MPF>();
     __syncthreads();
     if (i < 2 || !active) continue;
@@ -333,12 +375,25 @@ __global__ void __launch_bounds__(MT) stage_march_kernel(StageArgs a, int TY) {
     const float* s0 = ring + ((i - 2) & (MS - 1)) * C * RS;   // row r-2
     const float* s1 = ring + ((i - 1) & (MS - 1)) * C * RS;   // row r-1
     const float* s2 = ring + (i & (MS - 1)) * C * RS;         // row r
+    // a ghost row behind a wall carries the mirrored normal momentum -hv
+    float m0 = 1.f, m1 = 1.f, m2 = 1.f;
+    if (wall) {
+      const int v0r = Y0 + i - 4, v1r = v0r + 1, v2r = v0r + 2;   // virtual rows of s0, s1, s2
+      m0 = v0r < 0 || v0r >= a.ny ? -1.f : 1.f;
+      m1 = v1r < 0 || v1r >= a.ny ? -1.f : 1.f;
+      m2 = v2r < 0 || v2r >= a.ny ? -1.f : 1.f;
+    }
     float2 q0[C][2], q1[C][2], sy[C][2];
 #pragma unroll
     for (int c = 0; c < C; ++c) {
-      const float4 v0 = *reinterpret_cast<const float4*>(s0 + c * RS + col);
-      const float4 v1 = *reinterpret_cast<const float4*>(s1 + c * RS + col);
-      const float4 v2 = *reinterpret_cast<const float4*>(s2 + c * RS + col);
+      float4 v0 = *reinterpret_cast<const float4*>(s0 + c * RS + col);
+      float4 v1 = *reinterpret_cast<const float4*>(s1 + c * RS + col);
+      float4 v2 = *reinterpret_cast<const float4*>(s2 + c * RS + col);
+      if (BND && c == 2) {
+        v0 = make_float4(m0 * v0.x, m0 * v0.y, m0 * v0.z, m0 * v0.w);
+        v1 = make_float4(m1 * v1.x, m1 * v1.y, m1 * v1.z, m1 * v1.w);
+        v2 = make_float4(m2 * v2.x, m2 * v2.y, m2 * v2.z, m2 * v2.w);
+      }
       q0[c][0] = lo(v0); q0[c][1] = hi(v0);
       q1[c][0] = lo(v1); q1[c][1] = hi(v1);
       // y slope at row r-1
@@ -372,6 +427,19 @@ __global__ void __launch_bounds__(MT) stage_march_kernel(StageArgs a, int TY) {
           e[c][0] = lft.x; e[c][1] = lft.y;
           e[c][2] = q0[c][0].x; e[c][3] = q0[c][0].y; e[c][4] = q0[c][1].x; e[c][5] = q0[c][1].y;
           e[c][6] = rgt.x; e[c][7] = rgt.y;
+          if (BND) {
+            // wall ghosts: cell -2 = cell 1, -1 = cell 0 (and nx, nx+1 = nx-1,
+            // nx-2), normal momentum negated
+            const float sg = c == 1 ? -1.f : 1.f;
+            if (wall_w && t == 0) {
+              e[c][0] = sg * lft.y;
+              e[c][1] = sg * lft.x;
+            }
+            if (wall_e && 4 * t + 4 == wact) {
+              e[c][6] = sg * rgt.y;
+              e[c][7] = sg * rgt.x;
+            }
+          }
         }
         float sx[C][6];
 #pragma unroll
@@ -415,8 +483,23 @@ __global__ void __launch_bounds__(MT) stage_march_kernel(StageArgs a, int TY) {
           const float2 Fe0 = make_float2(Fx2[c][0].y, Fx2[c][1].x);
           const float2 Fw1 = Fx2[c][1];
           const float2 Fe1 = make_float2(Fx2[c][1].y, Fx4[c]);
-          const float2 L0 = divergence(Fw0, Fe0, Gp[c][0], Gn[c][0], a.rdx, a.rdy);
-          const float2 L1 = divergence(Fw1, Fe1, Gp[c][1], Gn[c][1], a.rdx, a.rdy);
+          float2 L0 = divergence(Fw0, Fe0, Gp[c][0], Gn[c][0], a.rdx, a.rdy);
+          float2 L1 = divergence(Fw1, Fe1, Gp[c][1], Gn[c][1], a.rdx, a.rdy);
+          if constexpr (BND && EQ == SWE) {
+            if (a.z && c > 0) {
+              // bed slope: -g h (z_e - z_w) / (2 dx) on hu, -g h (z_n - z_s) / (2 dy) on hv
+              float sk[4];
+#pragma unroll
+              for (int k = 0; k < 4; ++k) {
+                const float h = (k & 1) ? q0[0][k >> 1].y : q0[0][k >> 1].x;
+                const float gh = vmul(a.phys, h);
+                sk[k] = c == 1 ? vmul(gh, vmul(vsub(zr[k + 2], zr[k]), 0.5f * a.rdx))
+                               : vmul(gh, vmul(vsub(zn[k], zs[k]), 0.5f * a.rdy));
+              }
+              L0 = vsub(L0, make_float2(sk[0], sk[1]));
+              L1 = vsub(L1, make_float2(sk[2], sk[3]));
+            }
+          }
           if (STAGE == 1) {
             out[c][0] = rk_stage1(q0[c][0], dt, L0);
             out[c][1] = rk_stage1(q0[c][1], dt, L1);
@@ -597,10 +680,10 @@ int march_rows_per_block(int ny, int columns_x_members, int per_sm) {
   return best;
 }
 
-template <int C, int EQ, int STAGE, bool GEN>
+template <int C, int EQ, int STAGE, bool GEN, bool BND = false>
 cudaError_t launch_march(const StageArgs& a, const Geom& g, cudaStream_t s) {
   constexpr int smem = march_smem_bytes<C>();
-  auto kern = stage_march_kernel<C, EQ, STAGE, GEN>;
+  auto kern = stage_march_kernel<C, EQ, STAGE, GEN, BND>;
   static int per_sm = 0;   // resident blocks per SM, queried once per instance
   if (!per_sm) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -616,17 +699,24 @@ cudaError_t launch_march(const StageArgs& a, const Geom& g, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+template <int C, int EQ, bool BND>
+cudaError_t launch_general_b(const StageArgs& a, const Geom& g, int stage, cudaStream_t s) {
+  switch (stage) {
+    case 1: return launch_march<C, EQ, 1, true, BND>(a, g, s);
+    case 2: return launch_march<C, EQ, 2, true, BND>(a, g, s);
+    case 3: return launch_march<C, EQ, 3, true, BND>(a, g, s);
+    default: return launch_march<C, EQ, 4, true, BND>(a, g, s);
+  }
+}
+
 template <int C, int EQ>
 cudaError_t launch_general_t(const Geom& g, int stage, int flux, const float* qin, const float* qn,
-                             float* qout, Ctrl* ctrl, const DtParams* dp, cudaStream_t s) {
+                             float* qout, Ctrl* ctrl, const DtParams* dp, cudaStream_t s, int bc,
+                             const float* z) {
   StageArgs a{qin, qn, qout, ctrl, dp, g.nx, g.ny, g.plane(), g.member(),
-              (float)(1.0 / g.dx), (float)(1.0 / g.dy), g.phys, flux};
-  switch (stage) {
-    case 1: return launch_march<C, EQ, 1, true>(a, g, s);
-    case 2: return launch_march<C, EQ, 2, true>(a, g, s);
-    case 3: return launch_march<C, EQ, 3, true>(a, g, s);
-    default: return launch_march<C, EQ, 4, true>(a, g, s);
-  }
+              (float)(1.0 / g.dx), (float)(1.0 / g.dy), g.phys, flux, bc, z};
+  if (bc != BC_PERIODIC || z) return launch_general_b<C, EQ, true>(a, g, stage, s);
+  return launch_general_b<C, EQ, false>(a, g, stage, s);
 }
 
 template <int C, int EQ, int STAGE>
@@ -666,10 +756,12 @@ cudaError_t launch_stage_minmod(const Geom& g, int stage, const float* qin, cons
 bool march_supported(const Geom& g) { return (g.nx % 4 == 0) && g.nx >= 8; }
 
 cudaError_t launch_stage_general(const Geom& g, int stage, int flux, const float* qin, const float* qn,
-                                 float* qout, Ctrl* ctrl, const DtParams* dp, cudaStream_t s) {
+                                 float* qout, Ctrl* ctrl, const DtParams* dp, cudaStream_t s, int bc,
+                                 const float* z) {
   if (!march_supported(g)) return cudaErrorInvalidValue;
-  return g.eq == SWE ? launch_general_t<3, SWE>(g, stage, flux, qin, qn, qout, ctrl, dp, s)
-                     : launch_general_t<4, EULER>(g, stage, flux, qin, qn, qout, ctrl, dp, s);
+  if ((bc == BC_WALL && g.ny < 2) || (z && g.eq != SWE)) return cudaErrorInvalidValue;
+  return g.eq == SWE ? launch_general_t<3, SWE>(g, stage, flux, qin, qn, qout, ctrl, dp, s, bc, z)
+                     : launch_general_t<4, EULER>(g, stage, flux, qin, qn, qout, ctrl, dp, s, bc, z);
 }
 
 cudaError_t launch_wavespeed_init(const Geom& g, const float* q, Ctrl* ctrl, const DtParams* dp,

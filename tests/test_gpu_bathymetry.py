@@ -1,6 +1,7 @@
 """Parity of the bed-slope source (Eq. 2.3) and of reflecting walls (Section
 4.2) on the GPU against the FP64 oracle (``oracle.bathymetry``), through the
-C ABI.  The oracle's adaptive dt sequence is replayed on the GPU; tolerances
+C ABI, for both stage kernels (row march where nx is a multiple of 4, the
+shared-memory tile kernel everywhere).  The oracle's adaptive dt sequence is replayed on the GPU; tolerances
 are max(fixed floor, 5 x the oracle's own FP32-vs-FP64 distance on the same
 case), the latter measured in the test by replaying the oracle in float32."""
 import numpy as np
@@ -39,10 +40,11 @@ def euler_case(nx, ny):
     return W.as_f32_exact(W.euler_kelvin_helmholtz(nx, ny, seed=2)), None
 
 
-def gpu_run(fv, q0, eq, z, bc, flux, rk, dts):
+def gpu_run(fv, q0, eq, z, bc, flux, rk, dts, variant="auto"):
     q0t = f32(q0).cuda()
     s = fv.swe_init(q0t, dt_mode="replay") if eq == ofv.SWE else fv.euler_init(q0t, dt_mode="replay")
     fv.fv_set_scheme(s, flux, rk)
+    fv.fv_set_stage_variant(s, variant)
     fv.fv_set_boundary(s, bc)
     if z is not None:
         fv.fv_set_bathymetry(s, torch.tensor(z, dtype=torch.float32))
@@ -59,9 +61,18 @@ CASES = [
     (ofv.SWE, 62, 37, True, OB.WALL, "hllc", 3, 60),       # ragged tiles on both axes
     (ofv.SWE, 20, 9, True, OB.WALL, "lf", 2, 40),          # one partial tile, shorter than a tile
     (ofv.SWE, 2, 2, True, OB.WALL, "hll", 2, 10),          # the smallest grid walls accept
+    (ofv.SWE, 8, 12, True, OB.WALL, "roe", 2, 30),         # march: one strip, both walls in it
+    (ofv.SWE, 516, 6, True, OB.WALL, "hllc", 3, 20),       # march: 4-column last strip at the east wall
+    (ofv.SWE, 1024, 40, True, OB.WALL, "roe", 2, 20),      # march: two strips, several row blocks
+    (ofv.SWE, 64, 2, True, OB.WALL, "roe", 2, 20),         # two rows: every y ghost is a mirror
     (ofv.EULER, 64, 64, False, OB.WALL, "hllc", 3, 60),
     (ofv.EULER, 62, 40, False, OB.WALL, "hlle", 2, 60),
+    (ofv.EULER, 516, 12, False, OB.WALL, "rusanov", 2, 20),
 ]
+
+
+def variants(nx):
+    return ("tile", "march") if nx % 4 == 0 and nx >= 8 else ("auto",)
 
 
 @pytest.mark.parametrize("eq,nx,ny,bed,bc,flux,rk,steps", CASES)
@@ -69,20 +80,22 @@ def test_matches_oracle(fv, eq, nx, ny, bed, bc, flux, rk, steps):
     q0, z = swe_case(nx, ny, bed) if eq == ofv.SWE else euler_case(nx, ny)
     zt = None if z is None else torch.tensor(z)
     qr, tr, dts = OB.run(torch.tensor(q0), steps, flux=flux, rk=rk, z=zt, bc=bc, eq=eq)
-    q, s = gpu_run(fv, q0, eq, z, bc, flux, rk, dts[:, 0].numpy())
     q32, _, _ = OB.run(torch.tensor(q0), steps, flux=flux, rk=rk, z=zt, bc=bc, eq=eq,
                        dt_mode=ofv.DT_REPLAY, dts=dts[:, 0], dtype=torch.float32)
     yard = rel_errors(q32.double(), qr)
     tols = [TOL_O1, TOL_MOM, TOL_MOM] + ([TOL_O1] if eq == ofv.EULER else [])
-    err = rel_errors(q, qr)
-    for c, ((e2, ei), (l2, li), (y2, yi)) in enumerate(zip(err, tols, yard)):
-        assert e2 <= max(l2, 5 * y2) and ei <= max(li, 5 * yi), (c, err, yard)
-    t, _, n = fv.fv_get_time(s)
-    assert n[0] == steps and abs(t[0] - float(tr[0])) < 1e-9
+    for variant in variants(nx):
+        q, s = gpu_run(fv, q0, eq, z, bc, flux, rk, dts[:, 0].numpy(), variant)
+        err = rel_errors(q, qr)
+        for c, ((e2, ei), (l2, li), (y2, yi)) in enumerate(zip(err, tols, yard)):
+            assert e2 <= max(l2, 5 * y2) and ei <= max(li, 5 * yi), (variant, c, err, yard)
+        t, _, n = fv.fv_get_time(s)
+        assert n[0] == steps and abs(t[0] - float(tr[0])) < 1e-9
 
 
+@pytest.mark.parametrize("variant", ["tile", "march"])
 @pytest.mark.parametrize("axis", ["x", "y"])
-def test_lake_at_rest_on_a_linear_bed(fv, axis):
+def test_lake_at_rest_on_a_linear_bed(fv, axis, variant):
     """A flat surface over a bed linear along one axis, between walls: one
     step leaves the interior at rest up to FP32 rounding of the pressure
     flux (the centred bed slope cancels the pressure-flux difference); the
@@ -103,6 +116,7 @@ def test_lake_at_rest_on_a_linear_bed(fv, axis):
     for bed in (True, False):
         s = fv.swe_init(q0.cuda(), dt_mode="fixed", dt_fixed=dt)
         fv.fv_set_scheme(s, "roe", 2)
+        fv.fv_set_stage_variant(s, variant)
         fv.fv_set_boundary(s, "wall")
         if bed:
             fv.fv_set_bathymetry(s, torch.tensor(z, dtype=torch.float32).cuda())
@@ -112,18 +126,30 @@ def test_lake_at_rest_on_a_linear_bed(fv, axis):
     assert float(out[1].min()) > 0.5 * scale
 
 
-def test_walls_conserve_mass_over_a_bed(fv):
+@pytest.mark.parametrize("variant", ["tile", "march"])
+def test_walls_conserve_mass_over_a_bed(fv, variant):
     """No mass crosses a wall: over a Perlin bed with an adaptive dt the
     total depth changes only by FP32 rounding of the cell updates."""
     q0, z = swe_case(48, 48, True, seed=7)
     s = fv.swe_init(f32(q0).cuda())
     fv.fv_set_scheme(s, "roe", 2)
+    fv.fv_set_stage_variant(s, variant)
     fv.fv_set_boundary(s, "wall")
     fv.fv_set_bathymetry(s, torch.tensor(z, dtype=torch.float32))
     fv.fv_rollout(s, 300)
     m0 = float(f32(q0)[:, 0].double().sum())
     m = float(fv.fv_get_state(s).double()[:, 0].sum())
     assert abs(m - m0) < 2e-6 * m0, (m, m0)
+
+
+def test_tile_and_march_agree(fv):
+    """Walls and bed in both kernels: the same per-face and per-cell formulas,
+    so after a few steps they agree to a few FP32 ulps of the state."""
+    q0, z = swe_case(128, 40, True, seed=5)
+    _, _, dts = OB.run(torch.tensor(q0), 5, flux="hllc", rk=3, z=torch.tensor(z), bc=OB.WALL)
+    out = [gpu_run(fv, q0, ofv.SWE, z, OB.WALL, "hllc", 3, dts[:, 0].numpy(), v)[0] for v in ("tile", "march")]
+    scale = out[0].abs().amax(dim=(0, 2, 3), keepdim=True)
+    assert ((out[0] - out[1]).abs() / scale).max() < 2e-5
 
 
 def test_clearing_restores_the_periodic_flat_step(fv):
