@@ -251,6 +251,31 @@ def swe_bump_over_bed(z: np.ndarray, amp: float = 0.1, width2: float = 0.005,
     return q
 
 
+def euler_four_quadrant(nx: int, ny: int, seed: int, split=(0.5, 0.5),
+                        gamma: float = GAMMA_IDEAL) -> np.ndarray:
+    """A 2D Riemann problem for Euler (Section 4.2's planar Euler test): four
+    constant states in the quadrants around ``split``, drawn from the seed
+    (rho in [0.5, 2], p in [0.3, 1.5], u and v in [-0.75, 0.75]).  The
+    thesis runs one of Liska and Wendroff's configurations, whose states it
+    does not print; these seeded states stand in for it.  Returns conserved
+    variables ``[1][4][ny][nx]``; quadrant k = 0 (x, y >= split), 1 (x <
+    split, y >= split), 2 (both below), 3 (x >= split, y < split)."""
+    rng = _rng(seed)
+    X, Y = _mesh(nx, ny)
+    rho = rng.uniform(0.5, 2.0, 4)
+    p = rng.uniform(0.3, 1.5, 4)
+    u = rng.uniform(-0.75, 0.75, 4)
+    v = rng.uniform(-0.75, 0.75, 4)
+    east, north = X >= split[0], Y >= split[1]
+    k = np.where(north, np.where(east, 0, 1), np.where(east, 3, 2))
+    q = np.zeros((1, 4, ny, nx))
+    q[0, 0] = rho[k]
+    q[0, 1] = rho[k] * u[k]
+    q[0, 2] = rho[k] * v[k]
+    q[0, 3] = p[k] / (gamma - 1.0) + 0.5 * rho[k] * (u[k] ** 2 + v[k] ** 2)
+    return q
+
+
 @dataclasses.dataclass
 class Request:
     """One solve request of the serving workload."""
