@@ -460,6 +460,27 @@ def schemes_block(args):
         out[key] = {"cell_updates_per_s": rate, "ms_per_step": ms / K,
                     "hbm_gbs": gbs, "frac_of_measured_hbm": gbs / peak}
         del st
+    # Section 4.2's planar Euler test: a four-quadrant Riemann problem between
+    # walls (seeded states), HLLE with SSP-RK2, 80 bytes per cell-update
+    qe = torch.tensor(W.euler_four_quadrant(N_EULER, N_EULER, seed=4), dtype=torch.float32).cuda()
+    with torch.cuda.stream(bs):
+        st = fv.euler_init(qe, cfl=0.5)
+    fv.fv_set_scheme(st, "hlle", 2)
+    fv.fv_set_boundary(st, "wall")
+    fv.fv_enqueue_steps(st, 3)
+    fv.fv_sync(st)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(bs)
+    fv.fv_enqueue_steps(st, K)
+    e1.record(bs)
+    fv.fv_sync(st)
+    ms = e0.elapsed_time(e1)
+    rate = N_EULER * N_EULER * K / (ms * 1e-3)
+    out["euler_four_quadrant_walls_hlle_rk2"] = {
+        "workload": f"Euler four-quadrant Riemann problem {N_EULER}^2, walls, CFL 0.5",
+        "cell_updates_per_s": rate, "ms_per_step": ms / K, "hbm_gbs": 80 * rate / 1e9,
+        "frac_of_measured_hbm": 80 * rate / 1e9 / peak}
+    del st
     return out
 
 

@@ -177,9 +177,10 @@ int fv_set_scheme(fv_state* s, int flux, int rk);
  * FV_BC_PERIODIC (default) or FV_BC_WALL, a reflecting wall as in the
  * bathymetry test of Section 4.2: the halo cells mirror the interior with the
  * momentum normal to the wall negated, so no mass crosses it.  Walls run in
- * the shared-memory tile kernel (any flux and integrator of fv_set_scheme);
- * the learned step stays periodic (FV_EINVAL there).  FV_EINVAL for an
- * unknown value or a grid narrower than 2 cells. */
+ * the plain step's stage kernels (row march or tile, per
+ * fv_set_stage_variant; any flux and integrator of fv_set_scheme); the
+ * learned step stays periodic (FV_EINVAL there).  FV_EINVAL for an unknown
+ * value or a grid narrower than 2 cells. */
 enum { FV_BC_PERIODIC = 0, FV_BC_WALL = 1 };
 int fv_set_boundary(fv_state* s, int bc);
 
@@ -188,8 +189,9 @@ int fv_set_boundary(fv_state* s, int bc);
  * [ny][nx] (one bed for every member; host or device memory per z_loc,
  * copied, not retained) and its slope taken as the centred difference
  * (z_{i+1} - z_{i-1}) / (2 dx) (mirrored at walls, wrapped when periodic).
- * z = NULL returns to the flat bed.  Runs in the tile kernel; the learned
- * step needs a flat bed.  FV_EINVAL for an Euler state or a bad z_loc. */
+ * z = NULL returns to the flat bed.  Runs in the plain step's stage kernels;
+ * the learned step needs a flat bed.  FV_EINVAL for an Euler state or a bad
+ * z_loc. */
 int fv_set_bathymetry(fv_state* s, const float* z, int z_loc);
 
 /* Implementation of the learned step (Section 2.5.3, fourth approach):

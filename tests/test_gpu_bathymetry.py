@@ -93,6 +93,23 @@ def test_matches_oracle(fv, eq, nx, ny, bed, bc, flux, rk, steps):
         assert n[0] == steps and abs(t[0] - float(tr[0])) < 1e-9
 
 
+@pytest.mark.parametrize("flux", ["rusanov", "roe", "hll", "hlle"])
+def test_four_quadrant_riemann_matches_oracle(fv, flux):
+    """Section 4.2's planar Euler test (a four-quadrant Riemann problem
+    between walls, the fluxes of its tables) on seeded quadrant states."""
+    q0 = W.as_f32_exact(W.euler_four_quadrant(64, 64, seed=4))
+    qr, tr, dts = OB.run(torch.tensor(q0), 60, flux=flux, rk=2, bc=OB.WALL, eq=ofv.EULER)
+    q32, _, _ = OB.run(torch.tensor(q0), 60, flux=flux, rk=2, bc=OB.WALL, eq=ofv.EULER,
+                       dt_mode=ofv.DT_REPLAY, dts=dts[:, 0], dtype=torch.float32)
+    yard = rel_errors(q32.double(), qr)
+    for variant in ("tile", "march"):
+        q, _ = gpu_run(fv, q0, ofv.EULER, None, OB.WALL, flux, 2, dts[:, 0].numpy(), variant)
+        err = rel_errors(q, qr)
+        for c, ((e2, ei), (y2, yi)) in enumerate(zip(err, yard)):
+            l2, li = TOL_O1 if c in (0, 3) else TOL_MOM
+            assert e2 <= max(l2, 5 * y2) and ei <= max(li, 5 * yi), (variant, c, err, yard)
+
+
 @pytest.mark.parametrize("variant", ["tile", "march"])
 @pytest.mark.parametrize("axis", ["x", "y"])
 def test_lake_at_rest_on_a_linear_bed(fv, axis, variant):
