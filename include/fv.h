@@ -290,6 +290,45 @@ int stencil_net_get_params(const fv_net* n, float* params, int loc);
 int stencil_net_forward(const fv_net* n, const float* q, int B, int ny, int nx, float* coeffs,
                         int raw, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Face-state network (Section 2.5.3, third approach; Section 5.3)
+ *
+ * A CNN gives each cell the states on its four sides directly.  Architecture:
+ * x = (q - mean) / std; four 3x3 periodic convolutions 3 -> 32 -> 32 -> 32
+ * -> 12 with GeLU (x Phi(x), erf form) after the first three; BF16 operands,
+ * FP32 accumulation on the tensor cores.  Output channel 3 s + v is side s
+ * (0 west, 1 east, 2 south, 3 north) of variable v (h, hu, hv); depths are
+ * Softplus(r), momenta mean_v + std_v r.  The flux through the face between
+ * cells i-1 and i is HLL of (east state of i-1, west state of i); in y of
+ * (north state of j-1, south state of j).  fv_step, fv_enqueue_steps,
+ * fv_rollout and the server take a face-state network wherever they take a
+ * stencil network (HLL, SSP-RK2, periodic flat bed, adaptive or fixed dt;
+ * the network runs at both stages).  stencil_net_destroy, _set_params,
+ * _get_params and _adam_step accept either kind, with fv_net_num_params()
+ * parameters; training tapes hold stencil networks only.
+ * ------------------------------------------------------------------------- */
+
+/* W1[32][3][3][3] b1[32] W2[32][32][3][3] b2[32] W3[32][32][3][3] b3[32]
+ * W4[12][32][3][3] b4[12] (PyTorch Conv2d layout). */
+#define FV_FACE_NET_PARAMS 22860
+
+/* Create a face-state network; params host [FV_FACE_NET_PARAMS] FP32 (NULL =
+ * all zeros), norm as for stencil_net_create.  Errors: FV_EINVAL, FV_ENOMEM,
+ * FV_ECUDA. */
+int face_net_create(const float* params, const float* norm, fv_net** out);
+
+/* Forward on q (device [B][3][ny][nx] FP32): sides (device [B][12][ny][nx]
+ * FP32) receives the side states, or the raw network outputs r if raw != 0.
+ * Grid rules, stream and errors as stencil_net_forward; FV_EINVAL for a
+ * stencil network. */
+int face_net_forward(const fv_net* n, const float* q, int B, int ny, int nx, float* sides, int raw,
+                     void* stream);
+
+/* Kind of a network: 0 = stencil (fourth approach), 1 = face-state (third);
+ * -1 for NULL.  Parameter count of its kind (0 for NULL). */
+int fv_net_kind(const fv_net* n);
+int fv_net_num_params(const fv_net* n);
+
 /* Coarse graining (Section 2.5.1): coarse[p][j][i] = mean of the factor x
  * factor block of fine[p][.][.] (FP64 sum), for `planes` planes of ny x nx
  * (device pointers; nx, ny multiples of factor).  Synchronous on `stream`
@@ -386,8 +425,8 @@ int fv_tape_loss(fv_tape* t, const float* targets, const float* scale3, double* 
 int fv_tape_backward(fv_tape* t, const float* dsnaps, float* dparams, float* dq0);
 
 /* One Adam step (bias-corrected; moments kept in the network) with the
- * gradient grad (device [FV_NET_PARAMS]); step counts from 1.  Repacks the
- * tensor-core weights. */
+ * gradient grad (device [fv_net_num_params(n)]); step counts from 1.  Repacks
+ * the tensor-core weights. */
 int stencil_net_adam_step(fv_net* n, const float* grad, int step, double lr, double b1, double b2,
                           double eps);
 

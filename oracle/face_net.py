@@ -28,7 +28,12 @@ the design notes):
 
 Precision mirror: with ``round_bf16=True`` the network input and every hidden
 activation are rounded to bfloat16 and the weights are expected to be
-bfloat16 values, as on the GPU; sums stay FP64.
+bfloat16 values, as on the GPU; sums stay FP64.  ``run(..., dtype=float32)``
+replays the same algorithm in single precision (sums, GeLU, the flux and
+the update): its distance from the FP64 run is the roundoff yardstick of the
+GPU parity tests.  Because the depth outputs feed the pressure flux
+directly, a BF16 rounding of a hidden activation that flips between the two
+precisions moves the momentum by far more than FP32 roundoff alone.
 """
 from __future__ import annotations
 
@@ -94,17 +99,27 @@ def softplus(x: torch.Tensor) -> torch.Tensor:
     return torch.logaddexp(torch.zeros_like(x), x)
 
 
+def _round_bf16(x: torch.Tensor) -> torch.Tensor:
+    """Round to bfloat16 (nearest-even), in the precision of x; the FP64
+    path keeps the graph through the rounding."""
+    if x.dtype == torch.float64:
+        return bf16(x)
+    return x.to(torch.bfloat16).to(x.dtype)
+
+
 def net_raw(q: torch.Tensor, p: FaceNetParams, round_bf16: bool = True) -> torch.Tensor:
-    """Raw network output r[B][12][ny][nx] for the state q (SWE)."""
-    x = (q - p.mean.view(1, -1, 1, 1)) / p.std.view(1, -1, 1, 1)
+    """Raw network output r[B][12][ny][nx] for the state q (SWE), computed
+    in the precision of q."""
+    dt_ = q.dtype
+    x = (q - p.mean.to(dt_).view(1, -1, 1, 1)) / p.std.to(dt_).view(1, -1, 1, 1)
     if round_bf16:
-        x = bf16(x)
+        x = _round_bf16(x)
     for layer in range(4):
-        x = conv3x3_periodic(x, p.W[layer], p.b[layer])
+        x = conv3x3_periodic(x, p.W[layer].to(dt_), p.b[layer].to(dt_))
         if layer < 3:
             x = gelu(x)
             if round_bf16:
-                x = bf16(x)
+                x = _round_bf16(x)
     return x
 
 
@@ -113,9 +128,10 @@ def side_states(raw: torch.Tensor, p: FaceNetParams) -> torch.Tensor:
     outputs: Softplus on the depths, de-normalised momenta."""
     B, _, ny, nx = raw.shape
     r = raw.reshape(B, 4, 3, ny, nx)
+    mean, std = p.mean.to(raw.dtype), p.std.to(raw.dtype)
     h = softplus(r[:, :, 0])
-    hu = p.mean[1] + p.std[1] * r[:, :, 1]
-    hv = p.mean[2] + p.std[2] * r[:, :, 2]
+    hu = mean[1] + std[1] * r[:, :, 1]
+    hv = mean[2] + std[2] * r[:, :, 2]
     return torch.stack([h, hu, hv], dim=2)
 
 
@@ -141,21 +157,22 @@ def step(q, p: FaceNetParams, dt, g=9.81, round_bf16=True):
 
 
 def run(q0, p: FaceNetParams, nsteps: int, *, cfl: float = 0.5, dt_mode: str = fv.DT_ADAPTIVE,
-        dt_fixed=None, dts=None, g: float = 9.81, round_bf16: bool = True):
+        dt_fixed=None, dts=None, g: float = 9.81, round_bf16: bool = True, dtype=torch.float64):
     """``nsteps`` steps; dt by the CFL rule (Eq. 2.10) of the state at the
-    start of each step, fixed, or replayed.  Returns (q, t, dt_history)."""
-    q = torch.as_tensor(q0, dtype=torch.float64).clone()
+    start of each step, fixed, or replayed.  Returns (q, t, dt_history).
+    ``dtype`` float32 replays the algorithm in single precision."""
+    q = torch.as_tensor(q0).to(dtype).clone()
     B = q.shape[0]
     dx, dy = fv.grid_spacing(q)
-    t = torch.zeros(B, dtype=torch.float64)
+    t = torch.zeros(B, dtype=dtype)
     hist = []
     for n in range(nsteps):
         if dt_mode == fv.DT_ADAPTIVE:
-            dt = fv.cfl_dt(q, fv.SWE, cfl, dx, dy, g)
+            dt = fv.cfl_dt(q, fv.SWE, cfl, dx, dy, g).to(dtype)
         elif dt_mode == fv.DT_FIXED:
-            dt = torch.full((B,), float(dt_fixed), dtype=torch.float64)
+            dt = torch.full((B,), float(dt_fixed), dtype=dtype)
         else:
-            d = torch.as_tensor(dts[n], dtype=torch.float64)
+            d = torch.as_tensor(dts[n]).to(dtype)
             dt = d.expand(B).clone() if d.dim() == 0 else d.clone()
         q = step(q, p, dt.view(B, 1, 1, 1), g, round_bf16)
         t = t + dt

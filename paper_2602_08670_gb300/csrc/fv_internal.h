@@ -28,6 +28,10 @@ cudaError_t enqueue_scheme_step(const Geom& g, int flux, int rk, float* qa, floa
 cudaError_t launch_stage_learned(const Geom& g, int stage, const float* qin, const float* qn,
                                  float* qout, const float* w, const float* hmin, Ctrl* ctrl,
                                  const DtParams* dp, cudaStream_t s);
+// One SSP-RK2 stage of the face-state path (Section 2.5.3, third approach)
+// from the side states [B][12][plane] of qin.
+cudaError_t launch_stage_face(const Geom& g, int stage, const float* qin, const float* qn, float* qout,
+                              const float* sides, Ctrl* ctrl, const DtParams* dp, cudaStream_t s);
 }
 
 struct fv_learned_ws;   // per-state workspace of the learned step (fv_learned.cu)
@@ -71,8 +75,9 @@ cudaError_t enqueue_plain_step(fv_state* s);
 cudaError_t enqueue_step(fv_state* s, const fv_net* net);
 int check_health(fv_state* s);
 // learned path (fv_learned.cu)
-int learned_prepare(fv_state* s);                    // host side, before enqueueing
+int learned_prepare(fv_state* s, const fv_net* net);  // host side, before enqueueing
 cudaError_t enqueue_learned_step(fv_state* s, const fv_net* net);
 void learned_workspace_free(fv_state* s);
+bool learned_hmin_fixed(const fv_state* s);           // a stencil-network step has set h_min
 int net_check(const fv_net* n);                      // device error word of a network
 }  // namespace fvs

@@ -104,7 +104,7 @@ int start_request(fv_server* S, Req* q) {
   if (rc != FV_OK) return rc;
   if (cudaEventCreateWithFlags(&q->ev, cudaEventDisableTiming) != cudaSuccess) return FV_ECUDA;
   if (q->r.learned) {
-    rc = fvs::learned_prepare(q->st);
+    rc = fvs::learned_prepare(q->st, S->net);
     if (rc != FV_OK) return rc;
   }
   return FV_OK;

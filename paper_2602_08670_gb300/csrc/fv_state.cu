@@ -255,7 +255,7 @@ extern "C" int fv_step(fv_state* s, const fv_net* net) {
   if (!s) return fvh::fail(FV_EINVAL, "null state");
   if (net && s->g.eq != fvk::SWE) return fvh::fail(FV_EINVAL, "learned step is SWE only");
   if (net) {
-    int rc = fvs::learned_prepare(s);
+    int rc = fvs::learned_prepare(s, net);
     if (rc != FV_OK) return rc;
   }
   FV_CUDA_TRY(fvs::enter(s));
@@ -319,7 +319,7 @@ extern "C" int fv_enqueue_steps(fv_state* s, const fv_net* net, long nsteps) {
   if (nsteps < 0) return fvh::fail(FV_EINVAL, "nsteps < 0");
   if (net && s->g.eq != fvk::SWE) return fvh::fail(FV_EINVAL, "learned step is SWE only");
   if (net) {
-    int rc = fvs::learned_prepare(s);
+    int rc = fvs::learned_prepare(s, net);
     if (rc != FV_OK) return rc;
   }
   FV_CUDA_TRY(fvs::enter(s));
@@ -337,7 +337,7 @@ extern "C" int fv_rollout(fv_state* s, const fv_net* net, long nsteps, double t_
   if (net && s->g.eq != fvk::SWE) return fvh::fail(FV_EINVAL, "learned step is SWE only");
   if (snaps && snap_every <= 0) return fvh::fail(FV_EINVAL, "snap_every must be > 0 with snaps");
   if (net) {
-    int rc = fvs::learned_prepare(s);
+    int rc = fvs::learned_prepare(s, net);
     if (rc != FV_OK) return rc;
   }
   FV_CUDA_TRY(fvs::enter(s));
@@ -497,7 +497,7 @@ extern "C" int fv_set_learned_variant(fv_state* s, int variant) {
 extern "C" int fv_set_learned_hmin(fv_state* s, double hmin_frac) {
   if (!s) return fvh::fail(FV_EINVAL, "null state");
   if (!(hmin_frac >= 0.0) || hmin_frac >= 1.0) return fvh::fail(FV_EINVAL, "hmin_frac must be in [0, 1)");
-  if (s->lws) return fvh::fail(FV_EINVAL, "h_min is fixed once the state has taken a learned step");
+  if (fvs::learned_hmin_fixed(s)) return fvh::fail(FV_EINVAL, "h_min is fixed once the state has taken a learned step");
   s->hmin_frac = (float)hmin_frac;
   return FV_OK;
 }

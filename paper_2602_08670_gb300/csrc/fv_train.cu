@@ -425,6 +425,7 @@ extern "C" int fv_tape_create(fv_net* net, int B, int ny, int nx, int T, double 
                               double hmin_frac, fv_tape** out) {
   if (!net || !out) return fvh::fail(FV_EINVAL, "null argument");
   *out = nullptr;
+  if (net->n.kind != snk::NET_STENCIL) return fvh::fail(FV_EINVAL, "training tapes hold stencil networks");
   if (B < 1 || T < 1 || !(dt > 0) || !(g > 0) || hmin_frac < 0 || hmin_frac >= 1)
     return fvh::fail(FV_EINVAL, "bad tape arguments");
   if (!snk::grid_supported(nx) || ((long long)nx * ny) % snk::TILE != 0)
@@ -570,15 +571,16 @@ extern "C" int fv_tape_backward(fv_tape* t, const float* dsnaps, float* dparams,
 extern "C" int stencil_net_adam_step(fv_net* n, const float* grad, int step, double lr, double b1,
                                      double b2, double eps) {
   if (!n || !grad || step < 1) return fvh::fail(FV_EINVAL, "bad Adam arguments");
+  const int np = snk::n_params(n->n.kind);
   if (!n->adam_m) {
-    FV_CUDA_TRY(cudaMalloc(&n->adam_m, sizeof(float) * snk::N_PARAMS));
-    FV_CUDA_TRY(cudaMalloc(&n->adam_v, sizeof(float) * snk::N_PARAMS));
-    FV_CUDA_TRY(cudaMemsetAsync(n->adam_m, 0, sizeof(float) * snk::N_PARAMS, n->stream));
-    FV_CUDA_TRY(cudaMemsetAsync(n->adam_v, 0, sizeof(float) * snk::N_PARAMS, n->stream));
+    FV_CUDA_TRY(cudaMalloc(&n->adam_m, sizeof(float) * np));
+    FV_CUDA_TRY(cudaMalloc(&n->adam_v, sizeof(float) * np));
+    FV_CUDA_TRY(cudaMemsetAsync(n->adam_m, 0, sizeof(float) * np, n->stream));
+    FV_CUDA_TRY(cudaMemsetAsync(n->adam_v, 0, sizeof(float) * np, n->stream));
   }
   const double c1 = 1.0 - pow(b1, step), c2 = 1.0 - pow(b2, step);
-  fvk::adam_kernel<<<(snk::N_PARAMS + 255) / 256, 256, 0, n->stream>>>(
-      n->n.params, grad, n->adam_m, n->adam_v, snk::N_PARAMS, (float)lr, (float)b1, (float)b2,
+  fvk::adam_kernel<<<(np + 255) / 256, 256, 0, n->stream>>>(
+      n->n.params, grad, n->adam_m, n->adam_v, np, (float)lr, (float)b1, (float)b2,
       (float)eps, (float)c1, (float)c2);
   FV_CUDA_TRY(cudaGetLastError());
   FV_CUDA_TRY(snk::repack(n->n, n->stream));

@@ -11,7 +11,10 @@
 // bias and either applies ReLU and stores BF16 activations, or normalises
 // each 3-tap stencil (w = e_centre + r - mean(r)) and stores the FP32
 // coefficients.  The first layer reads the FP32 state and normalises it
-// (x = (q - mean) / std) while staging.
+// (x = (q - mean) / std) while staging.  The face-state network (third
+// approach) uses the same kernel with a GeLU epilogue on the hidden layers
+// and a side-state epilogue (Softplus depths, de-normalised momenta) on the
+// last one.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -24,9 +27,9 @@
 
 namespace snk {
 
-ParamLayout param_layout() {
+ParamLayout param_layout(int kind) {
   ParamLayout L{};
-  const int cout[4] = {HID, HID, HID, N_OUT};
+  const int cout[4] = {HID, HID, HID, kind == NET_FACE ? N_OUT_FACE : N_OUT};
   const int cin[4] = {C_IN, HID, HID, HID};
   int off = 0;
   for (int l = 0; l < 4; ++l) {
@@ -40,6 +43,8 @@ ParamLayout param_layout() {
   return L;
 }
 
+int n_params(int kind) { return kind == NET_FACE ? N_PARAMS_FACE : N_PARAMS; }
+
 bool grid_supported(int nx) { return nx % TILE == 0 || nx == 8 || nx == 16 || nx == 32 || nx == 64; }
 
 namespace {
@@ -51,7 +56,7 @@ constexpr int NPOS_MAX = 3 * (TILE + 2 * 64);   // flat mode with nx <= 64
 constexpr uint32_t WAIT_ITERS = 1u << 22;
 
 enum { IN_STATE = 0, IN_ACT = 1 };
-enum { OUT_RELU = 0, OUT_W = 1, OUT_RAW = 2, OUT_MASK = 3 };
+enum { OUT_RELU = 0, OUT_W = 1, OUT_RAW = 2, OUT_MASK = 3, OUT_GELU = 4, OUT_SIDES = 5, OUT_SIDES_RAW = 6 };
 
 struct ConvArgs {
   const float* q;          // IN_STATE: [B][3][plane]
@@ -59,9 +64,10 @@ struct ConvArgs {
   const uint16_t* wpk;     // [9][CG][N][8]
   const float* bias;
   uint16_t* y;             // OUT_RELU: [B][4][plane][8]
-  float* w;                // OUT_W / OUT_RAW: [B][36][plane]
+  float* w;                // OUT_W / OUT_RAW: [B][36][plane]; OUT_SIDES(_RAW): [B][12][plane]
   const uint16_t* mask;    // OUT_MASK: activation [B][4][plane][8]; output kept where it is > 0
   float mean0, mean1, mean2, rstd0, rstd1, rstd2;
+  float std1, std2;        // OUT_SIDES: momentum de-normalisation
   int nx, ny;
   long long plane;
   unsigned* err;
@@ -86,6 +92,12 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
   const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
   return *reinterpret_cast<const uint32_t*>(&v);
 }
+
+// GeLU, x Phi(x), with Phi written through the error function.
+__device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.f + erff(x * 0.70710678118654752f)); }
+
+// Softplus, log(1 + e^x) = max(x, 0) + log(1 + e^-|x|).
+__device__ __forceinline__ float softplus(float x) { return fmaxf(x, 0.f) + log1pf(expf(-fabsf(x))); }
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(tc::smem_u32(smem)), "l"(gmem)
@@ -200,7 +212,7 @@ __global__ void __launch_bounds__(NT) conv_kernel(ConvArgs a) {
         *reinterpret_cast<uint4*>(a.y + (((long long)b * 4 + g) * a.plane + cell) * 8) =
             make_uint4(pk[0], pk[1], pk[2], pk[3]);
       }
-    } else if constexpr (OUT == OUT_RELU) {
+    } else if constexpr (OUT == OUT_RELU || OUT == OUT_GELU) {
       float v[32];
       tc::tmem_ld32(lane_addr, v);
 #pragma unroll
@@ -209,10 +221,30 @@ __global__ void __launch_bounds__(NT) conv_kernel(ConvArgs a) {
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
           const int c0 = 8 * g + 2 * j;
-          pk[j] = pack_bf16x2(fmaxf(v[c0] + a.bias[c0], 0.f), fmaxf(v[c0 + 1] + a.bias[c0 + 1], 0.f));
+          const float z0 = v[c0] + a.bias[c0], z1 = v[c0 + 1] + a.bias[c0 + 1];
+          if constexpr (OUT == OUT_RELU) {
+            pk[j] = pack_bf16x2(fmaxf(z0, 0.f), fmaxf(z1, 0.f));
+          } else {
+            pk[j] = pack_bf16x2(gelu(z0), gelu(z1));
+          }
         }
         *reinterpret_cast<uint4*>(a.y + (((long long)b * 4 + g) * a.plane + cell) * 8) =
             make_uint4(pk[0], pk[1], pk[2], pk[3]);
+      }
+    } else if constexpr (OUT == OUT_SIDES || OUT == OUT_SIDES_RAW) {
+      // side states of the face-state network: channel 3 side + var
+      float v[16];
+      tc::tmem_ld16(lane_addr, v);
+      float* sb = a.w + (long long)b * N_OUT_FACE * a.plane + cell;
+#pragma unroll
+      for (int k = 0; k < N_OUT_FACE; ++k) {
+        const float r = v[k] + a.bias[k];
+        float o = r;
+        if constexpr (OUT == OUT_SIDES) {
+          const int var = k % 3;
+          o = var == 0 ? softplus(r) : (var == 1 ? fmaf(a.std1, r, a.mean1) : fmaf(a.std2, r, a.mean2));
+        }
+        sb[k * a.plane] = o;
       }
     } else {
       float v[32], v2[16];
@@ -246,16 +278,18 @@ __global__ void __launch_bounds__(NT) conv_kernel(ConvArgs a) {
 // FP32 master parameters -> BF16 operand layouts.
 //   forward  wf[l][tap][g][n][k8] = W_l[n][8g + k8][ky][kx]
 //   backward wb[l][tap][g][n][k8] = W_l[8g + k8][n][2 - ky][2 - kx]   (l >= 1)
+// The row-pipelined operands (w1g, wpair, w4ring) exist for the stencil
+// network only; they are skipped when null.  n_last: N of the last layer.
 __global__ void repack_kernel(const float* params, ParamLayout L, uint16_t* wf0, uint16_t* wf1,
                               uint16_t* wf2, uint16_t* wf3, uint16_t* wb1, uint16_t* wb2,
                               uint16_t* wb3, uint16_t* w1g, uint16_t* wp1, uint16_t* wp2,
-                              uint16_t* w4r) {
+                              uint16_t* w4r, int n_last) {
   uint16_t* wf[4] = {wf0, wf1, wf2, wf3};
   uint16_t* wb[4] = {nullptr, wb1, wb2, wb3};
   const int cgs[4] = {CG_IN0, CG_HID, CG_HID, CG_HID};
-  const int ns[4] = {HID, HID, HID, N_OUT_PAD};
+  const int ns[4] = {HID, HID, HID, n_last};
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < W1G_ELEMS) {
+  if (w1g && i < W1G_ELEMS) {
     // w1g[ky][g][n][k8] = W_1[n][var][ky][kx] with 8 g + k8 = 3 kx + var
     const int k8 = i % 8, n = (i / 8) % HID, g = (i / (8 * HID)) % 2, ky = i / (16 * HID);
     const int c = 8 * g + k8;
@@ -264,7 +298,7 @@ __global__ void repack_kernel(const float* params, ParamLayout L, uint16_t* wf0,
     const __nv_bfloat16 h = __float2bfloat16_rn(v);
     w1g[i] = *reinterpret_cast<const uint16_t*>(&h);
   }
-  if (i < W4R_ELEMS) {
+  if (w4r && i < W4R_ELEMS) {
     // w4ring[kx][g][n][k8]: block n / 24 holds the tap ky = 2, 1, 0, 2, 1; row
     // r = n % 24 = 2 s + j the difference W_4[3 s + j] - W_4[3 s + 2]
     const int k8 = i % 8, n = (i / 8) % W4R_ROWS, g = (i / (8 * W4R_ROWS)) % CG_HID,
@@ -287,7 +321,7 @@ __global__ void repack_kernel(const float* params, ParamLayout L, uint16_t* wf0,
     // [ky = 0: kx][g][n][k8], then [kx][g][ky = 2 | ky = 1][k8]
     const int N = HID;
     const int part0 = 3 * CG_HID * N * 8;
-    if (i < 9 * CG_HID * N * 8) {
+    if (wp[l] && i < 9 * CG_HID * N * 8) {
       int kx, g, n, k8, ky;
       if (i < part0) {
         k8 = i % 8;
@@ -363,12 +397,13 @@ int backward_groups(int cout) {
 }
 
 cudaError_t repack(Net& net, cudaStream_t s) {
-  const ParamLayout L = param_layout();
   const int maxn = 9 * CG_HID * N_OUT_PAD * 8 > 9 * 6 * HID * 8 ? 9 * CG_HID * N_OUT_PAD * 8 : 9 * 6 * HID * 8;
   static_assert(W4R_ELEMS <= 9 * CG_HID * N_OUT_PAD * 8, "repack grid covers the layer-4 ring weights");
-  repack_kernel<<<(maxn + 255) / 256, 256, 0, s>>>(net.params, L, net.wf[0], net.wf[1], net.wf[2],
+  const ParamLayout Lk = param_layout(net.kind);
+  repack_kernel<<<(maxn + 255) / 256, 256, 0, s>>>(net.params, Lk, net.wf[0], net.wf[1], net.wf[2],
                                                    net.wf[3], net.wb[1], net.wb[2], net.wb[3],
-                                                   net.w1g, net.wpair[1], net.wpair[2], net.w4ring);
+                                                   net.w1g, net.wpair[1], net.wpair[2], net.w4ring,
+                                                   net.kind == NET_FACE ? N_OUT_FACE_PAD : N_OUT_PAD);
   return cudaGetLastError();
 }
 
@@ -434,6 +469,50 @@ cudaError_t forward(const Net& net, const float* q, int B, int ny, int nx, Acts&
   }
   a.w = w;
   return launch_conv<CG_HID, N_OUT_PAD, IN_ACT, OUT_W>(a, B, s);
+}
+
+cudaError_t forward_faces(const Net& net, const float* q, int B, int ny, int nx, Acts& acts,
+                          float* sides, float* raw, cudaStream_t s) {
+  if (net.kind != NET_FACE) return cudaErrorInvalidValue;
+  const ParamLayout L = param_layout(NET_FACE);
+  ConvArgs a{};
+  a.nx = nx;
+  a.ny = ny;
+  a.plane = (long long)nx * ny;
+  a.err = net.err;
+  a.mean0 = net.mean[0];
+  a.mean1 = net.mean[1];
+  a.mean2 = net.mean[2];
+  a.rstd0 = 1.f / net.std_[0];
+  a.rstd1 = 1.f / net.std_[1];
+  a.rstd2 = 1.f / net.std_[2];
+  a.std1 = net.std_[1];
+  a.std2 = net.std_[2];
+  // layer 1: state -> a0 (GeLU)
+  a.q = q;
+  a.wpk = net.wf[0];
+  a.bias = net.params + L.b[0];
+  a.y = acts.a[0];
+  cudaError_t e = launch_conv<CG_IN0, HID, IN_STATE, OUT_GELU>(a, B, s);
+  if (e != cudaSuccess) return e;
+  for (int l = 1; l < 3; ++l) {
+    a.x = acts.a[l - 1];
+    a.wpk = net.wf[l];
+    a.bias = net.params + L.b[l];
+    a.y = acts.a[l];
+    e = launch_conv<CG_HID, HID, IN_ACT, OUT_GELU>(a, B, s);
+    if (e != cudaSuccess) return e;
+  }
+  // layer 4: a2 -> the 12 side states
+  a.x = acts.a[2];
+  a.wpk = net.wf[3];
+  a.bias = net.params + L.b[3];
+  if (raw) {
+    a.w = raw;
+    return launch_conv<CG_HID, N_OUT_FACE_PAD, IN_ACT, OUT_SIDES_RAW>(a, B, s);
+  }
+  a.w = sides;
+  return launch_conv<CG_HID, N_OUT_FACE_PAD, IN_ACT, OUT_SIDES>(a, B, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -754,23 +833,32 @@ cudaError_t backward(const Net& net, const float* q, int B, int ny, int nx, cons
 // ---------------------------------------------------------------------------
 namespace {
 
-int net_alloc(fv_net* n) {
+int net_alloc(fv_net* n, int kind) {
   snk::Net& N = n->n;
+  N.kind = kind;
+  const bool face = kind == snk::NET_FACE;
   cudaError_t e;
-  if ((e = cudaMalloc(&N.params, sizeof(float) * snk::N_PARAMS)) != cudaSuccess) return fvh::cuda_fail(e, "cudaMalloc(params)");
+  if ((e = cudaMalloc(&N.params, sizeof(float) * snk::n_params(kind))) != cudaSuccess)
+    return fvh::cuda_fail(e, "cudaMalloc(params)");
   const int fsz[4] = {9 * snk::CG_IN0 * snk::HID * 8, 9 * snk::CG_HID * snk::HID * 8,
-                      9 * snk::CG_HID * snk::HID * 8, 9 * snk::CG_HID * snk::N_OUT_PAD * 8};
+                      9 * snk::CG_HID * snk::HID * 8,
+                      9 * snk::CG_HID * (face ? snk::N_OUT_FACE_PAD : snk::N_OUT_PAD) * 8};
   for (int l = 0; l < 4; ++l)
     if ((e = cudaMalloc(&N.wf[l], 2 * fsz[l])) != cudaSuccess) return fvh::cuda_fail(e, "cudaMalloc(wf)");
   for (int l = 1; l < 4; ++l) {
-    const int cg = snk::backward_groups(snk::param_layout().cout[l]);
+    const int cg = snk::backward_groups(snk::param_layout(kind).cout[l]);
     if ((e = cudaMalloc(&N.wb[l], 2 * 9 * cg * snk::HID * 8)) != cudaSuccess)
       return fvh::cuda_fail(e, "cudaMalloc(wb)");
   }
-  if ((e = cudaMalloc(&N.w1g, 2 * snk::W1G_ELEMS)) != cudaSuccess) return fvh::cuda_fail(e, "cudaMalloc(w1g)");
-  for (int l = 1; l < 3; ++l)
-    if ((e = cudaMalloc(&N.wpair[l], 2 * fsz[l])) != cudaSuccess) return fvh::cuda_fail(e, "cudaMalloc(wpair)");
-  if ((e = cudaMalloc(&N.w4ring, 2 * snk::W4R_ELEMS)) != cudaSuccess) return fvh::cuda_fail(e, "cudaMalloc(w4ring)");
+  if (face) {
+    // the row-pipelined operand layouts serve the fused stencil kernel only
+  } else {
+    if ((e = cudaMalloc(&N.w1g, 2 * snk::W1G_ELEMS)) != cudaSuccess) return fvh::cuda_fail(e, "cudaMalloc(w1g)");
+    for (int l = 1; l < 3; ++l)
+      if ((e = cudaMalloc(&N.wpair[l], 2 * fsz[l])) != cudaSuccess) return fvh::cuda_fail(e, "cudaMalloc(wpair)");
+    if ((e = cudaMalloc(&N.w4ring, 2 * snk::W4R_ELEMS)) != cudaSuccess)
+      return fvh::cuda_fail(e, "cudaMalloc(w4ring)");
+  }
   if ((e = cudaMalloc(&N.err, sizeof(unsigned))) != cudaSuccess) return fvh::cuda_fail(e, "cudaMalloc(err)");
   if ((e = cudaMemset(N.err, 0, sizeof(unsigned))) != cudaSuccess) return fvh::cuda_fail(e, "cudaMemset");
   if ((e = cudaStreamCreateWithFlags(&n->stream, cudaStreamNonBlocking)) != cudaSuccess)
@@ -811,11 +899,13 @@ namespace fvs {
 int net_check(const fv_net* n) { return net_check_err(n); }
 }  // namespace fvs
 
-extern "C" int stencil_net_create(const float* params, const float* norm, fv_net** out) {
+namespace {
+
+int create_net(int kind, const float* params, const float* norm, fv_net** out) {
   if (!out) return fvh::fail(FV_EINVAL, "null output");
   *out = nullptr;
   fv_net* n = new fv_net();
-  int rc = net_alloc(n);
+  int rc = net_alloc(n, kind);
   if (rc != FV_OK) {
     net_free(n);
     return rc;
@@ -831,20 +921,35 @@ extern "C" int stencil_net_create(const float* params, const float* norm, fv_net
     }
   }
   cudaError_t e;
+  const size_t pbytes = sizeof(float) * snk::n_params(kind);
   if (params) {
-    e = cudaMemcpy(n->n.params, params, sizeof(float) * snk::N_PARAMS, cudaMemcpyHostToDevice);
+    e = cudaMemcpy(n->n.params, params, pbytes, cudaMemcpyHostToDevice);
   } else {
-    e = cudaMemset(n->n.params, 0, sizeof(float) * snk::N_PARAMS);
+    e = cudaMemset(n->n.params, 0, pbytes);
   }
   if (e == cudaSuccess) e = snk::repack(n->n, n->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(n->stream);
   if (e != cudaSuccess) {
     net_free(n);
-    return fvh::cuda_fail(e, "stencil_net_create");
+    return fvh::cuda_fail(e, "network creation");
   }
   *out = n;
   return FV_OK;
 }
+
+}  // namespace
+
+extern "C" int stencil_net_create(const float* params, const float* norm, fv_net** out) {
+  return create_net(snk::NET_STENCIL, params, norm, out);
+}
+
+extern "C" int face_net_create(const float* params, const float* norm, fv_net** out) {
+  return create_net(snk::NET_FACE, params, norm, out);
+}
+
+extern "C" int fv_net_kind(const fv_net* n) { return n ? n->n.kind : -1; }
+
+extern "C" int fv_net_num_params(const fv_net* n) { return n ? snk::n_params(n->n.kind) : 0; }
 
 extern "C" int stencil_net_destroy(fv_net* n) {
   net_free(n);
@@ -853,7 +958,7 @@ extern "C" int stencil_net_destroy(fv_net* n) {
 
 extern "C" int stencil_net_set_params(fv_net* n, const float* params, int loc) {
   if (!n || !params) return fvh::fail(FV_EINVAL, "null argument");
-  FV_CUDA_TRY(cudaMemcpyAsync(n->n.params, params, sizeof(float) * snk::N_PARAMS,
+  FV_CUDA_TRY(cudaMemcpyAsync(n->n.params, params, sizeof(float) * snk::n_params(n->n.kind),
                               loc == FV_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                               n->stream));
   FV_CUDA_TRY(snk::repack(n->n, n->stream));
@@ -864,7 +969,7 @@ extern "C" int stencil_net_set_params(fv_net* n, const float* params, int loc) {
 extern "C" int stencil_net_get_params(const fv_net* n, float* params, int loc) {
   if (!n || !params) return fvh::fail(FV_EINVAL, "null argument");
   FV_CUDA_TRY(cudaStreamSynchronize(n->stream));
-  FV_CUDA_TRY(cudaMemcpy(params, n->n.params, sizeof(float) * snk::N_PARAMS,
+  FV_CUDA_TRY(cudaMemcpy(params, n->n.params, sizeof(float) * snk::n_params(n->n.kind),
                          loc == FV_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost));
   return FV_OK;
 }
@@ -873,12 +978,28 @@ extern "C" int stencil_net_forward(const fv_net* cn, const float* q, int B, int 
                                    float* coeffs, int raw, void* stream) {
   fv_net* n = const_cast<fv_net*>(cn);
   if (!n || !q || !coeffs) return fvh::fail(FV_EINVAL, "null argument");
+  if (n->n.kind != snk::NET_STENCIL) return fvh::fail(FV_EINVAL, "not a stencil network (use face_net_forward)");
   if (B < 1 || ny < 1 || !snk::grid_supported(nx) || ((long long)nx * ny) % snk::TILE != 0)
     return fvh::fail(FV_EINVAL, "unsupported grid: nx must be 8, 16, 32, 64 or a multiple of 128, "
                                 "and nx*ny a multiple of 128");
   cudaStream_t s = stream ? (cudaStream_t)stream : n->stream;
   FV_CUDA_TRY(snk::acts_reserve(n->ws, (long long)B * nx * ny));
   FV_CUDA_TRY(snk::forward(n->n, q, B, ny, nx, n->ws, raw ? nullptr : coeffs, raw ? coeffs : nullptr, s));
+  FV_CUDA_TRY(cudaStreamSynchronize(s));
+  return net_check_err(n);
+}
+
+extern "C" int face_net_forward(const fv_net* cn, const float* q, int B, int ny, int nx, float* sides,
+                                int raw, void* stream) {
+  fv_net* n = const_cast<fv_net*>(cn);
+  if (!n || !q || !sides) return fvh::fail(FV_EINVAL, "null argument");
+  if (n->n.kind != snk::NET_FACE) return fvh::fail(FV_EINVAL, "not a face-state network");
+  if (B < 1 || ny < 1 || !snk::grid_supported(nx) || ((long long)nx * ny) % snk::TILE != 0)
+    return fvh::fail(FV_EINVAL, "unsupported grid: nx must be 8, 16, 32, 64 or a multiple of 128, "
+                                "and nx*ny a multiple of 128");
+  cudaStream_t s = stream ? (cudaStream_t)stream : n->stream;
+  FV_CUDA_TRY(snk::acts_reserve(n->ws, (long long)B * nx * ny));
+  FV_CUDA_TRY(snk::forward_faces(n->n, q, B, ny, nx, n->ws, raw ? nullptr : sides, raw ? sides : nullptr, s));
   FV_CUDA_TRY(cudaStreamSynchronize(s));
   return net_check_err(n);
 }

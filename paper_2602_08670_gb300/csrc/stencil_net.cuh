@@ -7,6 +7,12 @@
 // 2 directions x 3 variables x 2 sides x 3 taps; each 3-tap stencil is
 // normalised to w = e_centre + r - mean(r) (weights sum to one; r = 0 is the
 // first-order scheme).
+//
+// Section 2.5.3, third approach (NET_FACE): the same backbone with GeLU in
+// place of ReLU and 12 outputs per cell, the states on its four sides
+// (west, east, south, north) x (h, hu, hv) at channel 3 side + var; the
+// depths pass through Softplus, the momenta are de-normalised
+// (mean + std r).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -24,16 +30,22 @@ constexpr int N_PARAMS = 29796;      // W1 b1 W2 b2 W3 b3 W4 b4 (PyTorch order)
 constexpr int CG_IN0 = 2;            // layer-1 input: 3 channels padded to 16 (2 groups of 8)
 constexpr int CG_HID = 4;            // 32 channels = 4 groups of 8
 constexpr int TILE = 128;            // cells per MMA tile (M)
+enum { NET_STENCIL = 0, NET_FACE = 1 };
+constexpr int N_OUT_FACE = 12;       // 4 sides x 3 variables
+constexpr int N_OUT_FACE_PAD = 16;
+constexpr int N_PARAMS_FACE = 22860; // W1 b1 W2 b2 W3 b3 W4[12] b4[12]
 
 // Offsets of each layer's weight and bias in the flat parameter vector.
 struct ParamLayout {
   int w[4], b[4], cout[4], cin[4];
 };
-ParamLayout param_layout();
+ParamLayout param_layout(int kind = NET_STENCIL);
+int n_params(int kind);
 
 // Device buffers of one network.
 struct Net {
-  float* params = nullptr;     // FP32 master parameters [N_PARAMS]
+  int kind = NET_STENCIL;      // NET_STENCIL (fourth approach) or NET_FACE (third)
+  float* params = nullptr;     // FP32 master parameters [n_params(kind)]
   uint16_t* wf[4] = {};        // forward B operands, BF16 [9][CG_in][N][8]
   uint16_t* wb[4] = {};        // backward (dX) B operands, BF16 [9][CG_out][N_in][8], layers 1..3
   uint16_t* w1g = nullptr;     // layer 1 with the three x taps gathered into K, BF16
@@ -53,7 +65,7 @@ struct Net {
 
 // Per-call activation workspace for `cells` = B * plane cells.
 struct Acts {
-  uint16_t* a[3] = {};         // post-ReLU activations of layers 1..3, BF16 [B][4][plane][8]
+  uint16_t* a[3] = {};         // post-activation outputs of layers 1..3, BF16 [B][4][plane][8]
   long long cells = 0;
 };
 
@@ -72,6 +84,11 @@ cudaError_t repack(Net& net, cudaStream_t s);
 // the un-normalised outputs r [B][36][ny][nx] are written instead of w.
 cudaError_t forward(const Net& net, const float* q, int B, int ny, int nx, Acts& acts, float* w,
                     float* raw, cudaStream_t s);
+
+// Forward of a NET_FACE network: the side states [B][12][ny][nx] (FP32) into
+// `sides`, or, if raw != nullptr, the un-activated outputs r there instead.
+cudaError_t forward_faces(const Net& net, const float* q, int B, int ny, int nx, Acts& acts,
+                          float* sides, float* raw, cudaStream_t s);
 
 cudaError_t acts_reserve(Acts& acts, long long cells);
 void acts_free(Acts& acts);

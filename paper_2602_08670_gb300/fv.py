@@ -74,6 +74,10 @@ _SIGS = {
     "stencil_net_set_params": [c_void_p, c_void_p, c_int],
     "stencil_net_get_params": [c_void_p, c_void_p, c_int],
     "stencil_net_forward": [c_void_p, c_void_p, c_int, c_int, c_int, c_void_p, c_int, c_void_p],
+    "face_net_create": [c_void_p, c_void_p, ctypes.POINTER(c_void_p)],
+    "face_net_forward": [c_void_p, c_void_p, c_int, c_int, c_int, c_void_p, c_int, c_void_p],
+    "fv_net_kind": [c_void_p],
+    "fv_net_num_params": [c_void_p],
     "fv_tape_create": [c_void_p, c_int, c_int, c_int, c_int, c_double, c_double, c_double,
                        ctypes.POINTER(c_void_p)],
     "fv_tape_destroy": [c_void_p],
@@ -283,13 +287,16 @@ def fv_diagnostics(s: State) -> np.ndarray:
 # ---------------------------------------------------------------------------
 
 FV_NET_PARAMS = 29796
+FV_FACE_NET_PARAMS = 22860
 
 
 class Net:
-    """Owner of an ``fv_net*`` handle."""
+    """Owner of an ``fv_net*`` handle (a stencil or a face-state network)."""
 
     def __init__(self, handle: int):
         self.handle = ctypes.c_void_p(handle)
+        self.n_params = int(lib().fv_net_num_params(self.handle))
+        self.kind = "face" if int(lib().fv_net_kind(self.handle)) == 1 else "stencil"
 
     def __del__(self):
         if getattr(self, "handle", None) and self.handle.value and _lib is not None:
@@ -297,10 +304,10 @@ class Net:
             self.handle = ctypes.c_void_p(0)
 
 
-def _host_params(params):
+def _host_params(params, n=FV_NET_PARAMS):
     a = np.ascontiguousarray(np.asarray(params, dtype=np.float32).reshape(-1))
-    if a.size != FV_NET_PARAMS:
-        raise ValueError(f"expected {FV_NET_PARAMS} parameters, got {a.size}")
+    if a.size != n:
+        raise ValueError(f"expected {n} parameters, got {a.size}")
     return a
 
 
@@ -320,7 +327,7 @@ def stencil_net_set_params(net: Net, params) -> None:
         t = params.contiguous().float()
         _check(lib().stencil_net_set_params(net.handle, c_void_p(t.data_ptr()), FV_DEVICE))
         return
-    hp = _host_params(params)
+    hp = _host_params(params, net.n_params)
     _check(lib().stencil_net_set_params(net.handle, hp.ctypes.data_as(c_void_p), FV_HOST))
 
 
@@ -329,7 +336,7 @@ def stencil_net_get_params(net: Net, out: torch.Tensor | None = None):
     if out is not None:
         _check(lib().stencil_net_get_params(net.handle, _dev(out), FV_DEVICE))
         return out
-    host = np.zeros(FV_NET_PARAMS, dtype=np.float32)
+    host = np.zeros(net.n_params, dtype=np.float32)
     _check(lib().stencil_net_get_params(net.handle, host.ctypes.data_as(c_void_p), FV_HOST))
     return host
 
@@ -344,6 +351,31 @@ def stencil_net_forward(net: Net, q: torch.Tensor, raw: bool = False) -> torch.T
     _check(lib().stencil_net_forward(net.handle, c_void_p(q.data_ptr()), B, ny, nx,
                                      c_void_p(out.data_ptr()), int(raw),
                                      c_void_p(_torch_stream())))
+    return out
+
+
+def face_net_create(params=None, mean=(0.0, 0.0, 0.0), std=(1.0, 1.0, 1.0)) -> Net:
+    """Face-state network (Section 2.5.3, third approach); params host
+    [FV_FACE_NET_PARAMS] or None (zeros)."""
+    norm = np.ascontiguousarray(np.asarray(list(mean) + list(std), dtype=np.float32))
+    out = c_void_p()
+    p = None
+    if params is not None:
+        hp = _host_params(params, FV_FACE_NET_PARAMS)
+        p = hp.ctypes.data_as(c_void_p)
+    _check(lib().face_net_create(p, norm.ctypes.data_as(c_void_p), ctypes.byref(out)))
+    return Net(out.value)
+
+
+def face_net_forward(net: Net, q: torch.Tensor, raw: bool = False) -> torch.Tensor:
+    """Side states (or raw outputs) [B][12][ny][nx] for q on the GPU."""
+    q = q.contiguous()
+    if not q.is_cuda or q.dtype != torch.float32 or q.dim() != 4 or q.shape[1] != 3:
+        raise ValueError("q must be a CUDA float32 tensor [B][3][ny][nx]")
+    B, _, ny, nx = q.shape
+    out = torch.empty((B, 12, ny, nx), dtype=torch.float32, device=q.device)
+    _check(lib().face_net_forward(net.handle, c_void_p(q.data_ptr()), B, ny, nx,
+                                  c_void_p(out.data_ptr()), int(raw), c_void_p(_torch_stream())))
     return out
 
 
