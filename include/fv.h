@@ -277,7 +277,8 @@ int fv_diagnostics_noalloc(const float* q, int eq, int batch, int ny, int nx, do
 int stencil_net_create(const float* params, const float* norm, fv_net** out);
 int stencil_net_destroy(fv_net* n);
 
-/* Replace / read the FP32 parameters ([FV_NET_PARAMS], location loc). */
+/* Replace / read the FP32 parameters ([fv_net_num_params(n)]: FV_NET_PARAMS
+ * or, for a face-state network, FV_FACE_NET_PARAMS; location loc). */
 int stencil_net_set_params(fv_net* n, const float* params, int loc);
 int stencil_net_get_params(const fv_net* n, float* params, int loc);
 
@@ -305,7 +306,9 @@ int stencil_net_forward(const fv_net* n, const float* q, int B, int ny, int nx, 
  * stencil network (HLL, SSP-RK2, periodic flat bed, adaptive or fixed dt;
  * the network runs at both stages).  stencil_net_destroy, _set_params,
  * _get_params and _adam_step accept either kind, with fv_net_num_params()
- * parameters; training tapes hold stencil networks only.
+ * parameters, and so do the training tapes (fv_tape_*: dparams then holds
+ * FV_FACE_NET_PARAMS floats; the tape keeps the BF16 pre-activations for
+ * the GeLU derivative).
  * ------------------------------------------------------------------------- */
 
 /* W1[32][3][3][3] b1[32] W2[32][32][3][3] b2[32] W3[32][32][3][3] b3[32]
@@ -397,9 +400,10 @@ typedef struct fv_tape fv_tape;
 
 /* A tape for T learned SSP-RK2 steps of B shallow-water members on an
  * nx x ny periodic unit square with a fixed dt, gravity g and positivity
- * threshold h_min = hmin_frac * (mean depth of each member's q0).  The tape
- * owns device buffers for every stage input, the CNN activations and the
- * coefficients.  net is borrowed and must outlive the tape. */
+ * threshold h_min = hmin_frac * (mean depth of each member's q0; unused by
+ * a face-state network).  The tape owns device buffers for every stage
+ * input, the CNN activations and the coefficients (or side states).  net is
+ * borrowed and must outlive the tape. */
 int fv_tape_create(fv_net* net, int B, int ny, int nx, int T, double dt, double g, double hmin_frac,
                    fv_tape** out);
 int fv_tape_destroy(fv_tape* t);
@@ -419,7 +423,7 @@ int fv_tape_loss(fv_tape* t, const float* targets, const float* scale3, double* 
 /* Reverse pass through the recorded rollout.  dsnaps: device [T][B][3][ny][nx]
  * cotangents of q_1 .. q_T, or NULL for the gradient of the last
  * fv_tape_loss.  Adds the parameter gradient to dparams (device
- * [FV_NET_PARAMS]); dq0 (device [B][3][ny][nx], may be NULL) receives the
+ * [fv_net_num_params(net)]); dq0 (device [B][3][ny][nx], may be NULL) receives the
  * cotangent of q0.  Cotangents between CNN layers are BF16 (tensor-core
  * operands); everything else is FP32. */
 int fv_tape_backward(fv_tape* t, const float* dsnaps, float* dparams, float* dq0);

@@ -191,17 +191,21 @@ def rollout(q0, p: FaceNetParams, dt, T: int, g=9.81, round_bf16=True):
     return out
 
 
-def loss_and_grads(q0, targets, p: FaceNetParams, dt, scale, g=9.81, round_bf16=True):
+def loss_and_grads(q0, targets, p: FaceNetParams, dt, scale, g=9.81, round_bf16=True, want_dq0=False):
     """Rollout loss (Eq. 2.28, the same per-variable scaling as the fourth
     approach) of a T-step rollout and its gradient with respect to the flat
-    parameter vector, by reverse-mode differentiation of this FP64 forward."""
+    parameter vector (and, with want_dq0, the initial state), by reverse-mode
+    differentiation of this FP64 forward.  Returns (loss, dparams) or
+    (loss, dparams, dq0)."""
     from .stencil_net import rollout_loss
     flat = p.flat().detach().clone().requires_grad_(True)
     pp = FaceNetParams.from_flat(flat, p.mean, p.std)
-    preds = rollout(torch.as_tensor(q0, dtype=torch.float64), pp, dt, len(targets), g, round_bf16)
+    q0 = torch.as_tensor(q0, dtype=torch.float64).clone().requires_grad_(want_dq0)
+    preds = rollout(q0, pp, dt, len(targets), g, round_bf16)
     loss = rollout_loss(preds, targets, scale)
     loss.backward()
-    return float(loss.detach()), flat.grad.detach().clone()
+    out = (float(loss.detach()), flat.grad.detach().clone())
+    return out + (q0.grad.detach().clone(),) if want_dq0 else out
 
 
 def init_params(seed: int, mean, std, scale: float = 1.0) -> FaceNetParams:

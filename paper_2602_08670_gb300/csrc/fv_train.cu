@@ -9,6 +9,9 @@
 // divergence, of the HLL flux (Eq. 2.15, on the branch taken) and of the
 // reconstruction (learned stencils, or minmod where the positivity fallback
 // was taken), plus the CNN backward for the coefficients' dependence on q.
+// The face-state network (third approach) has no direct path from q to the
+// faces: the adjoint of its stage gives the cotangents of the side states
+// (one HLL VJP per face), and the CNN backward turns them into dq.
 #include <cuda_runtime.h>
 
 #include <vector>
@@ -260,6 +263,56 @@ __global__ void __launch_bounds__(ANT) learned_adjoint_kernel(AdjArgs a) {
   }
 }
 
+// Adjoint of one face-state stage: mu = dLoss/dL(q) per cell.  The face
+// between cells i-1 and i carries F = HLL(E_{i-1}, W_i) with
+// dLoss/dF = (mu_i - mu_{i-1}) / dx; its VJP is the cotangent of exactly those
+// two side states (each side state meets one face), written once.  The
+// thread of cell i handles its west and south faces.
+__global__ void face_adjoint_kernel(const float* sides, const float* mu, float* gs, int nx, int ny,
+                                    long long plane, long long cells, float rdx, float rdy, float g) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= cells) return;
+  const long long b = t / plane, cell = t - b * plane;
+  const int y = (int)(cell / nx), x = (int)(cell - (long long)y * nx);
+  const float* sb = sides + b * 12 * plane;
+  const float* mb = mu + b * 3 * plane;
+  float* gb = gs + b * 12 * plane;
+  {
+    const long long cl = (long long)y * nx + wrap(x - 1, nx);
+    float L[3], R[3], m[3], dl[3] = {0.f, 0.f, 0.f}, dr[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int v = 0; v < 3; ++v) {
+      L[v] = sb[(3 * 1 + v) * plane + cl];      // east side of the west cell
+      R[v] = sb[(3 * 0 + v) * plane + cell];    // west side of this cell
+      m[v] = (mb[v * plane + cell] - mb[v * plane + cl]) * rdx;
+    }
+    hll_swe_vjp(L, R, g, m, dl, dr);
+#pragma unroll
+    for (int v = 0; v < 3; ++v) {
+      gb[(3 * 1 + v) * plane + cl] = dl[v];
+      gb[(3 * 0 + v) * plane + cell] = dr[v];
+    }
+  }
+  {
+    const long long cs = (long long)wrap(y - 1, ny) * nx + x;
+    float L[3], R[3], m[3], dl[3] = {0.f, 0.f, 0.f}, dr[3] = {0.f, 0.f, 0.f};
+    // face frame of a y face: (h, hv, hu)
+    const int perm[3] = {0, 2, 1};
+#pragma unroll
+    for (int v = 0; v < 3; ++v) {
+      L[v] = sb[(3 * 3 + perm[v]) * plane + cs];      // north side of the south cell
+      R[v] = sb[(3 * 2 + perm[v]) * plane + cell];    // south side of this cell
+      m[v] = (mb[perm[v] * plane + cell] - mb[perm[v] * plane + cs]) * rdy;
+    }
+    hll_swe_vjp(L, R, g, m, dl, dr);
+#pragma unroll
+    for (int v = 0; v < 3; ++v) {
+      gb[(3 * 3 + perm[v]) * plane + cs] = dl[v];
+      gb[(3 * 2 + perm[v]) * plane + cell] = dr[v];
+    }
+  }
+}
+
 // out = alpha * x + beta * y + gamma * z (elementwise, any of y, z may be null).
 __global__ void axpbypcz_kernel(float* out, const float* x, float alpha, const float* y, float beta,
                                 const float* z, float gamma, long long n) {
@@ -339,6 +392,13 @@ cudaError_t launch_axpbypcz(float* out, const float* x, float alpha, const float
   return cudaGetLastError();
 }
 
+cudaError_t launch_face_adjoint(const Geom& g, const float* sides, const float* mu, float* gs, cudaStream_t s) {
+  const long long cells = (long long)g.B * g.plane();
+  face_adjoint_kernel<<<(unsigned)((cells + 255) / 256), 256, 0, s>>>(
+      sides, mu, gs, g.nx, g.ny, g.plane(), cells, (float)(1.0 / g.dx), (float)(1.0 / g.dy), g.phys);
+  return cudaGetLastError();
+}
+
 }  // namespace fvk
 
 // ---------------------------------------------------------------------------
@@ -352,7 +412,8 @@ struct fv_tape {
   cudaStream_t stream = nullptr;
   float* states = nullptr;      // q_0 .. q_T  [T+1][B][3][plane]
   float* stage1 = nullptr;      // q1_0 .. q1_{T-1} [T][B][3][plane]
-  float* coeffs = nullptr;      // w per stage [2T][B][36][plane]
+  float* coeffs = nullptr;      // w per stage [2T][B][36][plane] (face-state: side states [2T][B][12][plane])
+  bool face = false;            // the network is a face-state network
   snk::Acts* acts = nullptr;    // per stage [2T]
   float* hmin = nullptr;        // [B]
   fvk::Ctrl* ctrl = nullptr;
@@ -370,6 +431,7 @@ cudaError_t launch_learned_adjoint(const Geom& g, const float* q, const float* w
                                    const float* mu, float* gq, float* gw, cudaStream_t s);
 cudaError_t launch_axpbypcz(float* out, const float* x, float alpha, const float* y, float beta,
                             const float* z, float gamma, long long n, cudaStream_t s);
+cudaError_t launch_face_adjoint(const Geom& g, const float* sides, const float* mu, float* gs, cudaStream_t s);
 }  // namespace fvk
 
 namespace {
@@ -425,13 +487,14 @@ extern "C" int fv_tape_create(fv_net* net, int B, int ny, int nx, int T, double 
                               double hmin_frac, fv_tape** out) {
   if (!net || !out) return fvh::fail(FV_EINVAL, "null argument");
   *out = nullptr;
-  if (net->n.kind != snk::NET_STENCIL) return fvh::fail(FV_EINVAL, "training tapes hold stencil networks");
   if (B < 1 || T < 1 || !(dt > 0) || !(g > 0) || hmin_frac < 0 || hmin_frac >= 1)
     return fvh::fail(FV_EINVAL, "bad tape arguments");
   if (!snk::grid_supported(nx) || ((long long)nx * ny) % snk::TILE != 0)
     return fvh::fail(FV_EINVAL, "unsupported grid for the learned step");
   fv_tape* t = new fv_tape();
   t->net = net;
+  t->face = net->n.kind == snk::NET_FACE;
+  const int nout = t->face ? snk::N_OUT_FACE : snk::N_OUT;
   t->T = T;
   t->dt = dt;
   t->g.nx = nx;
@@ -447,10 +510,10 @@ extern "C" int fv_tape_create(fv_net* net, int B, int ny, int nx, int T, double 
   cudaError_t e = cudaStreamCreateWithFlags(&t->stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaMalloc(&t->states, sizeof(float) * sc * (T + 1));
   if (e == cudaSuccess) e = cudaMalloc(&t->stage1, sizeof(float) * sc * T);
-  if (e == cudaSuccess) e = cudaMalloc(&t->coeffs, sizeof(float) * 36 * cells * 2 * T);
+  if (e == cudaSuccess) e = cudaMalloc(&t->coeffs, sizeof(float) * nout * cells * 2 * T);
   if (e == cudaSuccess) {
     t->acts = new snk::Acts[2 * T];
-    for (int k = 0; k < 2 * T && e == cudaSuccess; ++k) e = snk::acts_reserve(t->acts[k], cells);
+    for (int k = 0; k < 2 * T && e == cudaSuccess; ++k) e = snk::acts_reserve(t->acts[k], cells, t->face);
   }
   if (e == cudaSuccess) e = cudaMalloc(&t->hmin, sizeof(float) * B);
   if (e == cudaSuccess) e = cudaMalloc(&t->ctrl, sizeof(fvk::Ctrl) * B);
@@ -460,7 +523,7 @@ extern "C" int fv_tape_create(fv_net* net, int B, int ny, int nx, int T, double 
   if (e == cudaSuccess) e = cudaMalloc(&t->lam1, sizeof(float) * sc);
   if (e == cudaSuccess) e = cudaMalloc(&t->mu, sizeof(float) * sc);
   if (e == cudaSuccess) e = cudaMalloc(&t->gq, sizeof(float) * sc);
-  if (e == cudaSuccess) e = cudaMalloc(&t->gw, sizeof(float) * 36 * cells);
+  if (e == cudaSuccess) e = cudaMalloc(&t->gw, sizeof(float) * nout * cells);
   if (e == cudaSuccess) e = cudaMalloc(&t->loss_part, sizeof(double) * LOSS_BLOCKS);
   if (e == cudaSuccess) e = cudaMalloc(&t->dsn, sizeof(float) * sc * T);
   if (e == cudaSuccess) {
@@ -493,11 +556,19 @@ extern "C" int fv_tape_forward(fv_tape* t, const float* q0, float* snaps) {
   fvk::fixed_ctrl_kernel<<<(t->g.B + 127) / 128, 128, 0, s>>>(t->ctrl, t->g.B, t->dt);
   FV_CUDA_TRY(cudaGetLastError());
   const snk::Net& N = t->net->n;
+  const long long wsz = (t->face ? 4 : 12) * sc;   // 12 or 36 planes per member
   for (int n = 0; n < t->T; ++n) {
     float* qn = t->states + sc * n;
     float* q1 = t->stage1 + sc * n;
-    float* w0 = t->coeffs + 12 * sc * (2 * n);
-    float* w1 = t->coeffs + 12 * sc * (2 * n + 1);
+    float* w0 = t->coeffs + wsz * (2 * n);
+    float* w1 = t->coeffs + wsz * (2 * n + 1);
+    if (t->face) {
+      FV_CUDA_TRY(snk::forward_faces(N, qn, t->g.B, t->g.ny, t->g.nx, t->acts[2 * n], w0, nullptr, s));
+      FV_CUDA_TRY(fvk::launch_stage_face(t->g, 1, qn, nullptr, q1, w0, t->ctrl, t->dp, s));
+      FV_CUDA_TRY(snk::forward_faces(N, q1, t->g.B, t->g.ny, t->g.nx, t->acts[2 * n + 1], w1, nullptr, s));
+      FV_CUDA_TRY(fvk::launch_stage_face(t->g, 2, q1, qn, qn + sc, w1, t->ctrl, t->dp, s));
+      continue;
+    }
     FV_CUDA_TRY(snk::forward(N, qn, t->g.B, t->g.ny, t->g.nx, t->acts[2 * n], w0, nullptr, s));
     FV_CUDA_TRY(fvk::launch_stage_learned(t->g, 1, qn, nullptr, q1, w0, t->hmin, t->ctrl, t->dp, s));
     FV_CUDA_TRY(snk::forward(N, q1, t->g.B, t->g.ny, t->g.nx, t->acts[2 * n + 1], w1, nullptr, s));
@@ -545,11 +616,31 @@ extern "C" int fv_tape_backward(fv_tape* t, const float* dsnaps, float* dparams,
   const int B = t->g.B, ny = t->g.ny, nx = t->g.nx;
   FV_CUDA_TRY(cudaMemcpyAsync(t->lam, dsn + sc * (t->T - 1), sizeof(float) * sc,
                               cudaMemcpyDeviceToDevice, s));
+  const long long wsz = (t->face ? 4 : 12) * sc;
   for (int n = t->T - 1; n >= 0; --n) {
     const float* qn = t->states + sc * n;
     const float* q1 = t->stage1 + sc * n;
-    const float* w0 = t->coeffs + 12 * sc * (2 * n);
-    const float* w1 = t->coeffs + 12 * sc * (2 * n + 1);
+    const float* w0 = t->coeffs + wsz * (2 * n);
+    const float* w1 = t->coeffs + wsz * (2 * n + 1);
+    if (t->face) {
+      // stage 2: q' = q/2 + q1/2 + (dt/2) L(q1), L through the side states only
+      FV_CUDA_TRY(fvk::launch_axpbypcz(t->mu, t->lam, 0.5f * dt, nullptr, 0.f, nullptr, 0.f, sc, s));
+      FV_CUDA_TRY(fvk::launch_face_adjoint(t->g, w1, t->mu, t->gw, s));
+      FV_CUDA_TRY(cudaMemsetAsync(t->gq, 0, sizeof(float) * sc, s));
+      FV_CUDA_TRY(snk::backward_faces(N, q1, B, ny, nx, t->acts[2 * n + 1], w1, t->gw, t->gq, dparams, 1.f,
+                                      t->grads, s));
+      FV_CUDA_TRY(fvk::launch_axpbypcz(t->lam1, t->lam, 0.5f, t->gq, 1.f, nullptr, 0.f, sc, s));
+      // stage 1: q1 = q + dt L(q)
+      FV_CUDA_TRY(fvk::launch_axpbypcz(t->mu, t->lam1, dt, nullptr, 0.f, nullptr, 0.f, sc, s));
+      FV_CUDA_TRY(fvk::launch_face_adjoint(t->g, w0, t->mu, t->gw, s));
+      FV_CUDA_TRY(cudaMemsetAsync(t->gq, 0, sizeof(float) * sc, s));
+      FV_CUDA_TRY(snk::backward_faces(N, qn, B, ny, nx, t->acts[2 * n], w0, t->gw, t->gq, dparams, 1.f,
+                                      t->grads, s));
+      FV_CUDA_TRY(fvk::launch_axpbypcz(t->lam, t->lam, 0.5f, t->lam1, 1.f, t->gq, 1.f, sc, s));
+      if (n >= 1)
+        FV_CUDA_TRY(fvk::launch_axpbypcz(t->lam, t->lam, 1.f, dsn + sc * (n - 1), 1.f, nullptr, 0.f, sc, s));
+      continue;
+    }
     // stage 2
     FV_CUDA_TRY(fvk::launch_axpbypcz(t->mu, t->lam, 0.5f * dt, nullptr, 0.f, nullptr, 0.f, sc, s));
     FV_CUDA_TRY(fvk::launch_learned_adjoint(t->g, q1, w1, t->hmin, t->mu, t->gq, t->gw, s));

@@ -56,7 +56,8 @@ constexpr int NPOS_MAX = 3 * (TILE + 2 * 64);   // flat mode with nx <= 64
 constexpr uint32_t WAIT_ITERS = 1u << 22;
 
 enum { IN_STATE = 0, IN_ACT = 1 };
-enum { OUT_RELU = 0, OUT_W = 1, OUT_RAW = 2, OUT_MASK = 3, OUT_GELU = 4, OUT_SIDES = 5, OUT_SIDES_RAW = 6 };
+enum { OUT_RELU = 0, OUT_W = 1, OUT_RAW = 2, OUT_MASK = 3, OUT_GELU = 4, OUT_SIDES = 5, OUT_SIDES_RAW = 6,
+       OUT_GELU_GRAD = 7 };
 
 struct ConvArgs {
   const float* q;          // IN_STATE: [B][3][plane]
@@ -66,6 +67,7 @@ struct ConvArgs {
   uint16_t* y;             // OUT_RELU: [B][4][plane][8]
   float* w;                // OUT_W / OUT_RAW: [B][36][plane]; OUT_SIDES(_RAW): [B][12][plane]
   const uint16_t* mask;    // OUT_MASK: activation [B][4][plane][8]; output kept where it is > 0
+  uint16_t* z;             // OUT_GELU: pre-activations out (if non-null); OUT_GELU_GRAD: in
   float mean0, mean1, mean2, rstd0, rstd1, rstd2;
   float std1, std2;        // OUT_SIDES: momentum de-normalisation
   int nx, ny;
@@ -98,6 +100,11 @@ __device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.f + erff(x
 
 // Softplus, log(1 + e^x) = max(x, 0) + log(1 + e^-|x|).
 __device__ __forceinline__ float softplus(float x) { return fmaxf(x, 0.f) + log1pf(expf(-fabsf(x))); }
+
+// d GeLU / dx = Phi(x) + x phi(x), phi the standard normal density.
+__device__ __forceinline__ float gelu_grad(float x) {
+  return 0.5f * (1.f + erff(x * 0.70710678118654752f)) + x * 0.39894228040143268f * expf(-0.5f * x * x);
+}
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(tc::smem_u32(smem)), "l"(gmem)
@@ -212,12 +219,31 @@ __global__ void __launch_bounds__(NT) conv_kernel(ConvArgs a) {
         *reinterpret_cast<uint4*>(a.y + (((long long)b * 4 + g) * a.plane + cell) * 8) =
             make_uint4(pk[0], pk[1], pk[2], pk[3]);
       }
+    } else if constexpr (OUT == OUT_GELU_GRAD) {
+      // backward through GeLU: cotangent of the layer input times GeLU' of
+      // the stored pre-activation (BF16 out, 32 channels)
+      float v[32];
+      tc::tmem_ld32(lane_addr, v);
+#pragma unroll
+      for (int g = 0; g < 4; ++g) {
+        const uint4 zk = *reinterpret_cast<const uint4*>(a.z + (((long long)b * 4 + g) * a.plane + cell) * 8);
+        const uint32_t zw[4] = {zk.x, zk.y, zk.z, zk.w};
+        uint32_t pk[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int c0 = 8 * g + 2 * j;
+          const float z0 = __uint_as_float(zw[j] << 16), z1 = __uint_as_float(zw[j] & 0xFFFF0000u);
+          pk[j] = pack_bf16x2(v[c0] * gelu_grad(z0), v[c0 + 1] * gelu_grad(z1));
+        }
+        *reinterpret_cast<uint4*>(a.y + (((long long)b * 4 + g) * a.plane + cell) * 8) =
+            make_uint4(pk[0], pk[1], pk[2], pk[3]);
+      }
     } else if constexpr (OUT == OUT_RELU || OUT == OUT_GELU) {
       float v[32];
       tc::tmem_ld32(lane_addr, v);
 #pragma unroll
       for (int g = 0; g < 4; ++g) {
-        uint32_t pk[4];
+        uint32_t pk[4], pz[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
           const int c0 = 8 * g + 2 * j;
@@ -226,10 +252,14 @@ __global__ void __launch_bounds__(NT) conv_kernel(ConvArgs a) {
             pk[j] = pack_bf16x2(fmaxf(z0, 0.f), fmaxf(z1, 0.f));
           } else {
             pk[j] = pack_bf16x2(gelu(z0), gelu(z1));
+            pz[j] = pack_bf16x2(z0, z1);
           }
         }
         *reinterpret_cast<uint4*>(a.y + (((long long)b * 4 + g) * a.plane + cell) * 8) =
             make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        if (OUT == OUT_GELU && a.z)
+          *reinterpret_cast<uint4*>(a.z + (((long long)b * 4 + g) * a.plane + cell) * 8) =
+              make_uint4(pz[0], pz[1], pz[2], pz[3]);
       }
     } else if constexpr (OUT == OUT_SIDES || OUT == OUT_SIDES_RAW) {
       // side states of the face-state network: channel 3 side + var
@@ -407,11 +437,12 @@ cudaError_t repack(Net& net, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t acts_reserve(Acts& acts, long long cells) {
-  if (acts.cells >= cells) return cudaSuccess;
+cudaError_t acts_reserve(Acts& acts, long long cells, bool with_z) {
+  if (acts.cells >= cells && (!with_z || acts.z[0])) return cudaSuccess;
   acts_free(acts);
   for (int l = 0; l < 3; ++l) {
     cudaError_t e = cudaMalloc(&acts.a[l], (size_t)cells * CG_HID * 16);
+    if (e == cudaSuccess && with_z) e = cudaMalloc(&acts.z[l], (size_t)cells * CG_HID * 16);
     if (e != cudaSuccess) {
       acts_free(acts);
       return e;
@@ -424,7 +455,9 @@ cudaError_t acts_reserve(Acts& acts, long long cells) {
 void acts_free(Acts& acts) {
   for (int l = 0; l < 3; ++l) {
     cudaFree(acts.a[l]);
+    cudaFree(acts.z[l]);
     acts.a[l] = nullptr;
+    acts.z[l] = nullptr;
   }
   acts.cells = 0;
 }
@@ -493,6 +526,7 @@ cudaError_t forward_faces(const Net& net, const float* q, int B, int ny, int nx,
   a.wpk = net.wf[0];
   a.bias = net.params + L.b[0];
   a.y = acts.a[0];
+  a.z = acts.z[0];
   cudaError_t e = launch_conv<CG_IN0, HID, IN_STATE, OUT_GELU>(a, B, s);
   if (e != cudaSuccess) return e;
   for (int l = 1; l < 3; ++l) {
@@ -500,9 +534,11 @@ cudaError_t forward_faces(const Net& net, const float* q, int B, int ny, int nx,
     a.wpk = net.wf[l];
     a.bias = net.params + L.b[l];
     a.y = acts.a[l];
+    a.z = acts.z[l];
     e = launch_conv<CG_HID, HID, IN_ACT, OUT_GELU>(a, B, s);
     if (e != cudaSuccess) return e;
   }
+  a.z = nullptr;
   // layer 4: a2 -> the 12 side states
   a.x = acts.a[2];
   a.wpk = net.wf[3];
@@ -547,6 +583,34 @@ __global__ void coeff_to_raw_kernel(const float* dw, uint16_t* dr, long long pla
 #pragma unroll
     for (int j = 0; j < 4; ++j) pk[j] = pack_bf16x2(r[8 * g + 2 * j], r[8 * g + 2 * j + 1]);
     *reinterpret_cast<uint4*>(dr + ((b * 6 + g) * plane + cell) * 8) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+  }
+}
+
+// Cotangent of the side states -> cotangent of the raw outputs: Softplus'(r)
+// = 1 - e^-h on the depths (h the side depth), std_v on the momenta; BF16
+// in 2 channel groups (channels 12..15 zero).
+__global__ void sides_to_raw_kernel(const float* ds, const float* sides, uint16_t* dr, long long plane,
+                                    long long cells, float std1, float std2) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= cells) return;
+  const long long b = t / plane, cell = t - b * plane;
+  const float* g = ds + b * N_OUT_FACE * plane + cell;
+  const float* sd = sides + b * N_OUT_FACE * plane + cell;
+  float r[16];
+#pragma unroll
+  for (int k = 0; k < N_OUT_FACE; ++k) {
+    const int var = k % 3;
+    const float f = var == 0 ? -expm1f(-sd[k * plane]) : (var == 1 ? std1 : std2);
+    r[k] = g[k * plane] * f;
+  }
+#pragma unroll
+  for (int k = N_OUT_FACE; k < 16; ++k) r[k] = 0.f;
+#pragma unroll
+  for (int gg = 0; gg < 2; ++gg) {
+    uint32_t pk[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) pk[j] = pack_bf16x2(r[8 * gg + 2 * j], r[8 * gg + 2 * j + 1]);
+    *reinterpret_cast<uint4*>(dr + ((b * 2 + gg) * plane + cell) * 8) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
   }
 }
 
@@ -813,6 +877,61 @@ cudaError_t backward(const Net& net, const float* q, int B, int ny, int nx, cons
   a.mask = acts.a[0];
   a.y = g.da[0];
   if ((e = launch_conv<CG_HID, HID, IN_ACT, OUT_MASK>(a, B, s)) != cudaSuccess) return e;
+  // layer 1: dW1 from (da0, normalised state); dq += dX / std
+  if ((e = weight_grad<3, HID, 4>(nullptr, q, g.da[0], dparams + L.w[0], dparams + L.b[0], g.part,
+                                  B, ny, nx, net, scale, s)) != cudaSuccess)
+    return e;
+  if (dq) {
+    dx_first_kernel<<<(unsigned)((cells + 127) / 128), 128, 0, s>>>(
+        g.da[0], net.params + L.w[0], dq, nx, ny, plane, cells, 1.f / net.std_[0],
+        1.f / net.std_[1], 1.f / net.std_[2]);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t backward_faces(const Net& net, const float* q, int B, int ny, int nx, const Acts& acts,
+                           const float* sides, const float* ds, float* dq, float* dparams, float scale,
+                           Grads& g, cudaStream_t s) {
+  if (net.kind != NET_FACE || !acts.z[0]) return cudaErrorInvalidValue;
+  const ParamLayout L = param_layout(NET_FACE);
+  const long long plane = (long long)nx * ny, cells = (long long)B * plane;
+  cudaError_t e;
+  sides_to_raw_kernel<<<(unsigned)((cells + 255) / 256), 256, 0, s>>>(ds, sides, g.dr, plane, cells,
+                                                                      net.std_[1], net.std_[2]);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  ConvArgs a{};
+  a.nx = nx;
+  a.ny = ny;
+  a.plane = plane;
+  a.err = net.err;
+  // layer 4: dW4, db4 from (dr, a3); dX -> da[0] times GeLU'(z3)
+  if ((e = weight_grad<HID, N_OUT_FACE, 2>(acts.a[2], nullptr, g.dr, dparams + L.w[3], dparams + L.b[3],
+                                           g.part, B, ny, nx, net, scale, s)) != cudaSuccess)
+    return e;
+  a.x = g.dr;
+  a.wpk = net.wb[3];
+  a.z = acts.z[2];
+  a.y = g.da[0];
+  if ((e = launch_conv<2, HID, IN_ACT, OUT_GELU_GRAD>(a, B, s)) != cudaSuccess) return e;
+  // layer 3: dW3 from (da0, a2); dX -> da[1] times GeLU'(z2)
+  if ((e = weight_grad<HID, HID, 4>(acts.a[1], nullptr, g.da[0], dparams + L.w[2], dparams + L.b[2],
+                                    g.part, B, ny, nx, net, scale, s)) != cudaSuccess)
+    return e;
+  a.x = g.da[0];
+  a.wpk = net.wb[2];
+  a.z = acts.z[1];
+  a.y = g.da[1];
+  if ((e = launch_conv<CG_HID, HID, IN_ACT, OUT_GELU_GRAD>(a, B, s)) != cudaSuccess) return e;
+  // layer 2: dW2 from (da1, a1); dX -> da[0] times GeLU'(z1)
+  if ((e = weight_grad<HID, HID, 4>(acts.a[0], nullptr, g.da[1], dparams + L.w[1], dparams + L.b[1],
+                                    g.part, B, ny, nx, net, scale, s)) != cudaSuccess)
+    return e;
+  a.x = g.da[1];
+  a.wpk = net.wb[1];
+  a.z = acts.z[0];
+  a.y = g.da[0];
+  if ((e = launch_conv<CG_HID, HID, IN_ACT, OUT_GELU_GRAD>(a, B, s)) != cudaSuccess) return e;
   // layer 1: dW1 from (da0, normalised state); dq += dX / std
   if ((e = weight_grad<3, HID, 4>(nullptr, q, g.da[0], dparams + L.w[0], dparams + L.b[0], g.part,
                                   B, ny, nx, net, scale, s)) != cudaSuccess)

@@ -66,6 +66,7 @@ struct Net {
 // Per-call activation workspace for `cells` = B * plane cells.
 struct Acts {
   uint16_t* a[3] = {};         // post-activation outputs of layers 1..3, BF16 [B][4][plane][8]
+  uint16_t* z[3] = {};         // face-state training only: pre-activations, BF16 [B][4][plane][8]
   long long cells = 0;
 };
 
@@ -90,7 +91,8 @@ cudaError_t forward(const Net& net, const float* q, int B, int ny, int nx, Acts&
 cudaError_t forward_faces(const Net& net, const float* q, int B, int ny, int nx, Acts& acts,
                           float* sides, float* raw, cudaStream_t s);
 
-cudaError_t acts_reserve(Acts& acts, long long cells);
+// with_z: also the pre-activation buffers (backward of the face-state network).
+cudaError_t acts_reserve(Acts& acts, long long cells, bool with_z = false);
 void acts_free(Acts& acts);
 
 // Backward workspace.
@@ -113,6 +115,13 @@ void backward_free(Grads& g);
 cudaError_t backward(const Net& net, const float* q, int B, int ny, int nx, const Acts& acts,
                      const float* dw, float* dq, float* dparams, float scale, Grads& g,
                      cudaStream_t s);
+
+// The same for a NET_FACE network: ds is the cotangent of the side states
+// [B][12][ny][nx], `sides` the side states forward_faces() produced for this
+// q, and `acts` must hold its activations and pre-activations (with_z).
+cudaError_t backward_faces(const Net& net, const float* q, int B, int ny, int nx, const Acts& acts,
+                           const float* sides, const float* ds, float* dq, float* dparams, float scale,
+                           Grads& g, cudaStream_t s);
 
 }  // namespace snk
 
