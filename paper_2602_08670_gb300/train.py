@@ -1,4 +1,6 @@
-"""Training and evaluation of the learned-stencil solver (GPU, via libfv).
+"""Training and evaluation of the learned solvers (GPU, via libfv): the
+stencil network (Section 2.5.3, fourth approach) and the face-state network
+(third approach).
 
 Data (Section 2.5.1 / 5.4 recipe, on this build's synthetic workload): the
 plain FP32 GPU solver runs seeded multi-bump shallow-water states at a fine
@@ -23,6 +25,7 @@ from . import fv, workloads
 
 G = 9.81
 LAYERS = [(32, 3), (32, 32), (32, 32), (36, 32)]
+FACE_LAYERS = [(32, 3), (32, 32), (32, 32), (12, 32)]
 
 
 @dataclasses.dataclass
@@ -66,17 +69,23 @@ def generate(n_fine: int = 256, factor: int = 4, members: int = 64, seed: int = 
     return Dataset(coarse, dt_fine * factor, dt_fine, n_fine, factor, seed)
 
 
-def init_params(seed: int, zero_last: bool = True) -> np.ndarray:
-    """He-normal weights, small biases; a zero last layer makes the network
-    start as the first-order scheme (the paper's initialisation)."""
+def init_params(seed: int, zero_last: bool = True, kind: str = "stencil", depth: float = 1.0) -> np.ndarray:
+    """He-normal weights, small biases.  Stencil network: a zero last layer
+    makes it start as the first-order scheme (the paper's initialisation).
+    Face-state network (no initialisation is given for it): a zero last
+    layer with depth biases softplus^-1(depth) starts every side at the
+    resting depth with zero momentum."""
     g = torch.Generator().manual_seed(seed)
+    layers = FACE_LAYERS if kind == "face" else LAYERS
     parts = []
-    for layer, (co, ci) in enumerate(LAYERS):
+    for layer, (co, ci) in enumerate(layers):
         w = torch.randn(co, ci, 3, 3, generator=g) * math.sqrt(2.0 / (9 * ci))
         b = torch.randn(co, generator=g) * 0.01
         if layer == 3 and zero_last:
             w.zero_()
             b.zero_()
+            if kind == "face":
+                b[0::3] = math.log(math.expm1(depth))
         parts += [w.reshape(-1), b]
     return torch.cat(parts).numpy().astype(np.float32)
 
@@ -113,18 +122,22 @@ class TrainResult:
 
 
 def train(ds: Dataset, iters: int = 500, batch: int = 64, T: int = 8, lr: float = 3e-4,
-          seed: int = 0, params=None, log_every: int = 0, net=None) -> TrainResult:
+          seed: int = 0, params=None, log_every: int = 0, net=None, kind: str = "stencil") -> TrainResult:
     """Adam on the rollout loss.  An update after which a training rollout
     leaves the physical states (the library reports FV_EUNSTABLE) is undone
     and the learning rate halved."""
-    _, std = data_stats(ds)
+    mean, std = data_stats(ds)
     if net is None:
         in_mean, in_scale = input_scale(ds)
-        net = fv.stencil_net_create(init_params(seed) if params is None else params, in_mean, in_scale)
+        if kind == "face":
+            p0 = init_params(seed, kind="face", depth=float(mean[0])) if params is None else params
+            net = fv.face_net_create(p0, in_mean, in_scale)
+        else:
+            net = fv.stencil_net_create(init_params(seed) if params is None else params, in_mean, in_scale)
     S, B = ds.coarse.shape[:2]
     nc = ds.n_coarse
     tape = fv.fv_tape_create(net, batch, nc, nc, T, ds.dt_coarse)
-    dparams = torch.zeros(fv.FV_NET_PARAMS, dtype=torch.float32, device="cuda")
+    dparams = torch.zeros(net.n_params, dtype=torch.float32, device="cuda")
     prev = torch.empty_like(dparams)
     fv.stencil_net_get_params(net, out=prev)
     rng = np.random.Generator(np.random.Philox(seed))
@@ -211,13 +224,15 @@ def save_weights(path: str, net, ds: Dataset, result: TrainResult, extra: dict |
             "train_seconds": result.seconds}
     meta.update(extra or {})
     np.savez(path, params=fv.stencil_net_get_params(net), mean=mean, scale=scale,
-             meta=np.array(repr(meta)))
+             meta=np.array(repr(meta)), kind=np.array(net.kind))
 
 
 def load_weights(path: str):
     """(net, metadata) from a file written by save_weights."""
     d = np.load(path, allow_pickle=False)
-    net = fv.stencil_net_create(d["params"], d["mean"], d["scale"])
+    kind = str(d["kind"]) if "kind" in d.files else "stencil"
+    create = fv.face_net_create if kind == "face" else fv.stencil_net_create
+    net = create(d["params"], d["mean"], d["scale"])
     import ast
     return net, ast.literal_eval(str(d["meta"]))
 
@@ -231,10 +246,11 @@ def main(argv=None):
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--T", type=int, default=8)
     ap.add_argument("--lr", type=float, default=3e-4)
+    ap.add_argument("--kind", choices=["stencil", "face"], default="stencil")
     ap.add_argument("--out", required=True)
     a = ap.parse_args(argv)
     ds = generate(256, 4, members=a.members, seed=0, coarse_steps=a.coarse_steps)
-    res = train(ds, iters=a.iters, batch=a.batch, T=a.T, lr=a.lr, seed=0, log_every=100)
+    res = train(ds, iters=a.iters, batch=a.batch, T=a.T, lr=a.lr, seed=0, log_every=100, kind=a.kind)
     te = generate(256, 4, members=32, seed=2, coarse_steps=128, dt_fine=ds.dt_fine)
     _, std = data_stats(ds)
     ev = {k: evaluate(res.net, te, k, std) for k in (16, 64, 128)}
