@@ -38,6 +38,7 @@ EULER_BYTES_PER_CELL_UPDATE = 80   # C = 4
 CHUNK = 32                          # steps per enqueue between timing events
 WORKLOAD = "plain FV step: Euler KH 2048^2 + SWE Gaussian bump 4096^2, FP32, SSP-RK2, CFL 0.5"
 WEIGHTS = os.path.join(ROOT, "paper_2602_08670_gb300", "weights", "swe64_from256.npz")
+FACE_WEIGHTS = os.path.join(ROOT, "paper_2602_08670_gb300", "weights", "face64_from256.npz")
 
 
 def captured_traffic(key):
@@ -407,7 +408,74 @@ def learned_block(args):
                        "plain_resolution_matching_learned": n_eq,
                        "note": "plain needs (N_eq/64)^2 more cells and N_eq/64 more steps"}
     out["accuracy_matched"] = {"learned_rate_times_r3": learned_rate * r ** 3, "r": r}
+    out["face_state"] = face_state_block(args, te, std, plain)
     return out
+
+
+def _plain_resolution_matching(plain, err):
+    """Resolution at which the plain solver's error equals err (log-log
+    interpolation between the bracketing resolutions; the largest one if err
+    is below all of them)."""
+    ns = sorted(plain)
+    for a, b in zip(ns, ns[1:]):
+        if plain[a] >= err >= plain[b]:
+            t = (math.log(plain[a]) - math.log(err)) / (math.log(plain[a]) - math.log(plain[b]))
+            return math.exp(math.log(a) + t * (math.log(b) - math.log(a)))
+    return float(ns[-1]) if err < plain[ns[-1]] else None
+
+
+def face_state_block(args, te, std, plain):
+    """The face-state network (Section 2.5.3, third approach): rollout
+    throughput at 256 members x 256^2 (CNN with GeLU on tcgen05 writing the
+    12 side states, then the face-state stage kernel; two launches sets per
+    stage), one training iteration, and its accuracy on the same held-out
+    trajectories as the stencil network."""
+    import torch
+
+    from paper_2602_08670_gb300 import fv
+    from paper_2602_08670_gb300 import train as TR
+    from paper_2602_08670_gb300 import workloads as W
+
+    net, meta = TR.load_weights(FACE_WEIGHTS)
+    members, n = 256, 256
+    q0 = torch.tensor(W.swe_random_bumps(n, 3, members), dtype=torch.float32).cuda()
+    bs = torch.cuda.Stream()
+    with torch.cuda.stream(bs):
+        st = fv.swe_init(q0, dt_mode="fixed", dt_fixed=meta["dt_fine"])
+    fv.fv_enqueue_steps(st, 2, net=net)
+    fv.fv_sync(st)
+    K = args.learned_steps
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(bs)
+    fv.fv_enqueue_steps(st, K, net=net)
+    e1.record(bs)
+    fv.fv_sync(st)
+    ms = e0.elapsed_time(e1)
+    rate = members * n * n * K / (ms * 1e-3)
+    health = int((fv.fv_health(st) != 0).sum())
+    del st
+    # 45 504 FLOP (two per multiply-add) per cell and CNN pass, two passes per step
+    tflops = 45504 * 2 * rate / 1e12
+    tr = TR.generate(256, 4, members=64, seed=0, coarse_steps=32)
+    tnet = fv.face_net_create(TR.init_params(0, kind="face", depth=float(TR.data_stats(tr)[0][0])),
+                              *TR.input_scale(tr))
+    TR.train(tr, iters=3, batch=64, T=8, net=tnet)
+    res = TR.train(tr, iters=10, batch=64, T=8, net=tnet)
+    el = TR.evaluate(net, te, 64, std)["learned"]
+    n_eq = _plain_resolution_matching(plain, el)
+    r = (n_eq or 64.0) / 64.0
+    return {"rollout": {"workload": f"{members} members x {n}^2 SWE, face-state network, fixed dt, {K} steps",
+                        "kernel": "conv_kernel (GeLU / side-state epilogues) + stage_face_kernel",
+                        "cell_updates_per_s": rate, "ms_per_step": ms / K, "cnn_tflops": tflops,
+                        "algorithmic": "91008 FLOP per cell-update (2 CNN passes of 45504 FLOP); "
+                                       "HBM 156 B per cell-update in the stage kernels",
+                        "members_flagged_unstable": health},
+            "training": {"workload": "batch 64 windows, 64^2, T = 8, forward + loss + backward + Adam",
+                         "ms_per_iteration": 1e3 * res.seconds / res.iters},
+            "accuracy": {"learned_64": el, "plain_resolution_matching_learned": n_eq,
+                         "note": "same metric and held-out trajectories as the stencil network"},
+            "accuracy_matched": {"learned_rate_times_r3": rate * r ** 3, "r": r}}
 
 
 def schemes_block(args):
