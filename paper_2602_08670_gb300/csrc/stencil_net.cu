@@ -85,9 +85,14 @@ __device__ __forceinline__ int floordiv(int a, int b) {
   return (a % b != 0 && (a < 0) != (b < 0)) ? q - 1 : q;
 }
 
-template <int CG, int N>
+// Staged input positions: row mode (nx a multiple of the tile) needs 3 rows
+// of TILE + 2 cells, flat mode (nx <= 64) 3 strips of TILE + 2 nx.
+template <bool ROW>
+constexpr int npos_of() { return ROW ? NPOS_ROW : NPOS_MAX; }
+
+template <int CG, int N, bool ROW>
 constexpr int conv_smem_bytes() {
-  return CG * NPOS_MAX * 16 + 9 * CG * N * 16 + 64;
+  return CG * npos_of<ROW>() * 16 + 9 * CG * N * 16 + 64;
 }
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
@@ -111,11 +116,12 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
                : "memory");
 }
 
-template <int CG, int N, int IN, int OUT>
+template <int CG, int N, int IN, int OUT, bool ROW>
 __global__ void __launch_bounds__(NT) conv_kernel(ConvArgs a) {
+  constexpr int NP = npos_of<ROW>();
   extern __shared__ __align__(1024) uint8_t smem[];
-  uint8_t* sA = smem;                                   // [CG][NPOS_MAX][16 B]
-  uint8_t* sB = smem + CG * NPOS_MAX * 16;              // [9][CG][N][16 B]
+  uint8_t* sA = smem;                                   // [CG][NP][16 B]
+  uint8_t* sB = smem + CG * NP * 16;                    // [9][CG][N][16 B]
   uint64_t* mbar = reinterpret_cast<uint64_t*>(sB + 9 * CG * N * 16);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
 
@@ -124,7 +130,7 @@ __global__ void __launch_bounds__(NT) conv_kernel(ConvArgs a) {
   const int b = (int)(blockIdx.x / tiles_per_member);
   const int p0 = (int)(blockIdx.x - (long long)b * tiles_per_member) * TILE;
   const int nx = a.nx, ny = a.ny;
-  const bool rowmode = nx % TILE == 0;
+  constexpr bool rowmode = ROW;
   const int y0 = p0 / nx, x0 = p0 - (p0 / nx) * nx;
   const int Lf = TILE + 2 * nx;
   const int npos = rowmode ? NPOS_ROW : 3 * Lf;
@@ -153,7 +159,7 @@ __global__ void __launch_bounds__(NT) conv_kernel(ConvArgs a) {
     if constexpr (IN == IN_ACT) {
 #pragma unroll
       for (int g = 0; g < CG; ++g)
-        cp_async16(sA + (g * NPOS_MAX + n) * 16, a.x + (((long long)b * CG + g) * a.plane + cell) * 8);
+        cp_async16(sA + (g * NP + n) * 16, a.x + (((long long)b * CG + g) * a.plane + cell) * 8);
     } else {
       const float* qb = a.q + (long long)b * 3 * a.plane;
       const float h0 = (qb[cell] - a.mean0) * a.rstd0;
@@ -162,7 +168,7 @@ __global__ void __launch_bounds__(NT) conv_kernel(ConvArgs a) {
       uint4 v0 = make_uint4(pack_bf16x2(h0, h1), pack_bf16x2(h2, 0.f), 0u, 0u);
       *reinterpret_cast<uint4*>(sA + n * 16) = v0;
 #pragma unroll
-      for (int g = 1; g < CG; ++g) *reinterpret_cast<uint4*>(sA + (g * NPOS_MAX + n) * 16) = make_uint4(0, 0, 0, 0);
+      for (int g = 1; g < CG; ++g) *reinterpret_cast<uint4*>(sA + (g * NP + n) * 16) = make_uint4(0, 0, 0, 0);
     }
   }
   asm volatile("cp.async.wait_all;\n" ::: "memory");
@@ -182,7 +188,7 @@ __global__ void __launch_bounds__(NT) conv_kernel(ConvArgs a) {
       const int start = rowmode ? (1 + dy) * RW + (1 + dx) : (1 + dx) * Lf + nx + dy * nx;
 #pragma unroll
       for (int ks = 0; ks < CG / 2; ++ks) {
-        const uint64_t ad = tc::sdesc(a0 + (uint32_t)((2 * ks * NPOS_MAX + start) * 16), NPOS_MAX * 16, 128);
+        const uint64_t ad = tc::sdesc(a0 + (uint32_t)((2 * ks * NP + start) * 16), NP * 16, 128);
         const uint64_t bd = tc::sdesc(b0 + (uint32_t)(((tap * CG + 2 * ks) * N) * 16), N * 16, 128);
         tc::mma_bf16(tmem, ad, bd, idesc, acc);
         acc = true;
@@ -404,10 +410,10 @@ __global__ void repack_kernel(const float* params, ParamLayout L, uint16_t* wf0,
   }
 }
 
-template <int CG, int N, int IN, int OUT>
-cudaError_t launch_conv(const ConvArgs& a, int B, cudaStream_t s) {
-  constexpr int smem = conv_smem_bytes<CG, N>();
-  auto kern = conv_kernel<CG, N, IN, OUT>;
+template <int CG, int N, int IN, int OUT, bool ROW>
+cudaError_t launch_conv_t(const ConvArgs& a, int B, cudaStream_t s) {
+  constexpr int smem = conv_smem_bytes<CG, N, ROW>();
+  auto kern = conv_kernel<CG, N, IN, OUT, ROW>;
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -417,6 +423,14 @@ cudaError_t launch_conv(const ConvArgs& a, int B, cudaStream_t s) {
   const long long tiles = (long long)B * (a.plane / TILE);
   kern<<<(unsigned)tiles, NT, smem, s>>>(a);
   return cudaGetLastError();
+}
+
+// Row mode (nx a multiple of the tile) stages 3 rows and so fits more CTAs
+// per SM than the flat mode of the narrow grids.
+template <int CG, int N, int IN, int OUT>
+cudaError_t launch_conv(const ConvArgs& a, int B, cudaStream_t s) {
+  if (a.nx % TILE == 0) return launch_conv_t<CG, N, IN, OUT, true>(a, B, s);
+  return launch_conv_t<CG, N, IN, OUT, false>(a, B, s);
 }
 
 }  // namespace
@@ -623,17 +637,18 @@ __device__ __forceinline__ float bf16_hi(uint32_t v) { return __uint_as_float(v 
 // x in the tap-shifted position layout, FP32) and writes its partial sums;
 // dw_reduce_kernel adds the partials in CTA order.  CI: input channels (3 for
 // the first layer, read from the state and normalised), CO: output channels.
-template <int CI, int CO, int CGO>
+template <int CI, int CO, int CGO, bool ROW>
 __global__ void __launch_bounds__(288) dw_partial_kernel(const uint16_t* x, const float* q,
                                                          const uint16_t* dy, float* part, int nx,
                                                          int ny, long long plane, long long ntiles,
                                                          float m0, float m1, float m2, float r0,
                                                          float r1, float r2) {
+  constexpr int NP = npos_of<ROW>();
   extern __shared__ __align__(16) float dsm[];
-  float* xs = dsm;                            // [NPOS_MAX][CI]
-  float* ys = xs + NPOS_MAX * CI;             // [TILE][CO]
+  float* xs = dsm;                            // [NP][CI]
+  float* ys = xs + NP * CI;                   // [TILE][CO]
   const int tid = threadIdx.x;
-  const bool rowmode = nx % TILE == 0;
+  constexpr bool rowmode = ROW;
   const int Lf = TILE + 2 * nx;
   const int npos = rowmode ? NPOS_ROW : 3 * Lf;
   constexpr int NE = 9 * CO;                  // (tap, co) pairs
@@ -771,15 +786,15 @@ __global__ void dx_first_kernel(const uint16_t* dy, const float* W1, float* dq, 
   d[2 * plane] += acc[2] * r2;
 }
 
-template <int CI, int CO, int CGO>
-cudaError_t weight_grad(const uint16_t* x, const float* q, const uint16_t* dy, float* dW, float* db,
-                        float* part, int B, int ny, int nx, const Net& net, float scale,
-                        cudaStream_t s) {
+template <int CI, int CO, int CGO, bool ROW>
+cudaError_t weight_grad_t(const uint16_t* x, const float* q, const uint16_t* dy, float* dW, float* db,
+                          float* part, int B, int ny, int nx, const Net& net, float scale,
+                          cudaStream_t s) {
   const long long plane = (long long)nx * ny;
   const long long ntiles = (long long)B * (plane / TILE);
   const int nctas = (int)((ntiles + DW_TILES - 1) / DW_TILES);
-  const int smem = (NPOS_MAX * CI + TILE * CO) * 4;
-  auto kern = dw_partial_kernel<CI, CO, CGO>;
+  const int smem = (npos_of<ROW>() * CI + TILE * CO) * 4;
+  auto kern = dw_partial_kernel<CI, CO, CGO, ROW>;
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -793,6 +808,14 @@ cudaError_t weight_grad(const uint16_t* x, const float* q, const uint16_t* dy, f
   const int ne = 9 * CO * CI + CO;
   dw_reduce_kernel<CI, CO><<<(ne + 255) / 256, 256, 0, s>>>(part, nctas, dW, db, scale);
   return cudaGetLastError();
+}
+
+template <int CI, int CO, int CGO>
+cudaError_t weight_grad(const uint16_t* x, const float* q, const uint16_t* dy, float* dW, float* db,
+                        float* part, int B, int ny, int nx, const Net& net, float scale,
+                        cudaStream_t s) {
+  if (nx % TILE == 0) return weight_grad_t<CI, CO, CGO, true>(x, q, dy, dW, db, part, B, ny, nx, net, scale, s);
+  return weight_grad_t<CI, CO, CGO, false>(x, q, dy, dW, db, part, B, ny, nx, net, scale, s);
 }
 
 }  // namespace
