@@ -78,6 +78,9 @@ typedef struct { int nx, ny, batch; double lx, ly; } fv_grid;
  * FV_HEALTH_CFL when C exceeds 1. */
 typedef struct { double g; double cfl; int dt_mode; double dt_fixed; } fv_swe_params;
 typedef struct { double gamma; double cfl; int dt_mode; double dt_fixed; } fv_euler_params;
+/* Shallow water on the rotating unit sphere: gravity g and rotation rate
+ * omega in the units of the state (e.g. Earth radii and days). */
+typedef struct { double g; double omega; double cfl; int dt_mode; double dt_fixed; } fv_sphere_params;
 
 typedef struct fv_state fv_state;
 typedef struct fv_net fv_net;
@@ -104,6 +107,34 @@ int euler_init(const fv_grid* grid, const fv_euler_params* params, const float* 
                int q0_loc, void* stream, fv_state** out);
 
 /* Free a state and everything it owns (NULL is accepted). */
+/* Shallow water on the unit sphere (Sections 2.4 and 4.3).  q0: [batch][4]
+ * [ny][nx] FP32, (h, hu, hv, hw) with a Cartesian momentum, on the
+ * logically rectangular grid of two hemispheres: nx = 2 ny cells on the
+ * computational rectangle [-3, 1] x [-1, 1], the right square the upper
+ * hemisphere (the disk mapping D(d) = d / sqrt 2, R(d) = 1 lifted by
+ * z = sqrt(1 - x^2 - y^2), Eq. 2.25), the left square the lower one; x is
+ * periodic and the cell above row ny - 1 of column i is row ny - 1 of column
+ * nx - 1 - i.  The step: MUSCL-minmod faces in the logical directions, the
+ * HLL flux in each edge's (normal, tangent, radial) frame with great-circle
+ * edge lengths and spherical cell areas, Eq. 3.1's correction on the
+ * momenta, Coriolis (Eq. 3.2), projection of the momentum onto the tangent
+ * plane after each stage, SSP-RK2, dt from the Courant rate
+ * (|m| / h + sqrt(g h)) * perimeter / (2 area).  The grid metrics are
+ * computed once on the device (FP64, stored FP32) and shared by the members.
+ * fv_step / fv_rollout / fv_get_state / fv_set_state / fv_get_time /
+ * fv_health apply; fv_set_scheme accepts HLL with SSP-RK2 only, and
+ * fv_set_boundary, fv_set_bathymetry, fv_diagnostics and learned steps
+ * return FV_EINVAL.  Errors: FV_EINVAL (nx != 2 ny, ny < 2, g <= 0),
+ * FV_ENOMEM, FV_ECUDA. */
+int sphere_init(int nx, int ny, int batch, const fv_sphere_params* p, const float* q0, int q0_loc,
+                void* stream, fv_state** out);
+
+/* The grid of a sphere state: unit cell centres [3][ny][nx] (x, y, z
+ * planes) and spherical cell areas [ny][nx], FP32, into host or device
+ * memory per loc (either pointer may be NULL).  FV_EINVAL for another
+ * state. */
+int sphere_get_cells(const fv_state* s, float* centres, float* areas, int loc);
+
 int fv_destroy_state(fv_state* s);
 
 /* REPLAY mode: the dt of step k (k = 0..n-1, counted from the state's

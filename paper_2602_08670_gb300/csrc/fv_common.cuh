@@ -16,7 +16,7 @@
 
 namespace fvk {
 
-enum Eq { SWE = 0, EULER = 1 };
+enum Eq { SWE = 0, EULER = 1, SPHERE = 2 };   // SPHERE: shallow water on the sphere, C = 4
 
 // ---------------------------------------------------------------------------
 // Per-member control block (device memory, one per batch member)

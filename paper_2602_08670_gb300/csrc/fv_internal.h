@@ -64,6 +64,8 @@ struct fv_state {
   float* qC = nullptr;                 // q^(2) of SSP-RK3 (allocated on first use)
   int bc = 0;                          // FV_BC_PERIODIC or FV_BC_WALL
   float* zbed = nullptr;               // shallow-water bed [ny][nx] (device), or null
+  float* sphere = nullptr;             // sphere grid metrics (device), SPHERE states only
+  float omega = 0.f;                   // rotation rate of the sphere (Coriolis)
 };
 
 namespace fvs {
@@ -74,6 +76,7 @@ cudaError_t leave(fv_state* s);
 cudaError_t enqueue_plain_step(fv_state* s);
 cudaError_t enqueue_step(fv_state* s, const fv_net* net);
 int check_health(fv_state* s);
+cudaError_t wavespeed_init(fv_state* s);                // dt of the current state (no time advance)
 // learned path (fv_learned.cu)
 int learned_prepare(fv_state* s, const fv_net* net);  // host side, before enqueueing
 cudaError_t enqueue_learned_step(fv_state* s, const fv_net* net);

@@ -45,6 +45,18 @@ cudaError_t launch_stage_general(const Geom& g, int stage, int flux, const float
                                  float* qout, Ctrl* ctrl, const DtParams* dp, cudaStream_t s,
                                  int bc = BC_PERIODIC, const float* z = nullptr);
 
+// Shallow water on the sphere (fv_sphere.cu): metric planes of the nx x ny
+// two-hemisphere grid (computed once per state), the Courant-rate reduction
+// of a state, and one SSP-RK2 step (q^n in qa, updated in place; stage in qb).
+long long sphere_metric_floats(int nx, int ny);
+long long sphere_centre_offset(int nx, int ny);   // [3][ny][nx] unit cell centres
+long long sphere_area_offset(int nx, int ny);     // [ny][nx] spherical cell areas
+cudaError_t launch_sphere_metrics(float* M, int nx, int ny, cudaStream_t s);
+cudaError_t launch_sphere_wavespeed(const Geom& g, const float* q, const float* M, Ctrl* ctrl,
+                                    const DtParams* dp, cudaStream_t s);
+cudaError_t enqueue_sphere_step(const Geom& g, float* qa, float* qb, const float* M, float omega, Ctrl* ctrl,
+                                const DtParams* dp, cudaStream_t s);
+
 // Wave-speed reduction of q that sets each member's dt without advancing
 // time (state creation, fv_set_state).
 cudaError_t launch_wavespeed_init(const Geom& g, const float* q, Ctrl* ctrl, const DtParams* dp,

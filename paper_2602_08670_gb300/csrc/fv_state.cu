@@ -93,7 +93,8 @@ int create_state(const fv_grid* grid, int eq, double phys, double cfl, int dt_mo
                         s->stream);
   }
   if (e == cudaSuccess) e = cudaMemsetAsync(s->ctrl, 0, sizeof(fvk::Ctrl) * s->g.B, s->stream);
-  if (e == cudaSuccess) e = fvk::launch_wavespeed_init(s->g, s->qA, s->ctrl, s->dp, s->stream);
+  // sphere states set their dt once their metrics exist (sphere_init)
+  if (e == cudaSuccess && eq != fvk::SPHERE) e = fvk::launch_wavespeed_init(s->g, s->qA, s->ctrl, s->dp, s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   if (e != cudaSuccess) {
     fvs::state_free(s);
@@ -157,6 +158,7 @@ void state_free(fv_state* s) {
   cudaFree(s->replay);
   cudaFree(s->diag_partials);
   cudaFree(s->diag_out);
+  cudaFree(s->sphere);
   learned_workspace_free(s);
   if (s->ev) cudaEventDestroy(s->ev);
   if (s->stream && s->own_stream) cudaStreamDestroy(s->stream);
@@ -179,7 +181,14 @@ cudaError_t leave(fv_state* s) {
   return cudaStreamWaitEvent(s->user_stream, s->ev, 0);
 }
 
+cudaError_t wavespeed_init(fv_state* s) {
+  if (s->g.eq == fvk::SPHERE) return fvk::launch_sphere_wavespeed(s->g, s->qA, s->sphere, s->ctrl, s->dp, s->stream);
+  return fvk::launch_wavespeed_init(s->g, s->qA, s->ctrl, s->dp, s->stream);
+}
+
 cudaError_t enqueue_plain_step(fv_state* s) {
+  if (s->g.eq == fvk::SPHERE)
+    return fvk::enqueue_sphere_step(s->g, s->qA, s->qB, s->sphere, s->omega, s->ctrl, s->dp, s->stream);
   if (s->flux != FV_FLUX_HLL || s->rk != 2 || s->bc != FV_BC_PERIODIC || s->zbed)
     return fvk::enqueue_scheme_step(s->g, s->flux, s->rk, s->qA, s->qB, s->qC, s->ctrl, s->dp, s->stream,
                                     s->variant, s->bc, s->zbed);
@@ -228,6 +237,42 @@ extern "C" int euler_init(const fv_grid* grid, const fv_euler_params* p, const f
                       stream, out);
 }
 
+extern "C" int sphere_init(int nx, int ny, int batch, const fv_sphere_params* p, const float* q0, int q0_loc,
+                           void* stream, fv_state** out) {
+  if (!p || !out) return fvh::fail(FV_EINVAL, "null argument");
+  if (ny < 2 || nx != 2 * ny) return fvh::fail(FV_EINVAL, "sphere grid: nx must be 2 ny and ny >= 2");
+  if (!(p->g > 0.0)) return fvh::fail(FV_EINVAL, "g must be > 0");
+  if (!(fabs(p->omega) < 1e30)) return fvh::fail(FV_EINVAL, "omega must be finite");
+  fv_grid grid{nx, ny, batch, 4.0, 2.0};
+  int rc = create_state(&grid, fvk::SPHERE, p->g, p->cfl, p->dt_mode, p->dt_fixed, q0, q0_loc, stream, out);
+  if (rc != FV_OK) return rc;
+  fv_state* s = *out;
+  s->omega = (float)p->omega;
+  cudaError_t e = cudaMalloc(&s->sphere, sizeof(float) * fvk::sphere_metric_floats(nx, ny));
+  if (e == cudaSuccess) e = fvk::launch_sphere_metrics(s->sphere, nx, ny, s->stream);
+  if (e == cudaSuccess) e = fvs::wavespeed_init(s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) {
+    fvs::state_free(s);
+    *out = nullptr;
+    return fvh::cuda_fail(e, "sphere_init");
+  }
+  return FV_OK;
+}
+
+extern "C" int sphere_get_cells(const fv_state* s, float* centres, float* areas, int loc) {
+  if (!s || (!centres && !areas)) return fvh::fail(FV_EINVAL, "null argument");
+  if (s->g.eq != fvk::SPHERE) return fvh::fail(FV_EINVAL, "not a sphere state");
+  const int nx = s->g.nx, ny = s->g.ny;
+  const cudaMemcpyKind k = loc == FV_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  FV_CUDA_TRY(cudaStreamSynchronize(s->stream));
+  if (centres)
+    FV_CUDA_TRY(cudaMemcpy(centres, s->sphere + fvk::sphere_centre_offset(nx, ny), sizeof(float) * 3 * s->g.plane(), k));
+  if (areas)
+    FV_CUDA_TRY(cudaMemcpy(areas, s->sphere + fvk::sphere_area_offset(nx, ny), sizeof(float) * s->g.plane(), k));
+  return FV_OK;
+}
+
 extern "C" int fv_destroy_state(fv_state* s) {
   fvs::state_free(s);
   return FV_OK;
@@ -245,8 +290,7 @@ extern "C" int fv_set_replay_dt(fv_state* s, const double* dts, long n) {
   s->dp_host.replay_len = (int)n;
   FV_CUDA_TRY(cudaMemcpy(s->dp, &s->dp_host, sizeof(fvk::DtParams), cudaMemcpyHostToDevice));
   // the pending dt of a REPLAY state is the replay value of its current step
-  if (s->dt_mode == FV_DT_REPLAY)
-    FV_CUDA_TRY(fvk::launch_wavespeed_init(s->g, s->qA, s->ctrl, s->dp, s->stream));
+  if (s->dt_mode == FV_DT_REPLAY) FV_CUDA_TRY(fvs::wavespeed_init(s));
   FV_CUDA_TRY(cudaStreamSynchronize(s->stream));
   return FV_OK;
 }
@@ -375,7 +419,7 @@ extern "C" int fv_set_state(fv_state* s, const float* src, int src_loc) {
   FV_CUDA_TRY(fvs::enter(s));
   const size_t bytes = (size_t)s->g.member() * s->g.B * sizeof(float);
   FV_CUDA_TRY(cudaMemcpyAsync(s->qA, src, bytes, kind_to_device(src_loc), s->stream));
-  FV_CUDA_TRY(fvk::launch_wavespeed_init(s->g, s->qA, s->ctrl, s->dp, s->stream));
+  FV_CUDA_TRY(fvs::wavespeed_init(s));
   FV_CUDA_TRY(fvs::leave(s));
   FV_CUDA_TRY(cudaStreamSynchronize(s->stream));
   return FV_OK;
@@ -414,6 +458,7 @@ extern "C" int fv_health(const fv_state* cs, unsigned* flags) {
 extern "C" int fv_diagnostics(const fv_state* cs, double* sums) {
   fv_state* s = const_cast<fv_state*>(cs);
   if (!s || !sums) return fvh::fail(FV_EINVAL, "null argument");
+  if (s->g.eq == fvk::SPHERE) return fvh::fail(FV_EINVAL, "plain-grid diagnostics do not apply to a sphere state");
   FV_CUDA_TRY(fvs::enter(s));
   FV_CUDA_TRY(fvk::launch_diagnostics(s->g, s->qA, s->diag_partials, s->diag_out, s->stream));
   FV_CUDA_TRY(cudaMemcpyAsync(sums, s->diag_out, sizeof(double) * s->g.B * (s->g.C + 1),
@@ -440,6 +485,8 @@ extern "C" int fv_set_scheme(fv_state* s, int flux, int rk) {
   if (!s) return fvh::fail(FV_EINVAL, "null state");
   if (flux < FV_FLUX_HLL || flux > FV_FLUX_HLLC) return fvh::fail(FV_EINVAL, "unknown flux");
   if (rk != 2 && rk != 3) return fvh::fail(FV_EINVAL, "rk must be 2 or 3");
+  if (s->g.eq == fvk::SPHERE && (flux != FV_FLUX_HLL || rk != 2))
+    return fvh::fail(FV_EINVAL, "the sphere step uses HLL and SSP-RK2");
   FV_CUDA_TRY(cudaStreamSynchronize(s->stream));
   if (rk == 3 && !s->qC) {
     const size_t bytes = sizeof(float) * (size_t)s->g.B * (size_t)s->g.member();
@@ -455,6 +502,7 @@ extern "C" int fv_set_scheme(fv_state* s, int flux, int rk) {
 extern "C" int fv_set_boundary(fv_state* s, int bc) {
   if (!s) return fvh::fail(FV_EINVAL, "null state");
   if (bc != FV_BC_PERIODIC && bc != FV_BC_WALL) return fvh::fail(FV_EINVAL, "unknown boundary condition");
+  if (s->g.eq == fvk::SPHERE) return fvh::fail(FV_EINVAL, "a sphere state has no boundary");
   if (bc == FV_BC_WALL && (s->g.nx < 2 || s->g.ny < 2)) return fvh::fail(FV_EINVAL, "walls need nx, ny >= 2");
   FV_CUDA_TRY(cudaStreamSynchronize(s->stream));
   s->bc = bc;

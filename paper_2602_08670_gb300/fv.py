@@ -44,6 +44,11 @@ class fv_euler_params(ctypes.Structure):
     _fields_ = [("gamma", c_double), ("cfl", c_double), ("dt_mode", c_int), ("dt_fixed", c_double)]
 
 
+class fv_sphere_params(ctypes.Structure):
+    _fields_ = [("g", c_double), ("omega", c_double), ("cfl", c_double), ("dt_mode", c_int),
+                ("dt_fixed", c_double)]
+
+
 _lib = None
 
 # name -> argtypes (all functions return int unless listed in _RESTYPES)
@@ -54,6 +59,9 @@ _SIGS = {
     "euler_init": [ctypes.POINTER(fv_grid), ctypes.POINTER(fv_euler_params), c_void_p, c_int,
                    c_void_p, ctypes.POINTER(c_void_p)],
     "fv_destroy_state": [c_void_p],
+    "sphere_init": [c_int, c_int, c_int, ctypes.POINTER(fv_sphere_params), c_void_p, c_int, c_void_p,
+                    ctypes.POINTER(c_void_p)],
+    "sphere_get_cells": [c_void_p, c_void_p, c_void_p, c_int],
     "fv_set_replay_dt": [c_void_p, c_void_p, c_long],
     "fv_step": [c_void_p, c_void_p],
     "fv_rollout": [c_void_p, c_void_p, c_long, c_double, c_void_p, c_int, c_int, c_void_p],
@@ -197,6 +205,32 @@ def euler_init(q0: torch.Tensor, gamma: float = 1.4, cfl: float = 0.5, dt_mode: 
                             ctypes.byref(fv_euler_params(gamma, cfl, DT_MODES[dt_mode], dt_fixed)),
                             ptr, loc, stream, ctypes.byref(out)))
     return State(out.value, "euler", q0.shape)
+
+
+def sphere_init(q0: torch.Tensor, g: float, omega: float, cfl: float = 0.5, dt_mode: str = "adaptive",
+                dt_fixed: float = 0.0) -> State:
+    """Shallow water on the unit sphere: q0 [B][4][ny][nx] with nx = 2 ny,
+    (h, hu, hv, hw) on the two-hemisphere grid (host or device tensor)."""
+    q0 = q0.contiguous()
+    if q0.dim() != 4 or q0.shape[1] != 4:
+        raise ValueError("sphere state is [B][4][ny][nx]")
+    B, _, ny, nx = q0.shape
+    ptr, loc = _ptr_loc(q0)
+    out = c_void_p()
+    stream = c_void_p(_torch_stream()) if torch.cuda.is_available() else None
+    _check(lib().sphere_init(nx, ny, B, ctypes.byref(fv_sphere_params(g, omega, cfl, DT_MODES[dt_mode], dt_fixed)),
+                             ptr, loc, stream, ctypes.byref(out)))
+    return State(out.value, "sphere", q0.shape)
+
+
+def sphere_get_cells(s: State):
+    """(unit cell centres [3][ny][nx], cell areas [ny][nx]) of a sphere state,
+    as host numpy float32 arrays."""
+    _, _, ny, nx = s.shape
+    c = np.zeros((3, ny, nx), dtype=np.float32)
+    a = np.zeros((ny, nx), dtype=np.float32)
+    _check(lib().sphere_get_cells(s.handle, c.ctypes.data_as(c_void_p), a.ctypes.data_as(c_void_p), FV_HOST))
+    return c, a
 
 
 def fv_set_replay_dt(s: State, dts) -> None:

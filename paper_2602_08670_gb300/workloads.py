@@ -323,3 +323,30 @@ def as_f32_exact(q: np.ndarray) -> np.ndarray:
     """Round to FP32 and back: the exact values an FP32 GPU state starts from,
     which is what the oracle must be given for a like-for-like comparison."""
     return np.asarray(q, dtype=np.float32).astype(np.float64)
+
+
+def sphere_bumps(centres: np.ndarray, seed: int, members: int = 1, depth: float = 1.2e-3,
+                 amp: float = 2e-5, width2: float = 0.15, spin: float = 0.0) -> np.ndarray:
+    """Shallow water on the unit sphere given its cell centres [3][ny][nx]
+    (unit vectors; from the grid, e.g. ``sphere_get_cells``): depth plus
+    three seeded Gaussian bumps amp exp(-|x - c_k|^2 / width2) at random unit
+    centres c_k, and a seeded rigid rotation of angular speed ``spin``
+    (momentum h (w x x), tangent to the sphere).  Section 4.3's test is the
+    Rossby-Haurwitz wave of a published test suite; these states stand in
+    for it.  Returns ``[members][4][ny][nx]`` (h, hu, hv, hw), float64."""
+    rng = _rng(seed)
+    x = np.asarray(centres, dtype=np.float64)
+    _, ny, nx = x.shape
+    q = np.zeros((members, 4, ny, nx))
+    for b in range(members):
+        h = np.full((ny, nx), depth)
+        for _ in range(3):
+            c = rng.normal(size=3)
+            c /= np.linalg.norm(c)
+            h += amp * np.exp(-((x - c[:, None, None]) ** 2).sum(0) / width2)
+        w = rng.normal(size=3)
+        w *= spin / np.linalg.norm(w)
+        m = np.stack([w[1] * x[2] - w[2] * x[1], w[2] * x[0] - w[0] * x[2], w[0] * x[1] - w[1] * x[0]])
+        q[b, 0] = h
+        q[b, 1:] = m * h[None]
+    return q
