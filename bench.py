@@ -298,6 +298,7 @@ def run_gpu(args):
         line["serving"] = serving_block(args)
     if not args.no_schemes:
         line["schemes"] = schemes_block(args)
+        line["sphere"] = sphere_block(args)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         rate, secs, threads = oracle_sample(4, 512, 256)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
@@ -549,6 +550,52 @@ def schemes_block(args):
         "cell_updates_per_s": rate, "ms_per_step": ms / K, "hbm_gbs": 80 * rate / 1e9,
         "frac_of_measured_hbm": 80 * rate / 1e9 / peak}
     del st
+    return out
+
+
+def sphere_block(args):
+    """Shallow water on the sphere (Sections 2.4, 4.3) on the thesis's
+    finest grid, 1000 x 500 cells: one member (the thesis's run) and a
+    batch of 32 members sharing the grid metrics.  Algorithmic HBM bytes per
+    cell-update: 80 for the state (stage 1 reads q^n, writes q1; stage 2
+    reads q1 and q^n, writes q^{n+1}; 16 B per cell each) plus the metrics,
+    232 B per cell and step (x and y faces 40 B each, cells 36 B, read by
+    both stages), shared by the batch."""
+    import torch
+
+    from paper_2602_08670_gb300 import fv
+    from paper_2602_08670_gb300 import workloads as W
+
+    peak, _ = measured_peaks()
+    g_nd, omega = 11489.57, 6.300388          # Earth radii and days
+    nx, ny = 1000, 500
+    out = {"workload": f"sphere {nx} x {ny}, seeded bumps + rigid rotation, HLL SSP-RK2, CFL 0.5, "
+                       "g and Omega in Earth radii / days",
+           "kernel": "sphere_stage_kernel (tile, 4 variables, rotated HLL + correction + Coriolis + projection)"}
+    bs = torch.cuda.Stream()
+    for members, K in ((1, 50), (32, 10)):
+        with torch.cuda.stream(bs):
+            st = fv.sphere_init(torch.ones(1, 4, ny, nx, device="cuda"), g=g_nd, omega=omega)
+        c, _ = fv.sphere_get_cells(st)
+        del st
+        q0 = torch.tensor(W.sphere_bumps(c, 5, members, spin=1.0), dtype=torch.float32).cuda()
+        with torch.cuda.stream(bs):
+            st = fv.sphere_init(q0, g=g_nd, omega=omega)
+        fv.fv_enqueue_steps(st, 3)
+        fv.fv_sync(st)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(bs)
+        fv.fv_enqueue_steps(st, K)
+        e1.record(bs)
+        fv.fv_sync(st)
+        ms = e0.elapsed_time(e1)
+        rate = members * nx * ny * K / (ms * 1e-3)
+        bytes_per = 80 + 232 / members
+        out[f"members_{members}"] = {"cell_updates_per_s": rate, "ms_per_step": ms / K,
+                                     "algorithmic_bytes_per_cell_update": bytes_per,
+                                     "hbm_gbs": bytes_per * rate / 1e9,
+                                     "frac_of_measured_hbm": bytes_per * rate / 1e9 / peak}
+        del st
     return out
 
 
