@@ -168,6 +168,7 @@ struct SphArgs {
   long long plane, member;
   float g, omega;
   int stage;           // 1: q1 = q + dt L(q); 2: Heun's second stage and the CFL reduction
+  int B;               // members (looped over inside each block)
 };
 
 __device__ __forceinline__ float mm(float a, float b) {
@@ -223,123 +224,162 @@ __device__ void face_flux(const float (&m)[C], const float (&a)[C], const float 
   for (int k = 0; k < 3; ++k) out[1 + k] = (F[1] * fr[k] + F[2] * fr[3 + k] + F[3] * fr[6 + k]) * len;
 }
 
-__global__ void __launch_bounds__(NT) sphere_stage_kernel(SphArgs a) {
+// Metric cache of one tile (CACHED instances, dynamic shared memory):
+// x faces [10][TY][TX + 1], y faces [10][TY + 1][TX], cells [8][TY][TX].
+constexpr int MXP = TY * (TX + 1), MYP = (TY + 1) * TX, MCP = TY * TX;
+constexpr int cache_bytes() { return (F_PLANES * MXP + F_PLANES * MYP + C_AREA * MCP) * 4; }
+
+// CACHED: one block per tile looping over the members, with the tile's
+// metrics staged in shared memory once for all of them (batches); else one
+// block per (tile, member) reading the metrics where they lie (one member).
+template <bool CACHED>
+__global__ void __launch_bounds__(NT, CACHED ? 4 : 3) sphere_stage_kernel(SphArgs a) {
   __shared__ float sq[C][SY][SX];
   __shared__ float sF[C][TY][TX + 1];
   __shared__ float sG[C][TY + 1][TX];
   __shared__ unsigned red[2 * NT / 32];
-  const int b = blockIdx.z;
-  Ctrl* ctrl = a.ctrl + b;
-  if (skip_if_done(ctrl)) return;
-  const float dt = (float)ctrl->dt;
+  extern __shared__ float mcache[];
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
   const int tid = threadIdx.x;
   const int nx = a.nx, ny = a.ny;
-  const float* qin = a.qin + b * a.member;
-  // tile with a 2-cell halo: x periodic; beyond the top / bottom row the
-  // rows of the mirrored column (rows past the second ghost only occur in a
-  // partial tile and are clamped to it)
-  for (int idx = tid; idx < C * SY * SX; idx += NT) {
-    const int c = idx / (SY * SX), rr = idx - c * SY * SX;
-    const int sy = rr / SX, sx = rr - sy * SX;
-    int gx = wrap(x0 - 2 + sx, nx);
-    int gy = max(-2, min(y0 - 2 + sy, ny + 1));
-    if (gy < 0 || gy >= ny) {
-      gy = gy < 0 ? -1 - gy : 2 * ny - 1 - gy;
-      gx = nx - 1 - gx;
-    }
-    sq[c][sy][sx] = qin[c * a.plane + (long long)gy * nx + gx];
-  }
-  __syncthreads();
   const SphereLayout Lm = sphere_layout(nx, ny);
   const long long px = (long long)ny * nx, py = (long long)(ny + 1) * nx;
-  for (int idx = tid; idx < TY * (TX + 1); idx += NT) {
-    const int r = idx / (TX + 1), k = idx - r * (TX + 1);
-    const int gy = y0 + r;
-    if (gy >= ny || x0 + k > nx) continue;
-    float m[C], s0[C], s1[C], p[C], F[C];
-#pragma unroll
-    for (int c = 0; c < C; ++c) {
-      m[c] = sq[c][r + 2][k];
-      s0[c] = sq[c][r + 2][k + 1];
-      s1[c] = sq[c][r + 2][k + 2];
-      p[c] = sq[c][r + 2][k + 3];
+  // metric planes and strides as the face and cell loops index them
+  const float* xm = CACHED ? mcache : a.M + Lm.xf;
+  const float* ym = CACHED ? mcache + F_PLANES * MXP : a.M + Lm.yf;
+  const float* cmm = CACHED ? mcache + F_PLANES * (MXP + MYP) : a.M + Lm.cell;
+  const long long xps = CACHED ? MXP : px, yps = CACHED ? MYP : py, cps = CACHED ? MCP : px;
+  if (CACHED) {
+    float* cx = mcache;
+    float* cy = mcache + F_PLANES * MXP;
+    float* cc = mcache + F_PLANES * (MXP + MYP);
+    for (int idx = tid; idx < F_PLANES * MXP; idx += NT) {
+      const int k = idx / MXP, rr = idx - k * MXP;
+      const int r = rr / (TX + 1), c = rr - r * (TX + 1);
+      if (y0 + r < ny && x0 + c <= nx) cx[idx] = a.M[Lm.xf + k * px + (long long)(y0 + r) * nx + wrap(x0 + c, nx)];
     }
-    face_flux(m, s0, s1, p, a.M + Lm.xf, px, (long long)gy * nx + wrap(x0 + k, nx), a.g, F);
-#pragma unroll
-    for (int c = 0; c < C; ++c) sF[c][r][k] = F[c];
-  }
-  for (int idx = tid; idx < (TY + 1) * TX; idx += NT) {
-    const int k = idx / TX, i = idx - k * TX;
-    const int gx = x0 + i;
-    if (gx >= nx || y0 + k > ny) continue;
-    float m[C], s0[C], s1[C], p[C], F[C];
-#pragma unroll
-    for (int c = 0; c < C; ++c) {
-      m[c] = sq[c][k][i + 2];
-      s0[c] = sq[c][k + 1][i + 2];
-      s1[c] = sq[c][k + 2][i + 2];
-      p[c] = sq[c][k + 3][i + 2];
+    for (int idx = tid; idx < F_PLANES * MYP; idx += NT) {
+      const int k = idx / MYP, rr = idx - k * MYP;
+      const int r = rr / TX, c = rr - r * TX;
+      if (y0 + r <= ny && x0 + c < nx) cy[idx] = a.M[Lm.yf + k * py + (long long)(y0 + r) * nx + x0 + c];
     }
-    face_flux(m, s0, s1, p, a.M + Lm.yf, py, (long long)(y0 + k) * nx + gx, a.g, F);
-#pragma unroll
-    for (int c = 0; c < C; ++c) sG[c][k][i] = F[c];
+    for (int idx = tid; idx < C_AREA * MCP; idx += NT) {
+      const int k = idx / MCP, rr = idx - k * MCP;
+      const int r = rr / TX, c = rr - r * TX;
+      if (y0 + r < ny && x0 + c < nx) cc[idx] = a.M[Lm.cell + k * px + (long long)(y0 + r) * nx + x0 + c];
+    }
   }
-  __syncthreads();
+  const int b0 = CACHED ? 0 : blockIdx.z, b1 = CACHED ? a.B : blockIdx.z + 1;
+#pragma unroll 1
+  for (int b = b0; b < b1; ++b) {
+    Ctrl* ctrl = a.ctrl + b;
+    __syncthreads();   // metrics staged / the previous member's tile and fluxes consumed
+    if (skip_if_done(ctrl)) continue;
+    const float dt = (float)ctrl->dt;
+    const float* qin = a.qin + b * a.member;
+    // tile with a 2-cell halo: x periodic; beyond the top / bottom row the
+    // rows of the mirrored column (rows past the second ghost only occur in
+    // a partial tile and are clamped to it)
+    for (int idx = tid; idx < C * SY * SX; idx += NT) {
+      const int c = idx / (SY * SX), rr = idx - c * SY * SX;
+      const int sy = rr / SX, sx = rr - sy * SX;
+      int gx = wrap(x0 - 2 + sx, nx);
+      int gy = max(-2, min(y0 - 2 + sy, ny + 1));
+      if (gy < 0 || gy >= ny) {
+        gy = gy < 0 ? -1 - gy : 2 * ny - 1 - gy;
+        gx = nx - 1 - gx;
+      }
+      sq[c][sy][sx] = qin[c * a.plane + (long long)gy * nx + gx];
+    }
+    __syncthreads();
+    for (int idx = tid; idx < TY * (TX + 1); idx += NT) {
+      const int r = idx / (TX + 1), k = idx - r * (TX + 1);
+      if (y0 + r >= ny || x0 + k > nx) continue;
+      float m[C], s0[C], s1[C], p[C], F[C];
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        m[c] = sq[c][r + 2][k];
+        s0[c] = sq[c][r + 2][k + 1];
+        s1[c] = sq[c][r + 2][k + 2];
+        p[c] = sq[c][r + 2][k + 3];
+      }
+      const long long fx = CACHED ? (long long)r * (TX + 1) + k : (long long)(y0 + r) * nx + wrap(x0 + k, nx);
+      face_flux(m, s0, s1, p, xm, xps, fx, a.g, F);
+#pragma unroll
+      for (int c = 0; c < C; ++c) sF[c][r][k] = F[c];
+    }
+    for (int idx = tid; idx < (TY + 1) * TX; idx += NT) {
+      const int k = idx / TX, i = idx - k * TX;
+      if (x0 + i >= nx || y0 + k > ny) continue;
+      float m[C], s0[C], s1[C], p[C], F[C];
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        m[c] = sq[c][k][i + 2];
+        s0[c] = sq[c][k + 1][i + 2];
+        s1[c] = sq[c][k + 2][i + 2];
+        p[c] = sq[c][k + 3][i + 2];
+      }
+      const long long fy = CACHED ? (long long)k * TX + i : (long long)(y0 + k) * nx + x0 + i;
+      face_flux(m, s0, s1, p, ym, yps, fy, a.g, F);
+#pragma unroll
+      for (int c = 0; c < C; ++c) sG[c][k][i] = F[c];
+    }
+    __syncthreads();
 
-  float amax = 0.f;
-  unsigned bad = 0u;
-  const float* cm = a.M + Lm.cell;
-  const float* qn = a.qn + b * a.member;
-  float* qout = a.qout + b * a.member;
-  for (int idx = tid; idx < TY * TX; idx += NT) {
-    const int r = idx / TX, i = idx - r * TX;
-    const int gx = x0 + i, gy = y0 + r;
-    if (gx >= nx || gy >= ny) continue;
-    const long long off = (long long)gy * nx + gx;
-    float q[C];
+    float amax = 0.f;
+    unsigned bad = 0u;
+    const float* qn = a.qn + b * a.member;
+    float* qout = a.qout + b * a.member;
+    for (int idx = tid; idx < TY * TX; idx += NT) {
+      const int r = idx / TX, i = idx - r * TX;
+      const int gx = x0 + i, gy = y0 + r;
+      if (gx >= nx || gy >= ny) continue;
+      const long long off = (long long)gy * nx + gx;
+      float q[C];
 #pragma unroll
-    for (int c = 0; c < C; ++c) q[c] = sq[c][r + 2][i + 2];
-    const float ra = cm[C_RA * px + off];
-    const float xh[3] = {cm[(C_X + 0) * px + off], cm[(C_X + 1) * px + off], cm[(C_X + 2) * px + off]};
-    const float S[3] = {cm[(C_S + 0) * px + off], cm[(C_S + 1) * px + off], cm[(C_S + 2) * px + off]};
-    // Eq. 3.1's correction on the momenta: F(q) . S = m (m . S) / h + (g h^2 / 2) S
-    const float mS = q[1] * S[0] + q[2] * S[1] + q[3] * S[2];
-    const float ph = 0.5f * a.g * q[0] * q[0];
-    float L[C];
+      for (int c = 0; c < C; ++c) q[c] = sq[c][r + 2][i + 2];
+      const long long ci = CACHED ? (long long)r * TX + i : off;
+      const float ra = cmm[C_RA * cps + ci];
+      const float xh[3] = {cmm[C_X * cps + ci], cmm[(C_X + 1) * cps + ci], cmm[(C_X + 2) * cps + ci]};
+      const float S[3] = {cmm[C_S * cps + ci], cmm[(C_S + 1) * cps + ci], cmm[(C_S + 2) * cps + ci]};
+      // Eq. 3.1's correction on the momenta: F(q) . S = m (m . S) / h + (g h^2 / 2) S
+      const float mS = q[1] * S[0] + q[2] * S[1] + q[3] * S[2];
+      const float ph = 0.5f * a.g * q[0] * q[0];
+      float L[C];
 #pragma unroll
-    for (int c = 0; c < C; ++c) {
-      const float net = (sF[c][r][i + 1] - sF[c][r][i]) + (sG[c][r + 1][i] - sG[c][r][i]);
-      const float corr = c == 0 ? 0.f : q[c] * (mS / q[0]) + ph * S[c - 1];
-      L[c] = -(net - corr) * ra;
+      for (int c = 0; c < C; ++c) {
+        const float net = (sF[c][r][i + 1] - sF[c][r][i]) + (sG[c][r + 1][i] - sG[c][r][i]);
+        const float corr = c == 0 ? 0.f : q[c] * (mS / q[0]) + ph * S[c - 1];
+        L[c] = -(net - corr) * ra;
+      }
+      // Coriolis (Eq. 3.2): -2 Omega z (x cross m)
+      const float f = -2.f * a.omega * xh[2];
+      L[1] += f * (xh[1] * q[3] - xh[2] * q[2]);
+      L[2] += f * (xh[2] * q[1] - xh[0] * q[3]);
+      L[3] += f * (xh[0] * q[2] - xh[1] * q[1]);
+      float out[C];
+#pragma unroll
+      for (int c = 0; c < C; ++c)
+        out[c] = a.stage == 1 ? q[c] + dt * L[c] : 0.5f * qn[c * a.plane + off] + 0.5f * (q[c] + dt * L[c]);
+      // project the momentum onto the tangent plane at the cell centre
+      const float mx = out[1] * xh[0] + out[2] * xh[1] + out[3] * xh[2];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) out[1 + k] -= mx * xh[k];
+#pragma unroll
+      for (int c = 0; c < C; ++c) qout[c * a.plane + off] = out[c];
+      if (a.stage == 2) {
+        const float h = out[0];
+        const float sp = sqrtf(out[1] * out[1] + out[2] * out[2] + out[3] * out[3]) / h + sqrtf(a.g * h);
+        const float rate = sp * cmm[C_RATE * cps + ci];
+        bad |= (h > 0.f) ? 0u : (unsigned)FV_HEALTH_NONPOSITIVE;
+        bad |= (rate < INFINITY) ? 0u : (unsigned)FV_HEALTH_NONFINITE;
+        amax = fmaxf(amax, rate);
+      }
     }
-    // Coriolis (Eq. 3.2): -2 Omega z (x cross m)
-    const float f = -2.f * a.omega * xh[2];
-    L[1] += f * (xh[1] * q[3] - xh[2] * q[2]);
-    L[2] += f * (xh[2] * q[1] - xh[0] * q[3]);
-    L[3] += f * (xh[0] * q[2] - xh[1] * q[1]);
-    float out[C];
-#pragma unroll
-    for (int c = 0; c < C; ++c)
-      out[c] = a.stage == 1 ? q[c] + dt * L[c] : 0.5f * qn[c * a.plane + off] + 0.5f * (q[c] + dt * L[c]);
-    // project the momentum onto the tangent plane at the cell centre
-    const float mx = out[1] * xh[0] + out[2] * xh[1] + out[3] * xh[2];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) out[1 + k] -= mx * xh[k];
-#pragma unroll
-    for (int c = 0; c < C; ++c) qout[c * a.plane + off] = out[c];
     if (a.stage == 2) {
-      const float h = out[0];
-      const float sp = sqrtf(out[1] * out[1] + out[2] * out[2] + out[3] * out[3]) / h + sqrtf(a.g * h);
-      const float rate = sp * cm[C_RATE * px + off];
-      bad |= (h > 0.f) ? 0u : (unsigned)FV_HEALTH_NONPOSITIVE;
-      bad |= (rate < INFINITY) ? 0u : (unsigned)FV_HEALTH_NONFINITE;
-      amax = fmaxf(amax, rate);
+      block_reduce_max_or(amax, bad, red);
+      if (tid == 0) publish_and_close(ctrl, a.dp, amax, bad, gridDim.x * gridDim.y, true);
     }
-  }
-  if (a.stage == 2) {
-    block_reduce_max_or(amax, bad, red);
-    if (tid == 0) publish_and_close(ctrl, a.dp, amax, bad, gridDim.x * gridDim.y, true);
   }
 }
 
@@ -395,14 +435,21 @@ cudaError_t launch_sphere_wavespeed(const Geom& g, const float* q, const float* 
 
 cudaError_t enqueue_sphere_step(const Geom& g, float* qa, float* qb, const float* M, float omega, Ctrl* ctrl,
                                 const DtParams* dp, cudaStream_t s) {
-  SphArgs a{qa, nullptr, qb, M, ctrl, dp, g.nx, g.ny, g.plane(), g.member(), g.phys, omega, 1};
-  dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, g.B);
-  sphere_stage_kernel<<<grid, NT, 0, s>>>(a);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  SphArgs b2{qb, qa, qa, M, ctrl, dp, g.nx, g.ny, g.plane(), g.member(), g.phys, omega, 2};
-  sphere_stage_kernel<<<grid, NT, 0, s>>>(b2);
-  return cudaGetLastError();
+  SphArgs a{qa, nullptr, qb, M, ctrl, dp, g.nx, g.ny, g.plane(), g.member(), g.phys, omega, 1, g.B};
+  SphArgs b2{qb, qa, qa, M, ctrl, dp, g.nx, g.ny, g.plane(), g.member(), g.phys, omega, 2, g.B};
+  // batches share one metric load per tile; a single member reads them directly
+  const bool cached = g.B >= 4;
+  dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, cached ? 1 : g.B);
+  for (const SphArgs* k : {&a, &b2}) {
+    if (cached) {
+      sphere_stage_kernel<true><<<grid, NT, cache_bytes(), s>>>(*k);
+    } else {
+      sphere_stage_kernel<false><<<grid, NT, 0, s>>>(*k);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 }  // namespace fvk

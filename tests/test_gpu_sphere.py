@@ -44,10 +44,13 @@ def test_grid_matches_oracle(fv, ny):
     assert abs(a.astype(np.float64).sum() / (4 * np.pi) - 1) < 1e-6
 
 
-@pytest.mark.parametrize("nx,ny,B,steps,spin", [(16, 8, 1, 20, 0.5), (64, 32, 2, 30, 0.5), (100, 50, 1, 20, 1.0)])
+@pytest.mark.parametrize("nx,ny,B,steps,spin", [(16, 8, 1, 20, 0.5), (64, 32, 2, 30, 0.5), (100, 50, 1, 20, 1.0),
+                                                 (36, 18, 5, 15, 0.5)])
 def test_rollout_matches_oracle(fv, nx, ny, B, steps, spin):
     """(16, 8): one partial tile; (100, 50): the thesis's coarsest grid, a
-    ragged last tile in both directions; two members share the grid."""
+    ragged last tile in both directions; two members share the grid; five
+    members (ragged 36 x 18) take the batched kernel that stages each tile's
+    metrics once for all members."""
     G = S.Grid(nx, ny)
     q0 = initial(G, 4, B, spin)
     # member 0's adaptive dt sequence, replayed for every member
