@@ -233,7 +233,7 @@ constexpr int cache_bytes() { return (F_PLANES * MXP + F_PLANES * MYP + C_AREA *
 // metrics staged in shared memory once for all of them (batches); else one
 // block per (tile, member) reading the metrics where they lie (one member).
 template <bool CACHED>
-__global__ void __launch_bounds__(NT, CACHED ? 4 : 3) sphere_stage_kernel(SphArgs a) {
+__global__ void __launch_bounds__(NT, 4) sphere_stage_kernel(SphArgs a) {
   __shared__ float sq[C][SY][SX];
   __shared__ float sF[C][TY][TX + 1];
   __shared__ float sG[C][TY + 1][TX];
