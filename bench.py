@@ -556,7 +556,8 @@ def schemes_block(args):
 def sphere_block(args):
     """Shallow water on the sphere (Sections 2.4, 4.3) on the thesis's
     finest grid, 1000 x 500 cells: one member (the thesis's run) and a
-    batch of 32 members sharing the grid metrics.  Algorithmic HBM bytes per
+    batch of 32 members sharing the grid metrics, with HLL, and one member
+    with Roe (the thesis's flux for its sphere runs).  Algorithmic HBM bytes per
     cell-update: 80 for the state (stage 1 reads q^n, writes q1; stage 2
     reads q1 and q^n, writes q^{n+1}; 16 B per cell each) plus the metrics,
     232 B per cell and step (x and y faces 40 B each, cells 36 B, read by
@@ -573,7 +574,7 @@ def sphere_block(args):
                        "g and Omega in Earth radii / days",
            "kernel": "sphere_stage_kernel (tile, 4 variables, rotated HLL + correction + Coriolis + projection)"}
     bs = torch.cuda.Stream()
-    for members, K in ((1, 50), (32, 10)):
+    for members, K, flux in ((1, 50, "hll"), (32, 10, "hll"), (1, 50, "roe")):
         with torch.cuda.stream(bs):
             st = fv.sphere_init(torch.ones(1, 4, ny, nx, device="cuda"), g=g_nd, omega=omega)
         c, _ = fv.sphere_get_cells(st)
@@ -581,6 +582,7 @@ def sphere_block(args):
         q0 = torch.tensor(W.sphere_bumps(c, 5, members, spin=1.0), dtype=torch.float32).cuda()
         with torch.cuda.stream(bs):
             st = fv.sphere_init(q0, g=g_nd, omega=omega)
+        fv.fv_set_scheme(st, flux, 2)
         fv.fv_enqueue_steps(st, 3)
         fv.fv_sync(st)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -591,7 +593,8 @@ def sphere_block(args):
         ms = e0.elapsed_time(e1)
         rate = members * nx * ny * K / (ms * 1e-3)
         bytes_per = 80 + 232 / members
-        out[f"members_{members}"] = {"cell_updates_per_s": rate, "ms_per_step": ms / K,
+        key = f"members_{members}" + ("" if flux == "hll" else f"_{flux}")
+        out[key] = {"cell_updates_per_s": rate, "ms_per_step": ms / K,
                                      "algorithmic_bytes_per_cell_update": bytes_per,
                                      "hbm_gbs": bytes_per * rate / 1e9,
                                      "frac_of_measured_hbm": bytes_per * rate / 1e9 / peak}

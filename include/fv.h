@@ -122,7 +122,9 @@ int euler_init(const fv_grid* grid, const fv_euler_params* params, const float* 
  * (|m| / h + sqrt(g h)) * perimeter / (2 area).  The grid metrics are
  * computed once on the device (FP64, stored FP32) and shared by the members.
  * fv_step / fv_rollout / fv_get_state / fv_set_state / fv_get_time /
- * fv_health apply; fv_set_scheme accepts HLL with SSP-RK2 only, and
+ * fv_health apply; fv_set_scheme accepts HLL, Rusanov, Roe, HLLE or HLLC
+ * with SSP-RK2 (the tangential momenta m.t and m.r passive; Lax-Friedrichs
+ * and SSP-RK3 are FV_EINVAL), and
  * fv_set_boundary, fv_set_bathymetry, fv_diagnostics and learned steps
  * return FV_EINVAL.  Errors: FV_EINVAL (nx != 2 ny, ny < 2, g <= 0),
  * FV_ENOMEM, FV_ECUDA. */

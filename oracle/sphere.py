@@ -35,6 +35,11 @@ Discretisation (Section 4.3's steps 1-7):
   * after every Runge-Kutta stage the momentum is projected onto the tangent
     plane at the cell centre, m <- m - (m.x) x (Eq. 3.2's second term);
   * dt by the Courant rate (|m| / h + sqrt(g h)) (sum_e l_e) / (2 A_i).
+Fluxes other than HLL (Rusanov, Roe, HLLE, HLLC; Table 4 compares them on
+the sphere) come from ``oracle.schemes``' shallow-water solvers applied to
+(h, m.n, m.t) and to (h, m.n, m.r): both tangential momenta are passive, so
+the second call's depth and normal fluxes equal the first's and its third
+component is the flux of m.r.
 """
 from __future__ import annotations
 
@@ -43,6 +48,7 @@ import math
 import torch
 
 from . import fv
+from . import schemes
 
 SQRT2 = math.sqrt(2.0)
 
@@ -201,13 +207,22 @@ def flux_dot(q: torch.Tensor, S: torch.Tensor, g: float) -> torch.Tensor:
     return torch.cat([mS.unsqueeze(1), mom], dim=1)
 
 
-def rhs(q: torch.Tensor, G: Grid, g: float, omega: float) -> torch.Tensor:
+def edge_flux(flux: str, qL: torch.Tensor, qR: torch.Tensor, g: float) -> torch.Tensor:
+    """Normal flux of two edge-frame states (h, m_n, m_t, m_r) [B][4][...]."""
+    if flux == schemes.HLL:
+        return hll4(qL, qR, g)
+    a = schemes.normal_flux_solver(flux, qL[:, :3], qR[:, :3], fv.SWE, g, 1.4)
+    b = schemes.normal_flux_solver(flux, qL[:, [0, 1, 3]], qR[:, [0, 1, 3]], fv.SWE, g, 1.4)
+    return torch.cat([a, b[:, 2:3]], dim=1)
+
+
+def rhs(q: torch.Tensor, G: Grid, g: float, omega: float, flux: str = schemes.HLL) -> torch.Tensor:
     """L(q) for q [B][4][ny][nx]."""
     # x faces (periodic): face i between cells i - 1 and i
     QL, QR = fv.muscl_minmod(q, -1, 1.0)          # face i + 1/2 at index i (slopes in index units)
     QL = torch.roll(QL, 1, dims=-1)                # now face i (left cell i - 1)
     QR = torch.roll(QR, 1, dims=-1)
-    Fx = rotate_back(hll4(rotate(QL, G.fx_n, G.fx_t, G.fx_r), rotate(QR, G.fx_n, G.fx_t, G.fx_r), g),
+    Fx = rotate_back(edge_flux(flux, rotate(QL, G.fx_n, G.fx_t, G.fx_r), rotate(QR, G.fx_n, G.fx_t, G.fx_r), g),
                      G.fx_n, G.fx_t, G.fx_r) * G.fx_len
     # y faces: face j between rows j - 1 and j, j = 0..ny, from the padded array
     P = G.pad_y(q, 2)
@@ -218,7 +233,7 @@ def rhs(q: torch.Tensor, G: Grid, g: float, omega: float) -> torch.Tensor:
     dn = P0 - 0.5 * slope          # lower face state
     QL = up[..., :-1, :]           # rows -1 .. ny - 1  (face j's lower cell j - 1)
     QR = dn[..., 1:, :]            # rows 0 .. ny
-    Gy = rotate_back(hll4(rotate(QL, G.fy_n, G.fy_t, G.fy_r), rotate(QR, G.fy_n, G.fy_t, G.fy_r), g),
+    Gy = rotate_back(edge_flux(flux, rotate(QL, G.fy_n, G.fy_t, G.fy_r), rotate(QR, G.fy_n, G.fy_t, G.fy_r), g),
                      G.fy_n, G.fy_t, G.fy_r) * G.fy_len
     net = (torch.roll(Fx, -1, dims=-1) - Fx) + (Gy[..., 1:, :] - Gy[..., :-1, :])
     corr = flux_dot(q, G.ln_sum, g)
@@ -240,10 +255,10 @@ def project(q: torch.Tensor, G: Grid) -> torch.Tensor:
     return torch.cat([q[:, :1], m], dim=1)
 
 
-def step(q: torch.Tensor, G: Grid, dt, g: float, omega: float) -> torch.Tensor:
+def step(q: torch.Tensor, G: Grid, dt, g: float, omega: float, flux: str = schemes.HLL) -> torch.Tensor:
     """SSP-RK2 (Eq. 2.19) with the tangent projection after each stage."""
-    q1 = project(q + dt * rhs(q, G, g, omega), G)
-    return project(0.5 * q + 0.5 * q1 + 0.5 * dt * rhs(q1, G, g, omega), G)
+    q1 = project(q + dt * rhs(q, G, g, omega, flux), G)
+    return project(0.5 * q + 0.5 * q1 + 0.5 * dt * rhs(q1, G, g, omega, flux), G)
 
 
 def cfl_dt(q: torch.Tensor, G: Grid, cfl: float, g: float) -> torch.Tensor:
@@ -254,7 +269,7 @@ def cfl_dt(q: torch.Tensor, G: Grid, cfl: float, g: float) -> torch.Tensor:
 
 
 def run(q0, G: Grid, nsteps: int, *, g: float, omega: float, cfl: float = 0.5,
-        dt_mode: str = fv.DT_ADAPTIVE, dt_fixed=None, dts=None, dtype=torch.float64):
+        dt_mode: str = fv.DT_ADAPTIVE, dt_fixed=None, dts=None, dtype=torch.float64, flux: str = schemes.HLL):
     """``nsteps`` SSP-RK2 steps; returns (q, t, dt_history).  ``dtype``
     float32 replays the algorithm in single precision (metrics included)."""
     q = torch.as_tensor(q0).to(dtype).clone()
@@ -271,7 +286,7 @@ def run(q0, G: Grid, nsteps: int, *, g: float, omega: float, cfl: float = 0.5,
         else:
             d = torch.as_tensor(dts[n]).to(dtype)
             dt = d.expand(B).clone() if d.dim() == 0 else d.clone()
-        q = step(q, G, dt.view(B, 1, 1, 1), g, omega)
+        q = step(q, G, dt.view(B, 1, 1, 1), g, omega, flux)
         t = t + dt
         hist.append(dt)
     dt_hist = torch.stack(hist) if hist else torch.zeros(0, B, dtype=torch.float64)

@@ -54,8 +54,8 @@ long long sphere_area_offset(int nx, int ny);     // [ny][nx] spherical cell are
 cudaError_t launch_sphere_metrics(float* M, int nx, int ny, cudaStream_t s);
 cudaError_t launch_sphere_wavespeed(const Geom& g, const float* q, const float* M, Ctrl* ctrl,
                                     const DtParams* dp, cudaStream_t s);
-cudaError_t enqueue_sphere_step(const Geom& g, float* qa, float* qb, const float* M, float omega, Ctrl* ctrl,
-                                const DtParams* dp, cudaStream_t s);
+cudaError_t enqueue_sphere_step(const Geom& g, int flux, float* qa, float* qb, const float* M, float omega,
+                                Ctrl* ctrl, const DtParams* dp, cudaStream_t s);
 
 // Wave-speed reduction of q that sets each member's dt without advancing
 // time (state creation, fv_set_state).

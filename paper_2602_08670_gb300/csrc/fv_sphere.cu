@@ -17,11 +17,15 @@
 // correction F(q_i) . sum_e l_e n_e on the momenta, the Coriolis term of
 // Eq. 3.2, and the projection of the momentum onto the tangent plane at the
 // cell centre.  The grid metrics are computed once per state in FP64 and
-// stored in FP32; every member of a batch shares them.
+// stored in FP32; every member of a batch shares them.  The other fluxes of
+// the planar path (Rusanov, Roe, HLLE, HLLC) treat m.t and m.r as two passive
+// variables: the shallow-water solver runs on (h, m.n, m.t) and on
+// (h, m.n, m.r), and the second call contributes the flux of m.r.
 #include <cuda_runtime.h>
 
 #include "fv_common.cuh"
 #include "fv_kernels.h"
+#include "fv_schemes.cuh"
 
 namespace fvk {
 
@@ -169,6 +173,7 @@ struct SphArgs {
   float g, omega;
   int stage;           // 1: q1 = q + dt L(q); 2: Heun's second stage and the CFL reduction
   int B;               // members (looped over inside each block)
+  int flux;            // fvk::Flux (HLL, Rusanov, Roe, HLLE or HLLC)
 };
 
 __device__ __forceinline__ float mm(float a, float b) {
@@ -199,7 +204,7 @@ __device__ void hll4(const float (&L)[C], const float (&R)[C], float g, float (&
 // Face flux times length from the 4-cell stencil m, a | b, p (Cartesian
 // variables) and the face metrics at f (plane stride ps).
 __device__ void face_flux(const float (&m)[C], const float (&a)[C], const float (&b)[C], const float (&p)[C],
-                          const float* fm, long long ps, long long f, float g, float (&out)[C]) {
+                          const float* fm, long long ps, long long f, float g, int flux, float (&out)[C]) {
   float Lq[C], Rq[C];
 #pragma unroll
   for (int c = 0; c < C; ++c) {
@@ -218,7 +223,19 @@ __device__ void face_flux(const float (&m)[C], const float (&a)[C], const float 
     l[1 + v] = Lq[1] * fr[3 * v] + Lq[2] * fr[3 * v + 1] + Lq[3] * fr[3 * v + 2];
     r[1 + v] = Rq[1] * fr[3 * v] + Rq[2] * fr[3 * v + 1] + Rq[3] * fr[3 * v + 2];
   }
-  hll4(l, r, g, F);
+  if (flux == FLUX_HLL) {
+    hll4(l, r, g, F);
+  } else {
+    const float lt[3] = {l[0], l[1], l[2]}, rt[3] = {r[0], r[1], r[2]};
+    const float lr[3] = {l[0], l[1], l[3]}, rr[3] = {r[0], r[1], r[3]};
+    float Ft[3], Fr[3];
+    scheme_flux<3, SWE, float>(flux, lt, rt, g, 0.f, Ft);
+    scheme_flux<3, SWE, float>(flux, lr, rr, g, 0.f, Fr);
+    F[0] = Ft[0];
+    F[1] = Ft[1];
+    F[2] = Ft[2];
+    F[3] = Fr[2];
+  }
   out[0] = F[0] * len;
 #pragma unroll
   for (int k = 0; k < 3; ++k) out[1 + k] = (F[1] * fr[k] + F[2] * fr[3 + k] + F[3] * fr[6 + k]) * len;
@@ -304,7 +321,7 @@ __global__ void __launch_bounds__(NT, 4) sphere_stage_kernel(SphArgs a) {
         p[c] = sq[c][r + 2][k + 3];
       }
       const long long fx = CACHED ? (long long)r * (TX + 1) + k : (long long)(y0 + r) * nx + wrap(x0 + k, nx);
-      face_flux(m, s0, s1, p, xm, xps, fx, a.g, F);
+      face_flux(m, s0, s1, p, xm, xps, fx, a.g, a.flux, F);
 #pragma unroll
       for (int c = 0; c < C; ++c) sF[c][r][k] = F[c];
     }
@@ -320,7 +337,7 @@ __global__ void __launch_bounds__(NT, 4) sphere_stage_kernel(SphArgs a) {
         p[c] = sq[c][k + 3][i + 2];
       }
       const long long fy = CACHED ? (long long)k * TX + i : (long long)(y0 + k) * nx + x0 + i;
-      face_flux(m, s0, s1, p, ym, yps, fy, a.g, F);
+      face_flux(m, s0, s1, p, ym, yps, fy, a.g, a.flux, F);
 #pragma unroll
       for (int c = 0; c < C; ++c) sG[c][k][i] = F[c];
     }
@@ -433,10 +450,10 @@ cudaError_t launch_sphere_wavespeed(const Geom& g, const float* q, const float* 
   return cudaGetLastError();
 }
 
-cudaError_t enqueue_sphere_step(const Geom& g, float* qa, float* qb, const float* M, float omega, Ctrl* ctrl,
-                                const DtParams* dp, cudaStream_t s) {
-  SphArgs a{qa, nullptr, qb, M, ctrl, dp, g.nx, g.ny, g.plane(), g.member(), g.phys, omega, 1, g.B};
-  SphArgs b2{qb, qa, qa, M, ctrl, dp, g.nx, g.ny, g.plane(), g.member(), g.phys, omega, 2, g.B};
+cudaError_t enqueue_sphere_step(const Geom& g, int flux, float* qa, float* qb, const float* M, float omega,
+                                Ctrl* ctrl, const DtParams* dp, cudaStream_t s) {
+  SphArgs a{qa, nullptr, qb, M, ctrl, dp, g.nx, g.ny, g.plane(), g.member(), g.phys, omega, 1, g.B, flux};
+  SphArgs b2{qb, qa, qa, M, ctrl, dp, g.nx, g.ny, g.plane(), g.member(), g.phys, omega, 2, g.B, flux};
   // batches share one metric load per tile; a single member reads them directly
   const bool cached = g.B >= 4;
   dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, cached ? 1 : g.B);

@@ -188,7 +188,7 @@ cudaError_t wavespeed_init(fv_state* s) {
 
 cudaError_t enqueue_plain_step(fv_state* s) {
   if (s->g.eq == fvk::SPHERE)
-    return fvk::enqueue_sphere_step(s->g, s->qA, s->qB, s->sphere, s->omega, s->ctrl, s->dp, s->stream);
+    return fvk::enqueue_sphere_step(s->g, s->flux, s->qA, s->qB, s->sphere, s->omega, s->ctrl, s->dp, s->stream);
   if (s->flux != FV_FLUX_HLL || s->rk != 2 || s->bc != FV_BC_PERIODIC || s->zbed)
     return fvk::enqueue_scheme_step(s->g, s->flux, s->rk, s->qA, s->qB, s->qC, s->ctrl, s->dp, s->stream,
                                     s->variant, s->bc, s->zbed);
@@ -485,8 +485,8 @@ extern "C" int fv_set_scheme(fv_state* s, int flux, int rk) {
   if (!s) return fvh::fail(FV_EINVAL, "null state");
   if (flux < FV_FLUX_HLL || flux > FV_FLUX_HLLC) return fvh::fail(FV_EINVAL, "unknown flux");
   if (rk != 2 && rk != 3) return fvh::fail(FV_EINVAL, "rk must be 2 or 3");
-  if (s->g.eq == fvk::SPHERE && (flux != FV_FLUX_HLL || rk != 2))
-    return fvh::fail(FV_EINVAL, "the sphere step uses HLL and SSP-RK2");
+  if (s->g.eq == fvk::SPHERE && (flux == FV_FLUX_LF || rk != 2))
+    return fvh::fail(FV_EINVAL, "the sphere step takes HLL, Rusanov, Roe, HLLE or HLLC with SSP-RK2");
   FV_CUDA_TRY(cudaStreamSynchronize(s->stream));
   if (rk == 3 && !s->qC) {
     const size_t bytes = sizeof(float) * (size_t)s->g.B * (size_t)s->g.member();
