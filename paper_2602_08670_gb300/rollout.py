@@ -2,10 +2,12 @@
 
     python -m paper_2602_08670_gb300.rollout --members 64 --n 256 --steps 3 --variant fused
     python -m paper_2602_08670_gb300.rollout --members 16 --n 1024 --variant plain --flux hllc --rk 3
+    python -m paper_2602_08670_gb300.rollout --members 64 --n 256 --steps 3 --variant face
 
 Members are the random-bump initial states of `workloads.swe_random_bumps`
-(seed 3), the network the committed trained weights, dt the fine time step
-they were trained with.  The plain variant takes any flux and integrator of
+(seed 3), the network the committed trained weights (the stencil network, or
+with ``--variant face`` the face-state network), dt the fine time step they
+were trained with.  The plain variant takes any flux and integrator of
 `fv.fv_set_scheme` and the adaptive dt of CFL 0.5 (the fine time step is
 stable only on the 256^2 grid it was trained on).  Prints the wall-clock time per step and the rate in
 cell-updates per second.
@@ -22,7 +24,7 @@ def main(argv=None):
     ap.add_argument("--members", type=int, default=64)
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--steps", type=int, default=3)
-    ap.add_argument("--variant", choices=["auto", "fused", "two_pass", "plain"], default="fused")
+    ap.add_argument("--variant", choices=["auto", "fused", "two_pass", "plain", "face"], default="fused")
     ap.add_argument("--flux", choices=["hll", "rusanov", "lf", "roe", "hlle", "hllc"], default="hll",
                     help="numerical flux of the plain variant")
     ap.add_argument("--rk", type=int, choices=[2, 3], default=2, help="integrator of the plain variant")
@@ -33,13 +35,14 @@ def main(argv=None):
     from . import build, fv, train, workloads
 
     build.build()
-    weights = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights", "swe64_from256.npz")
-    net, meta = train.load_weights(weights)
+    wname = "face64_from256.npz" if args.variant == "face" else "swe64_from256.npz"
+    net, meta = train.load_weights(os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights", wname))
     q0 = torch.tensor(workloads.swe_random_bumps(args.n, 3, args.members), dtype=torch.float32).cuda()
     use = None if args.variant == "plain" else net
     if use is not None:
         st = fv.swe_init(q0, dt_mode="fixed", dt_fixed=meta["dt_fine"])
-        fv.fv_set_learned_variant(st, args.variant)
+        if args.variant != "face":
+            fv.fv_set_learned_variant(st, args.variant)
     else:
         st = fv.swe_init(q0, cfl=0.5)
         fv.fv_set_scheme(st, args.flux, args.rk)
