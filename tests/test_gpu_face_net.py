@@ -230,3 +230,37 @@ def test_rollout_gradients_match_oracle(fv, n, T, B):
     assert cos >= 0.9999 and rel <= 1e-2, ("dq0", cos, rel)
     cos, rel = _cos_rel(dparams.cpu().double(), g_ref)
     assert cos >= 0.999 and rel <= 2e-2, ("dparams", cos, rel)
+
+
+def test_device_gelu_matches_the_definition(fv):
+    """The GeLU of the hidden-layer epilogue against x Phi(x) in FP64, read
+    through bias-only networks: with W2 = W3 = 0 the third layer's
+    activations are BF16(GeLU(b3)) in every cell, and W4 copies channel k to
+    output k.  The BF16 roundings must agree except where the value lies
+    within the FP32 evaluation's error of a rounding boundary.  The sweep
+    stops at x = -4: further out the FP32 sum 1 + erf cancels (the epilogue
+    trades that tail, |GeLU| < 1e-4, for speed)."""
+    from oracle import face_net as ofn
+    xs = np.concatenate([np.linspace(-4.0, 6.0, 589), [0.0, 1.0, -1.0, 0.5, -0.5, 3.0, -3.0, 1e-3, -1e-3, 20.0, 7.5]])
+    xs = xs.astype(np.float32)
+    layout = ofn.FaceNetParams.from_flat(torch.zeros(ofn.n_params(), dtype=torch.float64), MEAN, STD)
+    sizes = [w.numel() + b.numel() for w, b in zip(layout.W, layout.b)]
+    off3 = sizes[0] + sizes[1] + layout.W[2].numel()           # b3
+    off4 = sum(sizes[:3])                                       # W4
+    got = []
+    for k0 in range(0, len(xs), 12):
+        chunk = xs[k0:k0 + 12]
+        flat = np.zeros(fv.FV_FACE_NET_PARAMS, dtype=np.float32)
+        flat[off3:off3 + len(chunk)] = chunk
+        for k in range(len(chunk)):
+            flat[off4 + ((k * 32 + k) * 3 + 1) * 3 + 1] = 1.0   # W4[k][k][1][1]
+        net = fv.face_net_create(flat, MEAN, STD)
+        raw = fv.face_net_forward(net, torch.ones(1, 3, 16, 128, device="cuda"), raw=True)
+        got.append(raw[0, :len(chunk), 3, 5].double().cpu().numpy())
+    got = np.concatenate(got)
+    x = torch.tensor(xs, dtype=torch.float64)
+    exact = (0.5 * x * (1.0 + torch.erf(x / np.sqrt(2.0))))
+    want = exact.to(torch.float32).to(torch.bfloat16).double().numpy()
+    ulp = np.maximum(np.abs(want), 1e-30) * 2.0 ** -7
+    assert np.all(np.abs(got - want) <= ulp), np.max(np.abs(got - want) / ulp)
+    assert np.mean(got == want) >= 0.95, np.mean(got == want)
