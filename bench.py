@@ -415,6 +415,16 @@ def learned_block(args):
     return out
 
 
+def _bf16_sustained_peak() -> float:
+    """Measured sustained BF16 tensor throughput (TFLOP/s), else the recipe's
+    fallback."""
+    pp = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pp):
+        with open(pp) as f:
+            return float(json.load(f).get("bf16_tflops_sustained", 1700.0))
+    return 1700.0
+
+
 def _plain_resolution_matching(plain, err):
     """Resolution at which the plain solver's error equals err (log-log
     interpolation between the bracketing resolutions; the largest one if err
@@ -430,7 +440,7 @@ def _plain_resolution_matching(plain, err):
 def face_state_block(args, te, std, plain):
     """The face-state network (Section 2.5.3, third approach): rollout
     throughput at 256 members x 256^2 (CNN with GeLU on tcgen05 writing the
-    12 side states, then the face-state stage kernel; two launches sets per
+    12 side states, then the face-state stage kernel; five launches per
     stage), one training iteration, and its accuracy on the same held-out
     trajectories as the stencil network."""
     import torch
@@ -473,6 +483,9 @@ def face_state_block(args, te, std, plain):
                         "cell_updates_per_s": rate, "ms_per_step": ms / K, "cnn_tflops": tflops,
                         "algorithmic": "91008 FLOP per cell-update (2 CNN passes of 45504 FLOP); "
                                        "HBM 156 B per cell-update in the stage kernels",
+                        "roofline": {"bound": "tensor", "achieved": tflops, "peak": _bf16_sustained_peak(),
+                                     "unit": "TFLOP/s", "frac": tflops / _bf16_sustained_peak(),
+                                     "peak_kind": "measured bf16 sustained"},
                         "members_flagged_unstable": health},
             "training": {"workload": "batch 64 windows, 64^2, T = 8, forward + loss + backward + Adam",
                          "ms_per_iteration": 1e3 * res.seconds / res.iters},
