@@ -21,4 +21,13 @@ stencil_net  the learned-stencil variant: CNN, coefficient normalisation,
              learned reconstruction with minmod fallback, rollout loss (2.28);
              its gradients come from reverse-mode differentiation of this FP64
              forward and are pinned by central finite differences.
+schemes      the other numerical fluxes (Lax-Friedrichs, Rusanov, Roe, HLLE,
+             HLLC) and SSP-RK3.
+bathymetry   the bed-slope source and reflecting walls (shallow water and
+             Euler).
+face_net     the face-state network (third data-driven approach): GeLU CNN,
+             Softplus depths, side states paired at faces, rollout gradients.
+sphere       shallow water on the sphere: the two-hemisphere grid and its
+             metrics, rotated fluxes, curvature correction, Coriolis and
+             tangent projection.
 """
