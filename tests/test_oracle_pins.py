@@ -310,11 +310,32 @@ def test_sod_converges_to_exact(axis):
     assert rate > 0.8 and errs[1] < 1.5e-2, (errs, rate)
 
 
+def _golden(name):
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", name)
+    out = {}
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            k, v = line.split()
+            out[k] = float(v)
+    return out
+
+
 def test_sod_star_state_textbook_values():
-    # Sod (gamma = 1.4): p* = 0.30313, u* = 0.92745 (Toro, Table 4.3)
+    """The exact Sod solution against the published star state (fixture
+    tests/golden/sod_star_toro.txt): pressure and velocity of the star
+    region, and the densities on either side of the contact sampled from the
+    exact solution (left of it: the isentrope behind the rarefaction; right:
+    the shock's Hugoniot)."""
+    ref = _golden("sod_star_toro.txt")
     ps, us = riemann.euler_star(1.0, 0.0, 1.0, 0.125, 0.0, 0.1, GAMMA)
-    assert ps == pytest.approx(0.30313, abs=1e-5)
-    assert us == pytest.approx(0.92745, abs=1e-5)
+    assert ps == pytest.approx(ref["p_star"], abs=1e-5)
+    assert us == pytest.approx(ref["u_star"], abs=1e-5)
+    xi = np.array([us - 1e-3, us + 1e-3])
+    rho, u, p = riemann.euler_sample(xi, 1.0, 0.0, 1.0, 0.125, 0.0, 0.1, GAMMA)
+    assert rho[0] == pytest.approx(ref["rho_star_left"], abs=1e-5)
+    assert rho[1] == pytest.approx(ref["rho_star_right"], abs=1e-5)
+    assert p[0] == pytest.approx(ref["p_star"], abs=1e-5) and p[1] == pytest.approx(ref["p_star"], abs=1e-5)
 
 
 @pytest.mark.parametrize("eq", [fv.SWE, fv.EULER])
