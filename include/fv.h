@@ -324,6 +324,16 @@ int stencil_net_get_params(const fv_net* n, float* params, int loc);
 int stencil_net_forward(const fv_net* n, const float* q, int B, int ny, int nx, float* coeffs,
                         int raw, void* stream);
 
+/* Vector-Jacobian product of stencil_net_forward at q (the forward is
+ * recomputed): dcoeffs (device [B][36][ny][nx] FP32) is the cotangent of the
+ * normalised coefficients; the parameter gradient is ADDED to dparams
+ * (device [FV_NET_PARAMS]) and, if dq != NULL, the cotangent of q is ADDED
+ * to dq (device [B][3][ny][nx]).  Cotangents between layers are BF16
+ * (tensor-core operands), weight gradients FP32 with a deterministic
+ * reduction.  Grid rules, stream and errors as stencil_net_forward. */
+int stencil_net_backward(fv_net* n, const float* q, int B, int ny, int nx, const float* dcoeffs,
+                         float* dq, float* dparams, void* stream);
+
 /* ---------------------------------------------------------------------------
  * Face-state network (Section 2.5.3, third approach; Section 5.3)
  *
@@ -359,6 +369,13 @@ int face_net_create(const float* params, const float* norm, fv_net** out);
  * stencil network. */
 int face_net_forward(const fv_net* n, const float* q, int B, int ny, int nx, float* sides, int raw,
                      void* stream);
+
+/* Vector-Jacobian product of face_net_forward at q: dsides (device
+ * [B][12][ny][nx]) is the cotangent of the side states; the gradient is
+ * ADDED to dparams (device [FV_FACE_NET_PARAMS]) and, if dq != NULL, to dq.
+ * As stencil_net_backward otherwise. */
+int face_net_backward(fv_net* n, const float* q, int B, int ny, int nx, const float* dsides, float* dq,
+                      float* dparams, void* stream);
 
 /* Kind of a network: 0 = stencil (fourth approach), 1 = face-state (third);
  * -1 for NULL.  Parameter count of its kind (0 for NULL). */

@@ -1027,8 +1027,21 @@ void net_free(fv_net* n) {
   cudaFree(n->adam_m);
   cudaFree(n->adam_v);
   snk::acts_free(n->ws);
+  snk::backward_free(n->bw);
+  cudaFree(n->scratch);
   if (n->stream) cudaStreamDestroy(n->stream);
   delete n;
+}
+
+// Scratch of at least `floats` floats for the recomputed forward outputs.
+cudaError_t scratch_reserve(fv_net* n, long long floats) {
+  if (n->scratch_floats >= floats) return cudaSuccess;
+  cudaFree(n->scratch);
+  n->scratch = nullptr;
+  n->scratch_floats = 0;
+  cudaError_t e = cudaMalloc(&n->scratch, sizeof(float) * floats);
+  if (e == cudaSuccess) n->scratch_floats = floats;
+  return e;
 }
 
 int net_check_err(const fv_net* n) {
@@ -1148,4 +1161,45 @@ extern "C" int face_net_forward(const fv_net* cn, const float* q, int B, int ny,
   FV_CUDA_TRY(snk::forward_faces(n->n, q, B, ny, nx, n->ws, raw ? nullptr : sides, raw ? sides : nullptr, s));
   FV_CUDA_TRY(cudaStreamSynchronize(s));
   return net_check_err(n);
+}
+
+// Vector-Jacobian products of the two forwards: the forward is recomputed at
+// q (activations into the network's workspace), then the hand-written
+// backward of snk::backward / snk::backward_faces runs.
+namespace {
+
+int net_backward(fv_net* n, int kind, const float* q, int B, int ny, int nx, const float* dout, float* dq,
+                 float* dparams, void* stream) {
+  if (!n || !q || !dout || !dparams) return fvh::fail(FV_EINVAL, "null argument");
+  if (n->n.kind != kind) return fvh::fail(FV_EINVAL, "network kind does not match the call");
+  if (B < 1 || ny < 1 || !snk::grid_supported(nx) || ((long long)nx * ny) % snk::TILE != 0)
+    return fvh::fail(FV_EINVAL, "unsupported grid: nx must be 8, 16, 32, 64 or a multiple of 128, "
+                                "and nx*ny a multiple of 128");
+  cudaStream_t s = stream ? (cudaStream_t)stream : n->stream;
+  const long long cells = (long long)B * nx * ny;
+  const bool face = kind == snk::NET_FACE;
+  FV_CUDA_TRY(snk::acts_reserve(n->ws, cells, face));
+  FV_CUDA_TRY(snk::backward_reserve(n->bw, cells, snk::backward_partials_floats(B, ny, nx)));
+  FV_CUDA_TRY(scratch_reserve(n, cells * (face ? snk::N_OUT_FACE : snk::N_OUT)));
+  if (face) {
+    FV_CUDA_TRY(snk::forward_faces(n->n, q, B, ny, nx, n->ws, n->scratch, nullptr, s));
+    FV_CUDA_TRY(snk::backward_faces(n->n, q, B, ny, nx, n->ws, n->scratch, dout, dq, dparams, 1.f, n->bw, s));
+  } else {
+    FV_CUDA_TRY(snk::forward(n->n, q, B, ny, nx, n->ws, n->scratch, nullptr, s));
+    FV_CUDA_TRY(snk::backward(n->n, q, B, ny, nx, n->ws, dout, dq, dparams, 1.f, n->bw, s));
+  }
+  FV_CUDA_TRY(cudaStreamSynchronize(s));
+  return net_check_err(n);
+}
+
+}  // namespace
+
+extern "C" int stencil_net_backward(fv_net* n, const float* q, int B, int ny, int nx, const float* dcoeffs,
+                                    float* dq, float* dparams, void* stream) {
+  return net_backward(n, snk::NET_STENCIL, q, B, ny, nx, dcoeffs, dq, dparams, stream);
+}
+
+extern "C" int face_net_backward(fv_net* n, const float* q, int B, int ny, int nx, const float* dsides,
+                                 float* dq, float* dparams, void* stream) {
+  return net_backward(n, snk::NET_FACE, q, B, ny, nx, dsides, dq, dparams, stream);
 }

@@ -127,7 +127,10 @@ cudaError_t backward_faces(const Net& net, const float* q, int B, int ny, int nx
 
 struct fv_net {
   snk::Net n;
-  snk::Acts ws;                 // workspace of stencil_net_forward
+  snk::Acts ws;                 // workspace of stencil_net_forward / _backward
+  snk::Grads bw;                // workspace of stencil_net_backward / face_net_backward
+  float* scratch = nullptr;     // forward outputs recomputed by the backward calls
+  long long scratch_floats = 0;
   float* adam_m = nullptr;      // Adam moments (stencil_net_adam_step)
   float* adam_v = nullptr;
   cudaStream_t stream = nullptr;

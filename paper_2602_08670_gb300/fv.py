@@ -83,6 +83,8 @@ _SIGS = {
     "stencil_net_get_params": [c_void_p, c_void_p, c_int],
     "stencil_net_forward": [c_void_p, c_void_p, c_int, c_int, c_int, c_void_p, c_int, c_void_p],
     "face_net_create": [c_void_p, c_void_p, ctypes.POINTER(c_void_p)],
+    "stencil_net_backward": [c_void_p, c_void_p, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p],
+    "face_net_backward": [c_void_p, c_void_p, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p],
     "face_net_forward": [c_void_p, c_void_p, c_int, c_int, c_int, c_void_p, c_int, c_void_p],
     "fv_net_kind": [c_void_p],
     "fv_net_num_params": [c_void_p],
@@ -411,6 +413,22 @@ def face_net_forward(net: Net, q: torch.Tensor, raw: bool = False) -> torch.Tens
     _check(lib().face_net_forward(net.handle, c_void_p(q.data_ptr()), B, ny, nx,
                                   c_void_p(out.data_ptr()), int(raw), c_void_p(_torch_stream())))
     return out
+
+
+def net_backward(net: Net, q: torch.Tensor, dout: torch.Tensor, want_dq: bool = True):
+    """Vector-Jacobian product of the network's forward at q: dout is the
+    cotangent of its output ([B][36][ny][nx] coefficients of a stencil
+    network, [B][12][ny][nx] side states of a face-state network).  Returns
+    (dparams [n_params], dq [B][3][ny][nx] or None) on the GPU."""
+    q = q.contiguous()
+    dout = dout.contiguous()
+    B, _, ny, nx = q.shape
+    dparams = torch.zeros(net.n_params, dtype=torch.float32, device=q.device)
+    dq = torch.zeros_like(q) if want_dq else None
+    fn = lib().face_net_backward if net.kind == "face" else lib().stencil_net_backward
+    _check(fn(net.handle, _dev(q), B, ny, nx, _dev(dout), _dev(dq) if want_dq else None, _dev(dparams),
+              c_void_p(_torch_stream())))
+    return dparams, dq
 
 
 FLUXES = {"hll": 0, "rusanov": 1, "lf": 2, "roe": 3, "hlle": 4, "hllc": 5}

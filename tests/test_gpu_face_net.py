@@ -264,3 +264,25 @@ def test_device_gelu_matches_the_definition(fv):
     ulp = np.maximum(np.abs(want), 1e-30) * 2.0 ** -7
     assert np.all(np.abs(got - want) <= ulp), np.max(np.abs(got - want) / ulp)
     assert np.mean(got == want) >= 0.95, np.mean(got == want)
+
+
+def test_face_net_backward_matches_oracle(fv):
+    """face_net_backward (the network's VJP at q) against the oracle's FP64
+    reverse mode through the BF16-mirrored forward and the side-state
+    epilogue."""
+    p = rand_params(9, last_scale=0.3, h_bias=1.05)
+    net = gpu_net(fv, p)
+    q0 = W.as_f32_exact(W.random_smooth_swe(128, seed=6, members=2, vel=0.2)[:, :, :16, :])
+    g = torch.Generator().manual_seed(3)
+    ds = torch.randn(2, 12, 16, 128, generator=g, dtype=torch.float64)
+    flat = p.flat().detach().clone().requires_grad_(True)
+    pp = ofn.FaceNetParams.from_flat(flat, p.mean, p.std)
+    q = torch.tensor(q0).requires_grad_(True)
+    sides = ofn.side_states(ofn.net_raw(q, pp, round_bf16=True), pp).reshape(2, 12, 16, 128)
+    (sides * ds).sum().backward()
+    dparams, dq = fv.net_backward(net, f32(q0).cuda(), f32(ds).cuda())
+    for got, ref, name in ((dparams, flat.grad, "dparams"), (dq, q.grad, "dq")):
+        a, b = got.double().cpu().reshape(-1), ref.reshape(-1)
+        cos = float(a @ b / (a.norm() * b.norm()))
+        rel = float((a - b).norm() / b.norm())
+        assert cos >= 0.999 and rel <= 2e-2, (name, cos, rel)

@@ -205,3 +205,30 @@ def test_rollout_gradients_match_oracle(fv, n, T, B, zero):
         nz = torch.nonzero(g_ref).reshape(-1)
         lo = 29796 - 36
         assert int(nz.min()) >= lo   # only b4
+
+
+def test_stencil_net_backward_matches_oracle(fv):
+    """stencil_net_backward (the network's VJP at q) against the oracle's FP64
+    reverse mode through the BF16-mirrored forward and the normalisation."""
+    p = rand_params(8, last_scale=0.3)
+    net = gpu_net(fv, p)
+    q0 = W.as_f32_exact(W.random_smooth_swe(128, seed=5, members=2, vel=0.2)[:, :, :16, :])
+    g = torch.Generator().manual_seed(2)
+    dw = torch.randn(2, 36, 16, 128, generator=g, dtype=torch.float64)
+    flat = p.flat().clone().requires_grad_(True)
+    W_, b_, off = [], [], 0
+    for co, ci in osn.LAYER_SHAPES:
+        n = co * ci * 9
+        W_.append(flat[off:off + n].reshape(co, ci, 3, 3))
+        off += n
+        b_.append(flat[off:off + co])
+        off += co
+    q = torch.tensor(q0).requires_grad_(True)
+    w = osn.normalise(osn.net_raw(q, osn.NetParams(W_, b_, p.mean, p.std), round_bf16=True))
+    (w * dw).sum().backward()
+    dparams, dq = fv.net_backward(net, f32(q0).cuda(), f32(dw).cuda())
+    for got, ref, name in ((dparams, flat.grad, "dparams"), (dq, q.grad, "dq")):
+        a, b = got.double().cpu().reshape(-1), ref.reshape(-1)
+        cos = float(a @ b / (a.norm() * b.norm()))
+        rel = float((a - b).norm() / b.norm())
+        assert cos >= 0.999 and rel <= 2e-2, (name, cos, rel)
