@@ -1,7 +1,8 @@
 """Training on the GPU by the library's own forward and backward kernels:
-coarse graining against the oracle, and a short training run whose network
+coarse graining against the oracle, a short training run whose network
 beats the plain (MUSCL-minmod) solver at the same coarse resolution against
-the 4x-resolution reference on held-out initial states."""
+the 4x-resolution reference on held-out initial states, and that reference
+itself against the FP64 oracle's 4x-resolution run."""
 import numpy as np
 import pytest
 import torch
@@ -42,3 +43,19 @@ def test_training_beats_plain_solver(mods):
     # error of the state scaled per variable (the loss normalisation) after
     # 32 coarse steps against the coarse-grained 256^2 run
     assert ev["learned"] < 0.7 * ev["plain"], ev
+
+
+def test_reference_run_matches_the_oracle(mods):
+    """The 4x-resolution reference that judges the learned error (the GPU
+    plain run at 256^2, coarse-grained to 64^2) against the FP64 oracle's
+    own 256^2 run of the same members, fixed dt, 16 coarse steps."""
+    from helpers import rel_errors
+    fv, TR = mods
+    te = TR.generate(256, 4, members=2, seed=2, coarse_steps=16)
+    q0 = torch.tensor(W.as_f32_exact(W.swe_random_bumps(256, 2, 2)))
+    qr, _, _, _ = ofv.run(q0, ofv.SWE, 16 * 4, dt_mode=ofv.DT_FIXED, dt_fixed=te.dt_fine)
+    ref = ofv.coarsen(qr, 4)
+    got = te.coarse[16].double().cpu()
+    for c, (e2, ei) in enumerate(rel_errors(got, ref)):
+        l2, li = (1e-5, 1e-4) if c == 0 else (1e-4, 1e-3)
+        assert e2 <= l2 and ei <= li, (c, e2, ei)
