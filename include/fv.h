@@ -324,7 +324,12 @@ int stencil_net_get_params(const fv_net* n, float* params, int loc);
 int stencil_net_forward(const fv_net* n, const float* q, int B, int ny, int nx, float* coeffs,
                         int raw, void* stream);
 
-/* Vector-Jacobian product of stencil_net_forward at q (the forward is
+/* stencil_net_forward / _backward and face_net_forward / _backward use a
+ * workspace held by the network: calls on one network from several threads
+ * must be serialised by the caller.  Steps (fv_step, fv_rollout, the server)
+ * only read a network's parameters and keep their workspaces in the state.
+ *
+ * Vector-Jacobian product of stencil_net_forward at q (the forward is
  * recomputed): dcoeffs (device [B][36][ny][nx] FP32) is the cotangent of the
  * normalised coefficients; the parameter gradient is ADDED to dparams
  * (device [FV_NET_PARAMS]) and, if dq != NULL, the cotangent of q is ADDED
