@@ -288,17 +288,6 @@ def run_gpu(args):
         "gpu_launches": 4 * K,
         "clocks": clk,
     }
-    if not args.no_learned:
-        line["learned"] = learned_block(args)
-        plain_swe = N_SWE * N_SWE * K / (swe_ms * 1e-3)
-        line["learned"]["accuracy_matched"]["plain_rate"] = plain_swe
-        line["learned"]["accuracy_matched"]["learned_wins"] = \
-            line["learned"]["accuracy_matched"]["learned_rate_times_r3"] > plain_swe
-    if not args.no_serving:
-        line["serving"] = serving_block(args)
-    if not args.no_schemes:
-        line["schemes"] = schemes_block(args)
-        line["sphere"] = sphere_block(args)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         # the bench's own grids (SWE 4096^2 + Euler 2048^2), four steps: about
         # ten seconds of FP64 work on the host cores
@@ -306,6 +295,15 @@ def run_gpu(args):
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
                                 "sample": f"4 SSP-RK2 steps of SWE bump {N_SWE}^2 + Euler KH {N_EULER}^2, "
                                           f"FP64 oracle, {secs:.1f} s"}
+    if not args.no_schemes:
+        line["schemes"] = schemes_block(args)
+        line["sphere"] = sphere_block(args)
+    if not args.no_learned:
+        line["learned"] = learned_block(args)
+    if not args.no_serving:
+        line["serving"] = serving_block(args)
+    # compact summary of the learned and serving results as the line's last key
+    line["summary"] = summary(line)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -314,12 +312,15 @@ def run_gpu(args):
 
 
 def learned_block(args):
-    """The learned-stencil path: batched learned rollout throughput (256
-    members x 256^2, BF16 tensor-core CNN + FP32 flux, fixed dt, graph-captured
-    rollout), one training iteration (batch 64, 64^2, T = 8, forward + loss +
-    backward + Adam), and the accuracy-matched comparison with the plain
-    solver on held-out 64^2 trajectories coarse-grained from 256^2."""
-    import numpy as np
+    """The learned-stencil path.  `accuracy_matched`: each trained network's
+    batched rollout on 256 members x 256^2 (fused tcgen05 kernel for the
+    stencil network, CNN + face-state stage kernels for the face-state
+    network), timed, with its state at every horizon compared against the
+    plain solver at 1024^2 coarse-grained 4x; the plain solver at 256^2 ..
+    768^2 gives the resolution N_eq of equal error and is timed there (the
+    plain rate at matched accuracy).  Also: the CNN's tensor-pipe roofline
+    from that rollout, the same rollout through the two-pass path, and one
+    training iteration of each network (batch 64, 64^2, T = 8)."""
     import torch
 
     from paper_2602_08670_gb300 import fv
@@ -328,90 +329,69 @@ def learned_block(args):
 
     out = {}
     net, meta = TR.load_weights(WEIGHTS)
-    # -- batched learned rollout (C4 shape)
-    members, n = 256, 256
-    q0 = torch.tensor(W.swe_random_bumps(n, 3, members), dtype=torch.float32).cuda()
-    bs = torch.cuda.Stream()
-    dt = meta["dt_fine"]                       # stable at 256^2 (CFL 0.4)
-    with torch.cuda.stream(bs):
-        st = fv.swe_init(q0, dt_mode="fixed", dt_fixed=dt)
-    fv.fv_enqueue_steps(st, 2, net=net)
-    fv.fv_sync(st)
-    K = args.learned_steps
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record(bs)
-    fv.fv_enqueue_steps(st, K, net=net)
-    e1.record(bs)
-    fv.fv_sync(st)
-    ms = e0.elapsed_time(e1)
-    learned_rate = members * n * n * K / (ms * 1e-3)
-    # 59 328 FLOP (two per multiply-add) per cell and CNN pass, two passes per step
-    cnn_tflops = 59328 * 2 * members * n * n * K / (ms * 1e-3) / 1e12
-    peaks = {}
-    pp = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(pp):
-        with open(pp) as f:
-            peaks = json.load(f)
-    bf16_peak = peaks.get("bf16_tflops_sustained", 1700.0)
-    out["rollout"] = {"workload": f"{members} members x {n}^2 SWE, learned, fixed dt, {K} steps",
+    fnet, _ = TR.load_weights(FACE_WEIGHTS)
+    tr = TR.generate(256, 4, members=64, seed=0, coarse_steps=32)
+    _, std = TR.data_stats(tr)
+    horizons = tuple(int(k) for k in args.learned_horizons.split(","))
+    m = TR.matched_accuracy({"stencil": net, "face_state": fnet}, meta["dt_coarse"], std, n=256, tiles=4,
+                            members=args.learned_members, seed=3, horizons=horizons)
+    out["accuracy_matched"] = m
+    bf16_peak = _bf16_sustained_peak()
+    members, n = args.learned_members, 256
+    rate = m["stencil"]["cell_updates_per_s"]
+    tflops = 118656 * rate / 1e12
+    out["rollout"] = {"workload": f"{members} members x {n}^2 SWE, stencil network, fixed dt, "
+                                  f"{horizons[-1]} steps (the accuracy_matched run)",
                       "kernel": "learned_fused_kernel (CNN on tcgen05 + learned faces + HLL + RK, "
                                 "one launch per stage)",
-                      "cell_updates_per_s": learned_rate, "ms_per_step": ms / K,
-                      "cnn_tflops": cnn_tflops,
-                      "roofline": {"bound": "tensor", "achieved": cnn_tflops, "peak": bf16_peak,
-                                   "unit": "TFLOP/s", "frac": cnn_tflops / bf16_peak,
+                      "cell_updates_per_s": rate, "cnn_tflops": tflops,
+                      "roofline": {"bound": "tensor", "achieved": tflops, "peak": bf16_peak,
+                                   "unit": "TFLOP/s", "frac": tflops / bf16_peak,
                                    "peak_kind": "measured bf16 sustained",
                                    "algorithmic": "118656 FLOP per cell-update (2 CNN passes of "
                                                   "59328 FLOP)"},
-                      "hbm_gbs": 60 * learned_rate / 1e9}
-    # the same rollout through the two-pass path (CNN coefficients via HBM)
+                      "hbm_gbs": 60 * rate / 1e9}
+    frate = m["face_state"]["cell_updates_per_s"]
+    out["face_state_rollout"] = {"kernel": "conv_kernel (GeLU / side-state epilogues) + stage_face_kernel",
+                                 "cell_updates_per_s": frate, "cnn_tflops": 91008 * frate / 1e12,
+                                 "roofline": {"bound": "tensor", "achieved": 91008 * frate / 1e12,
+                                              "peak": bf16_peak, "unit": "TFLOP/s",
+                                              "frac": 91008 * frate / 1e12 / bf16_peak,
+                                              "peak_kind": "measured bf16 sustained"},
+                                 "algorithmic": "91008 FLOP per cell-update (2 CNN passes of 45504 FLOP)"}
+    # the stencil network's rollout through the two-pass path (CNN coefficients via HBM)
+    q0 = torch.tensor(W.swe_random_bumps_tiled(n, 3, 32, 4), dtype=torch.float32).cuda()
+    bs = torch.cuda.Stream()
+    with torch.cuda.stream(bs):
+        st = fv.swe_init(q0, dt_mode="fixed", dt_fixed=meta["dt_coarse"] * 64 / n)
     fv.fv_set_learned_variant(st, "two_pass")
     fv.fv_enqueue_steps(st, 2, net=net)
     fv.fv_sync(st)
-    K2 = max(2, K // 4)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(bs)
-    fv.fv_enqueue_steps(st, K2, net=net)
+    fv.fv_enqueue_steps(st, 10, net=net)
     e1.record(bs)
     fv.fv_sync(st)
-    ms2 = e0.elapsed_time(e1)
-    out["rollout"]["two_pass_cell_updates_per_s"] = members * n * n * K2 / (ms2 * 1e-3)
+    out["rollout"]["two_pass_cell_updates_per_s"] = 32 * n * n * 10 / (e0.elapsed_time(e1) * 1e-3)
     del st
-    # -- one training iteration (C3 shape)
-    tr = TR.generate(256, 4, members=64, seed=0, coarse_steps=32)
-    _, std = TR.data_stats(tr)
+    # one training iteration of each network (C3 shape)
     tnet = fv.stencil_net_create(TR.init_params(0), *TR.input_scale(tr))
-    res = TR.train(tr, iters=3, batch=64, T=8, net=tnet)       # warm-up
+    TR.train(tr, iters=3, batch=64, T=8, net=tnet)       # warm-up
     res = TR.train(tr, iters=10, batch=64, T=8, net=tnet)
+    it_ms = 1e3 * res.seconds / res.iters
+    # forward 2 passes x 59328 FLOP per cell and stage-1/2 ... per step; backward ~2x forward
+    fwd = 64 * 64 * 64 * 16 * 59328
     out["training"] = {"workload": "batch 64 windows, 64^2, T = 8 steps (16 stages), forward + "
                                    "Eq. 2.28 loss + backward + Adam",
-                       "ms_per_iteration": 1e3 * res.seconds / res.iters}
-    # -- accuracy-matched rate on held-out trajectories (seed 2)
-    te = TR.generate(256, 4, members=32, seed=2, coarse_steps=64, dt_fine=meta["dt_fine"])
-    ev = TR.evaluate(net, te, 64, std)
-    plain = {64: ev["plain"]}
-    for nn in (128, 192):
-        plain[nn] = TR.plain_error_at(nn, te, 64, std)
-    el = ev["learned"]
-    # resolution at which the plain solver reaches the learned error
-    # (log-log interpolation between the bracketing resolutions)
-    ns = sorted(plain)
-    n_eq = None
-    for a, b in zip(ns, ns[1:]):
-        if plain[a] >= el >= plain[b]:
-            t = (math.log(plain[a]) - math.log(el)) / (math.log(plain[a]) - math.log(plain[b]))
-            n_eq = math.exp(math.log(a) + t * (math.log(b) - math.log(a)))
-    if n_eq is None and el < plain[ns[-1]]:
-        n_eq = float(ns[-1])                   # at least this resolution
-    r = (n_eq or 64.0) / 64.0
-    out["accuracy"] = {"metric": "RMS of the per-variable-scaled state error vs the 4x-resolution "
-                                 "(256^2) run coarse-grained to 64^2, after 64 coarse steps, 32 held-out members",
-                       "learned_64": el, "plain": {str(k): v for k, v in plain.items()},
-                       "plain_resolution_matching_learned": n_eq,
-                       "note": "plain needs (N_eq/64)^2 more cells and N_eq/64 more steps"}
-    out["accuracy_matched"] = {"learned_rate_times_r3": learned_rate * r ** 3, "r": r}
-    out["face_state"] = face_state_block(args, te, std, plain)
+                       "ms_per_iteration": it_ms,
+                       "cnn_flop_per_iteration": 3 * fwd,
+                       "cnn_tflops": 3 * fwd / (it_ms * 1e-3) / 1e12}
+    fnet_t = fv.face_net_create(TR.init_params(0, kind="face", depth=float(TR.data_stats(tr)[0][0])),
+                                *TR.input_scale(tr))
+    TR.train(tr, iters=3, batch=64, T=8, net=fnet_t)
+    res = TR.train(tr, iters=10, batch=64, T=8, net=fnet_t)
+    out["face_state_training"] = {"ms_per_iteration": 1e3 * res.seconds / res.iters}
     return out
 
 
@@ -425,73 +405,33 @@ def _bf16_sustained_peak() -> float:
     return 1700.0
 
 
-def _plain_resolution_matching(plain, err):
-    """Resolution at which the plain solver's error equals err (log-log
-    interpolation between the bracketing resolutions; the largest one if err
-    is below all of them)."""
-    ns = sorted(plain)
-    for a, b in zip(ns, ns[1:]):
-        if plain[a] >= err >= plain[b]:
-            t = (math.log(plain[a]) - math.log(err)) / (math.log(plain[a]) - math.log(plain[b]))
-            return math.exp(math.log(a) + t * (math.log(b) - math.log(a)))
-    return float(ns[-1]) if err < plain[ns[-1]] else None
+def _sig(x, k=3):
+    """x rounded to k significant digits (None and bools unchanged)."""
+    if x is None or isinstance(x, bool) or not isinstance(x, (int, float)):
+        return x
+    return float(f"{x:.{k}g}")
 
 
-def face_state_block(args, te, std, plain):
-    """The face-state network (Section 2.5.3, third approach): rollout
-    throughput at 256 members x 256^2 (CNN with GeLU on tcgen05 writing the
-    12 side states, then the face-state stage kernel; five launches per
-    stage), one training iteration, and its accuracy on the same held-out
-    trajectories as the stencil network."""
-    import torch
-
-    from paper_2602_08670_gb300 import fv
-    from paper_2602_08670_gb300 import train as TR
-    from paper_2602_08670_gb300 import workloads as W
-
-    net, meta = TR.load_weights(FACE_WEIGHTS)
-    members, n = 256, 256
-    q0 = torch.tensor(W.swe_random_bumps(n, 3, members), dtype=torch.float32).cuda()
-    bs = torch.cuda.Stream()
-    with torch.cuda.stream(bs):
-        st = fv.swe_init(q0, dt_mode="fixed", dt_fixed=meta["dt_fine"])
-    fv.fv_enqueue_steps(st, 2, net=net)
-    fv.fv_sync(st)
-    K = args.learned_steps
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record(bs)
-    fv.fv_enqueue_steps(st, K, net=net)
-    e1.record(bs)
-    fv.fv_sync(st)
-    ms = e0.elapsed_time(e1)
-    rate = members * n * n * K / (ms * 1e-3)
-    health = int((fv.fv_health(st) != 0).sum())
-    del st
-    # 45 504 FLOP (two per multiply-add) per cell and CNN pass, two passes per step
-    tflops = 45504 * 2 * rate / 1e12
-    tr = TR.generate(256, 4, members=64, seed=0, coarse_steps=32)
-    tnet = fv.face_net_create(TR.init_params(0, kind="face", depth=float(TR.data_stats(tr)[0][0])),
-                              *TR.input_scale(tr))
-    TR.train(tr, iters=3, batch=64, T=8, net=tnet)
-    res = TR.train(tr, iters=10, batch=64, T=8, net=tnet)
-    el = TR.evaluate(net, te, 64, std)["learned"]
-    n_eq = _plain_resolution_matching(plain, el)
-    r = (n_eq or 64.0) / 64.0
-    return {"rollout": {"workload": f"{members} members x {n}^2 SWE, face-state network, fixed dt, {K} steps",
-                        "kernel": "conv_kernel (GeLU / side-state epilogues) + stage_face_kernel",
-                        "cell_updates_per_s": rate, "ms_per_step": ms / K, "cnn_tflops": tflops,
-                        "algorithmic": "91008 FLOP per cell-update (2 CNN passes of 45504 FLOP); "
-                                       "HBM 156 B per cell-update in the stage kernels",
-                        "roofline": {"bound": "tensor", "achieved": tflops, "peak": _bf16_sustained_peak(),
-                                     "unit": "TFLOP/s", "frac": tflops / _bf16_sustained_peak(),
-                                     "peak_kind": "measured bf16 sustained"},
-                        "members_flagged_unstable": health},
-            "training": {"workload": "batch 64 windows, 64^2, T = 8, forward + loss + backward + Adam",
-                         "ms_per_iteration": 1e3 * res.seconds / res.iters},
-            "accuracy": {"learned_64": el, "plain_resolution_matching_learned": n_eq,
-                         "note": "same metric and held-out trajectories as the stencil network"},
-            "accuracy_matched": {"learned_rate_times_r3": rate * r ** 3, "r": r}}
+def summary(line) -> dict:
+    """The learned-vs-plain accuracy-matched numbers and the serving
+    latencies, compact, for the end of the JSON line."""
+    out = {"plain_cell_updates_per_s": _sig(line["value"])}
+    lm = line.get("learned", {}).get("accuracy_matched")
+    if lm:
+        for name in ("stencil", "face_state"):
+            a = lm[name]["accuracy_matched"]
+            out[name] = {"horizon": a["horizon"], "learned_rate": _sig(a["learned_rate"]),
+                         "err": _sig(a["learned_error"]), "plain_err_same_n": _sig(a["plain_error_same_n"]),
+                         "n_eq": _sig(a["n_eq"]), "matched_rate": _sig(a.get("learned_rate_times_r3")),
+                         "plain_rate_at_n_eq": _sig(a.get("plain_rate_at_n_eq")),
+                         "learned_wins": a["learned_wins"]}
+    sv = line.get("serving")
+    if sv:
+        out["serving"] = {"capacity_cell_updates_per_s": _sig(sv["capacity"]["throughput_cell_updates_per_s"]),
+                          "p50_p99_s": {str(d["rate_fraction_of_capacity"]):
+                                        [_sig(d["p50_latency_s"]), _sig(d["p99_latency_s"]), d["requests"]]
+                                        for d in sv["load"]}}
+    return out
 
 
 def schemes_block(args):
@@ -633,15 +573,16 @@ def serving_block(args):
     base = W.serving_requests(args.serve_requests, 1.0, seed=42, sizes=(64, 128, 256, 512),
                               horizon=(100, 1000))
     server = fv.fv_server_create(64 << 30, 16, net)
+    states = serve.initial_states(base)
     closed = serve.with_arrivals(base, 1e9, seed=42)
-    lat, span, fail = serve.run_load(server, closed)
+    lat, span, fail = serve.run_load(server, closed, states)
     cap = serve.summarize(closed, lat, span, fail)
     out = {"workload": "requests: 50 % learned SWE, 25 % plain SWE, 25 % plain Euler; grids "
                        "{64,128,256,512}^2; horizons U[100,1000]; seed 42; budget 64 GB, 16 slots",
            "capacity": cap, "load": []}
     for frac in (0.5, 0.9):
         reqs = serve.with_arrivals(base, frac * cap["requests_per_s"], seed=int(frac * 100))
-        lat, span, fail = serve.run_load(server, reqs)
+        lat, span, fail = serve.run_load(server, reqs, states)
         d = serve.summarize(reqs, lat, span, fail)
         d["rate_fraction_of_capacity"] = frac
         out["load"].append(d)
@@ -658,11 +599,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end run")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-path measurements")
-    ap.add_argument("--learned-steps", type=int, default=20)
+    ap.add_argument("--learned-horizons", default="64,256,1000,2000",
+                    help="coarse steps at which the learned rollout is compared with the reference")
+    ap.add_argument("--learned-members", type=int, default=256)
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurements")
     ap.add_argument("--no-schemes", action="store_true",
                     help="skip the other fluxes / SSP-RK3 measurements")
-    ap.add_argument("--serve-requests", type=int, default=48)
+    ap.add_argument("--serve-requests", type=int, default=128)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

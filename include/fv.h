@@ -281,7 +281,11 @@ int fv_set_learned_hmin(fv_state* s, double hmin_frac);
  * sums: [batch][C+1] at sums_loc; FV_HOST returns after the result is
  * copied, FV_DEVICE only enqueues on `stream` (cudaStream_t, NULL = default
  * stream).  The first call on a device looks up the scratch address with
- * that device current; make it before any stream capture.  All calls share
+ * that device current; make it before any stream capture.  That first call
+ * may also be the one that loads the library's device code on the device
+ * (CUDA loads modules lazily by default), which is when the fixed scratch is
+ * reserved: a caller whose running phase must not allocate makes one warm-up
+ * call before entering it.  All calls share
  * the scratch, so calls that overlap on the GPU (other streams, other host
  * threads) race; every slot a call reads is written by that call first. */
 int fv_diagnostics_noalloc(const float* q, int eq, int batch, int ny, int nx, double lx, double ly,

@@ -415,16 +415,22 @@ def face_net_forward(net: Net, q: torch.Tensor, raw: bool = False) -> torch.Tens
     return out
 
 
-def net_backward(net: Net, q: torch.Tensor, dout: torch.Tensor, want_dq: bool = True):
+def net_backward(net: Net, q: torch.Tensor, dout: torch.Tensor, want_dq: bool = True,
+                 dparams: torch.Tensor | None = None, dq: torch.Tensor | None = None):
     """Vector-Jacobian product of the network's forward at q: dout is the
     cotangent of its output ([B][36][ny][nx] coefficients of a stencil
-    network, [B][12][ny][nx] side states of a face-state network).  Returns
-    (dparams [n_params], dq [B][3][ny][nx] or None) on the GPU."""
+    network, [B][12][ny][nx] side states of a face-state network).  The
+    gradients are added to ``dparams`` [n_params] and ``dq`` [B][3][ny][nx]
+    (zero-filled when not given); returns (dparams, dq or None) on the GPU."""
     q = q.contiguous()
     dout = dout.contiguous()
     B, _, ny, nx = q.shape
-    dparams = torch.zeros(net.n_params, dtype=torch.float32, device=q.device)
-    dq = torch.zeros_like(q) if want_dq else None
+    if dparams is None:
+        dparams = torch.zeros(net.n_params, dtype=torch.float32, device=q.device)
+    if want_dq and dq is None:
+        dq = torch.zeros_like(q)
+    if not want_dq:
+        dq = None
     fn = lib().face_net_backward if net.kind == "face" else lib().stencil_net_backward
     _check(fn(net.handle, _dev(q), B, ny, nx, _dev(dout), _dev(dq) if want_dq else None, _dev(dparams),
               c_void_p(_torch_stream())))
@@ -487,6 +493,7 @@ class Tape:
         self.net = net
         self.shape = tuple(shape)   # (B, 3, ny, nx)
         self.T = T
+        self.recorded = 0           # forward passes recorded so far
 
     def __del__(self):
         if getattr(self, "handle", None) and self.handle.value and _lib is not None:
@@ -510,6 +517,7 @@ def _dev(t: torch.Tensor) -> c_void_p:
 def fv_tape_forward(tape: Tape, q0: torch.Tensor, want_snaps: bool = True):
     torch.cuda.current_stream().synchronize()
     snaps = torch.empty((tape.T,) + tape.shape, dtype=torch.float32, device="cuda") if want_snaps else None
+    tape.recorded += 1
     _check(lib().fv_tape_forward(tape.handle, _dev(q0.contiguous()), _dev(snaps) if want_snaps else None))
     return snaps
 
@@ -530,6 +538,40 @@ def fv_tape_backward(tape: Tape, dparams: torch.Tensor, dsnaps: torch.Tensor | N
     _check(lib().fv_tape_backward(tape.handle, _dev(dsnaps.contiguous()) if dsnaps is not None else None,
                                   _dev(dparams), _dev(dq0) if want_dq0 else None))
     return dq0
+
+
+class TapeRollout(torch.autograd.Function):
+    """The learned rollout as a differentiable torch function:
+    (params, q0) -> snaps [T][B][3][ny][nx], the states after steps 1..T.
+
+    forward sets the network's parameters and records the tape
+    (fv_tape_forward); backward is the library's hand-written adjoint
+    (fv_tape_backward) with the incoming cotangent of the snapshots.  A tape
+    holds one recorded window, so a backward must follow its own forward
+    before the tape records another one (checked)."""
+
+    @staticmethod
+    def forward(ctx, params, q0, tape):
+        stencil_net_set_params(tape.net, params.detach())
+        snaps = fv_tape_forward(tape, q0.detach().contiguous())
+        ctx.tape = tape
+        ctx.generation = tape.recorded
+        return snaps
+
+    @staticmethod
+    def backward(ctx, dsnaps):
+        tape = ctx.tape
+        if tape.recorded != ctx.generation:
+            raise RuntimeError("the tape has recorded another rollout since this forward")
+        dparams = torch.zeros(tape.net.n_params, dtype=torch.float32, device="cuda")
+        dq0 = fv_tape_backward(tape, dparams, dsnaps.float().contiguous(), want_dq0=True)
+        return dparams, dq0, None
+
+
+def tape_rollout(tape: Tape, params: torch.Tensor, q0: torch.Tensor) -> torch.Tensor:
+    """Differentiable learned rollout (see TapeRollout): params [n_params]
+    and q0 [B][3][ny][nx], CUDA float32."""
+    return TapeRollout.apply(params, q0, tape)
 
 
 def stencil_net_adam_step(net: Net, grad: torch.Tensor, step: int, lr: float = 1e-3,

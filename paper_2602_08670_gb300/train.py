@@ -216,6 +216,203 @@ def plain_error_at(n: int, ds: Dataset, nsteps: int, scale) -> float:
     return state_error(fv.fv_coarsen(q, factor), ds.coarse[nsteps], scale)
 
 
+def _tiled_state(n: int, seed: int, members: int, tiles: int, chunk: int = 16) -> torch.Tensor:
+    """swe_random_bumps_tiled on the device, generated in member chunks."""
+    out = torch.empty((members, 3, n, n), dtype=torch.float32, device="cuda")
+    for b0 in range(0, members, chunk):
+        m = min(chunk, members - b0)
+        q = workloads.swe_random_bumps_tiled(n, seed, m, tiles, first=b0)
+        out[b0:b0 + m] = torch.from_numpy(q.astype(np.float32))
+    return out
+
+
+def remap_mean(q: torch.Tensor, n: int) -> torch.Tensor:
+    """Cell averages on the n x n grid of a piecewise-constant [B][C][N][N]
+    field (N >= n): duplicate every cell k x k times so that n divides N k,
+    then take the block means (the coarse-graining kernel)."""
+    N = q.shape[-1]
+    if N == n:
+        return q
+    k = n // math.gcd(N, n)
+    if k > 1:
+        q = q.repeat_interleave(k, dim=-1).repeat_interleave(k, dim=-2)
+    return fv.fv_coarsen(q.contiguous(), N * k // n)
+
+
+class _ErrAcc:
+    """Accumulates, over member chunks, the error measures of a coarse state
+    against the reference: relative L2 per variable, Section 3's mean
+    relative depth error (E1), and the RMS of the per-variable scaled
+    difference (the normalisation of the Eq. 2.28 loss)."""
+
+    def __init__(self, scale):
+        self.s = torch.as_tensor(np.asarray(scale), dtype=torch.float64, device="cuda").view(1, -1, 1, 1)
+        self.d2 = torch.zeros(3, dtype=torch.float64, device="cuda")
+        self.r2 = torch.zeros(3, dtype=torch.float64, device="cuda")
+        self.e1 = torch.zeros((), dtype=torch.float64, device="cuda")
+        self.sc = torch.zeros((), dtype=torch.float64, device="cuda")
+        self.cells = 0
+
+    def add(self, a: torch.Tensor, ref: torch.Tensor) -> None:
+        a, ref = a.double(), ref.double()
+        d = a - ref
+        self.d2 += (d * d).sum(dim=(0, 2, 3))
+        self.r2 += (ref * ref).sum(dim=(0, 2, 3))
+        self.e1 += (d[:, 0].abs() / ref[:, 0]).sum()
+        self.sc += ((d / self.s) ** 2).sum()
+        self.cells += ref[:, 0].numel()
+
+    def result(self) -> dict:
+        rel = (self.d2 / self.r2).sqrt().tolist()
+        return {"scaled_rms": float((self.sc / (3 * self.cells)).sqrt()), "rel_l2": rel,
+                "e1_mean_rel_h": float(self.e1 / self.cells)}
+
+
+def _interp_resolution(errs: dict, err: float):
+    """Resolution at which the plain solver's error equals err: log-log
+    interpolation between the bracketing resolutions (None outside)."""
+    ns = sorted(errs)
+    for a, b in zip(ns, ns[1:]):
+        ea, eb = errs[a], errs[b]
+        if ea >= err >= eb and ea > eb:
+            t = (math.log(ea) - math.log(err)) / (math.log(ea) - math.log(eb))
+            return math.exp(math.log(a) + t * (math.log(b) - math.log(a)))
+    return None
+
+
+def _timed_rollout(q0: torch.Tensor, dt: float, segments, net=None, keep=True, stream=None):
+    """Fixed-dt rollout of q0 in consecutive segments of steps; returns (the
+    state after each segment (device copies) or None, device milliseconds of
+    the steps (CUDA events on the state's stream), members flagged unstable)."""
+    bs = stream or torch.cuda.Stream()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(bs):
+        st = fv.swe_init(q0, dt_mode="fixed", dt_fixed=dt)
+    out, ms = [], 0.0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def tolerate_unstable(call, *a):
+        # a member that left the physical states is reported (health word),
+        # and its NaNs show in the errors; the others carry on
+        try:
+            return call(*a)
+        except fv.FvError as e:
+            if e.code != fv.FV_EUNSTABLE:
+                raise
+            return a[-1] if len(a) > 1 else None
+
+    for k in segments:
+        torch.cuda.synchronize()
+        e0.record(bs)
+        fv.fv_enqueue_steps(st, k, net=net)
+        e1.record(bs)
+        tolerate_unstable(fv.fv_sync, st)
+        ms += e0.elapsed_time(e1)
+        if keep:
+            buf = torch.empty(tuple(q0.shape), dtype=torch.float32, device="cuda")
+            out.append(tolerate_unstable(lambda s_, b_: fv.fv_get_state(s_, out=b_), st, buf))
+    bad = int((fv.fv_health(st) != 0).sum())
+    del st
+    return (out if keep else None), ms, bad
+
+
+def matched_accuracy(nets: dict, dt_coarse64: float, scale, n: int = 256, tiles: int = 4,
+                     members: int = 256, seed: int = 3, horizons=(64, 256, 1000, 2000),
+                     plain_factors=(1.0, 1.5, 2.0, 3.0), headline: int | None = None) -> dict:
+    """Learned versus plain at matched accuracy on one configuration (Section
+    5.4's comparison; Eq. 2.28's error normalisation).
+
+    Workload: `members` states of swe_random_bumps_tiled(n, seed, ., tiles),
+    the training recipe with features scaled to the n^2 grid, so that a
+    network trained on the 64^2 coarse graining of 256^2 runs applies with
+    the coarse step dt_coarse64 * 64 / n.  Reference: the plain solver at
+    (4 n)^2 with a 4x smaller step, coarse-grained 4x (the training data's
+    coarse graining).  Each learned network runs once, timed (CUDA events),
+    and its state at every horizon is compared with the reference; the plain
+    solver runs at N = f n for f in plain_factors (steps and dt scaled by f),
+    remapped to n^2 by cell averages.  N_eq interpolates, in log-log, the
+    plain error over N to the learned error; the plain solver is then timed
+    at N_eq itself (rounded to a multiple of 4).  The accuracy-matched rate
+    is the plain work at N_eq (N_eq^2 cells x K N_eq / n steps per member)
+    over the learned run's time: learned rate x (N_eq / n)^3."""
+    assert all(k % 2 == 0 for k in horizons)
+    headline = headline or horizons[-1]
+    dt = dt_coarse64 * 64.0 / n
+    segs = [horizons[0]] + [b - a for a, b in zip(horizons, horizons[1:])]
+    out = {"workload": f"{members} members x {n}^2 SWE, random bumps scaled to the grid ({tiles}x{tiles} "
+                       f"tiles of the 64^2 training recipe, seed {seed}), fixed dt {dt:.4g}",
+           "reference": f"plain solver at {4 * n}^2, dt/4, coarse-grained 4x",
+           "horizons": list(horizons), "headline_horizon": headline}
+    bs = torch.cuda.Stream()
+    # reference at 4n
+    qf = _tiled_state(4 * n, seed, members, tiles)
+    refs, ref_ms, _ = _timed_rollout(qf, dt / 4, [4 * k for k in segs], stream=bs)
+    del qf
+    refs = [fv.fv_coarsen(r, 4) for r in refs]
+    torch.cuda.empty_cache()
+    q0 = _tiled_state(n, seed, members, tiles)
+    # plain solver at N = f n
+    plain = {}
+    for f in plain_factors:
+        N = int(round(f * n))
+        qN = q0 if N == n else _tiled_state(N, seed, members, tiles)
+        states, ms, bad = _timed_rollout(qN, dt * n / N, [int(round(k * f)) for k in segs], stream=bs)
+        errs = []
+        for st, ref in zip(states, refs):
+            acc = _ErrAcc(scale)
+            for b0 in range(0, members, 16):
+                acc.add(remap_mean(st[b0:b0 + 16], n), ref[b0:b0 + 16])
+            errs.append(acc.result())
+        steps = int(round(horizons[-1] * f))
+        plain[N] = {"errors": errs, "cell_updates_per_s": members * N * N * steps / (ms * 1e-3),
+                    "unstable_members": bad}
+        del states
+        torch.cuda.empty_cache()
+    out["plain"] = {str(N): v for N, v in plain.items()}
+    # learned networks
+    for name, net in nets.items():
+        # warm-up (graph capture, lazy set-up) on a short run
+        _timed_rollout(q0[: min(members, 8)].contiguous(), dt, [2], net=net, keep=False, stream=bs)
+        states, ms, bad = _timed_rollout(q0, dt, segs, net=net, stream=bs)
+        rate = members * n * n * horizons[-1] / (ms * 1e-3)
+        res = {"cell_updates_per_s": rate, "seconds": ms * 1e-3, "unstable_members": bad, "by_horizon": {}}
+        for K, st, ref in zip(horizons, states, refs):
+            acc = _ErrAcc(scale)
+            acc.add(st, ref)
+            e = acc.result()
+            row = {"learned": e}
+            for metric in ("scaled_rms", "e1_mean_rel_h"):
+                errs = {N: (v["errors"][horizons.index(K)][metric]) for N, v in plain.items()}
+                row[f"plain_{metric}"] = {str(N): v for N, v in errs.items()}
+                row[f"n_eq_{metric}"] = _interp_resolution(errs, e[metric])
+            res["by_horizon"][str(K)] = row
+        del states
+        # the headline: N_eq by the scaled RMS at the headline horizon, and the
+        # plain solver timed at N_eq itself
+        hrow = res["by_horizon"][str(headline)]
+        n_eq = hrow["n_eq_scaled_rms"]
+        m = {"horizon": headline, "metric": "scaled_rms", "n_eq": n_eq, "learned_rate": rate,
+             "learned_error": hrow["learned"]["scaled_rms"],
+             "plain_error_same_n": plain[n]["errors"][horizons.index(headline)]["scaled_rms"]}
+        if n_eq is not None:
+            r = n_eq / n
+            N4 = max(8, int(round(n_eq / 4.0)) * 4)
+            qN = _tiled_state(N4, seed, members, tiles)
+            steps = max(2, int(round(headline * N4 / n)))
+            _, pms, _ = _timed_rollout(qN, dt * n / N4, [steps], keep=False, stream=bs)
+            del qN
+            prate = members * N4 * N4 * steps / (pms * 1e-3)
+            m.update({"r": r, "learned_rate_times_r3": rate * r ** 3, "plain_n_timed": N4,
+                      "plain_rate_at_n_eq": prate, "learned_wins": rate * r ** 3 > prate})
+        else:
+            m.update({"r": None, "learned_wins": False,
+                      "note": "the learned error is outside the plain errors measured"})
+        res["accuracy_matched"] = m
+        out[name] = res
+        torch.cuda.empty_cache()
+    return out
+
+
 def save_weights(path: str, net, ds: Dataset, result: TrainResult, extra: dict | None = None) -> None:
     """Parameters, input normalisation and the training recipe in one .npz."""
     mean, scale = input_scale(ds)

@@ -122,6 +122,61 @@ def swe_random_bumps(n: int, seed: int, members: int) -> np.ndarray:
     return q
 
 
+def _gauss_cell_means(edges: np.ndarray, c: np.ndarray, w: np.ndarray) -> np.ndarray:
+    """[K][n] means over the cells [edges[i], edges[i+1]) of the 1-periodic
+    Gaussians exp(-(x - c_k)^2 / w_k^2) (images at -1, 0, +1)."""
+    from scipy.special import erf
+    h = edges[1:] - edges[:-1]
+    out = np.zeros((len(c), len(edges) - 1))
+    for k in (-1.0, 0.0, 1.0):
+        z = (edges[None, :] - c[:, None] - k) / w[:, None]
+        e = erf(z)
+        out += (0.5 * math.sqrt(math.pi) * w[:, None]) * (e[:, 1:] - e[:, :-1])
+    return out / h[None, :]
+
+
+def swe_random_bumps_tiled(n: int, seed: int, members: int, tiles: int, first: int = 0) -> np.ndarray:
+    """The training recipe with its features scaled to a finer grid: the unit
+    square is cut into tiles x tiles squares of side 1/tiles, and each square
+    gets its own draw of the random-bump recipe (K ~ U{1..5} bumps,
+    A ~ U[0.05, 0.2], widths U[0.02, 0.1] / tiles, centres uniform in the
+    square), h = 1 + sum_k A_k exp(-|x - c_k|^2 / w_k^2) with periodic images,
+    fluid at rest.  The shallow-water equations on a flat bed have no length
+    scale of their own (x -> x / t with time -> time / t leaves them
+    unchanged), so an n^2 run of this field is locally the same problem as an
+    (n / tiles)^2 run of the plain recipe.
+
+    Each cell holds the exact mean of the continuous field over the cell (the
+    Gaussian is separable; its cell means are differences of erf), so grids of
+    any resolution hold finite-volume averages of one and the same field and a
+    4x coarse graining of the n^2 state equals the (n/4)^2 state up to
+    rounding.  Returns members first .. first + members - 1 of the seed's
+    ensemble as ``[members][3][n][n]``."""
+    edges = np.arange(n + 1, dtype=np.float64) / n
+    specs = random_bump_specs(seed, (first + members) * tiles * tiles)[first * tiles * tiles:]
+    inv = 1.0 / tiles
+    kmax = 5 * tiles * tiles
+    # bumps of every member padded to kmax with zero amplitude
+    cx, cy = np.full((members, kmax), 0.5), np.full((members, kmax), 0.5)
+    a, w = np.zeros((members, kmax)), np.full((members, kmax), inv)
+    for b in range(members):
+        k = 0
+        for ty in range(tiles):
+            for tx in range(tiles):
+                spec = specs[(b * tiles + ty) * tiles + tx]
+                m = len(spec.amps)
+                cx[b, k:k + m] = (tx + spec.centres[:, 0]) * inv
+                cy[b, k:k + m] = (ty + spec.centres[:, 1]) * inv
+                a[b, k:k + m] = spec.amps
+                w[b, k:k + m] = spec.widths * inv
+                k += m
+    ex = _gauss_cell_means(edges, cx.reshape(-1), w.reshape(-1)).reshape(members, kmax, n)
+    ey = _gauss_cell_means(edges, cy.reshape(-1), w.reshape(-1)).reshape(members, kmax, n)
+    q = np.zeros((members, 3, n, n))
+    q[:, 0] = 1.0 + np.matmul((a[:, :, None] * ey).transpose(0, 2, 1), ex)   # h[b][j][i]
+    return q
+
+
 def swe_dam_break(nx: int, ny: int, h_left: float = 1.0, h_right: float = 0.35,
                   x0: float = 0.5) -> np.ndarray:
     """y-uniform dam break: h = h_left for x < x0, h_right otherwise, at rest.

@@ -266,23 +266,28 @@ def test_device_gelu_matches_the_definition(fv):
     assert np.mean(got == want) >= 0.95, np.mean(got == want)
 
 
-def test_face_net_backward_matches_oracle(fv):
+@pytest.mark.parametrize("ny,nx", [(16, 128), (64, 64)])
+def test_face_net_backward_matches_oracle(fv, ny, nx):
     """face_net_backward (the network's VJP at q) against the oracle's FP64
     reverse mode through the BF16-mirrored forward and the side-state
-    epilogue."""
+    epilogue, on a tile-mode grid and on the 64^2 training grid; dparams and
+    dq start from a known non-zero fill (the call adds to them)."""
     p = rand_params(9, last_scale=0.3, h_bias=1.05)
     net = gpu_net(fv, p)
-    q0 = W.as_f32_exact(W.random_smooth_swe(128, seed=6, members=2, vel=0.2)[:, :, :16, :])
+    q0 = W.as_f32_exact(W.random_smooth_swe(nx, seed=6, members=2, vel=0.2)[:, :, :ny, :])
     g = torch.Generator().manual_seed(3)
-    ds = torch.randn(2, 12, 16, 128, generator=g, dtype=torch.float64)
+    ds = torch.randn(2, 12, ny, nx, generator=g, dtype=torch.float64)
     flat = p.flat().detach().clone().requires_grad_(True)
     pp = ofn.FaceNetParams.from_flat(flat, p.mean, p.std)
     q = torch.tensor(q0).requires_grad_(True)
-    sides = ofn.side_states(ofn.net_raw(q, pp, round_bf16=True), pp).reshape(2, 12, 16, 128)
+    sides = ofn.side_states(ofn.net_raw(q, pp, round_bf16=True), pp).reshape(2, 12, ny, nx)
     (sides * ds).sum().backward()
-    dparams, dq = fv.net_backward(net, f32(q0).cuda(), f32(ds).cuda())
-    for got, ref, name in ((dparams, flat.grad, "dparams"), (dq, q.grad, "dq")):
-        a, b = got.double().cpu().reshape(-1), ref.reshape(-1)
+    fill_p = torch.linspace(-1.0, 1.0, fv.FV_FACE_NET_PARAMS, device="cuda")
+    fill_q = torch.full((2, 3, ny, nx), -0.5, device="cuda")
+    dparams, dq = fv.net_backward(net, f32(q0).cuda(), f32(ds).cuda(), dparams=fill_p.clone(),
+                                  dq=fill_q.clone())
+    for got, fill, ref, name in ((dparams, fill_p, flat.grad, "dparams"), (dq, fill_q, q.grad, "dq")):
+        a, b = (got - fill).double().cpu().reshape(-1), ref.reshape(-1)
         cos = float(a @ b / (a.norm() * b.norm()))
         rel = float((a - b).norm() / b.norm())
         assert cos >= 0.999 and rel <= 2e-2, (name, cos, rel)

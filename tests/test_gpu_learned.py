@@ -207,14 +207,17 @@ def test_rollout_gradients_match_oracle(fv, n, T, B, zero):
         assert int(nz.min()) >= lo   # only b4
 
 
-def test_stencil_net_backward_matches_oracle(fv):
+@pytest.mark.parametrize("ny,nx", [(16, 128), (64, 64)])
+def test_stencil_net_backward_matches_oracle(fv, ny, nx):
     """stencil_net_backward (the network's VJP at q) against the oracle's FP64
-    reverse mode through the BF16-mirrored forward and the normalisation."""
+    reverse mode through the BF16-mirrored forward and the normalisation, on
+    a tile-mode grid and on the 64^2 training grid (several rows per tile).
+    dparams and dq start from a known non-zero fill: the call adds to them."""
     p = rand_params(8, last_scale=0.3)
     net = gpu_net(fv, p)
-    q0 = W.as_f32_exact(W.random_smooth_swe(128, seed=5, members=2, vel=0.2)[:, :, :16, :])
+    q0 = W.as_f32_exact(W.random_smooth_swe(nx, seed=5, members=2, vel=0.2)[:, :, :ny, :])
     g = torch.Generator().manual_seed(2)
-    dw = torch.randn(2, 36, 16, 128, generator=g, dtype=torch.float64)
+    dw = torch.randn(2, 36, ny, nx, generator=g, dtype=torch.float64)
     flat = p.flat().clone().requires_grad_(True)
     W_, b_, off = [], [], 0
     for co, ci in osn.LAYER_SHAPES:
@@ -226,9 +229,12 @@ def test_stencil_net_backward_matches_oracle(fv):
     q = torch.tensor(q0).requires_grad_(True)
     w = osn.normalise(osn.net_raw(q, osn.NetParams(W_, b_, p.mean, p.std), round_bf16=True))
     (w * dw).sum().backward()
-    dparams, dq = fv.net_backward(net, f32(q0).cuda(), f32(dw).cuda())
-    for got, ref, name in ((dparams, flat.grad, "dparams"), (dq, q.grad, "dq")):
-        a, b = got.double().cpu().reshape(-1), ref.reshape(-1)
+    fill_p = torch.linspace(-1.0, 1.0, fv.FV_NET_PARAMS, device="cuda")
+    fill_q = torch.full((2, 3, ny, nx), 0.75, device="cuda")
+    dparams, dq = fv.net_backward(net, f32(q0).cuda(), f32(dw).cuda(), dparams=fill_p.clone(),
+                                  dq=fill_q.clone())
+    for got, fill, ref, name in ((dparams, fill_p, flat.grad, "dparams"), (dq, fill_q, q.grad, "dq")):
+        a, b = (got - fill).double().cpu().reshape(-1), ref.reshape(-1)
         cos = float(a @ b / (a.norm() * b.norm()))
         rel = float((a - b).norm() / b.norm())
         assert cos >= 0.999 and rel <= 2e-2, (name, cos, rel)

@@ -59,3 +59,49 @@ def test_reference_run_matches_the_oracle(mods):
     for c, (e2, ei) in enumerate(rel_errors(got, ref)):
         l2, li = (1e-5, 1e-4) if c == 0 else (1e-4, 1e-3)
         assert e2 <= l2 and ei <= li, (c, e2, ei)
+
+
+def test_scaled_reference_matches_the_oracle(mods):
+    """The reference of the 256^2 accuracy-matched comparison (the plain run at
+    1024^2 of the grid-scaled bump field, coarse-grained 4x) against the FP64
+    oracle's own 1024^2 run of the same member, fixed dt, 16 fine steps."""
+    import os
+
+    from helpers import ROOT, rel_errors
+    fv, TR = mods
+    _, meta = TR.load_weights(os.path.join(ROOT, "paper_2602_08670_gb300", "weights", "swe64_from256.npz"))
+    dt = meta["dt_coarse"] * 64 / 256 / 4
+    q0 = torch.tensor(W.as_f32_exact(W.swe_random_bumps_tiled(1024, 3, 1, 4)))
+    st = fv.swe_init(q0.float().cuda(), dt_mode="fixed", dt_fixed=dt)
+    fv.fv_rollout(st, 16)
+    got = fv.fv_coarsen(fv.fv_get_state(st), 4).double().cpu()
+    qr, _, _, _ = ofv.run(q0, ofv.SWE, 16, dt_mode=ofv.DT_FIXED, dt_fixed=dt)
+    ref = ofv.coarsen(qr, 4)
+    for c, (e2, ei) in enumerate(rel_errors(got, ref)):
+        l2, li = (1e-5, 1e-4) if c == 0 else (1e-4, 1e-3)
+        assert e2 <= l2 and ei <= li, (c, e2, ei)
+
+
+def _overlap(nc, nf):
+    """[nc][nf] weights of the exact mean over each coarse cell of a
+    piecewise-constant fine field: the length of the overlap of coarse cell i
+    and fine cell k divided by the coarse cell's width."""
+    A = np.zeros((nc, nf))
+    for i in range(nc):
+        a, b = i / nc, (i + 1) / nc
+        for k in range(nf):
+            lo, hi = max(a, k / nf), min(b, (k + 1) / nf)
+            if hi > lo:
+                A[i, k] = (hi - lo) * nc
+    return A
+
+
+@pytest.mark.parametrize("nf,nc", [(96, 64), (384, 256), (128, 64), (192, 128)])
+def test_remap_mean_is_the_cell_average(mods, nf, nc):
+    fv, TR = mods
+    g = torch.Generator().manual_seed(nf)
+    q = (1.0 + 0.1 * torch.rand((2, 3, nf, nf), generator=g, dtype=torch.float64)).float()
+    got = TR.remap_mean(q.cuda(), nc).double().cpu()
+    A = torch.tensor(_overlap(nc, nf))
+    ref = A @ q.double() @ A.T
+    assert float((got - ref).abs().max()) <= 1.2e-7 * float(ref.abs().max())

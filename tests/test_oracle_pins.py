@@ -384,20 +384,47 @@ def test_coarsen_block_mean():
     assert torch.allclose(c.sum(dim=(2, 3)) * 16, q.sum(dim=(2, 3)))
 
 
-def test_potential_enstrophy_solid_rotation():
-    # u = -w (y - 1/2), v = w (x - 1/2) has vorticity 2 w away from the wrap
-    n = 32
+def test_potential_enstrophy_closed_form():
+    # Plane wave theta = 2 pi (x + 2 y) with u = -A sin(theta), v = B sin(theta)
+    # on a constant depth H = 2.  Centred differences of sin(theta) are exact
+    # multiples of cos(theta): d/dx -> s1 cos(theta), d/dy -> s2 cos(theta) with
+    # s_k = n sin(2 pi k / n) / 1 (one and two wavelengths across the square).
+    # So zeta = (B s1 + A s2) cos(theta) at every cell and, since cos^2 averages
+    # to 1/2 over the grid, the integral of zeta^2 / (2 h) is
+    # (B s1 + A s2)^2 / (4 H).  A swapped derivative axis gives B s2 + A s1, a
+    # wrong sign B s1 - A s2, a missing 1/2 or 1/h a factor 2 or H.
+    n, A, B, H = 32, 0.3, 0.7, 2.0
     X, Y = np.meshgrid(W.cell_centres(n), W.cell_centres(n))
-    w = 0.3
+    th = 2 * np.pi * (X + 2 * Y)
     q = torch.zeros(1, 3, n, n, dtype=torch.float64)
-    q[0, 0] = 1.0
-    q[0, 1] = torch.tensor(-w * (Y - 0.5))
-    q[0, 2] = torch.tensor(w * (X - 0.5))
-    dx = 1 / n
-    h = q[:, 0]
-    u, v = q[:, 1] / h, q[:, 2] / h
-    zeta = (torch.roll(v, -1, -1) - torch.roll(v, 1, -1)) / (2 * dx) - \
-        (torch.roll(u, -1, -2) - torch.roll(u, 1, -2)) / (2 * dx)
-    assert torch.allclose(zeta[0, 2:-2, 2:-2], torch.full((n - 4, n - 4), 2 * w, dtype=torch.float64))
+    q[0, 0] = H
+    q[0, 1] = torch.tensor(H * (-A * np.sin(th)))
+    q[0, 2] = torch.tensor(H * (B * np.sin(th)))
+    s1 = n * np.sin(2 * np.pi / n)
+    s2 = n * np.sin(4 * np.pi / n)
+    expect = (B * s1 + A * s2) ** 2 / (4 * H)
     pe = float(fv.potential_enstrophy(q)[0])
-    assert pe > 0.5 * (2 * w) ** 2 * ((n - 4) / n) ** 2 * 0.99
+    assert abs(pe - expect) <= 1e-12 * expect, (pe, expect)
+    # u = v along the same wave: dv/dx = du/dy only when s1 = s2, so use the
+    # diagonal wave theta = 2 pi (x + y), for which zeta vanishes identically
+    th = 2 * np.pi * (X + Y)
+    q[0, 1] = torch.tensor(H * 0.4 * np.sin(th))
+    q[0, 2] = torch.tensor(H * 0.4 * np.sin(th))
+    assert float(fv.potential_enstrophy(q)[0]) < 1e-24
+
+
+def test_mean_relative_h_error_closed_forms():
+    # Section 3's metric: mean over cells of |h_high - h_low| / h_high.
+    # h_low = h_high (1 + eps_ij) with eps = +-e0 in a checkerboard gives
+    # exactly e0 (a signed mean would give 0); h_low = 2 h_high gives 1 and
+    # the swapped arguments 1/2 (the normalisation is by the high-resolution
+    # depth).
+    rng = np.random.default_rng(5)
+    hh = torch.tensor(1.0 + rng.uniform(0.0, 0.5, size=(2, 16, 16)))
+    sign = torch.tensor(np.where((np.add.outer(np.arange(16), np.arange(16)) % 2) == 0, 1.0, -1.0))
+    e0 = 0.0625
+    hl = hh * (1.0 + e0 * sign)
+    assert abs(fv.mean_relative_h_error(hl, hh) - e0) < 1e-15
+    assert fv.mean_relative_h_error(2 * hh, hh) == 1.0
+    assert abs(fv.mean_relative_h_error(hh, 2 * hh) - 0.5) < 1e-15
+    assert fv.mean_relative_h_error(hh, hh) == 0.0

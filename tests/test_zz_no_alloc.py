@@ -71,3 +71,36 @@ def test_noalloc_rejects_batches_beyond_the_fixed_scratch(fv):
                                   out.ctypes.data_as(ctypes.c_void_p), fv.FV_HOST, None)
     assert rc == fv.FV_EINVAL
     assert b"scratch" in L.fv_last_error()
+
+
+def _raw_call(fv, q, eq, B, phys):
+    L = fv.lib()
+    out = np.zeros((B, (3 if eq == 0 else 4) + 1))
+    torch.cuda.synchronize()
+    rc = L.fv_diagnostics_noalloc(ctypes.c_void_p(q.data_ptr()), eq, B, q.shape[2], q.shape[3], 1.0, 1.0,
+                                  phys, out.ctypes.data_as(ctypes.c_void_p), fv.FV_HOST, None)
+    return rc, out
+
+
+def test_noalloc_capacity_limits_are_exact(fv):
+    # 80 shallow-water members (80 x 4 slots) and 64 Euler members (64 x 5)
+    # fill the 320 slots exactly and must match the allocating entry point;
+    # one member more of either is rejected
+    qs = f32(W.random_smooth_swe(16, seed=3, members=80, vel=0.2)).cuda()
+    s = fv.swe_init(qs)
+    fv.fv_rollout(s, 3)
+    ref = fv.fv_diagnostics(s)
+    rc, got = _raw_call(fv, fv.fv_get_state(s), 0, 80, 9.81)
+    assert rc == fv.FV_OK, fv.lib().fv_last_error()
+    assert np.allclose(got, ref, rtol=1e-12, atol=1e-14)
+    qe = f32(np.concatenate([W.euler_kelvin_helmholtz(16, 8, seed=k) for k in range(64)])).cuda()
+    es = fv.euler_init(qe)
+    fv.fv_rollout(es, 2)
+    eref = fv.fv_diagnostics(es)
+    rc, egot = _raw_call(fv, fv.fv_get_state(es), 1, 64, 1.4)
+    assert rc == fv.FV_OK, fv.lib().fv_last_error()
+    assert np.allclose(egot, eref, rtol=1e-12, atol=1e-14)
+    q65 = torch.ones((65, 4, 8, 16), dtype=torch.float32, device="cuda")
+    rc, _ = _raw_call(fv, q65, 1, 65, 1.4)
+    assert rc == fv.FV_EINVAL
+    assert b"scratch" in fv.lib().fv_last_error()
