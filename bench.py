@@ -301,7 +301,9 @@ def run_gpu(args):
     if not args.no_learned:
         line["learned"] = learned_block(args)
     if not args.no_serving:
-        line["serving"] = serving_block(args)
+        lrate = line.get("learned", {}).get("accuracy_matched", {}).get("stencil", {}).get(
+            "learned_only_cell_updates_per_s")
+        line["serving"] = serving_block(args, N_SWE * N_SWE * K / (swe_ms * 1e-3), lrate)
     # compact summary of the learned and serving results as the line's last key
     line["summary"] = summary(line)
     if rank == 0:
@@ -413,21 +415,23 @@ def _sig(x, k=3):
 
 
 def summary(line) -> dict:
-    """The learned-vs-plain accuracy-matched numbers and the serving
-    latencies, compact, for the end of the JSON line."""
+    """The learned-vs-plain accuracy-matched numbers per horizon and the
+    serving latencies, compact, for the end of the JSON line."""
     out = {"plain_cell_updates_per_s": _sig(line["value"])}
     lm = line.get("learned", {}).get("accuracy_matched")
     if lm:
         for name in ("stencil", "face_state"):
-            a = lm[name]["accuracy_matched"]
-            out[name] = {"horizon": a["horizon"], "learned_rate": _sig(a["learned_rate"]),
-                         "err": _sig(a["learned_error"]), "plain_err_same_n": _sig(a["plain_error_same_n"]),
-                         "n_eq": _sig(a["n_eq"]), "matched_rate": _sig(a.get("learned_rate_times_r3")),
-                         "plain_rate_at_n_eq": _sig(a.get("plain_rate_at_n_eq")),
-                         "learned_wins": a["learned_wins"]}
+            out[name] = {K: [_sig(a["learned_error"], 2), _sig(a["plain_error_same_n"], 2),
+                             (">" if a["n_eq_is_lower_bound"] else "") + str(_sig(a["n_eq"])),
+                             _sig(a["learned_rate"], 2), _sig(a.get("learned_rate_times_r3"), 2),
+                             _sig(a.get("plain_rate_at_n_eq"), 2), a["learned_wins"], a["members_on_fallback"]]
+                         for K, a in lm[name]["accuracy_matched_by_horizon"].items()}
+        out["legend"] = ("horizon: [learned err, plain err at 256^2, N_eq, learned cu/s, learned cu/s x "
+                         "(N_eq/256)^3, plain cu/s at N_eq, learned wins, members on fallback]")
     sv = line.get("serving")
     if sv:
         out["serving"] = {"capacity_cell_updates_per_s": _sig(sv["capacity"]["throughput_cell_updates_per_s"]),
+                          "kernel_bound": _sig(sv.get("kernel_bound_cell_updates_per_s")),
                           "p50_p99_s": {str(d["rate_fraction_of_capacity"]):
                                         [_sig(d["p50_latency_s"]), _sig(d["p99_latency_s"]), d["requests"]]
                                         for d in sv["load"]}}
@@ -557,14 +561,15 @@ def sphere_block(args):
     return out
 
 
-def serving_block(args):
+def serving_block(args, plain_rate=None, learned_rate=None):
     """Continuous-batching server under Poisson load: requests of SWE (50 %
     learned, 25 % plain) and Euler (25 %), grids uniform over {64, 128, 256,
     512}^2, horizons uniform in [100, 1000] (a reduced version of the full
     serving workload, which has grids to 2048^2 and horizons to 5000 steps;
-    paper_2602_08670_gb300.serve runs that).  Capacity = requests per second
-    with all requests queued at t = 0; the Poisson runs use 0.5 and 0.9 x
-    capacity."""
+    `python -m paper_2602_08670_gb300.serve` runs that).  Capacity = requests
+    per second with all requests queued at t = 0; the Poisson runs use 0.5,
+    0.9 and 1.2 x capacity.  The kernel bound is the throughput the same mix
+    reaches at the plain and learned kernels' full-GPU rates."""
     from paper_2602_08670_gb300 import fv, serve
     from paper_2602_08670_gb300 import train as TR
     from paper_2602_08670_gb300 import workloads as W
@@ -572,20 +577,13 @@ def serving_block(args):
     net, _ = TR.load_weights(WEIGHTS)
     base = W.serving_requests(args.serve_requests, 1.0, seed=42, sizes=(64, 128, 256, 512),
                               horizon=(100, 1000))
-    server = fv.fv_server_create(64 << 30, 16, net)
-    states = serve.initial_states(base)
-    closed = serve.with_arrivals(base, 1e9, seed=42)
-    lat, span, fail = serve.run_load(server, closed, states)
-    cap = serve.summarize(closed, lat, span, fail)
-    out = {"workload": "requests: 50 % learned SWE, 25 % plain SWE, 25 % plain Euler; grids "
-                       "{64,128,256,512}^2; horizons U[100,1000]; seed 42; budget 64 GB, 16 slots",
-           "capacity": cap, "load": []}
-    for frac in (0.5, 0.9):
-        reqs = serve.with_arrivals(base, frac * cap["requests_per_s"], seed=int(frac * 100))
-        lat, span, fail = serve.run_load(server, reqs, states)
-        d = serve.summarize(reqs, lat, span, fail)
-        d["rate_fraction_of_capacity"] = frac
-        out["load"].append(d)
+    server = fv.fv_server_create(64 << 30, 256, net)
+    out = {"workload": f"{args.serve_requests} requests per rate: 50 % learned SWE, 25 % plain SWE, "
+                       "25 % plain Euler; grids {64,128,256,512}^2; horizons U[100,1000]; seed 42; "
+                       "budget 64 GB, 256 slots"}
+    out.update(serve.sweep(server, base, (0.5, 0.9, 1.2)))
+    if plain_rate and learned_rate:
+        out["kernel_bound_cell_updates_per_s"] = serve.kernel_bound(base, plain_rate, learned_rate)
     out["learned_fallbacks_to_plain"] = fv.fv_server_stats(server)[3]
     return out
 

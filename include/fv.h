@@ -292,6 +292,79 @@ int fv_diagnostics_noalloc(const float* q, int eq, int batch, int ny, int nx, do
                            double phys, double* sums, int sums_loc, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Subdomains of a block-decomposed grid
+ *
+ * The explicit step (Eqs. 2.9, 2.18, 2.19, 2.23) reads a bounded stencil, so
+ * a grid splits into px x py blocks that each advance on their own once a
+ * ring of their neighbours' cells is in place.  A subdomain is an ordinary
+ * state of (nx/px + 2 hx) x (ny/py + 2 hy) cells: its interior plus a ring of
+ * hx columns and hy rows copied from the periodic neighbours before every
+ * Runge-Kutta stage (hx, hy = 2 for the plain MUSCL-minmod step; 6 rows for
+ * the learned step, whose CNN adds 4 cells of reach to the 2 of the
+ * reconstruction, rounded up to keep rows 16-byte aligned).  The stage
+ * kernels also compute the ring cells (with wrong neighbours); the next
+ * refresh overwrites them.  One step of a decomposed grid is
+ *   fv_halo_exchange(buf 0); fv_enqueue_stage(1) on every subdomain;
+ *   fv_halo_exchange(buf 1); fv_enqueue_stage(2) on every subdomain;
+ *   fv_reduce_dt
+ * and its interiors equal the undecomposed grid's cells bitwise (the
+ * per-cell arithmetic does not depend on the cell's place in the grid, and
+ * the next dt is the minimum over the subdomains).  Between processes the
+ * ring travels as packed strips (fv_halo_pack / fv_halo_unpack; x first,
+ * then y over the full width, which carries the corners) and the dt as a
+ * minimum over processes (fv_get_time / fv_set_dt).
+ * ------------------------------------------------------------------------- */
+
+/* Declare the outer hx columns and hy rows of s a ring: the CFL reduction,
+ * the health bits and fv_diagnostics cover the interior [hx, nx-hx) x
+ * [hy, ny-hy) only, and the pending dt is recomputed from the interior.
+ * Needs 4 hx <= nx, 4 hy <= ny, a periodic flat-bed planar state.  The fused
+ * learned kernel takes rings of rows only (hx = 0).  Synchronous;
+ * FV_EUNSTABLE if the interior is not a physical state. */
+int fv_set_halo(fv_state* s, int hx, int hy);
+
+/* Enqueue one SSP-RK2 stage (Eq. 2.19): stage 1 maps q^n to the stage state,
+ * stage 2 combines them into q^{n+1} and closes the step (time, next dt).
+ * net = NULL: the plain HLL/MUSCL-minmod stage; else the learned stage of a
+ * stencil or face-state network.  Asynchronous on the state's stream;
+ * FV_EINVAL for other schemes, walls or a bed. */
+int fv_enqueue_stage(fv_state* s, const fv_net* net, int stage);
+
+/* Fill the ring of buffer `buf` (0: q^n, the input of stage 1; 1: the stage
+ * state, the input of stage 2) of px * py subdomains of one process,
+ * subs[iy * px + ix] holding block (ix, iy) of the periodic grid, from the
+ * interiors of the blocks that own those cells.  All subdomains: same
+ * equations, batch, shape and ring; at most 64.  One kernel on subs[0]'s
+ * stream, ordered after and before the other subdomains' streams.  A split
+ * direction needs a ring (FV_EINVAL). */
+int fv_halo_exchange(fv_state* const* subs, int px, int py, int buf);
+
+/* Set every member's pending dt of the n subdomains to its minimum over them
+ * (after stage 2, before the next step).  Asynchronous, ordered like
+ * fv_halo_exchange. */
+int fv_reduce_dt(fv_state* const* subs, int n);
+
+/* Copy the interior strip next to side `side` (0 west, 1 east, 2 south,
+ * 3 north) of buffer `buf` into dst (device, fv_halo_strip_floats floats,
+ * [B][C][rows][cols]), or write src into that side's ring.  West/east strips
+ * span the interior rows, south/north strips the full width: exchange west
+ * and east first, then south and north.  Asynchronous on the state's
+ * stream. */
+int fv_halo_pack(fv_state* s, int buf, int side, float* dst);
+int fv_halo_unpack(fv_state* s, int buf, int side, const float* src);
+int fv_halo_strip_floats(const fv_state* s, int side, long long* n);
+
+/* Set every member's pending dt (host [B], >= 0; e.g. the minimum over the
+ * processes of a decomposed grid).  Synchronous. */
+int fv_set_dt(fv_state* s, const double* dt);
+
+/* Positivity threshold of the learned faces as absolute depths per member
+ * (host [B]) instead of a fraction of the state's own mean depth: the
+ * subdomains of one grid share the whole grid's threshold.  Before the first
+ * learned step (FV_EINVAL after). */
+int fv_set_learned_hmin_values(fv_state* s, const double* hmin);
+
+/* ---------------------------------------------------------------------------
  * Learned stencil network (Section 2.5.3, fourth approach)
  *
  * x = (q - mean) / std per channel; four 3x3 convolutions with periodic

@@ -30,8 +30,9 @@ struct Ctrl {
   unsigned amax_bits;  // running max Courant rate of the state being produced (float bits)
   unsigned blocks_done;// blocks of the current reduction that have finished
   unsigned health;     // FV_HEALTH_* bits
-  unsigned done;       // 1 once t reached t_end (or REPLAY ran out): stages skip all work
+  unsigned done;       // 1 once t reached t_end, step reached step_end or REPLAY ran out: stages skip all work
   unsigned exhausted;  // REPLAY has no dt left for the next step
+  long long step_end;  // stop once this many steps are complete (<= 0: no limit)
 };
 
 // Parameters of the time-step rule, shared by all members (device memory).
@@ -335,7 +336,7 @@ __device__ inline void publish_and_close(Ctrl* c, const DtParams* dp, float m, u
     }
   }
   if (dp->mode != FV_DT_ADAPTIVE && (double)amax * dt > 1.0) c->health |= FV_HEALTH_CFL;
-  c->done = c->exhausted;
+  c->done = c->exhausted | (c->step_end > 0 && c->step >= c->step_end ? 1u : 0u);
   if (c->t_end > 0.0) {
     const double rem = c->t_end - c->t;
     if (rem <= 0.0) {

@@ -149,6 +149,7 @@ struct Args {
   long long nstreams;      // 2 x clusters
   float rdx, rdy, g;
   unsigned* err;
+  int hy;                  // ring rows of a subdomain: outside the CFL reduction
 };
 
 // ---------------------------------------------------------------------------
@@ -648,7 +649,8 @@ __device__ __forceinline__ void update_cell(Stream& Q, uint8_t* sbuf, const Args
       out[c] = STAGE == 1 ? rk_stage1<float>(q, Q.dt, Lc) : rk_stage2<float>(qnb[c * W + m], q, 0.5f * Q.dt, Lc);
       a.qout[off + c * a.plane] = out[c];
     }
-    if (STAGE == 2) Q.amax = fmaxf(Q.amax, cell_rate_swe(out[0], out[1], out[2], a.g, a.rdx, a.rdy, Q.bad));
+    if (STAGE == 2 && u >= a.hy && u < a.ny - a.hy)
+      Q.amax = fmaxf(Q.amax, cell_rate_swe(out[0], out[1], out[2], a.g, a.rdx, a.rdy, Q.bad));
   }
   if (STAGE == 2 && tau + 1 >= TICKS_AHEAD && tau + 1 < Q.ntau) {
     fetch_qn(qnb, a, Q.b, t - 7, X.X0, m);
@@ -1125,6 +1127,8 @@ __global__ void __launch_bounds__(NT, 1) learned_fused_kernel(Args a) {
 bool learned_fused_supported(int nx, int ny) {
   return nx % fused::W == 0 && nx / fused::W <= fused::MAX_CS && ny >= 1;
 }
+// (A subdomain ring in x would shift the 128-column tiles off the grid's
+// columns; the fused kernel takes rings of rows only.)
 
 namespace {
 
@@ -1203,6 +1207,7 @@ cudaError_t launch_learned_fused(const Geom& g, int stage, const float* qin, con
   a.rdy = (float)(1.0 / g.dy);
   a.g = g.phys;
   a.err = net.err;
+  a.hy = g.hy;
   return stage == 1 ? launch_fused_stage<1>(a, s) : launch_fused_stage<2>(a, s);
 }
 

@@ -70,6 +70,7 @@ struct fv_state {
 
 namespace fvs {
 int state_alloc(fv_state* s);
+cudaError_t enqueue_plain_stage(fv_state* s, int stage);   // HLL, SSP-RK2, periodic, flat bed
 void state_free(fv_state* s);
 cudaError_t enter(fv_state* s);
 cudaError_t leave(fv_state* s);
@@ -80,7 +81,12 @@ cudaError_t wavespeed_init(fv_state* s);                // dt of the current sta
 // learned path (fv_learned.cu)
 int learned_prepare(fv_state* s, const fv_net* net);  // host side, before enqueueing
 cudaError_t enqueue_learned_step(fv_state* s, const fv_net* net);
+cudaError_t enqueue_learned_stage(fv_state* s, const fv_net* net, int stage);   // 1 or 2
+int learned_set_hmin_values(fv_state* s, const double* hmin);   // absolute h_min per member
 void learned_workspace_free(fv_state* s);
 bool learned_hmin_fixed(const fv_state* s);           // a stencil-network step has set h_min
+float* learned_hmin_ptr(fv_state* s);                 // device [B] h_min, or null
+long long learned_ws_bytes(const fv_state* s);        // device memory of the learned workspace
+long long state_device_bytes(const fv_state* s);      // device memory held by the state
 int net_check(const fv_net* n);                      // device error word of a network
 }  // namespace fvs

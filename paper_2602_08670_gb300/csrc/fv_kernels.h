@@ -13,6 +13,12 @@ struct Geom {
   double dx, dy;
   float phys;             // g (SWE) or gamma (Euler), as used by the FP32 kernels
   double phys_d;          // the same constant in FP64 (diagnostics)
+  // Cells [hx, nx - hx) x [hy, ny - hy) are the grid's interior: the CFL
+  // reduction, the health bits and the diagnostics cover them only.  A state
+  // that is one subdomain of a decomposed grid carries a ring of hx columns
+  // and hy rows of its neighbours' cells, refreshed before every stage; a
+  // whole periodic grid has hx = hy = 0.
+  int hx, hy;
   long long plane() const { return (long long)nx * ny; }
   long long member() const { return plane() * C; }
 };
@@ -58,9 +64,9 @@ cudaError_t enqueue_sphere_step(const Geom& g, int flux, float* qa, float* qb, c
                                 Ctrl* ctrl, const DtParams* dp, cudaStream_t s);
 
 // Wave-speed reduction of q that sets each member's dt without advancing
-// time (state creation, fv_set_state).
+// time (state creation, fv_set_state); member >= 0: that member only.
 cudaError_t launch_wavespeed_init(const Geom& g, const float* q, Ctrl* ctrl, const DtParams* dp,
-                                  cudaStream_t s);
+                                  cudaStream_t s, int member = -1);
 
 // FP64 sums [B][C+1] into device memory `out` (deterministic order).
 // `partials` must hold diag_partials_size(g) doubles.

@@ -50,6 +50,7 @@ struct LArgs {
   int nx, ny;
   long long plane, member;
   float rdx, rdy, g;
+  int hx, hy;          // ring of a subdomain: outside the CFL reduction
 };
 
 template <int STAGE>
@@ -138,7 +139,13 @@ __global__ void __launch_bounds__(NT) stage_learned_kernel(LArgs a) {
       out[c] = STAGE == 1 ? rk_stage1<float>(q, dt, L) : rk_stage2<float>(qn[c * a.plane + off], q, 0.5f * dt, L);
       qout[c * a.plane + off] = out[c];
     }
-    if (STAGE == 2) amax = fmaxf(amax, cell_rate_swe(out[0], out[1], out[2], a.g, a.rdx, a.rdy, bad));
+    if (STAGE == 2) {
+      unsigned bk = 0u;
+      const float sp = cell_rate_swe(out[0], out[1], out[2], a.g, a.rdx, a.rdy, bk);
+      const bool in = gx >= a.hx && gx < a.nx - a.hx && gy >= a.hy && gy < a.ny - a.hy;
+      amax = in ? fmaxf(amax, sp) : amax;
+      bad |= in ? bk : 0u;
+    }
   }
   if (STAGE == 2) {
     block_reduce_max_or(amax, bad, red);
@@ -156,6 +163,7 @@ struct FArgs {
   int nx, ny;
   long long plane, member;
   float rdx, rdy, g;
+  int hx, hy;          // ring of a subdomain: outside the CFL reduction
 };
 
 enum { SIDE_W = 0, SIDE_E = 1, SIDE_S = 2, SIDE_N = 3 };
@@ -235,7 +243,13 @@ __global__ void __launch_bounds__(NT) stage_face_kernel(FArgs a) {
       out[c] = STAGE == 1 ? rk_stage1<float>(q, dt, L) : rk_stage2<float>(qn[c * a.plane + off], q, 0.5f * dt, L);
       qout[c * a.plane + off] = out[c];
     }
-    if (STAGE == 2) amax = fmaxf(amax, cell_rate_swe(out[0], out[1], out[2], a.g, a.rdx, a.rdy, bad));
+    if (STAGE == 2) {
+      unsigned bk = 0u;
+      const float sp = cell_rate_swe(out[0], out[1], out[2], a.g, a.rdx, a.rdy, bk);
+      const bool in = gx >= a.hx && gx < a.nx - a.hx && gy >= a.hy && gy < a.ny - a.hy;
+      amax = in ? fmaxf(amax, sp) : amax;
+      bad |= in ? bk : 0u;
+    }
   }
   if (STAGE == 2) {
     block_reduce_max_or(amax, bad, red);
@@ -263,7 +277,7 @@ cudaError_t launch_face_t(const FArgs& a, const Geom& g, cudaStream_t s) {
 cudaError_t launch_stage_face(const Geom& g, int stage, const float* qin, const float* qn, float* qout,
                               const float* sides, Ctrl* ctrl, const DtParams* dp, cudaStream_t s) {
   FArgs a{qin, qn, qout, sides, ctrl, dp, g.nx, g.ny, g.plane(), g.member(),
-          (float)(1.0 / g.dx), (float)(1.0 / g.dy), g.phys};
+          (float)(1.0 / g.dx), (float)(1.0 / g.dy), g.phys, g.hx, g.hy};
   return stage == 1 ? launch_face_t<1>(a, g, s) : launch_face_t<2>(a, g, s);
 }
 
@@ -272,7 +286,7 @@ cudaError_t launch_stage_learned(const Geom& g, int stage, const float* qin, con
                                  const DtParams* dp, cudaStream_t s) {
   constexpr int smem = learned_smem_bytes();
   LArgs a{qin, qn, qout, w, hmin, ctrl, dp, g.nx, g.ny, g.plane(), g.member(),
-          (float)(1.0 / g.dx), (float)(1.0 / g.dy), g.phys};
+          (float)(1.0 / g.dx), (float)(1.0 / g.dy), g.phys, g.hx, g.hy};
   dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, g.B);
   if (stage == 1) {
     static bool attr = false;
@@ -367,40 +381,70 @@ int learned_prepare(fv_state* s, const fv_net* net) {
   return learned_ws_ready(s, s->hmin_frac);
 }
 
-cudaError_t enqueue_learned_step(fv_state* s, const fv_net* net) {
+cudaError_t enqueue_learned_stage(fv_state* s, const fv_net* net, int stage) {
   if (!s->lws) return cudaErrorNotReady;   // learned_prepare() must run first (host side)
   fv_learned_ws* w = s->lws;
+  const int B = s->g.B, ny = s->g.ny, nx = s->g.nx;
+  // stage 1: q^n (qA) -> q1 (qB); stage 2: q1 (qB), q^n (qA) -> q^{n+1} (qA)
+  float* qin = stage == 1 ? s->qA : s->qB;
+  const float* qn = stage == 1 ? nullptr : s->qA;
+  float* qout = stage == 1 ? s->qB : s->qA;
   if (is_face(net)) {
     if (!w->sides) return cudaErrorNotReady;
-    const int B = s->g.B, ny = s->g.ny, nx = s->g.nx;
-    cudaError_t e = snk::forward_faces(net->n, s->qA, B, ny, nx, w->acts, w->sides, nullptr, s->stream);
+    cudaError_t e = snk::forward_faces(net->n, qin, B, ny, nx, w->acts, w->sides, nullptr, s->stream);
     if (e != cudaSuccess) return e;
-    e = fvk::launch_stage_face(s->g, 1, s->qA, nullptr, s->qB, w->sides, s->ctrl, s->dp, s->stream);
-    if (e != cudaSuccess) return e;
-    e = snk::forward_faces(net->n, s->qB, B, ny, nx, w->acts, w->sides, nullptr, s->stream);
-    if (e != cudaSuccess) return e;
-    return fvk::launch_stage_face(s->g, 2, s->qB, s->qA, s->qA, w->sides, s->ctrl, s->dp, s->stream);
+    return fvk::launch_stage_face(s->g, stage, qin, qn, qout, w->sides, s->ctrl, s->dp, s->stream);
   }
   if (!w->hmin) return cudaErrorNotReady;
-  if (use_fused(s)) {
-    cudaError_t e = fvk::launch_learned_fused(s->g, 1, s->qA, nullptr, s->qB, net->n, w->hmin, s->ctrl,
-                                              s->dp, s->stream);
-    if (e != cudaSuccess) return e;
-    return fvk::launch_learned_fused(s->g, 2, s->qB, s->qA, s->qA, net->n, w->hmin, s->ctrl, s->dp,
-                                     s->stream);
-  }
+  if (use_fused(s))
+    return fvk::launch_learned_fused(s->g, stage, qin, qn, qout, net->n, w->hmin, s->ctrl, s->dp, s->stream);
   if (!w->w) return cudaErrorNotReady;
-  const int B = s->g.B, ny = s->g.ny, nx = s->g.nx;
-  cudaError_t e = snk::forward(net->n, s->qA, B, ny, nx, w->acts, w->w, nullptr, s->stream);
+  cudaError_t e = snk::forward(net->n, qin, B, ny, nx, w->acts, w->w, nullptr, s->stream);
   if (e != cudaSuccess) return e;
-  e = fvk::launch_stage_learned(s->g, 1, s->qA, nullptr, s->qB, w->w, w->hmin, s->ctrl, s->dp, s->stream);
+  return fvk::launch_stage_learned(s->g, stage, qin, qn, qout, w->w, w->hmin, s->ctrl, s->dp, s->stream);
+}
+
+cudaError_t enqueue_learned_step(fv_state* s, const fv_net* net) {
+  cudaError_t e = enqueue_learned_stage(s, net, 1);
   if (e != cudaSuccess) return e;
-  e = snk::forward(net->n, s->qB, B, ny, nx, w->acts, w->w, nullptr, s->stream);
-  if (e != cudaSuccess) return e;
-  return fvk::launch_stage_learned(s->g, 2, s->qB, s->qA, s->qA, w->w, w->hmin, s->ctrl, s->dp, s->stream);
+  return enqueue_learned_stage(s, net, 2);
+}
+
+int learned_set_hmin_values(fv_state* s, const double* hmin) {
+  if (learned_hmin_fixed(s)) return fvh::fail(FV_EINVAL, "h_min is already fixed (a learned step was taken)");
+  if (!s->lws) s->lws = new fv_learned_ws();
+  std::vector<float> hm(s->g.B);
+  for (int b = 0; b < s->g.B; ++b) {
+    if (!(hmin[b] >= 0.0)) return fvh::fail(FV_EINVAL, "h_min must be >= 0");
+    hm[b] = (float)hmin[b];
+  }
+  float* d = nullptr;
+  cudaError_t e = cudaMalloc(&d, sizeof(float) * s->g.B);
+  if (e == cudaSuccess) e = cudaMemcpy(d, hm.data(), sizeof(float) * s->g.B, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(d);
+    return fvh::cuda_fail(e, "h_min values");
+  }
+  s->lws->hmin = d;
+  return FV_OK;
 }
 
 bool learned_hmin_fixed(const fv_state* s) { return s->lws && s->lws->hmin; }
+
+float* learned_hmin_ptr(fv_state* s) { return s->lws ? s->lws->hmin : nullptr; }
+
+long long learned_ws_bytes(const fv_state* s) {
+  if (!s->lws) return 0;
+  const fv_learned_ws* w = s->lws;
+  const long long cells = (long long)s->g.B * s->g.plane();
+  long long b = 0;
+  if (w->w) b += 36LL * 4 * cells;
+  if (w->sides) b += (long long)snk::N_OUT_FACE * 4 * cells;
+  if (w->hmin) b += 4LL * s->g.B;
+  for (int l = 0; l < 3; ++l)
+    if (w->acts.a[l]) b += 2LL * 32 * w->acts.cells;
+  return b;
+}
 
 void learned_workspace_free(fv_state* s) {
   if (!s->lws) return;

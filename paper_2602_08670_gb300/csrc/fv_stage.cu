@@ -43,7 +43,16 @@ struct StageArgs {
   int flux;            // fvk::Flux of the generic row-march stages
   int bc;              // BC_PERIODIC / BC_WALL (generic row-march stages)
   const float* z;      // shallow-water bed [ny][nx] or null (generic row-march stages)
+  int wx0, wx1, wy0, wy1;   // interior [wx0, wx1) x [wy0, wy1): the CFL reduction's cells
 };
+
+// The interior window of a geometry (the whole grid unless it carries a ring).
+inline void set_window(StageArgs& a, const Geom& g) {
+  a.wx0 = g.hx;
+  a.wx1 = g.nx - g.hx;
+  a.wy0 = g.hy;
+  a.wy1 = g.ny - g.hy;
+}
 
 // Normal-frame flux of one face from its four-cell stencil.  `rot` selects the
 // y-face frame (normal momentum = component 2).
@@ -155,12 +164,15 @@ __global__ void __launch_bounds__(NT) stage_minmod_kernel(StageArgs a) {
     }
     if (STAGE == 2) {
       float s;
+      unsigned bk = 0u;
       if constexpr (EQ == SWE) {
-        s = cell_rate_swe(out[0], out[1], out[2], a.phys, a.rdx, a.rdy, bad);
+        s = cell_rate_swe(out[0], out[1], out[2], a.phys, a.rdx, a.rdy, bk);
       } else {
-        s = cell_rate_euler(out, a.phys, a.rdx, a.rdy, bad);
+        s = cell_rate_euler(out, a.phys, a.rdx, a.rdy, bk);
       }
-      amax = fmaxf(amax, s);
+      const bool in = gx >= a.wx0 && gx < a.wx1 && gy >= a.wy0 && gy < a.wy1;
+      amax = in ? fmaxf(amax, s) : amax;
+      bad |= in ? bk : 0u;
     }
   }
   if (STAGE == 2) {
@@ -198,9 +210,9 @@ __global__ void __launch_bounds__(NT) stage_minmod_kernel(StageArgs a) {
 // ---------------------------------------------------------------------------
 constexpr int MT = 128;           // threads per block
 constexpr int MW = 4 * MT;        // strip width
-constexpr int MS = 8;             // ring rows
-constexpr int MPF = 3;            // rows prefetched ahead (MS >= MPF + 4)
 constexpr int RS = MW + 8;        // ring row stride: 4 left pad (2 used) + MW + 4 right
+constexpr int MS = 8;             // ring rows
+constexpr int MPF = 3;            // rows prefetched ahead (MS >= MPF + 4: rows r-3 .. r+MPF in use)
 static_assert(MS >= MPF + 4, "ring too shallow for the prefetch depth");
 
 template <int C>
@@ -297,7 +309,7 @@ __global__ void __launch_bounds__(MT) stage_march_kernel(StageArgs a, int TY) {
   int i_next = 0;
 
   auto issue_next = [&]() {
-    float* slot = ring + (i_next & (MS - 1)) * C * RS;
+    float* slot = ring + ((unsigned)i_next % MS) * C * RS;
     int gy = gy_next;
     if (wall) {
       // virtual row Y0 - 2 + i_next lies in [-2, ny + 1]: mirror it inside
@@ -372,9 +384,9 @@ __global__ void __launch_bounds__(MT) stage_march_kernel(StageArgs a, int TY) {
     __syncthreads();
     if (i < 2 || !active) continue;
 
-    const float* s0 = ring + ((i - 2) & (MS - 1)) * C * RS;   // row r-2
-    const float* s1 = ring + ((i - 1) & (MS - 1)) * C * RS;   // row r-1
-    const float* s2 = ring + (i & (MS - 1)) * C * RS;         // row r
+    const float* s0 = ring + ((unsigned)(i - 2) % MS) * C * RS;   // row r-2
+    const float* s1 = ring + ((unsigned)(i - 1) % MS) * C * RS;   // row r-1
+    const float* s2 = ring + ((unsigned)i % MS) * C * RS;         // row r
     // a ghost row behind a wall carries the mirrored normal momentum -hv
     float m0 = 1.f, m1 = 1.f, m2 = 1.f;
     if (wall) {
@@ -520,18 +532,23 @@ __global__ void __launch_bounds__(MT) stage_march_kernel(StageArgs a, int TY) {
           *reinterpret_cast<float4*>(qout + c * plane + off) =
               make_float4(out[c][0].x, out[c][0].y, out[c][1].x, out[c][1].y);
         if (CFL_STAGE) {
+          const bool row_in = orow >= a.wy0 && orow < a.wy1;
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
             float v[C];
 #pragma unroll
             for (int c = 0; c < C; ++c) v[c] = (k & 1) ? out[c][k >> 1].y : out[c][k >> 1].x;
             float sp;
+            unsigned bk = 0u;
             if constexpr (EQ == SWE) {
-              sp = cell_rate_swe(v[0], v[1], v[2], a.phys, a.rdx, a.rdy, bad);
+              sp = cell_rate_swe(v[0], v[1], v[2], a.phys, a.rdx, a.rdy, bk);
             } else {
-              sp = cell_rate_euler(v, a.phys, a.rdx, a.rdy, bad);
+              sp = cell_rate_euler(v, a.phys, a.rdx, a.rdy, bk);
             }
-            amax = fmaxf(amax, sp);
+            const int x = X0 + 4 * t + k;
+            const bool in = row_in && x >= a.wx0 && x < a.wx1;
+            amax = in ? fmaxf(amax, sp) : amax;
+            bad |= in ? bk : 0u;
           }
         }
       }
@@ -558,14 +575,17 @@ template <int C, int EQ>
 __global__ void __launch_bounds__(256) wavespeed_init_kernel(const float* q, Ctrl* ctrl,
                                                              const DtParams* dp, int nx, int ny,
                                                              long long plane, long long member,
-                                                             float phys, float rdx, float rdy) {
+                                                             float phys, float rdx, float rdy, int hx,
+                                                             int hy, int b0) {
   __shared__ unsigned red[16];
-  const int b = blockIdx.y;
+  const int b = b0 + blockIdx.y;
   const float* qb = q + b * member;
   float amax = 0.f;
   unsigned bad = 0u;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < plane;
        i += (long long)gridDim.x * blockDim.x) {
+    const int y = (int)(i / nx), x = (int)(i - (long long)y * nx);
+    if (x < hx || x >= nx - hx || y < hy || y >= ny - hy) continue;   // ring of a subdomain
     float v[C];
 #pragma unroll
     for (int c = 0; c < C; ++c) v[c] = qb[c * plane + i];
@@ -590,7 +610,8 @@ constexpr int DIAG_NT = 256;
 template <int C, int EQ>
 __global__ void __launch_bounds__(DIAG_NT) diag_partial_kernel(const float* q, double* partials,
                                                                long long plane, long long member,
-                                                               double phys) {
+                                                               double phys, int nx, int ny, int hx,
+                                                               int hy) {
   __shared__ double sh[DIAG_NT];
   const int b = blockIdx.y;
   const float* qb = q + b * member;
@@ -599,6 +620,10 @@ __global__ void __launch_bounds__(DIAG_NT) diag_partial_kernel(const float* q, d
   for (int c = 0; c <= C; ++c) acc[c] = 0.0;
   for (long long i = blockIdx.x * (long long)DIAG_NT + threadIdx.x; i < plane;
        i += (long long)DIAG_BLOCKS * DIAG_NT) {
+    if (hx | hy) {
+      const int y = (int)(i / nx), x = (int)(i - (long long)y * nx);
+      if (x < hx || x >= nx - hx || y < hy || y >= ny - hy) continue;   // ring of a subdomain
+    }
     double v[C];
 #pragma unroll
     for (int c = 0; c < C; ++c) {
@@ -640,7 +665,7 @@ __global__ void set_t_end_kernel(Ctrl* ctrl, int B, double t_end) {
   if (b >= B) return;
   Ctrl* c = ctrl + b;
   c->t_end = t_end;
-  c->done = c->exhausted;
+  c->done = c->exhausted | (c->step_end > 0 && c->step >= c->step_end ? 1u : 0u);
   if (t_end > 0.0) {
     const double rem = t_end - c->t;
     if (rem <= 0.0) {
@@ -715,6 +740,7 @@ cudaError_t launch_general_t(const Geom& g, int stage, int flux, const float* qi
                              const float* z) {
   StageArgs a{qin, qn, qout, ctrl, dp, g.nx, g.ny, g.plane(), g.member(),
               (float)(1.0 / g.dx), (float)(1.0 / g.dy), g.phys, flux, bc, z};
+  set_window(a, g);
   if (bc != BC_PERIODIC || z) return launch_general_b<C, EQ, true>(a, g, stage, s);
   return launch_general_b<C, EQ, false>(a, g, stage, s);
 }
@@ -724,6 +750,7 @@ cudaError_t launch_stage_t(const Geom& g, const float* qin, const float* qn, flo
                            Ctrl* ctrl, const DtParams* dp, cudaStream_t s, int variant) {
   StageArgs a{qin, qn, qout, ctrl, dp, g.nx, g.ny, g.plane(), g.member(),
               (float)(1.0 / g.dx), (float)(1.0 / g.dy), g.phys, 0};
+  set_window(a, g);
   const bool march_ok = (g.nx % 4 == 0) && g.nx >= 8;
   if (variant == STAGE_MARCH && !march_ok) return cudaErrorInvalidValue;
   if (variant != STAGE_TILE && march_ok) return launch_march<C, EQ, STAGE, false>(a, g, s);
@@ -765,18 +792,19 @@ cudaError_t launch_stage_general(const Geom& g, int stage, int flux, const float
 }
 
 cudaError_t launch_wavespeed_init(const Geom& g, const float* q, Ctrl* ctrl, const DtParams* dp,
-                                  cudaStream_t s) {
+                                  cudaStream_t s, int member) {
   long long blocks = (g.plane() + 255) / 256;
   if (blocks > 1024) blocks = 1024;
-  dim3 grid((unsigned)blocks, g.B);
+  const int b0 = member < 0 ? 0 : member;
+  dim3 grid((unsigned)blocks, member < 0 ? g.B : 1);
   if (g.eq == SWE) {
     wavespeed_init_kernel<3, SWE><<<grid, 256, 0, s>>>(q, ctrl, dp, g.nx, g.ny, g.plane(),
                                                        g.member(), g.phys, (float)(1.0 / g.dx),
-                                                       (float)(1.0 / g.dy));
+                                                       (float)(1.0 / g.dy), g.hx, g.hy, b0);
   } else {
     wavespeed_init_kernel<4, EULER><<<grid, 256, 0, s>>>(q, ctrl, dp, g.nx, g.ny, g.plane(),
                                                          g.member(), g.phys, (float)(1.0 / g.dx),
-                                                         (float)(1.0 / g.dy));
+                                                         (float)(1.0 / g.dy), g.hx, g.hy, b0);
   }
   return cudaGetLastError();
 }
@@ -788,10 +816,10 @@ cudaError_t launch_diagnostics(const Geom& g, const float* q, double* partials, 
   dim3 grid(DIAG_BLOCKS, g.B);
   if (g.eq == SWE) {
     diag_partial_kernel<3, SWE><<<grid, DIAG_NT, 0, s>>>(q, partials, g.plane(), g.member(),
-                                                         g.phys_d);
+                                                         g.phys_d, g.nx, g.ny, g.hx, g.hy);
   } else {
     diag_partial_kernel<4, EULER><<<grid, DIAG_NT, 0, s>>>(q, partials, g.plane(), g.member(),
-                                                           g.phys_d);
+                                                           g.phys_d, g.nx, g.ny, g.hx, g.hy);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;

@@ -145,6 +145,14 @@ int state_alloc(fv_state* s) {
   return FV_OK;
 }
 
+long long state_device_bytes(const fv_state* s) {
+  const long long q = (long long)s->g.member() * s->g.B * (long long)sizeof(float);
+  long long b = 2 * q + (s->qC ? q : 0);
+  b += (long long)sizeof(fvk::Ctrl) * s->g.B + (long long)sizeof(fvk::DtParams);
+  b += (long long)sizeof(double) * (fvk::diag_partials_size(s->g) + (long long)s->g.B * (s->g.C + 1));
+  return b + learned_ws_bytes(s);
+}
+
 void state_free(fv_state* s) {
   if (!s) return;
   if (s->stream) cudaStreamSynchronize(s->stream);
@@ -197,6 +205,12 @@ cudaError_t enqueue_plain_step(fv_state* s) {
   if (e != cudaSuccess) return e;
   return fvk::launch_stage_minmod(s->g, 2, s->qB, s->qA, s->qA, s->ctrl, s->dp, s->stream,
                                   s->variant);
+}
+
+cudaError_t enqueue_plain_stage(fv_state* s, int stage) {
+  if (stage == 1)
+    return fvk::launch_stage_minmod(s->g, 1, s->qA, nullptr, s->qB, s->ctrl, s->dp, s->stream, s->variant);
+  return fvk::launch_stage_minmod(s->g, 2, s->qB, s->qA, s->qA, s->ctrl, s->dp, s->stream, s->variant);
 }
 
 cudaError_t enqueue_step(fv_state* s, const fv_net* net) {

@@ -105,6 +105,15 @@ _SIGS = {
     "fv_diagnostics_noalloc": [c_void_p, c_int, c_int, c_int, c_int, c_double, c_double, c_double,
                                c_void_p, c_int, c_void_p],
     "fv_get_time": [c_void_p, c_void_p, c_void_p, c_void_p],
+    "fv_set_halo": [c_void_p, c_int, c_int],
+    "fv_enqueue_stage": [c_void_p, c_void_p, c_int],
+    "fv_halo_exchange": [c_void_p, c_int, c_int, c_int],
+    "fv_reduce_dt": [c_void_p, c_int],
+    "fv_halo_pack": [c_void_p, c_int, c_int, c_void_p],
+    "fv_halo_unpack": [c_void_p, c_int, c_int, c_void_p],
+    "fv_halo_strip_floats": [c_void_p, c_int, ctypes.POINTER(ctypes.c_longlong)],
+    "fv_set_dt": [c_void_p, c_void_p],
+    "fv_set_learned_hmin_values": [c_void_p, c_void_p],
     "fv_health": [c_void_p, c_void_p],
     "fv_diagnostics": [c_void_p, c_void_p],
 }
@@ -316,6 +325,55 @@ def fv_diagnostics(s: State) -> np.ndarray:
     out = np.zeros((B, C + 1), dtype=np.float64)
     _check(lib().fv_diagnostics(s.handle, out.ctypes.data_as(c_void_p)))
     return out
+
+
+# ---------------------------------------------------------------------------
+# Subdomains of a block-decomposed grid (see decomp.py)
+# ---------------------------------------------------------------------------
+
+def fv_set_halo(s: State, hx: int, hy: int) -> None:
+    _check(lib().fv_set_halo(s.handle, int(hx), int(hy)))
+
+
+def fv_enqueue_stage(s: State, stage: int, net=None) -> None:
+    _check(lib().fv_enqueue_stage(s.handle, _net_handle(net), int(stage)))
+
+
+def fv_halo_exchange(subs_array, px: int, py: int, buf: int) -> None:
+    """subs_array: a ctypes array of the px * py state handles (block order)."""
+    _check(lib().fv_halo_exchange(ctypes.cast(subs_array, c_void_p), int(px), int(py), int(buf)))
+
+
+def fv_reduce_dt(subs_array, n: int) -> None:
+    _check(lib().fv_reduce_dt(ctypes.cast(subs_array, c_void_p), int(n)))
+
+
+def fv_halo_strip_floats(s: State, side: int) -> int:
+    n = ctypes.c_longlong()
+    _check(lib().fv_halo_strip_floats(s.handle, int(side), ctypes.byref(n)))
+    return n.value
+
+
+def fv_halo_pack(s: State, buf: int, side: int, dst: torch.Tensor) -> None:
+    _check(lib().fv_halo_pack(s.handle, int(buf), int(side), _dev(dst)))
+
+
+def fv_halo_unpack(s: State, buf: int, side: int, src: torch.Tensor) -> None:
+    _check(lib().fv_halo_unpack(s.handle, int(buf), int(side), _dev(src)))
+
+
+def fv_set_dt(s: State, dt) -> None:
+    a = np.ascontiguousarray(np.asarray(dt, dtype=np.float64))
+    if a.size != s.shape[0]:
+        raise ValueError("one dt per member")
+    _check(lib().fv_set_dt(s.handle, a.ctypes.data_as(c_void_p)))
+
+
+def fv_set_learned_hmin_values(s: State, hmin) -> None:
+    a = np.ascontiguousarray(np.asarray(hmin, dtype=np.float64))
+    if a.size != s.shape[0]:
+        raise ValueError("one h_min per member")
+    _check(lib().fv_set_learned_hmin_values(s.handle, a.ctypes.data_as(c_void_p)))
 
 
 # ---------------------------------------------------------------------------

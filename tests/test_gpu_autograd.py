@@ -5,18 +5,18 @@ the GPU forward itself, along random directions.
 Loss: L = sum_t <w_t, q_t> over the T = 2 step snapshots with fixed random
 weights w (FP64 accumulation), so that dL/dsnaps = w is the cotangent the
 Function's backward receives.  Directions and their step sizes:
-  * FP32 directions: the last layer's biases (added in FP32 after the tensor
-    cores; the coefficients, the learned faces, HLL and the RK combine are
-    FP32, so the forward is smooth in them) and the initial state through a
-    network whose last-layer weights are zero (constant stencils: only the
-    FP32 flux path depends on q0).  Relative steps of about 1e-2 (biases) and
-    1e-4 (state); tolerance 1e-3 relative.
+  * FP32 directions, through a network whose last-layer weights are zero
+    (its stencils are the constants its last-layer biases set, so no
+    derivative passes through a BF16 layer): the last layer's biases (added
+    in FP32 after the tensor cores; coefficients, learned faces, HLL and the
+    RK combine are FP32) and the initial state.  Steps: at most 0.1 on a
+    bias, 1e-3 on a depth; tolerance 1e-3 relative (L2 over the directions).
   * BF16 directions: all parameters (multiplicative, 3 % per weight) and the
     initial state through a full random network.  Weights and activations are
     rounded to BF16 on the way to the tensor cores, so the forward is a
     staircase at the 2^-9 relative scale and the step must be much larger than
     that; the backward differentiates the rounding as the identity.
-    Tolerance 5e-2 relative.
+    Tolerance 5e-2 relative (L2 over the directions).
 """
 import numpy as np
 import pytest
@@ -86,18 +86,33 @@ def _fd(fv, tape, w, params, q0, dp, dq, eps):
 
 
 def _check(fv, tape, w, params, q0, dirs, tol):
+    """Relative L2 over the directions of (finite difference - autograd) of
+    the directional derivatives.  `dirs` holds (dparams, dq0, eps) or
+    ("grad", scale, eps): a direction along the autograd gradient itself,
+    scaled per component by U[0.5, 1.5] (its derivative cannot vanish)."""
     gp, gq = _grads(fv, tape, w, params, q0)
-    errs = []
+    gen = torch.Generator(device="cuda").manual_seed(99)
+    ad, fd = [], []
     for dp, dq, eps in dirs:
-        ad = float((gp.double() * dp.double()).sum() + (gq.double() * dq.double()).sum())
-        fd = _fd(fv, tape, w, params, q0, dp, dq, eps)
-        errs.append(abs(fd - ad) / max(abs(fd), 1e-30))
-    assert max(errs) <= tol, errs
+        if isinstance(dp, str):
+            dp = gp * (0.5 + torch.rand(gp.shape, generator=gen, device="cuda")) * dq
+            dq = torch.zeros_like(q0)
+            # largest parameter change: 1 % of the largest parameter
+            eps = 1e-2 * float(params.abs().max()) / float(dp.abs().max())
+        ad.append(float((gp.double() * dp.double()).sum() + (gq.double() * dq.double()).sum()))
+        fd.append(_fd(fv, tape, w, params, q0, dp, dq, eps))
+    ad, fd = np.array(ad), np.array(fd)
+    err = float(np.linalg.norm(fd - ad) / np.linalg.norm(fd))
+    assert err <= tol, (err, list(zip(fd.tolist(), ad.tolist())))
 
 
 def test_autograd_matches_finite_differences_fp32_directions(fv):
+    # zero last-layer weights: the stencils are the constants set by the
+    # last layer's biases, so no derivative passes through the BF16 layers
+    # (with random last-layer weights a bias change of stage 1 reaches the
+    # next stage's CNN input, whose cotangents are BF16)
     gen = torch.Generator(device="cuda").manual_seed(11)
-    params = _params(6)
+    params = _params(6, zero_w4=True)
     tape, w = _setup(fv, params)
     q0 = _state(21)
     nb4 = 36
@@ -105,18 +120,13 @@ def test_autograd_matches_finite_differences_fp32_directions(fv):
     for _ in range(3):
         dp = torch.zeros_like(params)
         dp[-nb4:] = torch.randn(nb4, generator=gen, device="cuda")
-        dirs.append((dp, torch.zeros_like(q0), 1e-2 / float(dp.abs().max())))
-    _check(fv, tape, w, params, q0, dirs, TOL_FP32)
-    # initial-state directions through constant stencils (zero last-layer weights)
-    params0 = _params(6, zero_w4=True)
-    tape0, w0 = _setup(fv, params0)
-    dirs = []
+        dirs.append((dp, torch.zeros_like(q0), 1e-1 / float(dp.abs().max())))
     for _ in range(3):
         dq = torch.randn(q0.shape, generator=gen, device="cuda")
         dq[:, 0] *= 0.05
         dq[:, 1:] *= 0.02
-        dirs.append((torch.zeros_like(params0), dq, 1e-4 / float(dq.abs().max() / 0.05)))
-    _check(fv, tape0, w0, params0, q0, dirs, TOL_FP32)
+        dirs.append((torch.zeros_like(params), dq, 1e-3 / float(dq[:, 0].abs().max())))
+    _check(fv, tape, w, params, q0, dirs, TOL_FP32)
 
 
 def test_autograd_matches_finite_differences_bf16_directions(fv):
@@ -128,6 +138,8 @@ def test_autograd_matches_finite_differences_bf16_directions(fv):
     for _ in range(3):
         dp = params * torch.randn(params.shape, generator=gen, device="cuda")
         dirs.append((dp, torch.zeros_like(q0), 3e-2))
+    # along the gradient: 3 % of the largest parameter change per unit
+    dirs.append(("grad", 1.0, None))
     for _ in range(2):
         dq = torch.randn(q0.shape, generator=gen, device="cuda")
         dq[:, 0] *= 0.05
