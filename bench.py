@@ -384,17 +384,32 @@ def learned_block(args):
     it_ms = 1e3 * res.seconds / res.iters
     # forward 2 passes x 59328 FLOP per cell and stage-1/2 ... per step; backward ~2x forward
     fwd = 64 * 64 * 64 * 16 * 59328
+    burst = _bf16_burst_peak()
+    tfl = 3 * fwd / (it_ms * 1e-3) / 1e12
     out["training"] = {"workload": "batch 64 windows, 64^2, T = 8 steps (16 stages), forward + "
                                    "Eq. 2.28 loss + backward + Adam",
                        "ms_per_iteration": it_ms,
                        "cnn_flop_per_iteration": 3 * fwd,
-                       "cnn_tflops": 3 * fwd / (it_ms * 1e-3) / 1e12}
+                       "roofline": {"bound": "tensor", "achieved": tfl, "peak": burst, "unit": "TFLOP/s",
+                                    "frac": tfl / burst, "peak_kind": "measured bf16 burst",
+                                    "algorithmic": "59328 FLOP per cell and CNN pass x 64 windows x 64^2 "
+                                                   "cells x 16 stages, x3 with the backward"}}
     fnet_t = fv.face_net_create(TR.init_params(0, kind="face", depth=float(TR.data_stats(tr)[0][0])),
                                 *TR.input_scale(tr))
     TR.train(tr, iters=3, batch=64, T=8, net=fnet_t)
     res = TR.train(tr, iters=10, batch=64, T=8, net=fnet_t)
     out["face_state_training"] = {"ms_per_iteration": 1e3 * res.seconds / res.iters}
     return out
+
+
+def _bf16_burst_peak() -> float:
+    """Measured burst BF16 tensor throughput (TFLOP/s), else the recipe's
+    fallback."""
+    pp = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pp):
+        with open(pp) as f:
+            return float(json.load(f).get("bf16_tflops", 1900.0))
+    return 1900.0
 
 
 def _bf16_sustained_peak() -> float:

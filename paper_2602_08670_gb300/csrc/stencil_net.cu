@@ -790,6 +790,239 @@ __global__ void dx_first_kernel(const uint16_t* dy, const float* W1, float* dq, 
   d[2 * plane] += acc[2] * r2;
 }
 
+// ---------------------------------------------------------------------------
+// Weight and bias gradients on the tensor cores.
+//
+//   dW[co][ci][tap] = sum_p dy[p][co] x[p + off(tap)][ci],   db[co] = sum_p dy[p][co]
+//
+// as one GEMM per CTA over a contiguous range of cells p (K): D[r][co] =
+// sum_p A[r][p] B[co][p] with A the 9-tap im2col of the layer input (rows
+// r = tap * CI + ci) plus a row of ones (r = 9 CI, which yields db), and B
+// the output cotangent (rows co, padded to NB).  Both operands are staged per
+// K-tile of 64 cells in the K-major canonical layout (core matrices of 8
+// rows x 8 cells, 16 bytes per row): the staging transposes the
+// [group][cell][8 channels] records of global memory and applies the tap
+// shifts with periodic wrap.  Two stage buffers alternate: the threads stage
+// tile i+1 while the tensor core runs the MMAs of tile i (one thread issues
+// MT x 4 tcgen05.mma of M = 128, N = NB, K = 16 per tile and commits them to
+// the buffer's mbarrier).  The FP32 accumulators stay in TMEM for the CTA's
+// whole range; the epilogue writes them as the CTA's partial sums, which
+// dw_tc_reduce_kernel adds in CTA order (deterministic).  BF16 products are
+// exact in FP32, so only the order of the FP32 sums differs from a CUDA-core
+// reduction.
+constexpr int DWK = 64;                  // cells per K-tile
+constexpr int DW_CTAS = 256;             // CTAs (fixed: the partial sums do not depend on the GPU)
+constexpr uint32_t DW_SBO = (DWK / 8) * 128;   // bytes between 8-row groups
+
+template <int CI>
+constexpr int dw_rows() { return 9 * CI + 1; }
+template <int CI>
+constexpr int dw_mt() { return (dw_rows<CI>() + 127) / 128; }
+template <int CI, int NB>
+constexpr int dw_buf_bytes() { return (dw_mt<CI>() * 128 + NB) * DWK * 2; }
+template <int CI, int NB>
+constexpr int dw_smem_bytes() { return 2 * dw_buf_bytes<CI, NB>() + 64; }
+
+// Byte offset of element (row r, cell k) in a K-major tile of DWK cells.
+__device__ __forceinline__ uint32_t dw_off(int r, int k) {
+  return (uint32_t)(r >> 3) * DW_SBO + (uint32_t)(k >> 3) * 128u + (uint32_t)(r & 7) * 16u + (uint32_t)(k & 7) * 2u;
+}
+
+template <int CI, int CO, int CGO>
+__global__ void __launch_bounds__(NT) dw_tc_kernel(const uint16_t* x, const float* q, const uint16_t* dy,
+                                                   float* part, int nx, int ny, long long plane,
+                                                   long long ntiles, float m0, float m1, float m2, float r0,
+                                                   float r1, float r2, unsigned* err) {
+  constexpr int NB = 8 * CGO;            // padded output channels (N)
+  constexpr int MT = dw_mt<CI>();
+  constexpr int ROWS = MT * 128;
+  constexpr int BUF = dw_buf_bytes<CI, NB>();
+  static_assert(NB % 16 == 0 && NB <= 256, "N of the MMA");
+  static_assert(MT * NB <= 256, "TMEM columns");
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + 2 * BUF);   // [2]
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
+  const int tid = threadIdx.x;
+  const long long t0 = (long long)blockIdx.x * ntiles / gridDim.x;
+  const long long t1 = (long long)(blockIdx.x + 1) * ntiles / gridDim.x;
+  const long long tiles_per_member = plane / DWK;
+
+  // constant rows of both buffers: the ones row (bias) and the zero padding
+  for (int buf = 0; buf < 2; ++buf) {
+    uint8_t* A = smem + buf * BUF;
+    for (int i = tid; i < (ROWS - 9 * CI) * DWK; i += NT) {
+      const int r = 9 * CI + i / DWK, k = i % DWK;
+      *reinterpret_cast<uint16_t*>(A + dw_off(r, k)) = r == 9 * CI ? (uint16_t)0x3F80u : (uint16_t)0u;
+    }
+    uint8_t* Bm = A + ROWS * DWK * 2;
+    for (int i = tid; i < (NB - CO) * DWK; i += NT) {
+      const int n = CO + i / DWK, k = i % DWK;
+      *reinterpret_cast<uint16_t*>(Bm + dw_off(n, k)) = 0;
+    }
+  }
+  if (tid == 0) {
+    tc::mbar_init(&mbar[0], 1);
+    tc::mbar_init(&mbar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if ((tid >> 5) == 0) tc::tmem_alloc(tslot, 256);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tslot;
+  constexpr uint32_t idesc = tc::idesc_bf16_f32(128, NB);
+  bool ok = true;
+  int issued = 0;                        // tiles whose MMAs were issued (the same in every thread)
+
+  for (long long tile = t0; tile < t1; ++tile) {
+    const int i = (int)(tile - t0);
+    const int buf = i & 1;
+    uint8_t* A = smem + buf * BUF;
+    uint8_t* Bm = A + ROWS * DWK * 2;
+    // the buffer is free once the MMAs of tile i - 2 are done
+    if (i >= 2) {
+      const bool w = tc::mbar_wait_bounded(&mbar[buf], (uint32_t)((i - 2) >> 1) & 1u, WAIT_ITERS);
+      ok = __syncthreads_and(w) && ok;
+      if (!ok) break;
+    }
+    const int b = (int)(tile / tiles_per_member);
+    const int p0 = (int)(tile - (long long)b * tiles_per_member) * DWK;
+    // B: output cotangent, one 16-byte record (8 channels of one cell) per item
+    for (int it = tid; it < DWK * CGO; it += NT) {
+      const int k = it % DWK, g = it / DWK;
+      const uint4 v = *reinterpret_cast<const uint4*>(dy + (((long long)b * CGO + g) * plane + p0 + k) * 8);
+      const uint32_t w4[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int n = 8 * g + j;
+        if (n < NB)
+          *reinterpret_cast<uint16_t*>(Bm + dw_off(n, k)) = (uint16_t)(w4[j >> 1] >> (16 * (j & 1)));
+      }
+    }
+    // A: the input at the 9 tap-shifted cells (periodic), rows tap * CI + ci
+    for (int it = tid; it < DWK * 9; it += NT) {
+      const int k = it % DWK, tap = it / DWK;
+      const int p = p0 + k;
+      const int y = p / nx, xx = p - y * nx;
+      const int ys = wrapi(y + tap / 3 - 1, ny), xs = wrapi(xx + tap % 3 - 1, nx);
+      const long long cell = (long long)ys * nx + xs;
+      if constexpr (CI == 3) {
+        const float* qb = q + (long long)b * 3 * plane;
+        const float v[3] = {(qb[cell] - m0) * r0, (qb[plane + cell] - m1) * r1, (qb[2 * plane + cell] - m2) * r2};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const __nv_bfloat16 h = __float2bfloat16_rn(v[c]);
+          *reinterpret_cast<__nv_bfloat16*>(A + dw_off(tap * 3 + c, k)) = h;
+        }
+      } else {
+#pragma unroll
+        for (int g = 0; g < CI / 8; ++g) {
+          const uint4 v = *reinterpret_cast<const uint4*>(x + (((long long)b * (CI / 8) + g) * plane + cell) * 8);
+          const uint32_t w4[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            *reinterpret_cast<uint16_t*>(A + dw_off(tap * CI + 8 * g + j, k)) =
+                (uint16_t)(w4[j >> 1] >> (16 * (j & 1)));
+        }
+      }
+    }
+    tc::fence_proxy_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (tid == 0) {
+      const uint32_t a0 = tc::smem_u32(A), b0 = tc::smem_u32(Bm);
+#pragma unroll
+      for (int mt = 0; mt < MT; ++mt) {
+#pragma unroll
+        for (int ks = 0; ks < DWK / 16; ++ks) {
+          const uint64_t ad = tc::sdesc(a0 + mt * 16 * DW_SBO + ks * 256, 128, DW_SBO);
+          const uint64_t bd = tc::sdesc(b0 + ks * 256, 128, DW_SBO);
+          tc::mma_bf16(tmem + mt * NB, ad, bd, idesc, i > 0 || ks > 0);
+        }
+      }
+      tc::mma_commit(&mbar[buf]);
+    }
+    issued = i + 1;
+  }
+  // every commit issued must have landed before TMEM is read or released: the
+  // last tile issued on each buffer (bounded waits; after a timeout the CTA
+  // flags the error and still releases its TMEM)
+  for (int bb = 0; bb < 2; ++bb) {
+    const int last = issued - 1 - ((issued - 1 - bb) & 1);   // largest tile < issued on buffer bb
+    if (last >= 0) {
+      const bool w = tc::mbar_wait_bounded(&mbar[bb], (uint32_t)(last >> 1) & 1u, WAIT_ITERS);
+      ok = __syncthreads_and(w) && ok;
+    }
+  }
+  const int n = issued;
+  tc::fence_after_sync();
+  if (!ok) {
+    if (tid == 0) atomicOr(err, 1u);
+  } else {
+    // warp w holds TMEM lanes 32w .. 32w+31 = rows 128 mt + 32 w + lane
+    const int warp = tid >> 5, lane = tid & 31;
+    float* pp = part + (long long)blockIdx.x * ROWS * CO;
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt) {
+      const int r = mt * 128 + warp * 32 + lane;
+#pragma unroll
+      for (int c0 = 0; c0 < NB; c0 += 16) {
+        float v[16];
+        tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + mt * NB + c0, v);
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          if (c0 + j < CO && n > 0) pp[(long long)r * CO + c0 + j] = v[j];
+          else if (c0 + j < CO) pp[(long long)r * CO + c0 + j] = 0.f;
+      }
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if ((tid >> 5) == 0) tc::tmem_dealloc(tmem, 256);
+}
+
+// Sum the CTAs' partial sums in CTA order into dparams (PyTorch layout):
+// row r = tap * CI + ci gives dW[co][ci][tap], row 9 CI gives db.
+template <int CI, int CO>
+__global__ void dw_tc_reduce_kernel(const float* part, int nparts, float* dW, float* db, float scale) {
+  constexpr int ROWS = dw_mt<CI>() * 128;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (9 * CI + 1) * CO) return;
+  const int r = i / CO, co = i - r * CO;
+  float s = 0.f;
+  for (int k = 0; k < nparts; ++k) s += part[((long long)k * ROWS + r) * CO + co];
+  if (r < 9 * CI) {
+    const int tap = r / CI, c = r - tap * CI;
+    dW[(co * CI + c) * 9 + tap] += scale * s;
+  } else {
+    db[co] += scale * s;
+  }
+}
+
+template <int CI, int CO, int CGO>
+cudaError_t weight_grad_tc(const uint16_t* x, const float* q, const uint16_t* dy, float* dW, float* db,
+                           float* part, int B, int ny, int nx, const Net& net, float scale, cudaStream_t s) {
+  const long long plane = (long long)nx * ny;
+  const long long ntiles = (long long)B * (plane / DWK);
+  const int nctas = (int)(ntiles < DW_CTAS ? ntiles : DW_CTAS);
+  constexpr int smem = dw_smem_bytes<CI, 8 * CGO>();
+  auto kern = dw_tc_kernel<CI, CO, CGO>;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  kern<<<nctas, NT, smem, s>>>(x, q, dy, part, nx, ny, plane, ntiles, net.mean[0], net.mean[1], net.mean[2],
+                               1.f / net.std_[0], 1.f / net.std_[1], 1.f / net.std_[2], net.err);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int ne = (9 * CI + 1) * CO;
+  dw_tc_reduce_kernel<CI, CO><<<(ne + 255) / 256, 256, 0, s>>>(part, nctas, dW, db, scale);
+  return cudaGetLastError();
+}
+
 template <int CI, int CO, int CGO, bool ROW>
 cudaError_t weight_grad_t(const uint16_t* x, const float* q, const uint16_t* dy, float* dW, float* db,
                           float* part, int B, int ny, int nx, const Net& net, float scale,
@@ -818,6 +1051,8 @@ template <int CI, int CO, int CGO>
 cudaError_t weight_grad(const uint16_t* x, const float* q, const uint16_t* dy, float* dW, float* db,
                         float* part, int B, int ny, int nx, const Net& net, float scale,
                         cudaStream_t s) {
+  if (((long long)nx * ny) % DWK == 0)
+    return weight_grad_tc<CI, CO, CGO>(x, q, dy, dW, db, part, B, ny, nx, net, scale, s);
   if (nx % TILE == 0) return weight_grad_t<CI, CO, CGO, true>(x, q, dy, dW, db, part, B, ny, nx, net, scale, s);
   return weight_grad_t<CI, CO, CGO, false>(x, q, dy, dW, db, part, B, ny, nx, net, scale, s);
 }
@@ -827,7 +1062,9 @@ cudaError_t weight_grad(const uint16_t* x, const float* q, const uint16_t* dy, f
 long long backward_partials_floats(int B, int ny, int nx) {
   const long long ntiles = (long long)B * ((long long)nx * ny / TILE);
   const long long nctas = (ntiles + DW_TILES - 1) / DW_TILES;
-  return nctas * (9 * N_OUT * HID + N_OUT);
+  const long long cuda_cores = nctas * (9 * N_OUT * HID + N_OUT);
+  const long long tensor = (long long)DW_CTAS * dw_mt<HID>() * 128 * N_OUT;   // largest tensor-core layer
+  return cuda_cores > tensor ? cuda_cores : tensor;
 }
 
 cudaError_t backward_reserve(Grads& g, long long cells, long long partial_floats) {

@@ -238,3 +238,18 @@ def test_stencil_net_backward_matches_oracle(fv, ny, nx):
         cos = float(a @ b / (a.norm() * b.norm()))
         rel = float((a - b).norm() / b.norm())
         assert cos >= 0.999 and rel <= 2e-2, (name, cos, rel)
+
+
+@pytest.mark.parametrize("ny,nx", [(64, 64), (32, 256)])
+def test_stencil_net_backward_is_deterministic(fv, ny, nx):
+    """The weight gradients are reduced in a fixed order (per-CTA partial sums
+    over fixed cell ranges, added in CTA order): two calls agree bit for bit."""
+    p = rand_params(8, last_scale=0.3)
+    net = gpu_net(fv, p)
+    q0 = W.as_f32_exact(W.random_smooth_swe(nx, seed=5, members=3, vel=0.2)[:, :, :ny, :])
+    g = torch.Generator().manual_seed(4)
+    dw = torch.randn(3, 36, ny, nx, generator=g).float().cuda()
+    a = fv.net_backward(net, f32(q0).cuda(), dw)
+    b = fv.net_backward(net, f32(q0).cuda(), dw)
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+    assert float(a[0].abs().max()) > 0
