@@ -291,6 +291,18 @@ int fv_set_learned_hmin(fv_state* s, double hmin_frac);
 int fv_diagnostics_noalloc(const float* q, int eq, int batch, int ny, int nx, double lx, double ly,
                            double phys, double* sums, int sums_loc, void* stream);
 
+/* Checkpoints.  fv_checkpoint_bytes gives the size of the host blob that
+ * fv_checkpoint_save fills (synchronous): a header (equations, batch, grid),
+ * every member's control block (time, pending dt, completed steps, health,
+ * stop rules) and the state q^n.  fv_checkpoint_load restores such a blob
+ * into a state of the same equations, batch and grid (FV_EINVAL otherwise);
+ * the steps that follow are bitwise those the saved state would have taken.
+ * Scheme settings (flux, boundary, bed, replay sequence, network) belong to
+ * the state object, not to the checkpoint. */
+int fv_checkpoint_bytes(const fv_state* s, size_t* bytes);
+int fv_checkpoint_save(fv_state* s, void* dst);
+int fv_checkpoint_load(fv_state* s, const void* src);
+
 /* ---------------------------------------------------------------------------
  * Subdomains of a block-decomposed grid
  *

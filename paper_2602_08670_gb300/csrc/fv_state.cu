@@ -569,3 +569,71 @@ extern "C" int fv_state_stream(const fv_state* s, void** stream) {
   *stream = (void*)s->stream;
   return FV_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Checkpoints: a host blob holding a header (magic, version, equations,
+// batch, grid), every member's control block (time, pending dt, steps,
+// health, stop rules) and the state q^n.  Loading it into a state of the same
+// shape and equations resumes the run: the following steps are bitwise those
+// the saved state would have taken.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct CkptHeader {
+  char magic[8];           // "FVCKPT1\0"
+  int eq, C, B, nx, ny;
+  int reserved;
+  long long ctrl_bytes, state_bytes;
+};
+
+constexpr char kCkptMagic[8] = {'F', 'V', 'C', 'K', 'P', 'T', '1', '\0'};
+
+}  // namespace
+
+extern "C" int fv_checkpoint_bytes(const fv_state* s, size_t* bytes) {
+  if (!s || !bytes) return fvh::fail(FV_EINVAL, "null argument");
+  *bytes = sizeof(CkptHeader) + sizeof(fvk::Ctrl) * (size_t)s->g.B + (size_t)s->g.member() * s->g.B * sizeof(float);
+  return FV_OK;
+}
+
+extern "C" int fv_checkpoint_save(fv_state* s, void* dst) {
+  if (!s || !dst) return fvh::fail(FV_EINVAL, "null argument");
+  CkptHeader h{};
+  for (int i = 0; i < 8; ++i) h.magic[i] = kCkptMagic[i];
+  h.eq = s->g.eq;
+  h.C = s->g.C;
+  h.B = s->g.B;
+  h.nx = s->g.nx;
+  h.ny = s->g.ny;
+  h.ctrl_bytes = (long long)sizeof(fvk::Ctrl) * s->g.B;
+  h.state_bytes = (long long)s->g.member() * s->g.B * (long long)sizeof(float);
+  uint8_t* p = static_cast<uint8_t*>(dst);
+  memcpy(p, &h, sizeof h);
+  FV_CUDA_TRY(fvs::enter(s));
+  FV_CUDA_TRY(cudaMemcpyAsync(p + sizeof h, s->ctrl, (size_t)h.ctrl_bytes, cudaMemcpyDeviceToHost, s->stream));
+  FV_CUDA_TRY(cudaMemcpyAsync(p + sizeof h + h.ctrl_bytes, s->qA, (size_t)h.state_bytes, cudaMemcpyDeviceToHost,
+                              s->stream));
+  FV_CUDA_TRY(fvs::leave(s));
+  FV_CUDA_TRY(cudaStreamSynchronize(s->stream));
+  return FV_OK;
+}
+
+extern "C" int fv_checkpoint_load(fv_state* s, const void* src) {
+  if (!s || !src) return fvh::fail(FV_EINVAL, "null argument");
+  CkptHeader h{};
+  const uint8_t* p = static_cast<const uint8_t*>(src);
+  memcpy(&h, p, sizeof h);
+  for (int i = 0; i < 8; ++i)
+    if (h.magic[i] != kCkptMagic[i]) return fvh::fail(FV_EINVAL, "not a checkpoint of this library");
+  if (h.eq != s->g.eq || h.C != s->g.C || h.B != s->g.B || h.nx != s->g.nx || h.ny != s->g.ny ||
+      h.ctrl_bytes != (long long)sizeof(fvk::Ctrl) * s->g.B ||
+      h.state_bytes != (long long)s->g.member() * s->g.B * (long long)sizeof(float))
+    return fvh::fail(FV_EINVAL, "checkpoint of another equation set, batch or grid");
+  FV_CUDA_TRY(fvs::enter(s));
+  FV_CUDA_TRY(cudaMemcpyAsync(s->ctrl, p + sizeof h, (size_t)h.ctrl_bytes, cudaMemcpyHostToDevice, s->stream));
+  FV_CUDA_TRY(cudaMemcpyAsync(s->qA, p + sizeof h + h.ctrl_bytes, (size_t)h.state_bytes, cudaMemcpyHostToDevice,
+                              s->stream));
+  FV_CUDA_TRY(fvs::leave(s));
+  FV_CUDA_TRY(cudaStreamSynchronize(s->stream));
+  return FV_OK;
+}

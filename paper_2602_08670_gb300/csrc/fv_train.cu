@@ -326,27 +326,31 @@ __global__ void axpbypcz_kernel(float* out, const float* x, float alpha, const f
 
 // Eq. 2.28: loss = sum_t sum_c mean_{b,cells} ((pred - target) / scale_c)^2 and
 // its gradient w.r.t. pred; per-block FP64 partial sums.
-__global__ void rollout_loss_kernel(const float* pred, const float* target, float* grad,
-                                    double* part, long long plane, long long per_var_count,
-                                    long long n, float s0, float s1, float s2) {
+// Eq. 2.28 over the recorded rollout: blockIdx.x = plane (step t, member b,
+// variable c in [T][B][3] order), blockIdx.y = part of the plane; FP32 differences scaled by 1 /
+// scale_c, squared and summed per thread, then per block in FP64; the host
+// adds the block sums in a fixed order.  grad receives d loss / d q.
+__global__ void __launch_bounds__(256) rollout_loss_kernel(const float* pred, const float* target, float* grad,
+                                                           double* part, long long plane, double inv_count,
+                                                           float is0, float is1, float is2, float gscale) {
   __shared__ double sh[256];
-  double acc = 0.0;
-  const double inv_count = 1.0 / (double)per_var_count;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int c = (int)((i / plane) % 3);
-    const float s = c == 0 ? s0 : (c == 1 ? s1 : s2);
-    const double d = ((double)pred[i] - (double)target[i]) / s;
-    acc += d * d * inv_count;
-    if (grad) grad[i] = (float)(2.0 * d / s * inv_count);
+  const int c = (int)(blockIdx.x % 3);
+  const float is = c == 0 ? is0 : (c == 1 ? is1 : is2);
+  const long long base = (long long)blockIdx.x * plane;
+  float acc = 0.f;
+  for (long long i = blockIdx.y * (long long)blockDim.x + threadIdx.x; i < plane;
+       i += (long long)gridDim.y * blockDim.x) {
+    const float d = (pred[base + i] - target[base + i]) * is;
+    acc = fmaf(d, d, acc);
+    if (grad) grad[base + i] = gscale * d * is;
   }
-  sh[threadIdx.x] = acc;
+  sh[threadIdx.x] = (double)acc;
   __syncthreads();
   for (int k = 128; k > 0; k >>= 1) {
     if (threadIdx.x < k) sh[threadIdx.x] += sh[threadIdx.x + k];
     __syncthreads();
   }
-  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+  if (threadIdx.x == 0) part[(long long)blockIdx.x * gridDim.y + blockIdx.y] = sh[0] * inv_count;
 }
 
 // Adam (bias-corrected) on the FP32 master parameters.
@@ -436,7 +440,12 @@ cudaError_t launch_face_adjoint(const Geom& g, const float* sides, const float* 
 
 namespace {
 
-constexpr int LOSS_BLOCKS = 512;
+// blocks per plane of the loss kernel (about 2048 cells per block)
+inline int loss_blocks_x(long long plane) {
+  long long bx = (plane + 2047) / 2048;
+  if (bx > 65535) bx = 65535;
+  return (int)(bx < 1 ? 1 : bx);
+}
 
 // h_min per member = frac * mean depth (FP64 sum of h over the member).
 __global__ void hmin_kernel(const float* q, float* hmin, long long plane, double frac) {
@@ -524,7 +533,8 @@ extern "C" int fv_tape_create(fv_net* net, int B, int ny, int nx, int T, double 
   if (e == cudaSuccess) e = cudaMalloc(&t->mu, sizeof(float) * sc);
   if (e == cudaSuccess) e = cudaMalloc(&t->gq, sizeof(float) * sc);
   if (e == cudaSuccess) e = cudaMalloc(&t->gw, sizeof(float) * nout * cells);
-  if (e == cudaSuccess) e = cudaMalloc(&t->loss_part, sizeof(double) * LOSS_BLOCKS);
+  if (e == cudaSuccess)
+    e = cudaMalloc(&t->loss_part, sizeof(double) * (size_t)T * B * 3 * loss_blocks_x((long long)nx * ny));
   if (e == cudaSuccess) e = cudaMalloc(&t->dsn, sizeof(float) * sc * T);
   if (e == cudaSuccess) {
     fvk::DtParams dp{};
@@ -590,13 +600,15 @@ extern "C" int fv_tape_loss(fv_tape* t, const float* targets, const float* scale
   if (!t || !targets || !scale3 || !loss) return fvh::fail(FV_EINVAL, "null argument");
   if (!t->have_forward) return fvh::fail(FV_EINVAL, "fv_tape_forward has not run");
   const long long sc = st_count(t);
-  const long long n = sc * t->T;
-  fvk::rollout_loss_kernel<<<LOSS_BLOCKS, 256, 0, t->stream>>>(
-      t->states + sc, targets, t->dsn, t->loss_part, t->g.plane(), (long long)t->g.B * t->g.plane(), n,
-      scale3[0], scale3[1], scale3[2]);
+  const int bx = loss_blocks_x(t->g.plane());
+  const int planes = t->T * t->g.B * 3;
+  const double inv_count = 1.0 / (double)((long long)t->g.B * t->g.plane());
+  fvk::rollout_loss_kernel<<<dim3(planes, bx), 256, 0, t->stream>>>(
+      t->states + sc, targets, t->dsn, t->loss_part, t->g.plane(), inv_count, (float)(1.0 / scale3[0]),
+      (float)(1.0 / scale3[1]), (float)(1.0 / scale3[2]), (float)(2.0 * inv_count));
   FV_CUDA_TRY(cudaGetLastError());
-  std::vector<double> part(LOSS_BLOCKS);
-  FV_CUDA_TRY(cudaMemcpyAsync(part.data(), t->loss_part, sizeof(double) * LOSS_BLOCKS,
+  std::vector<double> part((size_t)bx * planes);
+  FV_CUDA_TRY(cudaMemcpyAsync(part.data(), t->loss_part, sizeof(double) * part.size(),
                               cudaMemcpyDeviceToHost, t->stream));
   FV_CUDA_TRY(cudaStreamSynchronize(t->stream));
   double sum = 0.0;

@@ -80,6 +80,9 @@ __device__ __forceinline__ int wrapi(int i, int n) {
   return i < 0 ? i + n : i;
 }
 
+// i in [-n, 2n): the periodic index in [0, n).
+__device__ __forceinline__ int wrap1(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
 __device__ __forceinline__ int floordiv(int a, int b) {
   const int q = a / b;
   return (a % b != 0 && (a < 0) != (b < 0)) ? q - 1 : q;
@@ -145,19 +148,21 @@ __global__ void __launch_bounds__(NT) conv_kernel(ConvArgs a) {
   // weights: 9 * CG * N chunks of 16 bytes
   for (int i = tid; i < 9 * CG * N; i += NT) cp_async16(sB + i * 16, a.wpk + i * 8);
 
-  // input positions
+  // input positions (every offset lies within one period of the grid, so
+  // one compare-and-select wraps it; a power-of-two width divides by a shift)
+  const int lg = (nx & (nx - 1)) == 0 ? __ffs(nx) - 1 : -1;
   for (int n = tid; n < npos; n += NT) {
     int yy, xx;
     if (rowmode) {
-      const int dyi = n / RW, xi = n - dyi * RW;
-      yy = wrapi(y0 - 1 + dyi, ny);
-      xx = wrapi(x0 - 1 + xi, nx);
+      const int dyi = (n >= RW) + (n >= 2 * RW), xi = n - dyi * RW;
+      yy = wrap1(y0 - 1 + dyi, ny);
+      xx = wrap1(x0 - 1 + xi, nx);
     } else {
-      const int dxi = n / Lf;
+      const int dxi = (n >= Lf) + (n >= 2 * Lf);
       const int c = p0 + (n - dxi * Lf) - nx;
-      const int r = floordiv(c, nx);
-      yy = wrapi(r, ny);
-      xx = wrapi(c - r * nx + dxi - 1, nx);
+      const int r = lg >= 0 ? (c >> lg) : floordiv(c, nx);
+      yy = wrap1(r, ny);
+      xx = wrap1(c - r * nx + dxi - 1, nx);
     }
     const long long cell = (long long)yy * nx + xx;
     if constexpr (IN == IN_ACT) {
@@ -828,6 +833,16 @@ __device__ __forceinline__ uint32_t dw_off(int r, int k) {
   return (uint32_t)(r >> 3) * DW_SBO + (uint32_t)(k >> 3) * 128u + (uint32_t)(r & 7) * 16u + (uint32_t)(k & 7) * 2u;
 }
 
+// Periodic neighbour of cell p (row-major nx x ny plane) at offset (dy, dx),
+// dy, dx in {-1, 0, 1}.
+__device__ __forceinline__ long long shifted_cell(int p, int nx, int ny, int dy, int dx, int lg) {
+  const int y = lg >= 0 ? p >> lg : p / nx, x = p - y * nx;
+  int ys = y + dy, xs = x + dx;
+  ys = ys < 0 ? ys + ny : (ys >= ny ? ys - ny : ys);
+  xs = xs < 0 ? xs + nx : (xs >= nx ? xs - nx : xs);
+  return (long long)ys * nx + xs;
+}
+
 template <int CI, int CO, int CGO>
 __global__ void __launch_bounds__(NT) dw_tc_kernel(const uint16_t* x, const float* q, const uint16_t* dy,
                                                    float* part, int nx, int ny, long long plane,
@@ -871,6 +886,7 @@ __global__ void __launch_bounds__(NT) dw_tc_kernel(const uint16_t* x, const floa
   tc::fence_after_sync();
   const uint32_t tmem = *tslot;
   constexpr uint32_t idesc = tc::idesc_bf16_f32(128, NB);
+  const int lg = (nx & (nx - 1)) == 0 ? __ffs(nx) - 1 : -1;   // power-of-two width: shift
   bool ok = true;
   int issued = 0;                        // tiles whose MMAs were issued (the same in every thread)
 
@@ -902,10 +918,7 @@ __global__ void __launch_bounds__(NT) dw_tc_kernel(const uint16_t* x, const floa
     // A: the input at the 9 tap-shifted cells (periodic), rows tap * CI + ci
     for (int it = tid; it < DWK * 9; it += NT) {
       const int k = it % DWK, tap = it / DWK;
-      const int p = p0 + k;
-      const int y = p / nx, xx = p - y * nx;
-      const int ys = wrapi(y + tap / 3 - 1, ny), xs = wrapi(xx + tap % 3 - 1, nx);
-      const long long cell = (long long)ys * nx + xs;
+      const long long cell = shifted_cell(p0 + k, nx, ny, tap / 3 - 1, tap % 3 - 1, lg);
       if constexpr (CI == 3) {
         const float* qb = q + (long long)b * 3 * plane;
         const float v[3] = {(qb[cell] - m0) * r0, (qb[plane + cell] - m1) * r1, (qb[2 * plane + cell] - m2) * r2};
@@ -982,21 +995,37 @@ __global__ void __launch_bounds__(NT) dw_tc_kernel(const uint16_t* x, const floa
   if ((tid >> 5) == 0) tc::tmem_dealloc(tmem, 256);
 }
 
-// Sum the CTAs' partial sums in CTA order into dparams (PyTorch layout):
-// row r = tap * CI + ci gives dW[co][ci][tap], row 9 CI gives db.
+// Sum the CTAs' partial sums into dparams (PyTorch layout): row r = tap *
+// CI + ci gives dW[co][ci][tap], row 9 CI gives db.  A block of 8 warps
+// handles 32 consecutive outputs; warp w sums partials [w P / 8, (w+1) P / 8)
+// in order, then the 8 sums are added in warp order (a fixed order: the
+// result does not depend on timing).
 template <int CI, int CO>
-__global__ void dw_tc_reduce_kernel(const float* part, int nparts, float* dW, float* db, float scale) {
+__global__ void __launch_bounds__(256) dw_tc_reduce_kernel(const float* part, int nparts, float* dW, float* db,
+                                                           float scale) {
   constexpr int ROWS = dw_mt<CI>() * 128;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= (9 * CI + 1) * CO) return;
-  const int r = i / CO, co = i - r * CO;
+  constexpr int NE = (9 * CI + 1) * CO;
+  __shared__ float sh[8][32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = blockIdx.x * 32 + lane;
   float s = 0.f;
-  for (int k = 0; k < nparts; ++k) s += part[((long long)k * ROWS + r) * CO + co];
-  if (r < 9 * CI) {
-    const int tap = r / CI, c = r - tap * CI;
-    dW[(co * CI + c) * 9 + tap] += scale * s;
-  } else {
-    db[co] += scale * s;
+  if (i < NE) {
+    const int k0 = warp * nparts / 8, k1 = (warp + 1) * nparts / 8;
+    for (int k = k0; k < k1; ++k) s += part[(long long)k * ROWS * CO + i];
+  }
+  sh[warp][lane] = s;
+  __syncthreads();
+  if (warp == 0 && i < NE) {
+    float t = sh[0][lane];
+#pragma unroll
+    for (int w = 1; w < 8; ++w) t += sh[w][lane];
+    const int r = i / CO, co = i - r * CO;
+    if (r < 9 * CI) {
+      const int tap = r / CI, c = r - tap * CI;
+      dW[(co * CI + c) * 9 + tap] += scale * t;
+    } else {
+      db[co] += scale * t;
+    }
   }
 }
 
@@ -1019,7 +1048,7 @@ cudaError_t weight_grad_tc(const uint16_t* x, const float* q, const uint16_t* dy
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int ne = (9 * CI + 1) * CO;
-  dw_tc_reduce_kernel<CI, CO><<<(ne + 255) / 256, 256, 0, s>>>(part, nctas, dW, db, scale);
+  dw_tc_reduce_kernel<CI, CO><<<(ne + 31) / 32, 256, 0, s>>>(part, nctas, dW, db, scale);
   return cudaGetLastError();
 }
 

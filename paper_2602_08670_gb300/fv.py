@@ -105,6 +105,9 @@ _SIGS = {
     "fv_diagnostics_noalloc": [c_void_p, c_int, c_int, c_int, c_int, c_double, c_double, c_double,
                                c_void_p, c_int, c_void_p],
     "fv_get_time": [c_void_p, c_void_p, c_void_p, c_void_p],
+    "fv_checkpoint_bytes": [c_void_p, ctypes.POINTER(ctypes.c_size_t)],
+    "fv_checkpoint_save": [c_void_p, c_void_p],
+    "fv_checkpoint_load": [c_void_p, c_void_p],
     "fv_set_halo": [c_void_p, c_int, c_int],
     "fv_enqueue_stage": [c_void_p, c_void_p, c_int],
     "fv_halo_exchange": [c_void_p, c_int, c_int, c_int],
@@ -325,6 +328,20 @@ def fv_diagnostics(s: State) -> np.ndarray:
     out = np.zeros((B, C + 1), dtype=np.float64)
     _check(lib().fv_diagnostics(s.handle, out.ctypes.data_as(c_void_p)))
     return out
+
+
+def fv_checkpoint_save(s: State) -> bytes:
+    """The state's checkpoint blob (header, control blocks, q^n)."""
+    n = ctypes.c_size_t()
+    _check(lib().fv_checkpoint_bytes(s.handle, ctypes.byref(n)))
+    buf = ctypes.create_string_buffer(n.value)
+    _check(lib().fv_checkpoint_save(s.handle, ctypes.cast(buf, c_void_p)))
+    return buf.raw
+
+
+def fv_checkpoint_load(s: State, blob: bytes) -> None:
+    buf = ctypes.create_string_buffer(blob, len(blob))
+    _check(lib().fv_checkpoint_load(s.handle, ctypes.cast(buf, c_void_p)))
 
 
 # ---------------------------------------------------------------------------

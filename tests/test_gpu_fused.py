@@ -67,8 +67,10 @@ def assert_close(q, ref, l2=1e-4, linf=1e-3):
         assert e2 < l2 and ei < linf, (c, e2, ei)
 
 
-@pytest.mark.parametrize("ny,nx,B", [(128, 128, 2), (64, 256, 2), (32, 512, 1)])
+@pytest.mark.parametrize("ny,nx,B", [(128, 128, 2), (64, 256, 2), (32, 512, 1), (8, 1024, 1)])
 def test_fused_matches_oracle(fv, ny, nx, B):
+    """Against the BF16-mirrored FP64 oracle, up to the largest cluster (8 CTAs
+    exchanging halos for a 1024-column row)."""
     p = rand_params(4)
     q0 = swe_state(ny, nx, 11, B)
     _, q = run_gpu(fv, q0, gpu_net(fv, p), 8, "fused")

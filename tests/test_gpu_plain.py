@@ -287,3 +287,26 @@ def test_full_size_sampled_cells(fv, eq, n):
         scale = np.abs(q0[0]).max(axis=(1, 2))
         scale[1:3] = scale[1:3].max()
         assert np.all(np.abs(got - ref) <= 2e-6 * scale), (j, i, got, ref)
+
+
+@pytest.mark.parametrize("eq", [ofv.SWE, ofv.EULER])
+def test_checkpoint_resume_is_bitwise(fv, eq):
+    """Save after 12 adaptive steps, load into a fresh state, run 20 more:
+    bitwise the state, time and step count of the uninterrupted run."""
+    q0 = W.random_smooth_swe(64, seed=8, members=2, vel=0.2) if eq == ofv.SWE else \
+        np.concatenate([W.euler_kelvin_helmholtz(64, 48, seed=k) for k in range(2)])
+    init = fv.swe_init if eq == ofv.SWE else fv.euler_init
+    a = init(f32(q0).cuda())
+    fv.fv_rollout(a, 12)
+    blob = fv.fv_checkpoint_save(a)
+    fv.fv_rollout(a, 20)
+    b = init(torch.ones_like(f32(q0)).cuda() if eq == ofv.SWE else f32(q0).cuda())
+    fv.fv_checkpoint_load(b, blob)
+    fv.fv_rollout(b, 20)
+    assert torch.equal(fv.fv_get_state(a), fv.fv_get_state(b))
+    ta, tb = fv.fv_get_time(a), fv.fv_get_time(b)
+    assert all(np.array_equal(x, y) for x, y in zip(ta, tb))
+    # a checkpoint of another shape is refused
+    c = init(f32(q0[:1]).cuda())
+    with pytest.raises(fv.FvError):
+        fv.fv_checkpoint_load(c, blob)
