@@ -122,10 +122,18 @@ class TrainResult:
 
 
 def train(ds: Dataset, iters: int = 500, batch: int = 64, T: int = 8, lr: float = 3e-4,
-          seed: int = 0, params=None, log_every: int = 0, net=None, kind: str = "stencil") -> TrainResult:
+          seed: int = 0, params=None, log_every: int = 0, net=None, kind: str = "stencil",
+          pushforward: int = 0) -> TrainResult:
     """Adam on the rollout loss.  An update after which a training rollout
     leaves the physical states (the library reports FV_EUNSTABLE) is undone
-    and the learning rate halved."""
+    and the learning rate halved.
+
+    pushforward = K > 0: before each batch the current network advances the
+    window starts by k ~ U{0..K} learned steps without a tape, and the loss
+    is taken on the T taped steps that follow, against the reference at the
+    matching times; the network learns to correct the states of its own long
+    rollouts without differentiating through them.  A batch whose untaped
+    steps leave the physical states is skipped (learning rate unchanged)."""
     mean, std = data_stats(ds)
     if net is None:
         in_mean, in_scale = input_scale(ds)
@@ -145,19 +153,36 @@ def train(ds: Dataset, iters: int = 500, batch: int = 64, T: int = 8, lr: float 
     losses = []
     rejected = 0
     step = 0
+    pre = None
+    if pushforward:
+        pre = fv.swe_init(ds.coarse[0, :batch].contiguous(), dt_mode="fixed", dt_fixed=ds.dt_coarse)
     t0 = time.perf_counter()
     for it in range(iters):
         traj = torch.tensor(rng.integers(0, B, size=batch), device="cuda")
-        start = torch.tensor(rng.integers(0, S - T, size=batch), device="cuda")
+        k_pre = int(rng.integers(0, pushforward + 1)) if pushforward else 0
+        start = torch.tensor(rng.integers(0, S - T - k_pre, size=batch), device="cuda")
         q0 = ds.coarse[start, traj].contiguous()
-        targets = torch.stack([ds.coarse[start + k, traj] for k in range(1, T + 1)]).contiguous()
+        targets = torch.stack([ds.coarse[start + k_pre + k, traj] for k in range(1, T + 1)]).contiguous()
+        if k_pre:
+            fv.fv_set_state(pre, q0)
+            try:
+                fv.fv_rollout(pre, k_pre, net=net)
+                q0 = fv.fv_get_state(pre)
+            except fv.FvError as e:
+                if e.code != fv.FV_EUNSTABLE:
+                    raise
+                # a fresh state: the health word of this one stays set
+                pre = fv.swe_init(ds.coarse[0, :batch].contiguous(), dt_mode="fixed", dt_fixed=ds.dt_coarse)
+                rejected += 1
+                continue
         try:
             fv.fv_tape_forward(tape, q0, want_snaps=False)
         except fv.FvError as e:
             if e.code != fv.FV_EUNSTABLE:
                 raise
             fv.stencil_net_set_params(net, prev)
-            lr *= 0.5
+            if not pushforward:
+                lr *= 0.5
             rejected += 1
             continue
         losses.append(fv.fv_tape_loss(tape, targets, scale))
@@ -467,7 +492,8 @@ def save_weights(path: str, net, ds: Dataset, result: TrainResult, extra: dict |
     scale), else that of the dataset) and the training recipe in one .npz."""
     mean, scale = norm if norm is not None else input_scale(ds)
     meta = {"n_fine": ds.n_fine, "factor": ds.factor, "dt_coarse": ds.dt_coarse, "dt_fine": ds.dt_fine,
-            "seed": ds.seed, "iters": result.iters, "final_loss": float(np.mean(result.losses[-50:])),
+            "seed": ds.seed, "iters": result.iters,
+            "final_loss": float(np.mean(result.losses[-50:])) if result.losses else None,
             "train_seconds": result.seconds}
     meta.update(extra or {})
     np.savez(path, params=fv.stencil_net_get_params(net), mean=mean, scale=scale,
@@ -518,6 +544,8 @@ def main(argv=None):
     ap.add_argument("--T", type=int, default=8)
     ap.add_argument("--lr", type=float, default=3e-4)
     ap.add_argument("--kind", choices=["stencil", "face"], default="stencil")
+    ap.add_argument("--pushforward", type=int, default=0,
+                    help="untaped learned steps (at most) before each window's taped steps")
     ap.add_argument("--init", default=None,
                     help="continue from a saved network (its parameters, normalisation and dt)")
     ap.add_argument("--out", default=None)
@@ -537,12 +565,13 @@ def main(argv=None):
         extra = {"init": {k: meta0[k] for k in ("iters", "final_loss") if k in meta0}}
     ds = generate(256, 4, members=a.members, seed=0, coarse_steps=a.coarse_steps, dt_fine=dt_fine)
     res = train(ds, iters=a.iters, batch=a.batch, T=a.T, lr=a.lr, seed=0, log_every=100, kind=a.kind,
-                net=net)
+                net=net, pushforward=a.pushforward)
     te = generate(256, 4, members=32, seed=2, coarse_steps=128, dt_fine=ds.dt_fine)
     _, std = data_stats(ds)
     ev = {k: evaluate(res.net, te, k, std) for k in (16, 64, 128)}
     print({k: (v["learned"], v["plain"]) for k, v in ev.items()})
-    extra.update({"T": a.T, "coarse_steps": a.coarse_steps, "lr": a.lr,
+    extra.update({"T": a.T, "coarse_steps": a.coarse_steps, "lr": a.lr, "pushforward": a.pushforward,
+                  "rejected": res.rejected,
                   "test_errors": {k: (v["learned"], v["plain"]) for k, v in ev.items()}})
     save_weights(a.out, res.net, ds, res, extra, norm=norm)
 
