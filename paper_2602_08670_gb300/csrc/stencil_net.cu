@@ -1029,12 +1029,219 @@ __global__ void __launch_bounds__(256) dw_tc_reduce_kernel(const float* part, in
   }
 }
 
+// The same GEMM with the staging done by the copy engines and the matrix
+// instructions (CI = 32): the raw 16-byte records the tile needs (the input
+// at the three x-shifted strips of positions the forward convolution stages,
+// and the cotangent of the tile's cells) arrive by cp.async; every warp then
+// transposes 8x8 blocks (8 cells x 8 channels) with ldmatrix.trans and writes
+// them as K-major rows with stmatrix.  The raw records of the next tile load
+// while the tensor core runs the current tile's MMAs.
+__device__ __forceinline__ void ldmatrix_x4_trans(uint32_t row_addr, uint32_t (&w)[4]) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];\n"
+               : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]) : "r"(row_addr));
+}
+__device__ __forceinline__ void stmatrix_x4(uint32_t row_addr, const uint32_t (&w)[4]) {
+  asm volatile("stmatrix.sync.aligned.m8n8.x4.shared.b16 [%0], {%1, %2, %3, %4};\n"
+               :: "r"(row_addr), "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3]) : "memory");
+}
+
+// Raw positions of a 64-cell tile: row mode (nx a multiple of 128) 3 rows of
+// DWK + 2 cells; flat mode (nx dividing DWK) 3 strips of DWK + 2 nx cells.
+constexpr int DW_RW = DWK + 2;
+constexpr int DW_NPOS_ROW = 3 * DW_RW;
+constexpr int DW_NPOS_FLAT = 3 * (DWK + 2 * 64);
+template <bool ROW>
+constexpr int dw_npos() { return ROW ? DW_NPOS_ROW : DW_NPOS_FLAT; }
+template <int CI, int CGO, bool ROW>
+constexpr int dwx_smem_bytes() {
+  return (CI / 8) * dw_npos<ROW>() * 16 + CGO * DWK * 16 + (dw_mt<CI>() * 128 + 8 * CGO) * DWK * 2 + 64;
+}
+
+template <int CI, int CO, int CGO, bool ROW>
+__global__ void __launch_bounds__(NT) dw_tx_kernel(const uint16_t* x, const uint16_t* dy, float* part, int nx,
+                                                   int ny, long long plane, long long ntiles, unsigned* err) {
+  constexpr int CG = CI / 8;
+  constexpr int NB = 8 * CGO;
+  constexpr int MT = dw_mt<CI>();
+  constexpr int ROWS = MT * 128;
+  constexpr int NP = dw_npos<ROW>();
+  static_assert(CI % 8 == 0 && NB % 16 == 0 && MT * NB <= 256, "shape of the MMA and TMEM columns");
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint8_t* R = smem;                                   // [CG][NP][16 B] raw input records
+  uint8_t* RB = R + CG * NP * 16;                      // [CGO][DWK][16 B] raw cotangent records
+  uint8_t* A = RB + CGO * DWK * 16;                    // K-major [ROWS][DWK]
+  uint8_t* Bm = A + ROWS * DWK * 2;                    // K-major [NB][DWK]
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(Bm + NB * DWK * 2);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const long long t0 = (long long)blockIdx.x * ntiles / gridDim.x;
+  const long long t1 = (long long)(blockIdx.x + 1) * ntiles / gridDim.x;
+  const long long tiles_per_member = plane / DWK;
+  const int lg = (nx & (nx - 1)) == 0 ? __ffs(nx) - 1 : -1;
+  const int Lf = DWK + 2 * nx;                         // flat-mode strip
+
+  // the ones row (bias) and the zero padding of A, once
+  for (int i = tid; i < (ROWS - 9 * CI) * DWK; i += NT) {
+    const int r = 9 * CI + i / DWK, k = i % DWK;
+    *reinterpret_cast<uint16_t*>(A + dw_off(r, k)) = r == 9 * CI ? (uint16_t)0x3F80u : (uint16_t)0u;
+  }
+  if (tid == 0) {
+    tc::mbar_init(mbar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 0) tc::tmem_alloc(tslot, 256);
+
+  // raw records of tile `tile` (cp.async, committed as one group)
+  auto stage_raw = [&](long long tile) {
+    const int b = (int)(tile / tiles_per_member);
+    const int p0 = (int)(tile - (long long)b * tiles_per_member) * DWK;
+    const int y0 = lg >= 0 ? p0 >> lg : p0 / nx, x0 = p0 - y0 * nx;
+    const int npos = ROW ? DW_NPOS_ROW : 3 * Lf;
+    for (int n = tid; n < npos; n += NT) {
+      int yy, xx;
+      if (ROW) {
+        const int dyi = (n >= DW_RW) + (n >= 2 * DW_RW), xi = n - dyi * DW_RW;
+        yy = wrap1(y0 - 1 + dyi, ny);
+        xx = wrap1(x0 - 1 + xi, nx);
+      } else {
+        const int dxi = (n >= Lf) + (n >= 2 * Lf);
+        const int c = p0 + (n - dxi * Lf) - nx;
+        const int r = lg >= 0 ? (c >> lg) : floordiv(c, nx);
+        yy = wrap1(r, ny);
+        xx = wrap1(c - r * nx + dxi - 1, nx);
+      }
+      const long long cell = (long long)yy * nx + xx;
+#pragma unroll
+      for (int g = 0; g < CG; ++g)
+        cp_async16(R + (g * NP + n) * 16, x + (((long long)b * CG + g) * plane + cell) * 8);
+    }
+    for (int n = tid; n < CGO * DWK; n += NT) {
+      const int g = n / DWK, k = n - g * DWK;
+      cp_async16(RB + n * 16, dy + (((long long)b * CGO + g) * plane + p0 + k) * 8);
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
+
+  if (t0 < t1) stage_raw(t0);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tslot;
+  constexpr uint32_t idesc = tc::idesc_bf16_f32(128, NB);
+  const uint32_t r_base = tc::smem_u32(R), rb_base = tc::smem_u32(RB);
+  const uint32_t a_base = tc::smem_u32(A), b_base = tc::smem_u32(Bm);
+  bool ok = true;
+  int issued = 0;
+  for (long long tile = t0; tile < t1; ++tile) {
+    const int i = (int)(tile - t0);
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    // A and B are free once the MMAs of the previous tile are done
+    bool w = true;
+    if (i >= 1) w = tc::mbar_wait_bounded(mbar, (uint32_t)(i - 1) & 1u, WAIT_ITERS);
+    ok = __syncthreads_and(w) && ok;
+    if (!ok) break;
+    tc::fence_after_sync();
+    // A: 8x8 blocks (tap, g, kb): raw positions start(tap) + 8 kb .. + 7 of group g
+    constexpr int NBLK_A = 9 * CG * 8;
+    for (int ins = warp; ins < NBLK_A / 4; ins += NT / 32) {
+      const int m = lane >> 3, row = lane & 7;
+      const int t = 4 * ins + m, kb = t & 7, g = (t >> 3) % CG, tap = (t >> 3) / CG;
+      const int dy_ = tap / 3 - 1, dx_ = tap % 3 - 1;
+      const int start = ROW ? (1 + dy_) * DW_RW + (1 + dx_) : (1 + dx_) * Lf + nx + dy_ * nx;
+      uint32_t v[4];
+      ldmatrix_x4_trans(r_base + (uint32_t)((g * NP + start + 8 * kb + row) * 16), v);
+      stmatrix_x4(a_base + dw_off(tap * CI + 8 * g + row, 8 * kb), v);
+    }
+    // B: 8x8 blocks (g, kb) of the cotangent
+    for (int ins = warp; ins < CGO * 8 / 4; ins += NT / 32) {
+      const int m = lane >> 3, row = lane & 7;
+      const int t = 4 * ins + m, kb = t & 7, g = t >> 3;
+      uint32_t v[4];
+      ldmatrix_x4_trans(rb_base + (uint32_t)((g * DWK + 8 * kb + row) * 16), v);
+      stmatrix_x4(b_base + dw_off(8 * g + row, 8 * kb), v);
+    }
+    tc::fence_proxy_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (tid == 0) {
+#pragma unroll
+      for (int mt = 0; mt < MT; ++mt) {
+#pragma unroll
+        for (int ks = 0; ks < DWK / 16; ++ks) {
+          const uint64_t ad = tc::sdesc(a_base + mt * 16 * DW_SBO + ks * 256, 128, DW_SBO);
+          const uint64_t bd = tc::sdesc(b_base + ks * 256, 128, DW_SBO);
+          tc::mma_bf16(tmem + mt * NB, ad, bd, idesc, i > 0 || ks > 0);
+        }
+      }
+      tc::mma_commit(mbar);
+    }
+    issued = i + 1;
+    // the raw records of the next tile load while the tensor core works
+    if (tile + 1 < t1) stage_raw(tile + 1);
+  }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+  if (issued > 0) {
+    const bool w = tc::mbar_wait_bounded(mbar, (uint32_t)(issued - 1) & 1u, WAIT_ITERS);
+    ok = __syncthreads_and(w) && ok;
+  }
+  tc::fence_after_sync();
+  if (!ok) {
+    if (tid == 0) atomicOr(err, 1u);
+  } else {
+    float* pp = part + (long long)blockIdx.x * ROWS * CO;
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt) {
+      const int r = mt * 128 + warp * 32 + lane;
+#pragma unroll
+      for (int c0 = 0; c0 < NB; c0 += 16) {
+        float v[16];
+        tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + mt * NB + c0, v);
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          if (c0 + j < CO) pp[(long long)r * CO + c0 + j] = issued > 0 ? v[j] : 0.f;
+      }
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, 256);
+}
+
+template <int CI, int CO, int CGO, bool ROW>
+cudaError_t launch_dw_tx(const uint16_t* x, const uint16_t* dy, float* part, int nx, int ny, long long plane,
+                         long long ntiles, int nctas, const Net& net, cudaStream_t s) {
+  constexpr int smem = dwx_smem_bytes<CI, CGO, ROW>();
+  auto kern = dw_tx_kernel<CI, CO, CGO, ROW>;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  kern<<<nctas, NT, smem, s>>>(x, dy, part, nx, ny, plane, ntiles, net.err);
+  return cudaGetLastError();
+}
+
 template <int CI, int CO, int CGO>
 cudaError_t weight_grad_tc(const uint16_t* x, const float* q, const uint16_t* dy, float* dW, float* db,
                            float* part, int B, int ny, int nx, const Net& net, float scale, cudaStream_t s) {
   const long long plane = (long long)nx * ny;
   const long long ntiles = (long long)B * (plane / DWK);
   const int nctas = (int)(ntiles < DW_CTAS ? ntiles : DW_CTAS);
+  if constexpr (CI % 8 == 0) {
+    // staging by cp.async + ldmatrix / stmatrix: a tile is half a row
+    // (nx a multiple of 128) or whole rows (nx dividing 64)
+    if (nx % 128 == 0 || (nx <= 64 && DWK % nx == 0)) {
+      cudaError_t e;
+      if (nx % 128 == 0) e = launch_dw_tx<CI, CO, CGO, true>(x, dy, part, nx, ny, plane, ntiles, nctas, net, s);
+      else e = launch_dw_tx<CI, CO, CGO, false>(x, dy, part, nx, ny, plane, ntiles, nctas, net, s);
+      if (e != cudaSuccess) return e;
+      const int ne = (9 * CI + 1) * CO;
+      dw_tc_reduce_kernel<CI, CO><<<(ne + 31) / 32, 256, 0, s>>>(part, nctas, dW, db, scale);
+      return cudaGetLastError();
+    }
+  }
   constexpr int smem = dw_smem_bytes<CI, 8 * CGO>();
   auto kern = dw_tc_kernel<CI, CO, CGO>;
   static bool attr = false;
