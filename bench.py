@@ -39,6 +39,10 @@ CHUNK = 32                          # steps per enqueue between timing events
 WORKLOAD = "plain FV step: Euler KH 2048^2 + SWE Gaussian bump 4096^2, FP32, SSP-RK2, CFL 0.5"
 WEIGHTS = os.path.join(ROOT, "paper_2602_08670_gb300", "weights", "swe64_from256.npz")
 FACE_WEIGHTS = os.path.join(ROOT, "paper_2602_08670_gb300", "weights", "face64_from256.npz")
+# Seed of the accuracy-matched evaluation field.  The fine-tuning runs behind
+# the committed stencil network were compared on seed 3; the bench evaluates
+# on a field that took no part in that choice.
+EVAL_SEED = 5
 
 
 def captured_traffic(key):
@@ -336,7 +340,7 @@ def learned_block(args):
     _, std = TR.data_stats(tr)
     horizons = tuple(int(k) for k in args.learned_horizons.split(","))
     m = TR.matched_accuracy({"stencil": net, "face_state": fnet}, meta["dt_coarse"], std, n=256, tiles=4,
-                            members=args.learned_members, seed=3, horizons=horizons)
+                            members=args.learned_members, seed=EVAL_SEED, horizons=horizons)
     out["accuracy_matched"] = m
     bf16_peak = _bf16_sustained_peak()
     members, n = args.learned_members, 256

@@ -18,6 +18,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -52,7 +53,9 @@ namespace {
 constexpr int NT = 128;                 // threads per CTA (4 warps = 128 TMEM lanes)
 constexpr int RW = TILE + 2;            // row mode: staged row width (1-cell halo each side)
 constexpr int NPOS_ROW = 3 * RW;        // row mode: 3 rows
-constexpr int NPOS_MAX = 3 * (TILE + 2 * 64);   // flat mode with nx <= 64
+constexpr int NPOS_MAX = 3 * (TILE + 2 * 64);   // strip mode with nx <= 64 (CUDA-core dW)
+constexpr int GSLOT = 10;               // grouped mode: 8 cells + the x-neighbour on each side
+constexpr int NPOS_GRP = (TILE / 8 + 2 * 64 / 8) * GSLOT;   // grouped mode with nx <= 64
 constexpr uint32_t WAIT_ITERS = 1u << 22;
 
 enum { IN_STATE = 0, IN_ACT = 1 };
@@ -88,14 +91,25 @@ __device__ __forceinline__ int floordiv(int a, int b) {
   return (a % b != 0 && (a < 0) != (b < 0)) ? q - 1 : q;
 }
 
-// Staged input positions: row mode (nx a multiple of the tile) needs 3 rows
-// of TILE + 2 cells, flat mode (nx <= 64) 3 strips of TILE + 2 nx.
+// Staged input positions of the CUDA-core weight gradient: row mode (nx a
+// multiple of the tile) 3 rows of TILE + 2 cells, strip mode (nx <= 64) 3
+// x-shifted strips of TILE + 2 nx.
 template <bool ROW>
 constexpr int npos_of() { return ROW ? NPOS_ROW : NPOS_MAX; }
 
+// Staged input positions of the convolution: row mode as above; grouped mode
+// (nx <= 64 dividing the tile, which then covers TILE / nx whole rows) keeps
+// every run of 8 cells of the rows y0 - 1 .. y0 + TILE / nx with its two
+// periodic x-neighbours, 10 positions per run.  The MMA rows of a tap (dy,
+// dx) are then 8-row groups 10 positions apart: one descriptor with a
+// 160-byte group stride covers the tile for every tap, with a third of the
+// staging of three x-shifted strips.
+template <bool ROW>
+constexpr int conv_np() { return ROW ? NPOS_ROW : NPOS_GRP; }
+
 template <int CG, int N, bool ROW>
 constexpr int conv_smem_bytes() {
-  return CG * npos_of<ROW>() * 16 + 9 * CG * N * 16 + 64;
+  return CG * conv_np<ROW>() * 16 + 9 * CG * N * 16 + 64;
 }
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
@@ -123,46 +137,30 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
                : "memory");
 }
 
-template <int CG, int N, int IN, int OUT, bool ROW>
-__global__ void __launch_bounds__(NT) conv_kernel(ConvArgs a) {
-  constexpr int NP = npos_of<ROW>();
-  extern __shared__ __align__(1024) uint8_t smem[];
-  uint8_t* sA = smem;                                   // [CG][NP][16 B]
-  uint8_t* sB = smem + CG * NP * 16;                    // [9][CG][N][16 B]
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(sB + 9 * CG * N * 16);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
-
-  const int tid = threadIdx.x;
-  const long long tiles_per_member = a.plane / TILE;
-  const int b = (int)(blockIdx.x / tiles_per_member);
-  const int p0 = (int)(blockIdx.x - (long long)b * tiles_per_member) * TILE;
+// Stage the input positions of the 128-cell tile at p0 of member b into sA
+// ([CG][NP][16 B], row or grouped mode, see conv_np).  Activations arrive by
+// cp.async (the caller commits and waits); the state is normalised and
+// stored directly.  Every offset lies within one period of the grid, so one
+// compare-and-select wraps it; a power-of-two width divides by a shift.
+template <int CG, int IN, bool ROW>
+__device__ __forceinline__ void conv_stage(const ConvArgs& a, uint8_t* sA, int b, int p0, int tid) {
+  constexpr int NP = conv_np<ROW>();
   const int nx = a.nx, ny = a.ny;
-  constexpr bool rowmode = ROW;
-  const int y0 = p0 / nx, x0 = p0 - (p0 / nx) * nx;
-  const int Lf = TILE + 2 * nx;
-  const int npos = rowmode ? NPOS_ROW : 3 * Lf;
-
-  if (tid < 32) tc::tmem_alloc(tslot, 64);
-  if (tid == 0) tc::mbar_init(mbar, 1);
-
-  // weights: 9 * CG * N chunks of 16 bytes
-  for (int i = tid; i < 9 * CG * N; i += NT) cp_async16(sB + i * 16, a.wpk + i * 8);
-
-  // input positions (every offset lies within one period of the grid, so
-  // one compare-and-select wraps it; a power-of-two width divides by a shift)
   const int lg = (nx & (nx - 1)) == 0 ? __ffs(nx) - 1 : -1;
+  const int y0 = lg >= 0 ? p0 >> lg : p0 / nx, x0 = p0 - y0 * nx;
+  const int gpr = nx >> 3;                             // grouped mode: runs of 8 per row
+  const int npos = ROW ? NPOS_ROW : (TILE / 8 + 2 * gpr) * GSLOT;
   for (int n = tid; n < npos; n += NT) {
     int yy, xx;
-    if (rowmode) {
+    if (ROW) {
       const int dyi = (n >= RW) + (n >= 2 * RW), xi = n - dyi * RW;
       yy = wrap1(y0 - 1 + dyi, ny);
       xx = wrap1(x0 - 1 + xi, nx);
     } else {
-      const int dxi = (n >= Lf) + (n >= 2 * Lf);
-      const int c = p0 + (n - dxi * Lf) - nx;
-      const int r = lg >= 0 ? (c >> lg) : floordiv(c, nx);
-      yy = wrap1(r, ny);
-      xx = wrap1(c - r * nx + dxi - 1, nx);
+      const int run = n / GSLOT, sl = n - run * GSLOT;
+      const int ry = run / gpr, gi = run - ry * gpr;  // x0 = 0: the tile starts a row
+      yy = wrap1(y0 - 1 + ry, ny);
+      xx = wrap1(8 * gi - 1 + sl, nx);
     }
     const long long cell = (long long)yy * nx + xx;
     if constexpr (IN == IN_ACT) {
@@ -180,6 +178,137 @@ __global__ void __launch_bounds__(NT) conv_kernel(ConvArgs a) {
       for (int g = 1; g < CG; ++g) *reinterpret_cast<uint4*>(sA + (g * NP + n) * 16) = make_uint4(0, 0, 0, 0);
     }
   }
+}
+
+// Epilogue of one tile: thread m (TMEM lane m) finishes cell `cell` of
+// member b from the accumulator at lane_addr.
+template <int N, int OUT>
+__device__ __forceinline__ void conv_epilogue(const ConvArgs& a, int b, long long cell, uint32_t lane_addr) {
+  if constexpr (OUT == OUT_MASK) {
+    // backward through ReLU: cotangent of the layer input, zero where the
+    // stored activation is zero (BF16 out, 32 channels)
+    float v[32];
+    tc::tmem_ld32(lane_addr, v);
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+      const uint4 mk = *reinterpret_cast<const uint4*>(a.mask + (((long long)b * 4 + g) * a.plane + cell) * 8);
+      const uint32_t mw[4] = {mk.x, mk.y, mk.z, mk.w};
+      uint32_t pk[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int c0 = 8 * g + 2 * j;
+        const bool p0 = (mw[j] & 0x7FFFu) != 0 && !(mw[j] & 0x8000u);
+        const bool p1 = ((mw[j] >> 16) & 0x7FFFu) != 0 && !((mw[j] >> 16) & 0x8000u);
+        pk[j] = pack_bf16x2(p0 ? v[c0] : 0.f, p1 ? v[c0 + 1] : 0.f);
+      }
+      *reinterpret_cast<uint4*>(a.y + (((long long)b * 4 + g) * a.plane + cell) * 8) =
+          make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    }
+  } else if constexpr (OUT == OUT_GELU_GRAD) {
+    // backward through GeLU: cotangent of the layer input times GeLU' of
+    // the stored pre-activation (BF16 out, 32 channels)
+    float v[32];
+    tc::tmem_ld32(lane_addr, v);
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+      const uint4 zk = *reinterpret_cast<const uint4*>(a.z + (((long long)b * 4 + g) * a.plane + cell) * 8);
+      const uint32_t zw[4] = {zk.x, zk.y, zk.z, zk.w};
+      uint32_t pk[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int c0 = 8 * g + 2 * j;
+        const float z0 = __uint_as_float(zw[j] << 16), z1 = __uint_as_float(zw[j] & 0xFFFF0000u);
+        pk[j] = pack_bf16x2(v[c0] * gelu_grad(z0), v[c0 + 1] * gelu_grad(z1));
+      }
+      *reinterpret_cast<uint4*>(a.y + (((long long)b * 4 + g) * a.plane + cell) * 8) =
+          make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    }
+  } else if constexpr (OUT == OUT_RELU || OUT == OUT_GELU) {
+    float v[32];
+    tc::tmem_ld32(lane_addr, v);
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+      uint32_t pk[4], pz[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int c0 = 8 * g + 2 * j;
+        const float z0 = v[c0] + a.bias[c0], z1 = v[c0 + 1] + a.bias[c0 + 1];
+        if constexpr (OUT == OUT_RELU) {
+          pk[j] = pack_bf16x2(fmaxf(z0, 0.f), fmaxf(z1, 0.f));
+        } else {
+          pk[j] = pack_bf16x2(gelu(z0), gelu(z1));
+          pz[j] = pack_bf16x2(z0, z1);
+        }
+      }
+      *reinterpret_cast<uint4*>(a.y + (((long long)b * 4 + g) * a.plane + cell) * 8) =
+          make_uint4(pk[0], pk[1], pk[2], pk[3]);
+      if (OUT == OUT_GELU && a.z)
+        *reinterpret_cast<uint4*>(a.z + (((long long)b * 4 + g) * a.plane + cell) * 8) =
+            make_uint4(pz[0], pz[1], pz[2], pz[3]);
+    }
+  } else if constexpr (OUT == OUT_SIDES || OUT == OUT_SIDES_RAW) {
+    // side states of the face-state network: channel 3 side + var
+    float v[16];
+    tc::tmem_ld16(lane_addr, v);
+    float* sb = a.w + (long long)b * N_OUT_FACE * a.plane + cell;
+#pragma unroll
+    for (int k = 0; k < N_OUT_FACE; ++k) {
+      const float r = v[k] + a.bias[k];
+      float o = r;
+      if constexpr (OUT == OUT_SIDES) {
+        const int var = k % 3;
+        o = var == 0 ? softplus(r) : (var == 1 ? fmaf(a.std1, r, a.mean1) : fmaf(a.std2, r, a.mean2));
+      }
+      sb[k * a.plane] = o;
+    }
+  } else {
+    float v[32], v2[16];
+    tc::tmem_ld32(lane_addr, v);
+    tc::tmem_ld16(lane_addr + 32, v2);
+    float r[N_OUT];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) r[k] = v[k] + a.bias[k];
+#pragma unroll
+    for (int k = 32; k < N_OUT; ++k) r[k] = v2[k - 32] + a.bias[k];
+    float* wb = a.w + (long long)b * N_OUT * a.plane + cell;
+    if constexpr (OUT == OUT_RAW) {
+#pragma unroll
+      for (int k = 0; k < N_OUT; ++k) wb[k * a.plane] = r[k];
+    } else {
+#pragma unroll
+      for (int s = 0; s < N_OUT / 3; ++s) {
+        const float mean = (r[3 * s] + r[3 * s + 1] + r[3 * s + 2]) * (1.f / 3.f);
+        wb[(3 * s) * a.plane] = r[3 * s] - mean;
+        wb[(3 * s + 1) * a.plane] = 1.f + (r[3 * s + 1] - mean);
+        wb[(3 * s + 2) * a.plane] = r[3 * s + 2] - mean;
+      }
+    }
+  }
+}
+
+template <int CG, int N, int IN, int OUT, bool ROW>
+__global__ void __launch_bounds__(NT) conv_kernel(ConvArgs a) {
+  constexpr int NP = conv_np<ROW>();
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint8_t* sA = smem;                                   // [CG][NP][16 B]
+  uint8_t* sB = smem + CG * NP * 16;                    // [9][CG][N][16 B]
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sB + 9 * CG * N * 16);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+
+  const int tid = threadIdx.x;
+  const long long tiles_per_member = a.plane / TILE;
+  const int b = (int)(blockIdx.x / tiles_per_member);
+  const int p0 = (int)(blockIdx.x - (long long)b * tiles_per_member) * TILE;
+  constexpr bool rowmode = ROW;
+  const int gpr = a.nx >> 3;
+
+  if (tid < 32) tc::tmem_alloc(tslot, 64);
+  if (tid == 0) tc::mbar_init(mbar, 1);
+
+  // weights: 9 * CG * N chunks of 16 bytes
+  for (int i = tid; i < 9 * CG * N; i += NT) cp_async16(sB + i * 16, a.wpk + i * 8);
+
+  conv_stage<CG, IN, ROW>(a, sA, b, p0, tid);
   asm volatile("cp.async.wait_all;\n" ::: "memory");
   tc::fence_proxy_async_smem();
   tc::fence_before_sync();
@@ -194,10 +323,12 @@ __global__ void __launch_bounds__(NT) conv_kernel(ConvArgs a) {
 #pragma unroll 1
     for (int tap = 0; tap < 9; ++tap) {
       const int dy = tap / 3 - 1, dx = tap % 3 - 1;
-      const int start = rowmode ? (1 + dy) * RW + (1 + dx) : (1 + dx) * Lf + nx + dy * nx;
+      // row mode: 8-row groups 128 B apart; grouped mode: 160 B apart
+      const int start = rowmode ? (1 + dy) * RW + (1 + dx) : (1 + dy) * gpr * GSLOT + (1 + dx);
+      constexpr uint32_t sbo = rowmode ? 128u : 16u * GSLOT;
 #pragma unroll
       for (int ks = 0; ks < CG / 2; ++ks) {
-        const uint64_t ad = tc::sdesc(a0 + (uint32_t)((2 * ks * NP + start) * 16), NP * 16, 128);
+        const uint64_t ad = tc::sdesc(a0 + (uint32_t)((2 * ks * NP + start) * 16), NP * 16, sbo);
         const uint64_t bd = tc::sdesc(b0 + (uint32_t)(((tap * CG + 2 * ks) * N) * 16), N * 16, 128);
         tc::mma_bf16(tmem, ad, bd, idesc, acc);
         acc = true;
@@ -214,106 +345,7 @@ __global__ void __launch_bounds__(NT) conv_kernel(ConvArgs a) {
     const int m = tid;                                   // TMEM lane = tile row
     const long long cell = p0 + m;
     const uint32_t lane_addr = tmem + ((uint32_t)(32 * w) << 16);
-    if constexpr (OUT == OUT_MASK) {
-      // backward through ReLU: cotangent of the layer input, zero where the
-      // stored activation is zero (BF16 out, 32 channels)
-      float v[32];
-      tc::tmem_ld32(lane_addr, v);
-#pragma unroll
-      for (int g = 0; g < 4; ++g) {
-        const uint4 mk = *reinterpret_cast<const uint4*>(a.mask + (((long long)b * 4 + g) * a.plane + cell) * 8);
-        const uint32_t mw[4] = {mk.x, mk.y, mk.z, mk.w};
-        uint32_t pk[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int c0 = 8 * g + 2 * j;
-          const bool p0 = (mw[j] & 0x7FFFu) != 0 && !(mw[j] & 0x8000u);
-          const bool p1 = ((mw[j] >> 16) & 0x7FFFu) != 0 && !((mw[j] >> 16) & 0x8000u);
-          pk[j] = pack_bf16x2(p0 ? v[c0] : 0.f, p1 ? v[c0 + 1] : 0.f);
-        }
-        *reinterpret_cast<uint4*>(a.y + (((long long)b * 4 + g) * a.plane + cell) * 8) =
-            make_uint4(pk[0], pk[1], pk[2], pk[3]);
-      }
-    } else if constexpr (OUT == OUT_GELU_GRAD) {
-      // backward through GeLU: cotangent of the layer input times GeLU' of
-      // the stored pre-activation (BF16 out, 32 channels)
-      float v[32];
-      tc::tmem_ld32(lane_addr, v);
-#pragma unroll
-      for (int g = 0; g < 4; ++g) {
-        const uint4 zk = *reinterpret_cast<const uint4*>(a.z + (((long long)b * 4 + g) * a.plane + cell) * 8);
-        const uint32_t zw[4] = {zk.x, zk.y, zk.z, zk.w};
-        uint32_t pk[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int c0 = 8 * g + 2 * j;
-          const float z0 = __uint_as_float(zw[j] << 16), z1 = __uint_as_float(zw[j] & 0xFFFF0000u);
-          pk[j] = pack_bf16x2(v[c0] * gelu_grad(z0), v[c0 + 1] * gelu_grad(z1));
-        }
-        *reinterpret_cast<uint4*>(a.y + (((long long)b * 4 + g) * a.plane + cell) * 8) =
-            make_uint4(pk[0], pk[1], pk[2], pk[3]);
-      }
-    } else if constexpr (OUT == OUT_RELU || OUT == OUT_GELU) {
-      float v[32];
-      tc::tmem_ld32(lane_addr, v);
-#pragma unroll
-      for (int g = 0; g < 4; ++g) {
-        uint32_t pk[4], pz[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int c0 = 8 * g + 2 * j;
-          const float z0 = v[c0] + a.bias[c0], z1 = v[c0 + 1] + a.bias[c0 + 1];
-          if constexpr (OUT == OUT_RELU) {
-            pk[j] = pack_bf16x2(fmaxf(z0, 0.f), fmaxf(z1, 0.f));
-          } else {
-            pk[j] = pack_bf16x2(gelu(z0), gelu(z1));
-            pz[j] = pack_bf16x2(z0, z1);
-          }
-        }
-        *reinterpret_cast<uint4*>(a.y + (((long long)b * 4 + g) * a.plane + cell) * 8) =
-            make_uint4(pk[0], pk[1], pk[2], pk[3]);
-        if (OUT == OUT_GELU && a.z)
-          *reinterpret_cast<uint4*>(a.z + (((long long)b * 4 + g) * a.plane + cell) * 8) =
-              make_uint4(pz[0], pz[1], pz[2], pz[3]);
-      }
-    } else if constexpr (OUT == OUT_SIDES || OUT == OUT_SIDES_RAW) {
-      // side states of the face-state network: channel 3 side + var
-      float v[16];
-      tc::tmem_ld16(lane_addr, v);
-      float* sb = a.w + (long long)b * N_OUT_FACE * a.plane + cell;
-#pragma unroll
-      for (int k = 0; k < N_OUT_FACE; ++k) {
-        const float r = v[k] + a.bias[k];
-        float o = r;
-        if constexpr (OUT == OUT_SIDES) {
-          const int var = k % 3;
-          o = var == 0 ? softplus(r) : (var == 1 ? fmaf(a.std1, r, a.mean1) : fmaf(a.std2, r, a.mean2));
-        }
-        sb[k * a.plane] = o;
-      }
-    } else {
-      float v[32], v2[16];
-      tc::tmem_ld32(lane_addr, v);
-      tc::tmem_ld16(lane_addr + 32, v2);
-      float r[N_OUT];
-#pragma unroll
-      for (int k = 0; k < 32; ++k) r[k] = v[k] + a.bias[k];
-#pragma unroll
-      for (int k = 32; k < N_OUT; ++k) r[k] = v2[k - 32] + a.bias[k];
-      float* wb = a.w + (long long)b * N_OUT * a.plane + cell;
-      if constexpr (OUT == OUT_RAW) {
-#pragma unroll
-        for (int k = 0; k < N_OUT; ++k) wb[k * a.plane] = r[k];
-      } else {
-#pragma unroll
-        for (int s = 0; s < N_OUT / 3; ++s) {
-          const float mean = (r[3 * s] + r[3 * s + 1] + r[3 * s + 2]) * (1.f / 3.f);
-          wb[(3 * s) * a.plane] = r[3 * s] - mean;
-          wb[(3 * s + 1) * a.plane] = 1.f + (r[3 * s + 1] - mean);
-          wb[(3 * s + 2) * a.plane] = r[3 * s + 2] - mean;
-        }
-      }
-    }
+    conv_epilogue<N, OUT>(a, b, cell, lane_addr);
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -985,8 +1017,7 @@ __global__ void __launch_bounds__(NT) dw_tc_kernel(const uint16_t* x, const floa
         tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + mt * NB + c0, v);
 #pragma unroll
         for (int j = 0; j < 16; ++j)
-          if (c0 + j < CO && n > 0) pp[(long long)r * CO + c0 + j] = v[j];
-          else if (c0 + j < CO) pp[(long long)r * CO + c0 + j] = 0.f;
+          if (c0 + j < CO) pp[(long long)(c0 + j) * ROWS + r] = n > 0 ? v[j] : 0.f;
       }
     }
   }
@@ -995,23 +1026,27 @@ __global__ void __launch_bounds__(NT) dw_tc_kernel(const uint16_t* x, const floa
   if ((tid >> 5) == 0) tc::tmem_dealloc(tmem, 256);
 }
 
-// Sum the CTAs' partial sums into dparams (PyTorch layout): row r = tap *
-// CI + ci gives dW[co][ci][tap], row 9 CI gives db.  A block of 8 warps
-// handles 32 consecutive outputs; warp w sums partials [w P / 8, (w+1) P / 8)
-// in order, then the 8 sums are added in warp order (a fixed order: the
-// result does not depend on timing).
+// Sum the CTAs' partial sums into dparams (PyTorch layout).  A CTA's
+// partials are [CO][ROWS] (column co of the accumulator, row r = tap * CI +
+// ci gives dW[co][ci][tap], row 9 CI gives db; the lanes of a warp write
+// consecutive rows).  A block of 8 warps handles 32 consecutive (co, r)
+// outputs; warp w sums partials [w P / 8, (w+1) P / 8) in order, then the 8
+// sums are added in warp order (a fixed order: the result does not depend
+// on timing).
 template <int CI, int CO>
 __global__ void __launch_bounds__(256) dw_tc_reduce_kernel(const float* part, int nparts, float* dW, float* db,
                                                            float scale) {
   constexpr int ROWS = dw_mt<CI>() * 128;
-  constexpr int NE = (9 * CI + 1) * CO;
+  constexpr int NR = 9 * CI + 1;
+  constexpr int NE = NR * CO;
   __shared__ float sh[8][32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int i = blockIdx.x * 32 + lane;
+  const int co = i / NR, r = i - co * NR;
   float s = 0.f;
   if (i < NE) {
     const int k0 = warp * nparts / 8, k1 = (warp + 1) * nparts / 8;
-    for (int k = k0; k < k1; ++k) s += part[(long long)k * ROWS * CO + i];
+    for (int k = k0; k < k1; ++k) s += part[(long long)k * ROWS * CO + co * ROWS + r];
   }
   sh[warp][lane] = s;
   __syncthreads();
@@ -1019,7 +1054,6 @@ __global__ void __launch_bounds__(256) dw_tc_reduce_kernel(const float* part, in
     float t = sh[0][lane];
 #pragma unroll
     for (int w = 1; w < 8; ++w) t += sh[w][lane];
-    const int r = i / CO, co = i - r * CO;
     if (r < 9 * CI) {
       const int tap = r / CI, c = r - tap * CI;
       dW[(co * CI + c) * 9 + tap] += scale * t;
@@ -1045,7 +1079,7 @@ __device__ __forceinline__ void stmatrix_x4(uint32_t row_addr, const uint32_t (&
                :: "r"(row_addr), "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3]) : "memory");
 }
 
-// Raw positions of a 64-cell tile: row mode (nx a multiple of 128) 3 rows of
+// Raw positions of a 64-cell tile: row mode (nx a multiple of DWK) 3 rows of
 // DWK + 2 cells; flat mode (nx dividing DWK) 3 strips of DWK + 2 nx cells.
 constexpr int DW_RW = DWK + 2;
 constexpr int DW_NPOS_ROW = 3 * DW_RW;
@@ -1066,6 +1100,7 @@ __global__ void __launch_bounds__(NT) dw_tx_kernel(const uint16_t* x, const uint
   constexpr int ROWS = MT * 128;
   constexpr int NP = dw_npos<ROW>();
   static_assert(CI % 8 == 0 && NB % 16 == 0 && MT * NB <= 256, "shape of the MMA and TMEM columns");
+  constexpr uint32_t NCOLS = MT * NB <= 32 ? 32u : (MT * NB <= 64 ? 64u : (MT * NB <= 128 ? 128u : 256u));
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* R = smem;                                   // [CG][NP][16 B] raw input records
   uint8_t* RB = R + CG * NP * 16;                      // [CGO][DWK][16 B] raw cotangent records
@@ -1089,7 +1124,7 @@ __global__ void __launch_bounds__(NT) dw_tx_kernel(const uint16_t* x, const uint
     tc::mbar_init(mbar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
-  if (warp == 0) tc::tmem_alloc(tslot, 256);
+  if (warp == 0) tc::tmem_alloc(tslot, NCOLS);
 
   // raw records of tile `tile` (cp.async, committed as one group)
   auto stage_raw = [&](long long tile) {
@@ -1199,13 +1234,13 @@ __global__ void __launch_bounds__(NT) dw_tx_kernel(const uint16_t* x, const uint
         tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + mt * NB + c0, v);
 #pragma unroll
         for (int j = 0; j < 16; ++j)
-          if (c0 + j < CO) pp[(long long)r * CO + c0 + j] = issued > 0 ? v[j] : 0.f;
+          if (c0 + j < CO) pp[(long long)(c0 + j) * ROWS + r] = issued > 0 ? v[j] : 0.f;
       }
     }
   }
   tc::fence_before_sync();
   __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(tmem, 256);
+  if (warp == 0) tc::tmem_dealloc(tmem, NCOLS);
 }
 
 template <int CI, int CO, int CGO, bool ROW>
@@ -1230,11 +1265,11 @@ cudaError_t weight_grad_tc(const uint16_t* x, const float* q, const uint16_t* dy
   const long long ntiles = (long long)B * (plane / DWK);
   const int nctas = (int)(ntiles < DW_CTAS ? ntiles : DW_CTAS);
   if constexpr (CI % 8 == 0) {
-    // staging by cp.async + ldmatrix / stmatrix: a tile is half a row
-    // (nx a multiple of 128) or whole rows (nx dividing 64)
-    if (nx % 128 == 0 || (nx <= 64 && DWK % nx == 0)) {
+    // staging by cp.async + ldmatrix / stmatrix: a tile lies within one row
+    // (nx a multiple of 64) or covers whole rows (nx dividing 64)
+    if (nx % DWK == 0 || DWK % nx == 0) {
       cudaError_t e;
-      if (nx % 128 == 0) e = launch_dw_tx<CI, CO, CGO, true>(x, dy, part, nx, ny, plane, ntiles, nctas, net, s);
+      if (nx % DWK == 0) e = launch_dw_tx<CI, CO, CGO, true>(x, dy, part, nx, ny, plane, ntiles, nctas, net, s);
       else e = launch_dw_tx<CI, CO, CGO, false>(x, dy, part, nx, ny, plane, ntiles, nctas, net, s);
       if (e != cudaSuccess) return e;
       const int ne = (9 * CI + 1) * CO;

@@ -253,3 +253,30 @@ def test_stencil_net_backward_is_deterministic(fv, ny, nx):
     b = fv.net_backward(net, f32(q0).cuda(), dw)
     assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
     assert float(a[0].abs().max()) > 0
+
+
+@pytest.mark.parametrize("ny,nx,B", [(64, 64, 64), (256, 256, 16)])
+def test_batched_convolutions_equal_single_members(fv, ny, nx, B):
+    """A batch of many tiles runs the persistent convolution (weights resident
+    per CTA, two staging buffers and accumulators); one member alone runs one
+    tile per CTA.  Both issue each tile's MMAs in the same order, so the
+    forward outputs of both networks and the backward's dq agree bit for
+    bit, member by member."""
+    from oracle import face_net as ofn
+    p = rand_params(8, last_scale=0.3)
+    net = gpu_net(fv, p)
+    pf = ofn.init_params(3, MEAN, STD, scale=0.5)
+    fnet = fv.face_net_create(pf.flat().numpy().astype(np.float32), MEAN, STD)
+    q = f32(W.as_f32_exact(W.random_smooth_swe(nx, seed=7, members=B, vel=0.2)[:, :, :ny, :])).cuda()
+    g = torch.Generator().manual_seed(9)
+    dw = torch.randn(B, 36, ny, nx, generator=g).float().cuda()
+    w_all = fv.stencil_net_forward(net, q)
+    s_all = fv.face_net_forward(fnet, q)
+    ds = dw[:, :12].contiguous()
+    dq_all = fv.net_backward(net, q, dw)[1]
+    dqf_all = fv.net_backward(fnet, q, ds)[1]
+    for b in range(0, B, max(1, B // 8)):
+        assert torch.equal(w_all[b:b + 1], fv.stencil_net_forward(net, q[b:b + 1])), b
+        assert torch.equal(s_all[b:b + 1], fv.face_net_forward(fnet, q[b:b + 1])), b
+        assert torch.equal(dq_all[b:b + 1], fv.net_backward(net, q[b:b + 1], dw[b:b + 1])[1]), b
+        assert torch.equal(dqf_all[b:b + 1], fv.net_backward(fnet, q[b:b + 1], ds[b:b + 1])[1]), b
