@@ -848,7 +848,7 @@ __global__ void dx_first_kernel(const uint16_t* dy, const float* W1, float* dq, 
 // exact in FP32, so only the order of the FP32 sums differs from a CUDA-core
 // reduction.
 constexpr int DWK = 64;                  // cells per K-tile
-constexpr int DW_CTAS = 256;             // CTAs (fixed: the partial sums do not depend on the GPU)
+constexpr int DW_CTAS = 304;             // CTAs (fixed: the partial sums do not depend on the GPU)
 constexpr uint32_t DW_SBO = (DWK / 8) * 128;   // bytes between 8-row groups
 
 template <int CI>
@@ -1064,12 +1064,13 @@ __global__ void __launch_bounds__(256) dw_tc_reduce_kernel(const float* part, in
 }
 
 // The same GEMM with the staging done by the copy engines and the matrix
-// instructions (CI = 32): the raw 16-byte records the tile needs (the input
-// at the three x-shifted strips of positions the forward convolution stages,
-// and the cotangent of the tile's cells) arrive by cp.async; every warp then
-// transposes 8x8 blocks (8 cells x 8 channels) with ldmatrix.trans and writes
-// them as K-major rows with stmatrix.  The raw records of the next tile load
-// while the tensor core runs the current tile's MMAs.
+// instructions (CI a multiple of 8): the raw 16-byte records the tile needs
+// (the input at the three rows or x-shifted strips of positions the tile's
+// taps read, and the cotangent of the tile's cells) arrive by cp.async, two
+// tiles ahead of use (two raw buffers); every warp then transposes 8x8 blocks
+// (8 cells x 8 channels) with ldmatrix.trans and writes them as K-major rows
+// with stmatrix.  The shared-memory addresses of a warp's blocks do not
+// depend on the tile and are computed once.
 __device__ __forceinline__ void ldmatrix_x4_trans(uint32_t row_addr, uint32_t (&w)[4]) {
   asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];\n"
                : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]) : "r"(row_addr));
@@ -1080,15 +1081,18 @@ __device__ __forceinline__ void stmatrix_x4(uint32_t row_addr, const uint32_t (&
 }
 
 // Raw positions of a 64-cell tile: row mode (nx a multiple of DWK) 3 rows of
-// DWK + 2 cells; flat mode (nx dividing DWK) 3 strips of DWK + 2 nx cells.
+// DWK + 2 cells; strip mode (nx < DWK dividing it) 3 x-shifted strips of
+// DWK + 2 nx cells.
 constexpr int DW_RW = DWK + 2;
 constexpr int DW_NPOS_ROW = 3 * DW_RW;
-constexpr int DW_NPOS_FLAT = 3 * (DWK + 2 * 64);
+constexpr int DW_NPOS_FLAT = 3 * (DWK + 2 * (DWK / 2));
 template <bool ROW>
 constexpr int dw_npos() { return ROW ? DW_NPOS_ROW : DW_NPOS_FLAT; }
 template <int CI, int CGO, bool ROW>
+constexpr int dwx_raw_bytes() { return (CI / 8) * dw_npos<ROW>() * 16 + CGO * DWK * 16; }
+template <int CI, int CGO, bool ROW>
 constexpr int dwx_smem_bytes() {
-  return (CI / 8) * dw_npos<ROW>() * 16 + CGO * DWK * 16 + (dw_mt<CI>() * 128 + 8 * CGO) * DWK * 2 + 64;
+  return 2 * dwx_raw_bytes<CI, CGO, ROW>() + (dw_mt<CI>() * 128 + 8 * CGO) * DWK * 2 + 64;
 }
 
 template <int CI, int CO, int CGO, bool ROW>
@@ -1099,12 +1103,16 @@ __global__ void __launch_bounds__(NT) dw_tx_kernel(const uint16_t* x, const uint
   constexpr int MT = dw_mt<CI>();
   constexpr int ROWS = MT * 128;
   constexpr int NP = dw_npos<ROW>();
+  constexpr int RAW = dwx_raw_bytes<CI, CGO, ROW>();
+  constexpr int NW = NT / 32;
+  constexpr int A_PER_WARP = 9 * CG * 8 / 4 / NW;     // ldmatrix.x4 blocks of A per warp and tile
+  constexpr int B_PER_WARP = CGO * 8 / 4 / NW;
   static_assert(CI % 8 == 0 && NB % 16 == 0 && MT * NB <= 256, "shape of the MMA and TMEM columns");
+  static_assert((9 * CG * 8 / 4) % NW == 0 && (CGO * 8 / 4) % NW == 0, "blocks per warp");
   constexpr uint32_t NCOLS = MT * NB <= 32 ? 32u : (MT * NB <= 64 ? 64u : (MT * NB <= 128 ? 128u : 256u));
   extern __shared__ __align__(1024) uint8_t smem[];
-  uint8_t* R = smem;                                   // [CG][NP][16 B] raw input records
-  uint8_t* RB = R + CG * NP * 16;                      // [CGO][DWK][16 B] raw cotangent records
-  uint8_t* A = RB + CGO * DWK * 16;                    // K-major [ROWS][DWK]
+  uint8_t* R = smem;                                   // 2 x {[CG][NP][16 B] input, [CGO][DWK][16 B] cotangent}
+  uint8_t* A = smem + 2 * RAW;                         // K-major [ROWS][DWK]
   uint8_t* Bm = A + ROWS * DWK * 2;                    // K-major [NB][DWK]
   uint64_t* mbar = reinterpret_cast<uint64_t*>(Bm + NB * DWK * 2);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
@@ -1113,7 +1121,7 @@ __global__ void __launch_bounds__(NT) dw_tx_kernel(const uint16_t* x, const uint
   const long long t1 = (long long)(blockIdx.x + 1) * ntiles / gridDim.x;
   const long long tiles_per_member = plane / DWK;
   const int lg = (nx & (nx - 1)) == 0 ? __ffs(nx) - 1 : -1;
-  const int Lf = DWK + 2 * nx;                         // flat-mode strip
+  const int Lf = DWK + 2 * nx;                         // strip mode
 
   // the ones row (bias) and the zero padding of A, once
   for (int i = tid; i < (ROWS - 9 * CI) * DWK; i += NT) {
@@ -1126,8 +1134,34 @@ __global__ void __launch_bounds__(NT) dw_tx_kernel(const uint16_t* x, const uint
   }
   if (warp == 0) tc::tmem_alloc(tslot, NCOLS);
 
-  // raw records of tile `tile` (cp.async, committed as one group)
-  auto stage_raw = [&](long long tile) {
+  // this lane's row addresses of its warp's 8x8 blocks: block t = (tap, g,
+  // kb) of A reads raw positions start(tap) + 8 kb .. + 7 of group g and
+  // writes rows tap CI + 8 g .. + 7 at cells 8 kb .. + 7; block (g, kb) of B
+  // likewise from the cotangent
+  const uint32_t r_base = tc::smem_u32(R), a_base = tc::smem_u32(A), b_base = tc::smem_u32(Bm);
+  uint32_t a_ld[A_PER_WARP], a_st[A_PER_WARP], b_ld[B_PER_WARP], b_st[B_PER_WARP];
+  {
+    const int m = lane >> 3, row = lane & 7;
+#pragma unroll
+    for (int k = 0; k < A_PER_WARP; ++k) {
+      const int t = 4 * (warp + NW * k) + m, kb = t & 7, g = (t >> 3) % CG, tap = (t >> 3) / CG;
+      const int dy_ = tap / 3 - 1, dx_ = tap % 3 - 1;
+      const int start = ROW ? (1 + dy_) * DW_RW + (1 + dx_) : (1 + dx_) * Lf + nx + dy_ * nx;
+      a_ld[k] = (uint32_t)((g * NP + start + 8 * kb + row) * 16);
+      a_st[k] = a_base + dw_off(tap * CI + 8 * g + row, 8 * kb);
+    }
+#pragma unroll
+    for (int k = 0; k < B_PER_WARP; ++k) {
+      const int t = 4 * (warp + NW * k) + m, kb = t & 7, g = t >> 3;
+      b_ld[k] = (uint32_t)(CG * NP * 16 + (g * DWK + 8 * kb + row) * 16);
+      b_st[k] = b_base + dw_off(8 * g + row, 8 * kb);
+    }
+  }
+
+  // raw records of tile `tile` into raw buffer `buf` (cp.async; the caller commits)
+  auto stage_raw = [&](long long tile, int buf) {
+    uint8_t* Rb = R + buf * RAW;
+    uint8_t* RBb = Rb + CG * NP * 16;
     const int b = (int)(tile / tiles_per_member);
     const int p0 = (int)(tile - (long long)b * tiles_per_member) * DWK;
     const int y0 = lg >= 0 ? p0 >> lg : p0 / nx, x0 = p0 - y0 * nx;
@@ -1148,52 +1182,46 @@ __global__ void __launch_bounds__(NT) dw_tx_kernel(const uint16_t* x, const uint
       const long long cell = (long long)yy * nx + xx;
 #pragma unroll
       for (int g = 0; g < CG; ++g)
-        cp_async16(R + (g * NP + n) * 16, x + (((long long)b * CG + g) * plane + cell) * 8);
+        cp_async16(Rb + (g * NP + n) * 16, x + (((long long)b * CG + g) * plane + cell) * 8);
     }
     for (int n = tid; n < CGO * DWK; n += NT) {
       const int g = n / DWK, k = n - g * DWK;
-      cp_async16(RB + n * 16, dy + (((long long)b * CGO + g) * plane + p0 + k) * 8);
+      cp_async16(RBb + n * 16, dy + (((long long)b * CGO + g) * plane + p0 + k) * 8);
     }
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
   };
 
-  if (t0 < t1) stage_raw(t0);
+  if (t0 < t1) stage_raw(t0, 0);
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  if (t0 + 1 < t1) stage_raw(t0 + 1, 1);
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = *tslot;
   constexpr uint32_t idesc = tc::idesc_bf16_f32(128, NB);
-  const uint32_t r_base = tc::smem_u32(R), rb_base = tc::smem_u32(RB);
-  const uint32_t a_base = tc::smem_u32(A), b_base = tc::smem_u32(Bm);
   bool ok = true;
   int issued = 0;
   for (long long tile = t0; tile < t1; ++tile) {
     const int i = (int)(tile - t0);
-    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    const uint32_t rb = r_base + (uint32_t)((i & 1) * RAW);
+    asm volatile("cp.async.wait_group 1;\n" ::: "memory");   // this tile's records (one later group may pend)
     // A and B are free once the MMAs of the previous tile are done
     bool w = true;
     if (i >= 1) w = tc::mbar_wait_bounded(mbar, (uint32_t)(i - 1) & 1u, WAIT_ITERS);
     ok = __syncthreads_and(w) && ok;
     if (!ok) break;
     tc::fence_after_sync();
-    // A: 8x8 blocks (tap, g, kb): raw positions start(tap) + 8 kb .. + 7 of group g
-    constexpr int NBLK_A = 9 * CG * 8;
-    for (int ins = warp; ins < NBLK_A / 4; ins += NT / 32) {
-      const int m = lane >> 3, row = lane & 7;
-      const int t = 4 * ins + m, kb = t & 7, g = (t >> 3) % CG, tap = (t >> 3) / CG;
-      const int dy_ = tap / 3 - 1, dx_ = tap % 3 - 1;
-      const int start = ROW ? (1 + dy_) * DW_RW + (1 + dx_) : (1 + dx_) * Lf + nx + dy_ * nx;
+#pragma unroll
+    for (int k = 0; k < A_PER_WARP; ++k) {
       uint32_t v[4];
-      ldmatrix_x4_trans(r_base + (uint32_t)((g * NP + start + 8 * kb + row) * 16), v);
-      stmatrix_x4(a_base + dw_off(tap * CI + 8 * g + row, 8 * kb), v);
+      ldmatrix_x4_trans(rb + a_ld[k], v);
+      stmatrix_x4(a_st[k], v);
     }
-    // B: 8x8 blocks (g, kb) of the cotangent
-    for (int ins = warp; ins < CGO * 8 / 4; ins += NT / 32) {
-      const int m = lane >> 3, row = lane & 7;
-      const int t = 4 * ins + m, kb = t & 7, g = t >> 3;
+#pragma unroll
+    for (int k = 0; k < B_PER_WARP; ++k) {
       uint32_t v[4];
-      ldmatrix_x4_trans(rb_base + (uint32_t)((g * DWK + 8 * kb + row) * 16), v);
-      stmatrix_x4(b_base + dw_off(8 * g + row, 8 * kb), v);
+      ldmatrix_x4_trans(rb + b_ld[k], v);
+      stmatrix_x4(b_st[k], v);
     }
     tc::fence_proxy_async_smem();
     tc::fence_before_sync();
@@ -1212,8 +1240,9 @@ __global__ void __launch_bounds__(NT) dw_tx_kernel(const uint16_t* x, const uint
       tc::mma_commit(mbar);
     }
     issued = i + 1;
-    // the raw records of the next tile load while the tensor core works
-    if (tile + 1 < t1) stage_raw(tile + 1);
+    // this raw buffer is read: the records of tile + 2 go into it
+    if (tile + 2 < t1) stage_raw(tile + 2, i & 1);
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
   }
   asm volatile("cp.async.wait_all;\n" ::: "memory");
   if (issued > 0) {
