@@ -60,7 +60,7 @@ constexpr uint32_t WAIT_ITERS = 1u << 22;
 
 enum { IN_STATE = 0, IN_ACT = 1 };
 enum { OUT_RELU = 0, OUT_W = 1, OUT_RAW = 2, OUT_MASK = 3, OUT_GELU = 4, OUT_SIDES = 5, OUT_SIDES_RAW = 6,
-       OUT_GELU_GRAD = 7 };
+       OUT_GELU_GRAD = 7, OUT_DQ = 8 };
 
 struct ConvArgs {
   const float* q;          // IN_STATE: [B][3][plane]
@@ -68,7 +68,8 @@ struct ConvArgs {
   const uint16_t* wpk;     // [9][CG][N][8]
   const float* bias;
   uint16_t* y;             // OUT_RELU: [B][4][plane][8]
-  float* w;                // OUT_W / OUT_RAW: [B][36][plane]; OUT_SIDES(_RAW): [B][12][plane]
+  float* w;                // OUT_W / OUT_RAW: [B][36][plane]; OUT_SIDES(_RAW): [B][12][plane];
+                           // OUT_DQ: dq [B][3][plane], added to
   const uint16_t* mask;    // OUT_MASK: activation [B][4][plane][8]; output kept where it is > 0
   uint16_t* z;             // OUT_GELU: pre-activations out (if non-null); OUT_GELU_GRAD: in
   float mean0, mean1, mean2, rstd0, rstd1, rstd2;
@@ -246,6 +247,14 @@ __device__ __forceinline__ void conv_epilogue(const ConvArgs& a, int b, long lon
         *reinterpret_cast<uint4*>(a.z + (((long long)b * 4 + g) * a.plane + cell) * 8) =
             make_uint4(pz[0], pz[1], pz[2], pz[3]);
     }
+  } else if constexpr (OUT == OUT_DQ) {
+    // first layer's dX (3 channels of the normalised state): dq += dx / std
+    float v[16];
+    tc::tmem_ld16(lane_addr, v);
+    float* d = a.w + (long long)b * 3 * a.plane + cell;
+    d[0] += v[0] * a.rstd0;
+    d[a.plane] += v[1] * a.rstd1;
+    d[2 * a.plane] += v[2] * a.rstd2;
   } else if constexpr (OUT == OUT_SIDES || OUT == OUT_SIDES_RAW) {
     // side states of the face-state network: channel 3 side + var
     float v[16];
@@ -354,15 +363,16 @@ __global__ void __launch_bounds__(NT) conv_kernel(ConvArgs a) {
 
 // FP32 master parameters -> BF16 operand layouts.
 //   forward  wf[l][tap][g][n][k8] = W_l[n][8g + k8][ky][kx]
-//   backward wb[l][tap][g][n][k8] = W_l[8g + k8][n][2 - ky][2 - kx]   (l >= 1)
+//   backward wb[l][tap][g][n][k8] = W_l[8g + k8][n][2 - ky][2 - kx]   (l >= 1; l = 0 with
+//            N = 16, n < 3 the state's channels, the rest zero)
 // The row-pipelined operands (w1g, wpair, w4ring) exist for the stencil
 // network only; they are skipped when null.  n_last: N of the last layer.
 __global__ void repack_kernel(const float* params, ParamLayout L, uint16_t* wf0, uint16_t* wf1,
-                              uint16_t* wf2, uint16_t* wf3, uint16_t* wb1, uint16_t* wb2,
+                              uint16_t* wf2, uint16_t* wf3, uint16_t* wb0, uint16_t* wb1, uint16_t* wb2,
                               uint16_t* wb3, uint16_t* w1g, uint16_t* wp1, uint16_t* wp2,
                               uint16_t* w4r, int n_last) {
   uint16_t* wf[4] = {wf0, wf1, wf2, wf3};
-  uint16_t* wb[4] = {nullptr, wb1, wb2, wb3};
+  uint16_t* wb[4] = {wb0, wb1, wb2, wb3};
   const int cgs[4] = {CG_IN0, CG_HID, CG_HID, CG_HID};
   const int ns[4] = {HID, HID, HID, n_last};
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -433,10 +443,11 @@ __global__ void repack_kernel(const float* params, ParamLayout L, uint16_t* wf0,
       const __nv_bfloat16 h = __float2bfloat16_rn(v);
       wf[l][i] = *reinterpret_cast<const uint16_t*>(&h);
     }
-    if (l >= 1) {
-      // dX of layer l: K = its output channels (groups of 8), N = its inputs (32)
+    if (wb[l]) {
+      // dX of layer l: K = its output channels (groups of 8), N = its inputs
+      // (32; 16 for the 3 state channels of layer 1)
       const int CGo = (L.cout[l] + 7) / 8 + ((L.cout[l] + 7) / 8) % 2;   // even number of groups
-      const int Nb = HID;
+      const int Nb = l == 0 ? DQ_N : HID;
       const int totb = 9 * CGo * Nb * 8;
       if (i < totb) {
         const int k8 = i % 8, n = (i / 8) % Nb, g = (i / (8 * Nb)) % CGo, tap = i / (8 * Nb * CGo);
@@ -486,7 +497,7 @@ cudaError_t repack(Net& net, cudaStream_t s) {
   static_assert(W4R_ELEMS <= 9 * CG_HID * N_OUT_PAD * 8, "repack grid covers the layer-4 ring weights");
   const ParamLayout Lk = param_layout(net.kind);
   repack_kernel<<<(maxn + 255) / 256, 256, 0, s>>>(net.params, Lk, net.wf[0], net.wf[1], net.wf[2],
-                                                   net.wf[3], net.wb[1], net.wb[2], net.wb[3],
+                                                   net.wf[3], net.wb[0], net.wb[1], net.wb[2], net.wb[3],
                                                    net.w1g, net.wpair[1], net.wpair[2], net.w4ring,
                                                    net.kind == NET_FACE ? N_OUT_FACE_PAD : N_OUT_PAD);
   return cudaGetLastError();
@@ -792,40 +803,6 @@ __global__ void dw_reduce_kernel(const float* part, int nparts, float* dW, float
   }
 }
 
-// Cotangent of the normalised state from the first layer's output cotangent
-// (3 input channels: a small dot product per cell, CUDA cores):
-//   dx[ci](p) = sum_tap sum_co W1[co][ci][tap] dy[co](p - off(tap));  dq += dx / std.
-__global__ void dx_first_kernel(const uint16_t* dy, const float* W1, float* dq, int nx, int ny,
-                                long long plane, long long cells, float r0, float r1, float r2) {
-  __shared__ float w[HID * 3 * 9];
-  for (int i = threadIdx.x; i < HID * 3 * 9; i += blockDim.x) w[i] = W1[i];
-  __syncthreads();
-  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= cells) return;
-  const long long b = t / plane, cell = t - b * plane;
-  const int y = (int)(cell / nx), x = (int)(cell - (long long)(cell / nx) * nx);
-  float acc[3] = {0.f, 0.f, 0.f};
-  for (int tap = 0; tap < 9; ++tap) {
-    const int ky = tap / 3, kx = tap % 3;
-    const int yy = wrapi(y - (ky - 1), ny), xx = wrapi(x - (kx - 1), nx);
-    const long long c2 = (long long)yy * nx + xx;
-    for (int g = 0; g < 4; ++g) {
-      const uint4 v = *reinterpret_cast<const uint4*>(dy + ((b * 4 + g) * plane + c2) * 8);
-      const float vv[8] = {bf16_lo(v.x), bf16_hi(v.x), bf16_lo(v.y), bf16_hi(v.y),
-                           bf16_lo(v.z), bf16_hi(v.z), bf16_lo(v.w), bf16_hi(v.w)};
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const int co = 8 * g + j;
-#pragma unroll
-        for (int ci = 0; ci < 3; ++ci) acc[ci] = fmaf(w[(co * 3 + ci) * 9 + tap], vv[j], acc[ci]);
-      }
-    }
-  }
-  float* d = dq + b * 3 * plane + cell;
-  d[0] += acc[0] * r0;
-  d[plane] += acc[1] * r1;
-  d[2 * plane] += acc[2] * r2;
-}
 
 // ---------------------------------------------------------------------------
 // Weight and bias gradients on the tensor cores.
@@ -1033,11 +1010,12 @@ __global__ void __launch_bounds__(NT) dw_tc_kernel(const uint16_t* x, const floa
 // outputs; warp w sums partials [w P / 8, (w+1) P / 8) in order, then the 8
 // sums are added in warp order (a fixed order: the result does not depend
 // on timing).
-template <int CI, int CO>
+template <int CI, int CO, int CIP = CI>
 __global__ void __launch_bounds__(256) dw_tc_reduce_kernel(const float* part, int nparts, float* dW, float* db,
                                                            float scale) {
-  constexpr int ROWS = dw_mt<CI>() * 128;
-  constexpr int NR = 9 * CI + 1;
+  // CIP: input channels of the GEMM rows (CI padded; rows of channels >= CI are dropped)
+  constexpr int ROWS = dw_mt<CIP>() * 128;
+  constexpr int NR = 9 * CIP + 1;
   constexpr int NE = NR * CO;
   __shared__ float sh[8][32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1054,9 +1032,9 @@ __global__ void __launch_bounds__(256) dw_tc_reduce_kernel(const float* part, in
     float t = sh[0][lane];
 #pragma unroll
     for (int w = 1; w < 8; ++w) t += sh[w][lane];
-    if (r < 9 * CI) {
-      const int tap = r / CI, c = r - tap * CI;
-      dW[(co * CI + c) * 9 + tap] += scale * t;
+    if (r < 9 * CIP) {
+      const int tap = r / CIP, c = r - tap * CIP;
+      if (c < CI) dW[(co * CI + c) * 9 + tap] += scale * t;
     } else {
       db[co] += scale * t;
     }
@@ -1105,10 +1083,9 @@ __global__ void __launch_bounds__(NT) dw_tx_kernel(const uint16_t* x, const uint
   constexpr int NP = dw_npos<ROW>();
   constexpr int RAW = dwx_raw_bytes<CI, CGO, ROW>();
   constexpr int NW = NT / 32;
-  constexpr int A_PER_WARP = 9 * CG * 8 / 4 / NW;     // ldmatrix.x4 blocks of A per warp and tile
-  constexpr int B_PER_WARP = CGO * 8 / 4 / NW;
+  constexpr int A_X4 = 9 * CG * 8 / 4, B_X4 = CGO * 8 / 4;   // ldmatrix.x4 blocks of A, B per tile
+  constexpr int A_PER_WARP = (A_X4 + NW - 1) / NW, B_PER_WARP = (B_X4 + NW - 1) / NW;
   static_assert(CI % 8 == 0 && NB % 16 == 0 && MT * NB <= 256, "shape of the MMA and TMEM columns");
-  static_assert((9 * CG * 8 / 4) % NW == 0 && (CGO * 8 / 4) % NW == 0, "blocks per warp");
   constexpr uint32_t NCOLS = MT * NB <= 32 ? 32u : (MT * NB <= 64 ? 64u : (MT * NB <= 128 ? 128u : 256u));
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* R = smem;                                   // 2 x {[CG][NP][16 B] input, [CGO][DWK][16 B] cotangent}
@@ -1144,7 +1121,8 @@ __global__ void __launch_bounds__(NT) dw_tx_kernel(const uint16_t* x, const uint
     const int m = lane >> 3, row = lane & 7;
 #pragma unroll
     for (int k = 0; k < A_PER_WARP; ++k) {
-      const int t = 4 * (warp + NW * k) + m, kb = t & 7, g = (t >> 3) % CG, tap = (t >> 3) / CG;
+      const int ins = warp + NW * k < A_X4 ? warp + NW * k : 0;   // (a warp past the end skips it)
+      const int t = 4 * ins + m, kb = t & 7, g = (t >> 3) % CG, tap = (t >> 3) / CG;
       const int dy_ = tap / 3 - 1, dx_ = tap % 3 - 1;
       const int start = ROW ? (1 + dy_) * DW_RW + (1 + dx_) : (1 + dx_) * Lf + nx + dy_ * nx;
       a_ld[k] = (uint32_t)((g * NP + start + 8 * kb + row) * 16);
@@ -1152,7 +1130,8 @@ __global__ void __launch_bounds__(NT) dw_tx_kernel(const uint16_t* x, const uint
     }
 #pragma unroll
     for (int k = 0; k < B_PER_WARP; ++k) {
-      const int t = 4 * (warp + NW * k) + m, kb = t & 7, g = t >> 3;
+      const int ins = warp + NW * k < B_X4 ? warp + NW * k : 0;
+      const int t = 4 * ins + m, kb = t & 7, g = t >> 3;
       b_ld[k] = (uint32_t)(CG * NP * 16 + (g * DWK + 8 * kb + row) * 16);
       b_st[k] = b_base + dw_off(8 * g + row, 8 * kb);
     }
@@ -1213,15 +1192,19 @@ __global__ void __launch_bounds__(NT) dw_tx_kernel(const uint16_t* x, const uint
     tc::fence_after_sync();
 #pragma unroll
     for (int k = 0; k < A_PER_WARP; ++k) {
-      uint32_t v[4];
-      ldmatrix_x4_trans(rb + a_ld[k], v);
-      stmatrix_x4(a_st[k], v);
+      if (A_X4 % NW == 0 || warp + NW * k < A_X4) {
+        uint32_t v[4];
+        ldmatrix_x4_trans(rb + a_ld[k], v);
+        stmatrix_x4(a_st[k], v);
+      }
     }
 #pragma unroll
     for (int k = 0; k < B_PER_WARP; ++k) {
-      uint32_t v[4];
-      ldmatrix_x4_trans(rb + b_ld[k], v);
-      stmatrix_x4(b_st[k], v);
+      if (B_X4 % NW == 0 || warp + NW * k < B_X4) {
+        uint32_t v[4];
+        ldmatrix_x4_trans(rb + b_ld[k], v);
+        stmatrix_x4(b_st[k], v);
+      }
     }
     tc::fence_proxy_async_smem();
     tc::fence_before_sync();
@@ -1357,6 +1340,63 @@ cudaError_t weight_grad(const uint16_t* x, const float* q, const uint16_t* dy, f
   return weight_grad_t<CI, CO, CGO, false>(x, q, dy, dW, db, part, B, ny, nx, net, scale, s);
 }
 
+// The normalised state as the first layer's BF16 input records [B][1][plane][8]
+// (channels h, hu, hv, then zeros), rounded as the forward convolution rounds it.
+__global__ void pack_input_kernel(const float* q, uint16_t* x0, long long plane, long long cells, float m0,
+                                  float m1, float m2, float r0, float r1, float r2) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= cells) return;
+  const long long b = t / plane, cell = t - b * plane;
+  const float* qb = q + b * 3 * plane + cell;
+  const float h0 = (qb[0] - m0) * r0, h1 = (qb[plane] - m1) * r1, h2 = (qb[2 * plane] - m2) * r2;
+  *reinterpret_cast<uint4*>(x0 + t * 8) = make_uint4(pack_bf16x2(h0, h1), pack_bf16x2(h2, 0.f), 0u, 0u);
+}
+
+// Backward of the first layer (input: the normalised state, 3 channels): dW1
+// and db1 from the layer's output cotangent da0, and dq += dX / std.  dW runs
+// on the tensor cores over the state packed as 8-channel BF16 records (in
+// g.dr, free at this point), its rows of the 5 zero channels dropped in the
+// reduction; dX is the convolution with the flipped weights (N = 16).
+cudaError_t backward_first(const Net& net, const float* q, const uint16_t* da0, const ParamLayout& L, int B,
+                           int ny, int nx, Grads& g, float* dq, float* dparams, float scale, cudaStream_t s) {
+  const long long plane = (long long)nx * ny, cells = (long long)B * plane;
+  cudaError_t e;
+  if (plane % DWK == 0 && (nx % DWK == 0 || DWK % nx == 0)) {
+    pack_input_kernel<<<(unsigned)((cells + 255) / 256), 256, 0, s>>>(
+        q, g.dr, plane, cells, net.mean[0], net.mean[1], net.mean[2], 1.f / net.std_[0], 1.f / net.std_[1],
+        1.f / net.std_[2]);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const long long ntiles = (long long)B * (plane / DWK);
+    const int nctas = (int)(ntiles < DW_CTAS ? ntiles : DW_CTAS);
+    if (nx % DWK == 0) e = launch_dw_tx<8, HID, 4, true>(g.dr, da0, g.part, nx, ny, plane, ntiles, nctas, net, s);
+    else e = launch_dw_tx<8, HID, 4, false>(g.dr, da0, g.part, nx, ny, plane, ntiles, nctas, net, s);
+    if (e != cudaSuccess) return e;
+    constexpr int ne = (9 * 8 + 1) * HID;
+    dw_tc_reduce_kernel<3, HID, 8><<<(ne + 31) / 32, 256, 0, s>>>(g.part, nctas, dparams + L.w[0],
+                                                                   dparams + L.b[0], scale);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  } else {
+    if ((e = weight_grad<3, HID, 4>(nullptr, q, da0, dparams + L.w[0], dparams + L.b[0], g.part, B, ny, nx, net,
+                                    scale, s)) != cudaSuccess)
+      return e;
+  }
+  if (dq) {
+    ConvArgs a{};
+    a.nx = nx;
+    a.ny = ny;
+    a.plane = plane;
+    a.err = net.err;
+    a.x = da0;
+    a.wpk = net.wb[0];
+    a.w = dq;
+    a.rstd0 = 1.f / net.std_[0];
+    a.rstd1 = 1.f / net.std_[1];
+    a.rstd2 = 1.f / net.std_[2];
+    if ((e = launch_conv<CG_HID, DQ_N, IN_ACT, OUT_DQ>(a, B, s)) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 }  // namespace
 
 long long backward_partials_floats(int B, int ny, int nx) {
@@ -1442,16 +1482,7 @@ cudaError_t backward(const Net& net, const float* q, int B, int ny, int nx, cons
   a.y = g.da[0];
   if ((e = launch_conv<CG_HID, HID, IN_ACT, OUT_MASK>(a, B, s)) != cudaSuccess) return e;
   // layer 1: dW1 from (da0, normalised state); dq += dX / std
-  if ((e = weight_grad<3, HID, 4>(nullptr, q, g.da[0], dparams + L.w[0], dparams + L.b[0], g.part,
-                                  B, ny, nx, net, scale, s)) != cudaSuccess)
-    return e;
-  if (dq) {
-    dx_first_kernel<<<(unsigned)((cells + 127) / 128), 128, 0, s>>>(
-        g.da[0], net.params + L.w[0], dq, nx, ny, plane, cells, 1.f / net.std_[0],
-        1.f / net.std_[1], 1.f / net.std_[2]);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  }
-  return cudaSuccess;
+  return backward_first(net, q, g.da[0], L, B, ny, nx, g, dq, dparams, scale, s);
 }
 
 cudaError_t backward_faces(const Net& net, const float* q, int B, int ny, int nx, const Acts& acts,
@@ -1497,16 +1528,7 @@ cudaError_t backward_faces(const Net& net, const float* q, int B, int ny, int nx
   a.y = g.da[0];
   if ((e = launch_conv<CG_HID, HID, IN_ACT, OUT_GELU_GRAD>(a, B, s)) != cudaSuccess) return e;
   // layer 1: dW1 from (da0, normalised state); dq += dX / std
-  if ((e = weight_grad<3, HID, 4>(nullptr, q, g.da[0], dparams + L.w[0], dparams + L.b[0], g.part,
-                                  B, ny, nx, net, scale, s)) != cudaSuccess)
-    return e;
-  if (dq) {
-    dx_first_kernel<<<(unsigned)((cells + 127) / 128), 128, 0, s>>>(
-        g.da[0], net.params + L.w[0], dq, nx, ny, plane, cells, 1.f / net.std_[0],
-        1.f / net.std_[1], 1.f / net.std_[2]);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  }
-  return cudaSuccess;
+  return backward_first(net, q, g.da[0], L, B, ny, nx, g, dq, dparams, scale, s);
 }
 
 }  // namespace snk
@@ -1528,9 +1550,10 @@ int net_alloc(fv_net* n, int kind) {
                       9 * snk::CG_HID * (face ? snk::N_OUT_FACE_PAD : snk::N_OUT_PAD) * 8};
   for (int l = 0; l < 4; ++l)
     if ((e = cudaMalloc(&N.wf[l], 2 * fsz[l])) != cudaSuccess) return fvh::cuda_fail(e, "cudaMalloc(wf)");
-  for (int l = 1; l < 4; ++l) {
+  for (int l = 0; l < 4; ++l) {
     const int cg = snk::backward_groups(snk::param_layout(kind).cout[l]);
-    if ((e = cudaMalloc(&N.wb[l], 2 * 9 * cg * snk::HID * 8)) != cudaSuccess)
+    const int nb = l == 0 ? snk::DQ_N : snk::HID;
+    if ((e = cudaMalloc(&N.wb[l], 2 * 9 * cg * nb * 8)) != cudaSuccess)
       return fvh::cuda_fail(e, "cudaMalloc(wb)");
   }
   if (face) {

@@ -47,7 +47,8 @@ struct Net {
   int kind = NET_STENCIL;      // NET_STENCIL (fourth approach) or NET_FACE (third)
   float* params = nullptr;     // FP32 master parameters [n_params(kind)]
   uint16_t* wf[4] = {};        // forward B operands, BF16 [9][CG_in][N][8]
-  uint16_t* wb[4] = {};        // backward (dX) B operands, BF16 [9][CG_out][N_in][8], layers 1..3
+  uint16_t* wb[4] = {};        // backward (dX) B operands, BF16 [9][CG_out][N_in][8] (layer 1:
+                               // N_in = DQ_N, the 3 state channels padded)
   uint16_t* w1g = nullptr;     // layer 1 with the three x taps gathered into K, BF16
                                // [ky][2][HID][8]: channel c = 3 kx + var (c < 9, rest 0)
   uint16_t* wpair[3] = {};     // layers 2..3 for the row-pipelined kernel, BF16: the taps
@@ -72,6 +73,7 @@ struct Acts {
 
 bool grid_supported(int nx);   // nx % 128 == 0, or nx in {8, 16, 32, 64}
 constexpr int W1G_ELEMS = 3 * 2 * HID * 8;
+constexpr int DQ_N = 16;             // N of the first layer's dX convolution (3 channels padded)
 constexpr int W4R_BLOCK = 24;        // rows of one tap in w4ring: 12 stencils x 2 differences
 constexpr int W4R_ROWS = 128;        // 5 tap blocks + 8 zero rows
 constexpr int W4R_ELEMS = 3 * CG_HID * W4R_ROWS * 8;
