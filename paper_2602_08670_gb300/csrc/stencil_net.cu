@@ -1024,7 +1024,17 @@ __global__ void __launch_bounds__(256) dw_tc_reduce_kernel(const float* part, in
   float s = 0.f;
   if (i < NE) {
     const int k0 = warp * nparts / 8, k1 = (warp + 1) * nparts / 8;
-    for (int k = k0; k < k1; ++k) s += part[(long long)k * ROWS * CO + co * ROWS + r];
+    const float* src = part + co * ROWS + r;
+    int k = k0;
+    // eight loads in flight, then added in order (the same sum as one by one)
+    for (; k + 8 <= k1; k += 8) {
+      float v[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) v[j] = src[(long long)(k + j) * ROWS * CO];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) s += v[j];
+    }
+    for (; k < k1; ++k) s += src[(long long)k * ROWS * CO];
   }
   sh[warp][lane] = s;
   __syncthreads();
