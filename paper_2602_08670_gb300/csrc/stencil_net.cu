@@ -1366,28 +1366,30 @@ __global__ void pack_input_kernel(const float* q, uint16_t* x0, long long plane,
 // and db1 from the layer's output cotangent da0, and dq += dX / std.  dW runs
 // on the tensor cores over the state packed as 8-channel BF16 records (in
 // g.dr, free at this point), its rows of the 5 zero channels dropped in the
-// reduction; dX is the convolution with the flipped weights (N = 16).
+// reduction; dX is the convolution with the flipped weights (N = 16).  dW
+// goes to stream sw, dX to s; both only read da0.
 cudaError_t backward_first(const Net& net, const float* q, const uint16_t* da0, const ParamLayout& L, int B,
-                           int ny, int nx, Grads& g, float* dq, float* dparams, float scale, cudaStream_t s) {
+                           int ny, int nx, Grads& g, float* dq, float* dparams, float scale, cudaStream_t sw,
+                           cudaStream_t s) {
   const long long plane = (long long)nx * ny, cells = (long long)B * plane;
   cudaError_t e;
   if (plane % DWK == 0 && (nx % DWK == 0 || DWK % nx == 0)) {
-    pack_input_kernel<<<(unsigned)((cells + 255) / 256), 256, 0, s>>>(
+    pack_input_kernel<<<(unsigned)((cells + 255) / 256), 256, 0, sw>>>(
         q, g.dr, plane, cells, net.mean[0], net.mean[1], net.mean[2], 1.f / net.std_[0], 1.f / net.std_[1],
         1.f / net.std_[2]);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const long long ntiles = (long long)B * (plane / DWK);
     const int nctas = (int)(ntiles < DW_CTAS ? ntiles : DW_CTAS);
-    if (nx % DWK == 0) e = launch_dw_tx<8, HID, 4, true>(g.dr, da0, g.part, nx, ny, plane, ntiles, nctas, net, s);
-    else e = launch_dw_tx<8, HID, 4, false>(g.dr, da0, g.part, nx, ny, plane, ntiles, nctas, net, s);
+    if (nx % DWK == 0) e = launch_dw_tx<8, HID, 4, true>(g.dr, da0, g.part, nx, ny, plane, ntiles, nctas, net, sw);
+    else e = launch_dw_tx<8, HID, 4, false>(g.dr, da0, g.part, nx, ny, plane, ntiles, nctas, net, sw);
     if (e != cudaSuccess) return e;
     constexpr int ne = (9 * 8 + 1) * HID;
-    dw_tc_reduce_kernel<3, HID, 8><<<(ne + 31) / 32, 256, 0, s>>>(g.part, nctas, dparams + L.w[0],
+    dw_tc_reduce_kernel<3, HID, 8><<<(ne + 31) / 32, 256, 0, sw>>>(g.part, nctas, dparams + L.w[0],
                                                                    dparams + L.b[0], scale);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   } else {
     if ((e = weight_grad<3, HID, 4>(nullptr, q, da0, dparams + L.w[0], dparams + L.b[0], g.part, B, ny, nx, net,
-                                    scale, s)) != cudaSuccess)
+                                    scale, sw)) != cudaSuccess)
       return e;
   }
   if (dq) {
@@ -1418,6 +1420,12 @@ long long backward_partials_floats(int B, int ny, int nx) {
 }
 
 cudaError_t backward_reserve(Grads& g, long long cells, long long partial_floats) {
+  if (!g.aux) {
+    cudaError_t e = cudaStreamCreateWithFlags(&g.aux, cudaStreamNonBlocking);
+    for (int i = 0; i < Grads::NEV && e == cudaSuccess; ++i)
+      e = cudaEventCreateWithFlags(&g.ev[i], cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
+  }
   if (g.cells < cells) {
     cudaFree(g.dr);
     cudaFree(g.da[0]);
@@ -1443,12 +1451,24 @@ cudaError_t backward_reserve(Grads& g, long long cells, long long partial_floats
 }
 
 void backward_free(Grads& g) {
+  if (g.aux) cudaStreamSynchronize(g.aux);
   cudaFree(g.dr);
   cudaFree(g.da[0]);
   cudaFree(g.da[1]);
   cudaFree(g.part);
+  for (int i = 0; i < Grads::NEV; ++i)
+    if (g.ev[i]) cudaEventDestroy(g.ev[i]);
+  if (g.aux) cudaStreamDestroy(g.aux);
   g = Grads{};
 }
+
+namespace {
+// `to` waits for the work enqueued so far on `from` (event slot i).
+cudaError_t stream_after(Grads& g, int i, cudaStream_t from, cudaStream_t to) {
+  cudaError_t e = cudaEventRecord(g.ev[i], from);
+  return e == cudaSuccess ? cudaStreamWaitEvent(to, g.ev[i], 0) : e;
+}
+}  // namespace
 
 cudaError_t backward(const Net& net, const float* q, int B, int ny, int nx, const Acts& acts,
                      const float* dw, float* dq, float* dparams, float scale, Grads& g,
@@ -1459,40 +1479,51 @@ cudaError_t backward(const Net& net, const float* q, int B, int ny, int nx, cons
   coeff_to_raw_kernel<<<(unsigned)((cells + 255) / 256), 256, 0, s>>>(dw, g.dr, plane, cells);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
 
+  // Each layer's dW (stream g.aux, in layer order: they share the partial
+  // sums) runs beside its dX (stream s): both only read the layer's output
+  // cotangent.  dX of layer 2 overwrites da[0], which dW3 reads: it waits.
+  cudaStream_t w = g.aux;
   ConvArgs a{};
   a.nx = nx;
   a.ny = ny;
   a.plane = plane;
   a.err = net.err;
+  if ((e = stream_after(g, 0, s, w)) != cudaSuccess) return e;
   // layer 4: dW4, db4 from (dr, a3); dX -> da[0] masked by a3
   if ((e = weight_grad<HID, N_OUT, 6>(acts.a[2], nullptr, g.dr, dparams + L.w[3], dparams + L.b[3],
-                                      g.part, B, ny, nx, net, scale, s)) != cudaSuccess)
+                                      g.part, B, ny, nx, net, scale, w)) != cudaSuccess)
     return e;
   a.x = g.dr;
   a.wpk = net.wb[3];
   a.mask = acts.a[2];
   a.y = g.da[0];
   if ((e = launch_conv<6, HID, IN_ACT, OUT_MASK>(a, B, s)) != cudaSuccess) return e;
+  if ((e = stream_after(g, 1, s, w)) != cudaSuccess) return e;
   // layer 3: dW3 from (da0, a2); dX -> da[1] masked by a2
   if ((e = weight_grad<HID, HID, 4>(acts.a[1], nullptr, g.da[0], dparams + L.w[2], dparams + L.b[2],
-                                    g.part, B, ny, nx, net, scale, s)) != cudaSuccess)
+                                    g.part, B, ny, nx, net, scale, w)) != cudaSuccess)
     return e;
+  if ((e = cudaEventRecord(g.ev[2], w)) != cudaSuccess) return e;   // dW3 has read da[0]
   a.x = g.da[0];
   a.wpk = net.wb[2];
   a.mask = acts.a[1];
   a.y = g.da[1];
   if ((e = launch_conv<CG_HID, HID, IN_ACT, OUT_MASK>(a, B, s)) != cudaSuccess) return e;
+  if ((e = stream_after(g, 3, s, w)) != cudaSuccess) return e;
   // layer 2: dW2 from (da1, a1); dX -> da[0] masked by a1
   if ((e = weight_grad<HID, HID, 4>(acts.a[0], nullptr, g.da[1], dparams + L.w[1], dparams + L.b[1],
-                                    g.part, B, ny, nx, net, scale, s)) != cudaSuccess)
+                                    g.part, B, ny, nx, net, scale, w)) != cudaSuccess)
     return e;
   a.x = g.da[1];
   a.wpk = net.wb[1];
   a.mask = acts.a[0];
   a.y = g.da[0];
+  if ((e = cudaStreamWaitEvent(s, g.ev[2], 0)) != cudaSuccess) return e;
   if ((e = launch_conv<CG_HID, HID, IN_ACT, OUT_MASK>(a, B, s)) != cudaSuccess) return e;
+  if ((e = stream_after(g, 4, s, w)) != cudaSuccess) return e;
   // layer 1: dW1 from (da0, normalised state); dq += dX / std
-  return backward_first(net, q, g.da[0], L, B, ny, nx, g, dq, dparams, scale, s);
+  if ((e = backward_first(net, q, g.da[0], L, B, ny, nx, g, dq, dparams, scale, w, s)) != cudaSuccess) return e;
+  return stream_after(g, 5, w, s);
 }
 
 cudaError_t backward_faces(const Net& net, const float* q, int B, int ny, int nx, const Acts& acts,
@@ -1505,40 +1536,48 @@ cudaError_t backward_faces(const Net& net, const float* q, int B, int ny, int nx
   sides_to_raw_kernel<<<(unsigned)((cells + 255) / 256), 256, 0, s>>>(ds, sides, g.dr, plane, cells,
                                                                       net.std_[1], net.std_[2]);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  cudaStream_t w = g.aux;   // dW beside dX, as in backward()
   ConvArgs a{};
   a.nx = nx;
   a.ny = ny;
   a.plane = plane;
   a.err = net.err;
+  if ((e = stream_after(g, 0, s, w)) != cudaSuccess) return e;
   // layer 4: dW4, db4 from (dr, a3); dX -> da[0] times GeLU'(z3)
   if ((e = weight_grad<HID, N_OUT_FACE, 2>(acts.a[2], nullptr, g.dr, dparams + L.w[3], dparams + L.b[3],
-                                           g.part, B, ny, nx, net, scale, s)) != cudaSuccess)
+                                           g.part, B, ny, nx, net, scale, w)) != cudaSuccess)
     return e;
   a.x = g.dr;
   a.wpk = net.wb[3];
   a.z = acts.z[2];
   a.y = g.da[0];
   if ((e = launch_conv<2, HID, IN_ACT, OUT_GELU_GRAD>(a, B, s)) != cudaSuccess) return e;
+  if ((e = stream_after(g, 1, s, w)) != cudaSuccess) return e;
   // layer 3: dW3 from (da0, a2); dX -> da[1] times GeLU'(z2)
   if ((e = weight_grad<HID, HID, 4>(acts.a[1], nullptr, g.da[0], dparams + L.w[2], dparams + L.b[2],
-                                    g.part, B, ny, nx, net, scale, s)) != cudaSuccess)
+                                    g.part, B, ny, nx, net, scale, w)) != cudaSuccess)
     return e;
+  if ((e = cudaEventRecord(g.ev[2], w)) != cudaSuccess) return e;   // dW3 has read da[0]
   a.x = g.da[0];
   a.wpk = net.wb[2];
   a.z = acts.z[1];
   a.y = g.da[1];
   if ((e = launch_conv<CG_HID, HID, IN_ACT, OUT_GELU_GRAD>(a, B, s)) != cudaSuccess) return e;
+  if ((e = stream_after(g, 3, s, w)) != cudaSuccess) return e;
   // layer 2: dW2 from (da1, a1); dX -> da[0] times GeLU'(z1)
   if ((e = weight_grad<HID, HID, 4>(acts.a[0], nullptr, g.da[1], dparams + L.w[1], dparams + L.b[1],
-                                    g.part, B, ny, nx, net, scale, s)) != cudaSuccess)
+                                    g.part, B, ny, nx, net, scale, w)) != cudaSuccess)
     return e;
   a.x = g.da[1];
   a.wpk = net.wb[1];
   a.z = acts.z[0];
   a.y = g.da[0];
+  if ((e = cudaStreamWaitEvent(s, g.ev[2], 0)) != cudaSuccess) return e;
   if ((e = launch_conv<CG_HID, HID, IN_ACT, OUT_GELU_GRAD>(a, B, s)) != cudaSuccess) return e;
+  if ((e = stream_after(g, 4, s, w)) != cudaSuccess) return e;
   // layer 1: dW1 from (da0, normalised state); dq += dX / std
-  return backward_first(net, q, g.da[0], L, B, ny, nx, g, dq, dparams, scale, s);
+  if ((e = backward_first(net, q, g.da[0], L, B, ny, nx, g, dq, dparams, scale, w, s)) != cudaSuccess) return e;
+  return stream_after(g, 5, w, s);
 }
 
 }  // namespace snk

@@ -103,6 +103,9 @@ struct Grads {
   uint16_t* da[2] = {};         // cotangents of hidden pre-activations, BF16 [B][4][plane][8]
   float* part = nullptr;        // weight-gradient partial sums
   long long cells = 0, part_floats = 0;
+  static constexpr int NEV = 6;
+  cudaStream_t aux = nullptr;   // the weight gradients run here, beside the dX convolutions
+  cudaEvent_t ev[NEV] = {};     // fork / join points between the two streams
 };
 long long backward_partials_floats(int B, int ny, int nx);
 cudaError_t backward_reserve(Grads& g, long long cells, long long partial_floats);
