@@ -17,6 +17,8 @@
 #include <vector>
 
 #include "fv_common.cuh"
+#include <cuda_bf16.h>
+
 #include "fv_internal.h"
 #include "stencil_net.cuh"
 
@@ -36,13 +38,54 @@ struct AdjArgs {
   const float* q;       // stage input [B][3][plane]
   const float* w;       // coefficients [B][36][plane]
   const float* hmin;    // [B]
-  const float* mu;      // cotangent of L(q) [B][3][plane]
+  const float* lam;     // cotangent of the stage output [B][3][plane]; that of L(q) is mu_scale * lam
+  float mu_scale;
   float* gq;            // out: VJP w.r.t. q (reconstruction + flux path) [B][3][plane]
-  float* gw;            // out: VJP w.r.t. w [B][36][plane]
+  uint16_t* dr;         // out: VJP w.r.t. the network's raw outputs, BF16 [B][6][plane][8]
   int nx, ny;
   long long plane;
   float rdx, rdy, g;
 };
+
+__device__ __forceinline__ uint32_t pack2(float a, float b) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+// Cotangent of the 18 coefficients of one face direction of a cell (its 6
+// sum-to-one triples) -> cotangent of the raw outputs behind them (Section
+// 2.5.3's normalisation w = r - mean(r) + e: subtract each triple's mean),
+// BF16, written into the cell's records of dr.  x faces are channels 0..17
+// (records 0, 1 and the first word of record 2), y faces 18..35 (the rest of
+// record 2, records 3 and 4) plus the zero padding 36..47 (end of record 4,
+// record 5).
+__device__ __forceinline__ void store_raw_cotangent(uint16_t* dr, long long plane, int b, long long cell,
+                                                    bool ydir, const float (&gwd)[18]) {
+  float r[18];
+#pragma unroll
+  for (int t = 0; t < 6; ++t) {
+    const float m = (gwd[3 * t] + gwd[3 * t + 1] + gwd[3 * t + 2]) * (1.f / 3.f);
+    r[3 * t] = gwd[3 * t] - m;
+    r[3 * t + 1] = gwd[3 * t + 1] - m;
+    r[3 * t + 2] = gwd[3 * t + 2] - m;
+  }
+  auto rec = [&](int g) { return reinterpret_cast<uint32_t*>(dr + (((long long)b * 6 + g) * plane + cell) * 8); };
+  if (!ydir) {
+    *reinterpret_cast<uint4*>(rec(0)) = make_uint4(pack2(r[0], r[1]), pack2(r[2], r[3]), pack2(r[4], r[5]),
+                                                   pack2(r[6], r[7]));
+    *reinterpret_cast<uint4*>(rec(1)) = make_uint4(pack2(r[8], r[9]), pack2(r[10], r[11]), pack2(r[12], r[13]),
+                                                   pack2(r[14], r[15]));
+    rec(2)[0] = pack2(r[16], r[17]);
+  } else {
+    uint32_t* r2 = rec(2);
+    r2[1] = pack2(r[0], r[1]);
+    *reinterpret_cast<uint2*>(r2 + 2) = make_uint2(pack2(r[2], r[3]), pack2(r[4], r[5]));
+    *reinterpret_cast<uint4*>(rec(3)) = make_uint4(pack2(r[6], r[7]), pack2(r[8], r[9]), pack2(r[10], r[11]),
+                                                   pack2(r[12], r[13]));
+    *reinterpret_cast<uint4*>(rec(4)) = make_uint4(pack2(r[14], r[15]), pack2(r[16], r[17]), 0u, 0u);
+    *reinterpret_cast<uint4*>(rec(5)) = make_uint4(0u, 0u, 0u, 0u);
+  }
+}
 
 // VJP of the face-frame SWE HLL flux (three-branch form, written with the
 // clamped speeds zL = min(sL, 0), zR = max(sR, 0)): given mu = dLoss/dF,
@@ -179,9 +222,8 @@ __global__ void __launch_bounds__(ANT) learned_adjoint_kernel(AdjArgs a) {
   const int x0 = blockIdx.x * AX, y0 = blockIdx.y * AY;
   const int tid = threadIdx.x;
   const float* qb = a.q + (long long)b * 3 * a.plane;
-  const float* mb = a.mu + (long long)b * 3 * a.plane;
+  const float* mb = a.lam + (long long)b * 3 * a.plane;
   const float* wb = a.w + (long long)b * 36 * a.plane;
-  float* gwb = a.gw + (long long)b * 36 * a.plane;
   const float hmin = a.hmin[b];
   for (int i = tid; i < 3 * QY * QX; i += ANT) {
     const int c = i / (QY * QX), r = (i / QX) % QY, s = i % QX;
@@ -189,7 +231,7 @@ __global__ void __launch_bounds__(ANT) learned_adjoint_kernel(AdjArgs a) {
   }
   for (int i = tid; i < 3 * MY * MX; i += ANT) {
     const int c = i / (MY * MX), r = (i / MX) % MY, s = i % MX;
-    smu[i] = mb[c * a.plane + (long long)wrap(y0 - 2 + r, a.ny) * a.nx + wrap(x0 - 2 + s, a.nx)];
+    smu[i] = a.mu_scale * mb[c * a.plane + (long long)wrap(y0 - 2 + r, a.ny) * a.nx + wrap(x0 - 2 + s, a.nx)];
   }
   __syncthreads();
   // x faces: owner i = x0 - 2 + f, f = 0..AX+2, on tile rows
@@ -212,10 +254,8 @@ __global__ void __launch_bounds__(ANT) learned_adjoint_kernel(AdjArgs a) {
     for (int k = 0; k < 4; ++k)
 #pragma unroll
       for (int c = 0; c < 3; ++c) cx[(e * 4 + k) * 3 + c] = cq[k][c];
-    if (f >= 2 && f < AX + 2 && gy < a.ny && x0 - 2 + f < a.nx) {
-#pragma unroll
-      for (int j = 0; j < 18; ++j) gwb[j * a.plane + owner] = gwd[j];
-    }
+    if (f >= 2 && f < AX + 2 && gy < a.ny && x0 - 2 + f < a.nx)
+      store_raw_cotangent(a.dr, a.plane, b, owner, false, gwd);
   }
   // y faces: owner j = y0 - 2 + f on tile columns
   for (int e = tid; e < FYN * AX; e += ANT) {
@@ -237,10 +277,8 @@ __global__ void __launch_bounds__(ANT) learned_adjoint_kernel(AdjArgs a) {
     for (int k = 0; k < 4; ++k)
 #pragma unroll
       for (int c = 0; c < 3; ++c) cy[(e * 4 + k) * 3 + c] = cq[k][c];
-    if (f >= 2 && f < AY + 2 && y0 - 2 + f < a.ny && gx < a.nx) {
-#pragma unroll
-      for (int j = 0; j < 18; ++j) gwb[(18 + j) * a.plane + owner] = gwd[j];
-    }
+    if (f >= 2 && f < AY + 2 && y0 - 2 + f < a.ny && gx < a.nx)
+      store_raw_cotangent(a.dr, a.plane, b, owner, true, gwd);
   }
   __syncthreads();
   // gather: cell (r, i) gets contribution k from the face whose owner is
@@ -376,7 +414,7 @@ __global__ void fixed_ctrl_kernel(Ctrl* c, int B, double dt) {
 }  // namespace
 
 cudaError_t launch_learned_adjoint(const Geom& g, const float* q, const float* w, const float* hmin,
-                                   const float* mu, float* gq, float* gw, cudaStream_t s) {
+                                   const float* lam, float mu_scale, float* gq, uint16_t* dr, cudaStream_t s) {
   constexpr int smem = adj_smem_bytes();
   static bool attr = false;
   if (!attr) {
@@ -384,7 +422,7 @@ cudaError_t launch_learned_adjoint(const Geom& g, const float* q, const float* w
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  AdjArgs a{q, w, hmin, mu, gq, gw, g.nx, g.ny, g.plane(), (float)(1.0 / g.dx), (float)(1.0 / g.dy), g.phys};
+  AdjArgs a{q, w, hmin, lam, mu_scale, gq, dr, g.nx, g.ny, g.plane(), (float)(1.0 / g.dx), (float)(1.0 / g.dy), g.phys};
   dim3 grid((g.nx + AX - 1) / AX, (g.ny + AY - 1) / AY, g.B);
   learned_adjoint_kernel<<<grid, ANT, smem, s>>>(a);
   return cudaGetLastError();
@@ -432,7 +470,7 @@ struct fv_tape {
 
 namespace fvk {
 cudaError_t launch_learned_adjoint(const Geom& g, const float* q, const float* w, const float* hmin,
-                                   const float* mu, float* gq, float* gw, cudaStream_t s);
+                                   const float* lam, float mu_scale, float* gq, uint16_t* dr, cudaStream_t s);
 cudaError_t launch_axpbypcz(float* out, const float* x, float alpha, const float* y, float beta,
                             const float* z, float gamma, long long n, cudaStream_t s);
 cudaError_t launch_face_adjoint(const Geom& g, const float* sides, const float* mu, float* gs, cudaStream_t s);
@@ -653,15 +691,14 @@ extern "C" int fv_tape_backward(fv_tape* t, const float* dsnaps, float* dparams,
         FV_CUDA_TRY(fvk::launch_axpbypcz(t->lam, t->lam, 1.f, dsn + sc * (n - 1), 1.f, nullptr, 0.f, sc, s));
       continue;
     }
-    // stage 2
-    FV_CUDA_TRY(fvk::launch_axpbypcz(t->mu, t->lam, 0.5f * dt, nullptr, 0.f, nullptr, 0.f, sc, s));
-    FV_CUDA_TRY(fvk::launch_learned_adjoint(t->g, q1, w1, t->hmin, t->mu, t->gq, t->gw, s));
-    FV_CUDA_TRY(snk::backward(N, q1, B, ny, nx, t->acts[2 * n + 1], t->gw, t->gq, dparams, 1.f, t->grads, s));
+    // stage 2 (the adjoint takes mu = (dt/2) lam and writes the cotangent of
+    // the network's raw outputs)
+    FV_CUDA_TRY(fvk::launch_learned_adjoint(t->g, q1, w1, t->hmin, t->lam, 0.5f * dt, t->gq, t->grads.dr, s));
+    FV_CUDA_TRY(snk::backward_from_raw(N, q1, B, ny, nx, t->acts[2 * n + 1], t->gq, dparams, 1.f, t->grads, s));
     FV_CUDA_TRY(fvk::launch_axpbypcz(t->lam1, t->lam, 0.5f, t->gq, 1.f, nullptr, 0.f, sc, s));
-    // stage 1
-    FV_CUDA_TRY(fvk::launch_axpbypcz(t->mu, t->lam1, dt, nullptr, 0.f, nullptr, 0.f, sc, s));
-    FV_CUDA_TRY(fvk::launch_learned_adjoint(t->g, qn, w0, t->hmin, t->mu, t->gq, t->gw, s));
-    FV_CUDA_TRY(snk::backward(N, qn, B, ny, nx, t->acts[2 * n], t->gw, t->gq, dparams, 1.f, t->grads, s));
+    // stage 1 (mu = dt lam1)
+    FV_CUDA_TRY(fvk::launch_learned_adjoint(t->g, qn, w0, t->hmin, t->lam1, dt, t->gq, t->grads.dr, s));
+    FV_CUDA_TRY(snk::backward_from_raw(N, qn, B, ny, nx, t->acts[2 * n], t->gq, dparams, 1.f, t->grads, s));
     FV_CUDA_TRY(fvk::launch_axpbypcz(t->lam, t->lam, 0.5f, t->lam1, 1.f, t->gq, 1.f, sc, s));
     if (n >= 1)
       FV_CUDA_TRY(fvk::launch_axpbypcz(t->lam, t->lam, 1.f, dsn + sc * (n - 1), 1.f, nullptr, 0.f, sc, s));

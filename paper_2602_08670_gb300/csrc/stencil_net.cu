@@ -1473,11 +1473,18 @@ cudaError_t stream_after(Grads& g, int i, cudaStream_t from, cudaStream_t to) {
 cudaError_t backward(const Net& net, const float* q, int B, int ny, int nx, const Acts& acts,
                      const float* dw, float* dq, float* dparams, float scale, Grads& g,
                      cudaStream_t s) {
+  const long long cells = (long long)B * nx * ny;
+  coeff_to_raw_kernel<<<(unsigned)((cells + 255) / 256), 256, 0, s>>>(dw, g.dr, (long long)nx * ny, cells);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return backward_from_raw(net, q, B, ny, nx, acts, dq, dparams, scale, g, s);
+}
+
+cudaError_t backward_from_raw(const Net& net, const float* q, int B, int ny, int nx, const Acts& acts,
+                              float* dq, float* dparams, float scale, Grads& g, cudaStream_t s) {
   const ParamLayout L = param_layout();
-  const long long plane = (long long)nx * ny, cells = (long long)B * plane;
+  const long long plane = (long long)nx * ny;
   cudaError_t e;
-  coeff_to_raw_kernel<<<(unsigned)((cells + 255) / 256), 256, 0, s>>>(dw, g.dr, plane, cells);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
 
   // Each layer's dW (stream g.aux, in layer order: they share the partial
   // sums) runs beside its dX (stream s): both only read the layer's output

@@ -120,6 +120,10 @@ void backward_free(Grads& g);
 cudaError_t backward(const Net& net, const float* q, int B, int ny, int nx, const Acts& acts,
                      const float* dw, float* dq, float* dparams, float scale, Grads& g,
                      cudaStream_t s);
+// The same from the cotangent of the raw network outputs, already in g.dr
+// (BF16 [B][6][plane][8], the normalisation's VJP applied).
+cudaError_t backward_from_raw(const Net& net, const float* q, int B, int ny, int nx, const Acts& acts,
+                              float* dq, float* dparams, float scale, Grads& g, cudaStream_t s);
 
 // The same for a NET_FACE network: ds is the cotangent of the side states
 // [B][12][ny][nx], `sides` the side states forward_faces() produced for this
