@@ -105,3 +105,33 @@ def test_remap_mean_is_the_cell_average(mods, nf, nc):
     A = torch.tensor(_overlap(nc, nf))
     ref = A @ q.double() @ A.T
     assert float((got - ref).abs().max()) <= 1.2e-7 * float(ref.abs().max())
+
+
+def test_pushforward_windows_start_after_the_untaped_rollout(mods):
+    """With pushforward K the loss of a batch is the taped loss of windows
+    that start where k ~ U{0..K} untaped learned steps of the current network
+    took the sampled states, against the reference k steps later.  With a
+    zero learning rate the network does not change, so each logged loss can
+    be rebuilt from the same draws."""
+    fv, TR = mods
+    tr = TR.generate(256, 4, members=8, seed=0, coarse_steps=40)
+    res = TR.train(tr, iters=4, batch=4, T=4, lr=0.0, seed=5, pushforward=12)
+    assert len(res.losses) == 4 and res.rejected == 0
+    _, std = TR.data_stats(tr)
+    tape = fv.fv_tape_create(res.net, 4, tr.n_coarse, tr.n_coarse, 4, tr.dt_coarse)
+    S, B = tr.coarse.shape[:2]
+    st = fv.swe_init(tr.coarse[0, :4].contiguous(), dt_mode="fixed", dt_fixed=tr.dt_coarse)
+    rng = np.random.Generator(np.random.Philox(5))
+    for it in range(4):
+        traj = torch.tensor(rng.integers(0, B, size=4), device="cuda")
+        k_pre = int(rng.integers(0, 12 + 1))
+        start = torch.tensor(rng.integers(0, S - 4 - k_pre, size=4), device="cuda")
+        q0 = tr.coarse[start, traj].contiguous()
+        targets = torch.stack([tr.coarse[start + k_pre + k, traj] for k in range(1, 5)]).contiguous()
+        if k_pre:
+            fv.fv_set_state(st, q0)
+            fv.fv_rollout(st, k_pre, net=res.net)
+            q0 = fv.fv_get_state(st)
+        fv.fv_tape_forward(tape, q0, want_snaps=False)
+        loss = fv.fv_tape_loss(tape, targets, std)
+        assert loss == pytest.approx(res.losses[it], rel=1e-6), (it, k_pre, loss, res.losses[it])
