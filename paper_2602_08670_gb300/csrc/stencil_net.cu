@@ -1071,6 +1071,7 @@ __device__ __forceinline__ void stmatrix_x4(uint32_t row_addr, const uint32_t (&
 // Raw positions of a 64-cell tile: row mode (nx a multiple of DWK) 3 rows of
 // DWK + 2 cells; strip mode (nx < DWK dividing it) 3 x-shifted strips of
 // DWK + 2 nx cells.
+constexpr int DWT = 256;                 // threads of the cp.async/ldmatrix weight-gradient kernel
 constexpr int DW_RW = DWK + 2;
 constexpr int DW_NPOS_ROW = 3 * DW_RW;
 constexpr int DW_NPOS_FLAT = 3 * (DWK + 2 * (DWK / 2));
@@ -1084,7 +1085,7 @@ constexpr int dwx_smem_bytes() {
 }
 
 template <int CI, int CO, int CGO, bool ROW>
-__global__ void __launch_bounds__(NT) dw_tx_kernel(const uint16_t* x, const uint16_t* dy, float* part, int nx,
+__global__ void __launch_bounds__(DWT) dw_tx_kernel(const uint16_t* x, const uint16_t* dy, float* part, int nx,
                                                    int ny, long long plane, long long ntiles, unsigned* err) {
   constexpr int CG = CI / 8;
   constexpr int NB = 8 * CGO;
@@ -1092,7 +1093,7 @@ __global__ void __launch_bounds__(NT) dw_tx_kernel(const uint16_t* x, const uint
   constexpr int ROWS = MT * 128;
   constexpr int NP = dw_npos<ROW>();
   constexpr int RAW = dwx_raw_bytes<CI, CGO, ROW>();
-  constexpr int NW = NT / 32;
+  constexpr int NW = DWT / 32;
   constexpr int A_X4 = 9 * CG * 8 / 4, B_X4 = CGO * 8 / 4;   // ldmatrix.x4 blocks of A, B per tile
   constexpr int A_PER_WARP = (A_X4 + NW - 1) / NW, B_PER_WARP = (B_X4 + NW - 1) / NW;
   static_assert(CI % 8 == 0 && NB % 16 == 0 && MT * NB <= 256, "shape of the MMA and TMEM columns");
@@ -1111,7 +1112,7 @@ __global__ void __launch_bounds__(NT) dw_tx_kernel(const uint16_t* x, const uint
   const int Lf = DWK + 2 * nx;                         // strip mode
 
   // the ones row (bias) and the zero padding of A, once
-  for (int i = tid; i < (ROWS - 9 * CI) * DWK; i += NT) {
+  for (int i = tid; i < (ROWS - 9 * CI) * DWK; i += DWT) {
     const int r = 9 * CI + i / DWK, k = i % DWK;
     *reinterpret_cast<uint16_t*>(A + dw_off(r, k)) = r == 9 * CI ? (uint16_t)0x3F80u : (uint16_t)0u;
   }
@@ -1155,7 +1156,7 @@ __global__ void __launch_bounds__(NT) dw_tx_kernel(const uint16_t* x, const uint
     const int p0 = (int)(tile - (long long)b * tiles_per_member) * DWK;
     const int y0 = lg >= 0 ? p0 >> lg : p0 / nx, x0 = p0 - y0 * nx;
     const int npos = ROW ? DW_NPOS_ROW : 3 * Lf;
-    for (int n = tid; n < npos; n += NT) {
+    for (int n = tid; n < npos; n += DWT) {
       int yy, xx;
       if (ROW) {
         const int dyi = (n >= DW_RW) + (n >= 2 * DW_RW), xi = n - dyi * DW_RW;
@@ -1173,7 +1174,7 @@ __global__ void __launch_bounds__(NT) dw_tx_kernel(const uint16_t* x, const uint
       for (int g = 0; g < CG; ++g)
         cp_async16(Rb + (g * NP + n) * 16, x + (((long long)b * CG + g) * plane + cell) * 8);
     }
-    for (int n = tid; n < CGO * DWK; n += NT) {
+    for (int n = tid; n < CGO * DWK; n += DWT) {
       const int g = n / DWK, k = n - g * DWK;
       cp_async16(RBb + n * 16, dy + (((long long)b * CGO + g) * plane + p0 + k) * 8);
     }
@@ -1246,14 +1247,18 @@ __global__ void __launch_bounds__(NT) dw_tx_kernel(const uint16_t* x, const uint
   if (!ok) {
     if (tid == 0) atomicOr(err, 1u);
   } else {
+    // warp w reads TMEM lanes 32 (w % 4) ..; warps w and w + 4 take
+    // alternate 16-column chunks
     float* pp = part + (long long)blockIdx.x * ROWS * CO;
+    const int lq = warp & 3, half = warp >> 2;
 #pragma unroll
     for (int mt = 0; mt < MT; ++mt) {
-      const int r = mt * 128 + warp * 32 + lane;
+      const int r = mt * 128 + lq * 32 + lane;
 #pragma unroll
       for (int c0 = 0; c0 < NB; c0 += 16) {
+        if (((c0 >> 4) & 1) != half) continue;
         float v[16];
-        tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + mt * NB + c0, v);
+        tc::tmem_ld16(tmem + ((uint32_t)(lq * 32) << 16) + mt * NB + c0, v);
 #pragma unroll
         for (int j = 0; j < 16; ++j)
           if (c0 + j < CO) pp[(long long)(c0 + j) * ROWS + r] = issued > 0 ? v[j] : 0.f;
@@ -1276,7 +1281,7 @@ cudaError_t launch_dw_tx(const uint16_t* x, const uint16_t* dy, float* part, int
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  kern<<<nctas, NT, smem, s>>>(x, dy, part, nx, ny, plane, ntiles, net.err);
+  kern<<<nctas, DWT, smem, s>>>(x, dy, part, nx, ny, plane, ntiles, net.err);
   return cudaGetLastError();
 }
 
