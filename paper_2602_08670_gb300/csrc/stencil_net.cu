@@ -1201,21 +1201,22 @@ __global__ void __launch_bounds__(DWT) dw_tx_kernel(const uint16_t* x, const uin
     ok = __syncthreads_and(w) && ok;
     if (!ok) break;
     tc::fence_after_sync();
+    // all of this warp's loads first, then the stores (the matrix
+    // instructions are not reordered across each other)
+    {
+      uint32_t va[A_PER_WARP][4], vb[B_PER_WARP][4];
 #pragma unroll
-    for (int k = 0; k < A_PER_WARP; ++k) {
-      if (A_X4 % NW == 0 || warp + NW * k < A_X4) {
-        uint32_t v[4];
-        ldmatrix_x4_trans(rb + a_ld[k], v);
-        stmatrix_x4(a_st[k], v);
-      }
-    }
+      for (int k = 0; k < A_PER_WARP; ++k)
+        if (A_X4 % NW == 0 || warp + NW * k < A_X4) ldmatrix_x4_trans(rb + a_ld[k], va[k]);
 #pragma unroll
-    for (int k = 0; k < B_PER_WARP; ++k) {
-      if (B_X4 % NW == 0 || warp + NW * k < B_X4) {
-        uint32_t v[4];
-        ldmatrix_x4_trans(rb + b_ld[k], v);
-        stmatrix_x4(b_st[k], v);
-      }
+      for (int k = 0; k < B_PER_WARP; ++k)
+        if (B_X4 % NW == 0 || warp + NW * k < B_X4) ldmatrix_x4_trans(rb + b_ld[k], vb[k]);
+#pragma unroll
+      for (int k = 0; k < A_PER_WARP; ++k)
+        if (A_X4 % NW == 0 || warp + NW * k < A_X4) stmatrix_x4(a_st[k], va[k]);
+#pragma unroll
+      for (int k = 0; k < B_PER_WARP; ++k)
+        if (B_X4 % NW == 0 || warp + NW * k < B_X4) stmatrix_x4(b_st[k], vb[k]);
     }
     tc::fence_proxy_async_smem();
     tc::fence_before_sync();
