@@ -105,12 +105,17 @@ constexpr int npos_of() { return ROW ? NPOS_ROW : NPOS_MAX; }
 // dx) are then 8-row groups 10 positions apart: one descriptor with a
 // 160-byte group stride covers the tile for every tap, with a third of the
 // staging of three x-shifted strips.
-template <bool ROW>
-constexpr int conv_np() { return ROW ? NPOS_ROW : NPOS_GRP; }
+//
+// A CTA convolves TPC = 1 or 2 tiles: in row mode the tiles at the same
+// columns of rows y0 and y0 + 1 (4 staged rows for both), in grouped mode
+// two consecutive tiles (their rows and the two rows around them).  The
+// pair shares the staged rows between them and one load of the weights.
+template <bool ROW, int TPC = 1>
+constexpr int conv_np() { return ROW ? (TPC + 2) * RW : (TPC * TILE / 8 + 2 * 64 / 8) * GSLOT; }
 
-template <int CG, int N, bool ROW>
+template <int CG, int N, bool ROW, int TPC = 1>
 constexpr int conv_smem_bytes() {
-  return CG * conv_np<ROW>() * 16 + 9 * CG * N * 16 + 64;
+  return CG * conv_np<ROW, TPC>() * 16 + 9 * CG * N * 16 + 64;
 }
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
@@ -143,18 +148,18 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 // cp.async (the caller commits and waits); the state is normalised and
 // stored directly.  Every offset lies within one period of the grid, so one
 // compare-and-select wraps it; a power-of-two width divides by a shift.
-template <int CG, int IN, bool ROW>
+template <int CG, int IN, bool ROW, int TPC = 1>
 __device__ __forceinline__ void conv_stage(const ConvArgs& a, uint8_t* sA, int b, int p0, int tid) {
-  constexpr int NP = conv_np<ROW>();
+  constexpr int NP = conv_np<ROW, TPC>();
   const int nx = a.nx, ny = a.ny;
   const int lg = (nx & (nx - 1)) == 0 ? __ffs(nx) - 1 : -1;
   const int y0 = lg >= 0 ? p0 >> lg : p0 / nx, x0 = p0 - y0 * nx;
   const int gpr = nx >> 3;                             // grouped mode: runs of 8 per row
-  const int npos = ROW ? NPOS_ROW : (TILE / 8 + 2 * gpr) * GSLOT;
+  const int npos = ROW ? (TPC + 2) * RW : (TPC * TILE / 8 + 2 * gpr) * GSLOT;
   for (int n = tid; n < npos; n += NT) {
     int yy, xx;
     if (ROW) {
-      const int dyi = (n >= RW) + (n >= 2 * RW), xi = n - dyi * RW;
+      const int dyi = n / RW, xi = n - dyi * RW;
       yy = wrap1(y0 - 1 + dyi, ny);
       xx = wrap1(x0 - 1 + xi, nx);
     } else {
@@ -295,9 +300,11 @@ __device__ __forceinline__ void conv_epilogue(const ConvArgs& a, int b, long lon
   }
 }
 
-template <int CG, int N, int IN, int OUT, bool ROW>
+template <int CG, int N, int IN, int OUT, bool ROW, int TPC>
 __global__ void __launch_bounds__(NT) conv_kernel(ConvArgs a) {
-  constexpr int NP = conv_np<ROW>();
+  constexpr int NP = conv_np<ROW, TPC>();
+  constexpr uint32_t NCOLS = TPC * N <= 32 ? 32u : (TPC * N <= 64 ? 64u : 128u);
+  static_assert(TPC * N <= 128, "accumulator columns");
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* sA = smem;                                   // [CG][NP][16 B]
   uint8_t* sB = smem + CG * NP * 16;                    // [9][CG][N][16 B]
@@ -305,19 +312,30 @@ __global__ void __launch_bounds__(NT) conv_kernel(ConvArgs a) {
   uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
 
   const int tid = threadIdx.x;
-  const long long tiles_per_member = a.plane / TILE;
-  const int b = (int)(blockIdx.x / tiles_per_member);
-  const int p0 = (int)(blockIdx.x - (long long)b * tiles_per_member) * TILE;
   constexpr bool rowmode = ROW;
   const int gpr = a.nx >> 3;
+  // the CTA's tiles: p0 of tile u is p0 + u * tile_step
+  const long long units_per_member = a.plane / (TILE * TPC);
+  const int b = (int)(blockIdx.x / units_per_member);
+  const int unit = (int)(blockIdx.x - (long long)b * units_per_member);
+  int p0, tile_step;
+  if (ROW && TPC == 2) {
+    const int tpr = a.nx / TILE;                        // tiles per row
+    const int y2 = unit / tpr, xt = unit - y2 * tpr;
+    p0 = 2 * y2 * a.nx + xt * TILE;
+    tile_step = a.nx;                                   // the next row
+  } else {
+    p0 = unit * TILE * TPC;
+    tile_step = TILE;
+  }
 
-  if (tid < 32) tc::tmem_alloc(tslot, 64);
+  if (tid < 32) tc::tmem_alloc(tslot, NCOLS);
   if (tid == 0) tc::mbar_init(mbar, 1);
 
   // weights: 9 * CG * N chunks of 16 bytes
   for (int i = tid; i < 9 * CG * N; i += NT) cp_async16(sB + i * 16, a.wpk + i * 8);
 
-  conv_stage<CG, IN, ROW>(a, sA, b, p0, tid);
+  conv_stage<CG, IN, ROW, TPC>(a, sA, b, p0, tid);
   asm volatile("cp.async.wait_all;\n" ::: "memory");
   tc::fence_proxy_async_smem();
   tc::fence_before_sync();
@@ -328,19 +346,23 @@ __global__ void __launch_bounds__(NT) conv_kernel(ConvArgs a) {
   if (tid == 0) {
     constexpr uint32_t idesc = tc::idesc_bf16_f32(TILE, N);
     const uint32_t a0 = tc::smem_u32(sA), b0 = tc::smem_u32(sB);
-    bool acc = false;
-#pragma unroll 1
-    for (int tap = 0; tap < 9; ++tap) {
-      const int dy = tap / 3 - 1, dx = tap % 3 - 1;
-      // row mode: 8-row groups 128 B apart; grouped mode: 160 B apart
-      const int start = rowmode ? (1 + dy) * RW + (1 + dx) : (1 + dy) * gpr * GSLOT + (1 + dx);
-      constexpr uint32_t sbo = rowmode ? 128u : 16u * GSLOT;
 #pragma unroll
-      for (int ks = 0; ks < CG / 2; ++ks) {
-        const uint64_t ad = tc::sdesc(a0 + (uint32_t)((2 * ks * NP + start) * 16), NP * 16, sbo);
-        const uint64_t bd = tc::sdesc(b0 + (uint32_t)(((tap * CG + 2 * ks) * N) * 16), N * 16, 128);
-        tc::mma_bf16(tmem, ad, bd, idesc, acc);
-        acc = true;
+    for (int u = 0; u < TPC; ++u) {
+      bool acc = false;
+#pragma unroll 1
+      for (int tap = 0; tap < 9; ++tap) {
+        const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+        // row mode: 8-row groups 128 B apart, tile u one staged row down;
+        // grouped mode: 160 B apart, tile u 16 runs on
+        const int start = rowmode ? (u + 1 + dy) * RW + (1 + dx) : (u * (TILE / 8) + (1 + dy) * gpr) * GSLOT + (1 + dx);
+        constexpr uint32_t sbo = rowmode ? 128u : 16u * GSLOT;
+#pragma unroll
+        for (int ks = 0; ks < CG / 2; ++ks) {
+          const uint64_t ad = tc::sdesc(a0 + (uint32_t)((2 * ks * NP + start) * 16), NP * 16, sbo);
+          const uint64_t bd = tc::sdesc(b0 + (uint32_t)(((tap * CG + 2 * ks) * N) * 16), N * 16, 128);
+          tc::mma_bf16(tmem + (uint32_t)(u * N), ad, bd, idesc, acc);
+          acc = true;
+        }
       }
     }
     tc::mma_commit(mbar);
@@ -352,13 +374,14 @@ __global__ void __launch_bounds__(NT) conv_kernel(ConvArgs a) {
   if (ok) {
     const int w = tid >> 5;
     const int m = tid;                                   // TMEM lane = tile row
-    const long long cell = p0 + m;
     const uint32_t lane_addr = tmem + ((uint32_t)(32 * w) << 16);
-    conv_epilogue<N, OUT>(a, b, cell, lane_addr);
+#pragma unroll
+    for (int u = 0; u < TPC; ++u)
+      conv_epilogue<N, OUT>(a, b, (long long)p0 + u * tile_step + m, lane_addr + (uint32_t)(u * N));
   }
   tc::fence_before_sync();
   __syncthreads();
-  if (tid < 32) tc::tmem_dealloc(tmem, 64);
+  if (tid < 32) tc::tmem_dealloc(tmem, NCOLS);
 }
 
 // FP32 master parameters -> BF16 operand layouts.
@@ -462,27 +485,32 @@ __global__ void repack_kernel(const float* params, ParamLayout L, uint16_t* wf0,
   }
 }
 
-template <int CG, int N, int IN, int OUT, bool ROW>
+template <int CG, int N, int IN, int OUT, bool ROW, int TPC>
 cudaError_t launch_conv_t(const ConvArgs& a, int B, cudaStream_t s) {
-  constexpr int smem = conv_smem_bytes<CG, N, ROW>();
-  auto kern = conv_kernel<CG, N, IN, OUT, ROW>;
+  constexpr int smem = conv_smem_bytes<CG, N, ROW, TPC>();
+  auto kern = conv_kernel<CG, N, IN, OUT, ROW, TPC>;
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  const long long tiles = (long long)B * (a.plane / TILE);
-  kern<<<(unsigned)tiles, NT, smem, s>>>(a);
+  const long long ctas = (long long)B * (a.plane / (TILE * TPC));
+  kern<<<(unsigned)ctas, NT, smem, s>>>(a);
   return cudaGetLastError();
 }
 
-// Row mode (nx a multiple of the tile) stages 3 rows and so fits more CTAs
-// per SM than the flat mode of the narrow grids.
+// Row mode (nx a multiple of the tile) stages rows; grouped mode serves the
+// narrow grids.  Two tiles per CTA where the grid pairs them (an even number
+// of rows in row mode, whole 256-cell pairs in grouped mode).
 template <int CG, int N, int IN, int OUT>
 cudaError_t launch_conv(const ConvArgs& a, int B, cudaStream_t s) {
-  if (a.nx % TILE == 0) return launch_conv_t<CG, N, IN, OUT, true>(a, B, s);
-  return launch_conv_t<CG, N, IN, OUT, false>(a, B, s);
+  if (a.nx % TILE == 0) {
+    if (a.ny % 2 == 0) return launch_conv_t<CG, N, IN, OUT, true, 2>(a, B, s);
+    return launch_conv_t<CG, N, IN, OUT, true, 1>(a, B, s);
+  }
+  if (a.plane % (2 * TILE) == 0) return launch_conv_t<CG, N, IN, OUT, false, 2>(a, B, s);
+  return launch_conv_t<CG, N, IN, OUT, false, 1>(a, B, s);
 }
 
 }  // namespace
