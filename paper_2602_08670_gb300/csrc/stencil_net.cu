@@ -156,6 +156,46 @@ __device__ __forceinline__ void conv_stage(const ConvArgs& a, uint8_t* sA, int b
   const int y0 = lg >= 0 ? p0 >> lg : p0 / nx, x0 = p0 - y0 * nx;
   const int gpr = nx >> 3;                             // grouped mode: runs of 8 per row
   const int npos = ROW ? (TPC + 2) * RW : (TPC * TILE / 8 + 2 * gpr) * GSLOT;
+  if constexpr (IN == IN_STATE) {
+    // the state: every load of this thread issued before the first use
+    constexpr int IT = (NP + NT - 1) / NT;
+    const float* qb = a.q + (long long)b * 3 * a.plane;
+    float h[IT][3];
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+      const int n = tid + it * NT;
+      if (n < npos) {
+        int yy, xx;
+        if (ROW) {
+          const int dyi = n / RW, xi = n - dyi * RW;
+          yy = wrap1(y0 - 1 + dyi, ny);
+          xx = wrap1(x0 - 1 + xi, nx);
+        } else {
+          const int run = n / GSLOT, sl = n - run * GSLOT;
+          const int ry = run / gpr, gi = run - ry * gpr;
+          yy = wrap1(y0 - 1 + ry, ny);
+          xx = wrap1(8 * gi - 1 + sl, nx);
+        }
+        const long long cell = (long long)yy * nx + xx;
+        h[it][0] = __ldg(qb + cell);
+        h[it][1] = __ldg(qb + a.plane + cell);
+        h[it][2] = __ldg(qb + 2 * a.plane + cell);
+      }
+    }
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+      const int n = tid + it * NT;
+      if (n < npos) {
+        const float h0 = (h[it][0] - a.mean0) * a.rstd0;
+        const float h1 = (h[it][1] - a.mean1) * a.rstd1;
+        const float h2 = (h[it][2] - a.mean2) * a.rstd2;
+        *reinterpret_cast<uint4*>(sA + n * 16) = make_uint4(pack_bf16x2(h0, h1), pack_bf16x2(h2, 0.f), 0u, 0u);
+#pragma unroll
+        for (int g = 1; g < CG; ++g) *reinterpret_cast<uint4*>(sA + (g * NP + n) * 16) = make_uint4(0, 0, 0, 0);
+      }
+    }
+    return;
+  }
   for (int n = tid; n < npos; n += NT) {
     int yy, xx;
     if (ROW) {
