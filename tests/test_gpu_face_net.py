@@ -238,8 +238,9 @@ def test_device_gelu_matches_the_definition(fv):
     activations are BF16(GeLU(b3)) in every cell, and W4 copies channel k to
     output k.  The BF16 roundings must agree except where the value lies
     within the FP32 evaluation's error of a rounding boundary.  The sweep
-    stops at x = -4: further out the FP32 sum 1 + erf cancels (the epilogue
-    trades that tail, |GeLU| < 1e-4, for speed)."""
+    stops at x = -4: further out the relative accuracy of the epilogue's erf
+    (Hastings' approximation, absolute error <= 3e-7) fades, where
+    |GeLU| < 1e-4."""
     from oracle import face_net as ofn
     xs = np.concatenate([np.linspace(-4.0, 6.0, 589), [0.0, 1.0, -1.0, 0.5, -0.5, 3.0, -3.0, 1e-3, -1e-3, 20.0, 7.5]])
     xs = xs.astype(np.float32)
