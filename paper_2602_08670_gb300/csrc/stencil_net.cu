@@ -1375,9 +1375,27 @@ cudaError_t launch_dw_tx(const uint16_t* x, const uint16_t* dy, float* part, int
   return cudaGetLastError();
 }
 
+// Where a weight gradient's partial-sum reduction runs: by default on the
+// stream of its partial-sum kernel; with rs set, on rs after that kernel
+// (event ev), so that the stream goes on with the next kernel.
+struct RedOn {
+  cudaStream_t rs = nullptr;
+  cudaEvent_t ev = nullptr;
+};
+inline cudaError_t red_stream(cudaStream_t s, const RedOn& r, cudaStream_t& out) {
+  out = s;
+  if (!r.rs) return cudaSuccess;
+  cudaError_t e = cudaEventRecord(r.ev, s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(r.rs, r.ev, 0);
+  out = r.rs;
+  return e;
+}
+
 template <int CI, int CO, int CGO>
 cudaError_t weight_grad_tc(const uint16_t* x, const float* q, const uint16_t* dy, float* dW, float* db,
-                           float* part, int B, int ny, int nx, const Net& net, float scale, cudaStream_t s) {
+                           float* part, int B, int ny, int nx, const Net& net, float scale, cudaStream_t s,
+                           const RedOn& ro) {
+  cudaStream_t rs = s;
   const long long plane = (long long)nx * ny;
   const long long ntiles = (long long)B * (plane / DWK);
   const int nctas = (int)(ntiles < DW_CTAS ? ntiles : DW_CTAS);
@@ -1389,8 +1407,9 @@ cudaError_t weight_grad_tc(const uint16_t* x, const float* q, const uint16_t* dy
       if (nx % DWK == 0) e = launch_dw_tx<CI, CO, CGO, true>(x, dy, part, nx, ny, plane, ntiles, nctas, net, s);
       else e = launch_dw_tx<CI, CO, CGO, false>(x, dy, part, nx, ny, plane, ntiles, nctas, net, s);
       if (e != cudaSuccess) return e;
+      if ((e = red_stream(s, ro, rs)) != cudaSuccess) return e;
       const int ne = (9 * CI + 1) * CO;
-      dw_tc_reduce_kernel<CI, CO><<<(ne + 31) / 32, 256, 0, s>>>(part, nctas, dW, db, scale);
+      dw_tc_reduce_kernel<CI, CO><<<(ne + 31) / 32, 256, 0, rs>>>(part, nctas, dW, db, scale);
       return cudaGetLastError();
     }
   }
@@ -1406,15 +1425,16 @@ cudaError_t weight_grad_tc(const uint16_t* x, const float* q, const uint16_t* dy
                                1.f / net.std_[0], 1.f / net.std_[1], 1.f / net.std_[2], net.err);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  if ((e = red_stream(s, ro, rs)) != cudaSuccess) return e;
   const int ne = (9 * CI + 1) * CO;
-  dw_tc_reduce_kernel<CI, CO><<<(ne + 31) / 32, 256, 0, s>>>(part, nctas, dW, db, scale);
+  dw_tc_reduce_kernel<CI, CO><<<(ne + 31) / 32, 256, 0, rs>>>(part, nctas, dW, db, scale);
   return cudaGetLastError();
 }
 
 template <int CI, int CO, int CGO, bool ROW>
 cudaError_t weight_grad_t(const uint16_t* x, const float* q, const uint16_t* dy, float* dW, float* db,
                           float* part, int B, int ny, int nx, const Net& net, float scale,
-                          cudaStream_t s) {
+                          cudaStream_t s, const RedOn& ro) {
   const long long plane = (long long)nx * ny;
   const long long ntiles = (long long)B * (plane / TILE);
   const int nctas = (int)((ntiles + DW_TILES - 1) / DW_TILES);
@@ -1430,19 +1450,22 @@ cudaError_t weight_grad_t(const uint16_t* x, const float* q, const uint16_t* dy,
                                 net.mean[2], 1.f / net.std_[0], 1.f / net.std_[1], 1.f / net.std_[2]);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  cudaStream_t rs = s;
+  if ((e = red_stream(s, ro, rs)) != cudaSuccess) return e;
   const int ne = 9 * CO * CI + CO;
-  dw_reduce_kernel<CI, CO><<<(ne + 255) / 256, 256, 0, s>>>(part, nctas, dW, db, scale);
+  dw_reduce_kernel<CI, CO><<<(ne + 255) / 256, 256, 0, rs>>>(part, nctas, dW, db, scale);
   return cudaGetLastError();
 }
 
 template <int CI, int CO, int CGO>
 cudaError_t weight_grad(const uint16_t* x, const float* q, const uint16_t* dy, float* dW, float* db,
                         float* part, int B, int ny, int nx, const Net& net, float scale,
-                        cudaStream_t s) {
+                        cudaStream_t s, const RedOn& ro = RedOn{}) {
   if (((long long)nx * ny) % DWK == 0)
-    return weight_grad_tc<CI, CO, CGO>(x, q, dy, dW, db, part, B, ny, nx, net, scale, s);
-  if (nx % TILE == 0) return weight_grad_t<CI, CO, CGO, true>(x, q, dy, dW, db, part, B, ny, nx, net, scale, s);
-  return weight_grad_t<CI, CO, CGO, false>(x, q, dy, dW, db, part, B, ny, nx, net, scale, s);
+    return weight_grad_tc<CI, CO, CGO>(x, q, dy, dW, db, part, B, ny, nx, net, scale, s, ro);
+  if (nx % TILE == 0)
+    return weight_grad_t<CI, CO, CGO, true>(x, q, dy, dW, db, part, B, ny, nx, net, scale, s, ro);
+  return weight_grad_t<CI, CO, CGO, false>(x, q, dy, dW, db, part, B, ny, nx, net, scale, s, ro);
 }
 
 // The normalised state as the first layer's BF16 input records [B][1][plane][8]
@@ -1464,8 +1487,8 @@ __global__ void pack_input_kernel(const float* q, uint16_t* x0, long long plane,
 // reduction; dX is the convolution with the flipped weights (N = 16).  dW
 // goes to stream sw, dX to s; both only read da0.
 cudaError_t backward_first(const Net& net, const float* q, const uint16_t* da0, const ParamLayout& L, int B,
-                           int ny, int nx, Grads& g, float* dq, float* dparams, float scale, cudaStream_t sw,
-                           cudaStream_t s) {
+                           int ny, int nx, Grads& g, float* part, float* dq, float* dparams, float scale,
+                           cudaStream_t sw, cudaStream_t s, const RedOn& ro) {
   const long long plane = (long long)nx * ny, cells = (long long)B * plane;
   cudaError_t e;
   if (plane % DWK == 0 && (nx % DWK == 0 || DWK % nx == 0)) {
@@ -1475,16 +1498,18 @@ cudaError_t backward_first(const Net& net, const float* q, const uint16_t* da0, 
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const long long ntiles = (long long)B * (plane / DWK);
     const int nctas = (int)(ntiles < DW_CTAS ? ntiles : DW_CTAS);
-    if (nx % DWK == 0) e = launch_dw_tx<8, HID, 4, true>(g.dr, da0, g.part, nx, ny, plane, ntiles, nctas, net, sw);
-    else e = launch_dw_tx<8, HID, 4, false>(g.dr, da0, g.part, nx, ny, plane, ntiles, nctas, net, sw);
+    if (nx % DWK == 0) e = launch_dw_tx<8, HID, 4, true>(g.dr, da0, part, nx, ny, plane, ntiles, nctas, net, sw);
+    else e = launch_dw_tx<8, HID, 4, false>(g.dr, da0, part, nx, ny, plane, ntiles, nctas, net, sw);
     if (e != cudaSuccess) return e;
+    cudaStream_t rs = sw;
+    if ((e = red_stream(sw, ro, rs)) != cudaSuccess) return e;
     constexpr int ne = (9 * 8 + 1) * HID;
-    dw_tc_reduce_kernel<3, HID, 8><<<(ne + 31) / 32, 256, 0, sw>>>(g.part, nctas, dparams + L.w[0],
+    dw_tc_reduce_kernel<3, HID, 8><<<(ne + 31) / 32, 256, 0, rs>>>(part, nctas, dparams + L.w[0],
                                                                    dparams + L.b[0], scale);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   } else {
-    if ((e = weight_grad<3, HID, 4>(nullptr, q, da0, dparams + L.w[0], dparams + L.b[0], g.part, B, ny, nx, net,
-                                    scale, sw)) != cudaSuccess)
+    if ((e = weight_grad<3, HID, 4>(nullptr, q, da0, dparams + L.w[0], dparams + L.b[0], part, B, ny, nx, net,
+                                    scale, sw, ro)) != cudaSuccess)
       return e;
   }
   if (dq) {
@@ -1517,6 +1542,7 @@ long long backward_partials_floats(int B, int ny, int nx) {
 cudaError_t backward_reserve(Grads& g, long long cells, long long partial_floats) {
   if (!g.aux) {
     cudaError_t e = cudaStreamCreateWithFlags(&g.aux, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g.red, cudaStreamNonBlocking);
     for (int i = 0; i < Grads::NEV && e == cudaSuccess; ++i)
       e = cudaEventCreateWithFlags(&g.ev[i], cudaEventDisableTiming);
     if (e != cudaSuccess) return e;
@@ -1536,9 +1562,11 @@ cudaError_t backward_reserve(Grads& g, long long cells, long long partial_floats
   }
   if (g.part_floats < partial_floats) {
     cudaFree(g.part);
-    g.part = nullptr;
+    cudaFree(g.part2);
+    g.part = g.part2 = nullptr;
     g.part_floats = 0;
     cudaError_t e = cudaMalloc(&g.part, sizeof(float) * partial_floats);
+    if (e == cudaSuccess) e = cudaMalloc(&g.part2, sizeof(float) * partial_floats);
     if (e != cudaSuccess) return e;
     g.part_floats = partial_floats;
   }
@@ -1547,13 +1575,16 @@ cudaError_t backward_reserve(Grads& g, long long cells, long long partial_floats
 
 void backward_free(Grads& g) {
   if (g.aux) cudaStreamSynchronize(g.aux);
+  if (g.red) cudaStreamSynchronize(g.red);
   cudaFree(g.dr);
   cudaFree(g.da[0]);
   cudaFree(g.da[1]);
   cudaFree(g.part);
+  cudaFree(g.part2);
   for (int i = 0; i < Grads::NEV; ++i)
     if (g.ev[i]) cudaEventDestroy(g.ev[i]);
   if (g.aux) cudaStreamDestroy(g.aux);
+  if (g.red) cudaStreamDestroy(g.red);
   g = Grads{};
 }
 
@@ -1581,9 +1612,9 @@ cudaError_t backward_from_raw(const Net& net, const float* q, int B, int ny, int
   const long long plane = (long long)nx * ny;
   cudaError_t e;
 
-  // Each layer's dW (stream g.aux, in layer order: they share the partial
-  // sums) runs beside its dX (stream s): both only read the layer's output
-  // cotangent.  dX of layer 2 overwrites da[0], which dW3 reads: it waits.
+  // Each layer's dW (stream g.aux, in layer order) runs beside its dX
+  // (stream s): both only read the layer's output cotangent.  dX of layer 2
+  // overwrites da[0], which dW3 reads: it waits.
   cudaStream_t w = g.aux;
   ConvArgs a{};
   a.nx = nx;
@@ -1591,10 +1622,17 @@ cudaError_t backward_from_raw(const Net& net, const float* q, int B, int ny, int
   a.plane = plane;
   a.err = net.err;
   if ((e = stream_after(g, 0, s, w)) != cudaSuccess) return e;
+  // the reductions run on g.red; layers alternate between two partial
+  // buffers, and a layer's partial sums wait for the reduction that last
+  // read its buffer
+  const RedOn ro{g.red, g.ev[8]};
+  float* part[2] = {g.part, g.part2};
   // layer 4: dW4, db4 from (dr, a3); dX -> da[0] masked by a3
+  if ((e = cudaStreamWaitEvent(w, g.ev[6], 0)) != cudaSuccess) return e;
   if ((e = weight_grad<HID, N_OUT, 6>(acts.a[2], nullptr, g.dr, dparams + L.w[3], dparams + L.b[3],
-                                      g.part, B, ny, nx, net, scale, w)) != cudaSuccess)
+                                      part[0], B, ny, nx, net, scale, w, ro)) != cudaSuccess)
     return e;
+  if ((e = cudaEventRecord(g.ev[6], g.red)) != cudaSuccess) return e;
   a.x = g.dr;
   a.wpk = net.wb[3];
   a.mask = acts.a[2];
@@ -1602,9 +1640,11 @@ cudaError_t backward_from_raw(const Net& net, const float* q, int B, int ny, int
   if ((e = launch_conv<6, HID, IN_ACT, OUT_MASK>(a, B, s)) != cudaSuccess) return e;
   if ((e = stream_after(g, 1, s, w)) != cudaSuccess) return e;
   // layer 3: dW3 from (da0, a2); dX -> da[1] masked by a2
+  if ((e = cudaStreamWaitEvent(w, g.ev[7], 0)) != cudaSuccess) return e;
   if ((e = weight_grad<HID, HID, 4>(acts.a[1], nullptr, g.da[0], dparams + L.w[2], dparams + L.b[2],
-                                    g.part, B, ny, nx, net, scale, w)) != cudaSuccess)
+                                    part[1], B, ny, nx, net, scale, w, ro)) != cudaSuccess)
     return e;
+  if ((e = cudaEventRecord(g.ev[7], g.red)) != cudaSuccess) return e;
   if ((e = cudaEventRecord(g.ev[2], w)) != cudaSuccess) return e;   // dW3 has read da[0]
   a.x = g.da[0];
   a.wpk = net.wb[2];
@@ -1613,9 +1653,11 @@ cudaError_t backward_from_raw(const Net& net, const float* q, int B, int ny, int
   if ((e = launch_conv<CG_HID, HID, IN_ACT, OUT_MASK>(a, B, s)) != cudaSuccess) return e;
   if ((e = stream_after(g, 3, s, w)) != cudaSuccess) return e;
   // layer 2: dW2 from (da1, a1); dX -> da[0] masked by a1
+  if ((e = cudaStreamWaitEvent(w, g.ev[6], 0)) != cudaSuccess) return e;
   if ((e = weight_grad<HID, HID, 4>(acts.a[0], nullptr, g.da[1], dparams + L.w[1], dparams + L.b[1],
-                                    g.part, B, ny, nx, net, scale, w)) != cudaSuccess)
+                                    part[0], B, ny, nx, net, scale, w, ro)) != cudaSuccess)
     return e;
+  if ((e = cudaEventRecord(g.ev[6], g.red)) != cudaSuccess) return e;
   a.x = g.da[1];
   a.wpk = net.wb[1];
   a.mask = acts.a[0];
@@ -1624,8 +1666,11 @@ cudaError_t backward_from_raw(const Net& net, const float* q, int B, int ny, int
   if ((e = launch_conv<CG_HID, HID, IN_ACT, OUT_MASK>(a, B, s)) != cudaSuccess) return e;
   if ((e = stream_after(g, 4, s, w)) != cudaSuccess) return e;
   // layer 1: dW1 from (da0, normalised state); dq += dX / std
-  if ((e = backward_first(net, q, g.da[0], L, B, ny, nx, g, dq, dparams, scale, w, s)) != cudaSuccess) return e;
-  return stream_after(g, 5, w, s);
+  if ((e = cudaStreamWaitEvent(w, g.ev[7], 0)) != cudaSuccess) return e;
+  if ((e = backward_first(net, q, g.da[0], L, B, ny, nx, g, part[1], dq, dparams, scale, w, s, ro)) != cudaSuccess)
+    return e;
+  if ((e = stream_after(g, 5, w, s)) != cudaSuccess) return e;
+  return stream_after(g, 5, g.red, s);
 }
 
 cudaError_t backward_faces(const Net& net, const float* q, int B, int ny, int nx, const Acts& acts,
@@ -1645,10 +1690,17 @@ cudaError_t backward_faces(const Net& net, const float* q, int B, int ny, int nx
   a.plane = plane;
   a.err = net.err;
   if ((e = stream_after(g, 0, s, w)) != cudaSuccess) return e;
+  // the reductions run on g.red; layers alternate between two partial
+  // buffers, and a layer's partial sums wait for the reduction that last
+  // read its buffer
+  const RedOn ro{g.red, g.ev[8]};
+  float* part[2] = {g.part, g.part2};
   // layer 4: dW4, db4 from (dr, a3); dX -> da[0] times GeLU'(z3)
+  if ((e = cudaStreamWaitEvent(w, g.ev[6], 0)) != cudaSuccess) return e;
   if ((e = weight_grad<HID, N_OUT_FACE, 2>(acts.a[2], nullptr, g.dr, dparams + L.w[3], dparams + L.b[3],
-                                           g.part, B, ny, nx, net, scale, w)) != cudaSuccess)
+                                           part[0], B, ny, nx, net, scale, w, ro)) != cudaSuccess)
     return e;
+  if ((e = cudaEventRecord(g.ev[6], g.red)) != cudaSuccess) return e;
   a.x = g.dr;
   a.wpk = net.wb[3];
   a.z = acts.z[2];
@@ -1656,9 +1708,11 @@ cudaError_t backward_faces(const Net& net, const float* q, int B, int ny, int nx
   if ((e = launch_conv<2, HID, IN_ACT, OUT_GELU_GRAD>(a, B, s)) != cudaSuccess) return e;
   if ((e = stream_after(g, 1, s, w)) != cudaSuccess) return e;
   // layer 3: dW3 from (da0, a2); dX -> da[1] times GeLU'(z2)
+  if ((e = cudaStreamWaitEvent(w, g.ev[7], 0)) != cudaSuccess) return e;
   if ((e = weight_grad<HID, HID, 4>(acts.a[1], nullptr, g.da[0], dparams + L.w[2], dparams + L.b[2],
-                                    g.part, B, ny, nx, net, scale, w)) != cudaSuccess)
+                                    part[1], B, ny, nx, net, scale, w, ro)) != cudaSuccess)
     return e;
+  if ((e = cudaEventRecord(g.ev[7], g.red)) != cudaSuccess) return e;
   if ((e = cudaEventRecord(g.ev[2], w)) != cudaSuccess) return e;   // dW3 has read da[0]
   a.x = g.da[0];
   a.wpk = net.wb[2];
@@ -1667,9 +1721,11 @@ cudaError_t backward_faces(const Net& net, const float* q, int B, int ny, int nx
   if ((e = launch_conv<CG_HID, HID, IN_ACT, OUT_GELU_GRAD>(a, B, s)) != cudaSuccess) return e;
   if ((e = stream_after(g, 3, s, w)) != cudaSuccess) return e;
   // layer 2: dW2 from (da1, a1); dX -> da[0] times GeLU'(z1)
+  if ((e = cudaStreamWaitEvent(w, g.ev[6], 0)) != cudaSuccess) return e;
   if ((e = weight_grad<HID, HID, 4>(acts.a[0], nullptr, g.da[1], dparams + L.w[1], dparams + L.b[1],
-                                    g.part, B, ny, nx, net, scale, w)) != cudaSuccess)
+                                    part[0], B, ny, nx, net, scale, w, ro)) != cudaSuccess)
     return e;
+  if ((e = cudaEventRecord(g.ev[6], g.red)) != cudaSuccess) return e;
   a.x = g.da[1];
   a.wpk = net.wb[1];
   a.z = acts.z[0];
@@ -1678,8 +1734,11 @@ cudaError_t backward_faces(const Net& net, const float* q, int B, int ny, int nx
   if ((e = launch_conv<CG_HID, HID, IN_ACT, OUT_GELU_GRAD>(a, B, s)) != cudaSuccess) return e;
   if ((e = stream_after(g, 4, s, w)) != cudaSuccess) return e;
   // layer 1: dW1 from (da0, normalised state); dq += dX / std
-  if ((e = backward_first(net, q, g.da[0], L, B, ny, nx, g, dq, dparams, scale, w, s)) != cudaSuccess) return e;
-  return stream_after(g, 5, w, s);
+  if ((e = cudaStreamWaitEvent(w, g.ev[7], 0)) != cudaSuccess) return e;
+  if ((e = backward_first(net, q, g.da[0], L, B, ny, nx, g, part[1], dq, dparams, scale, w, s, ro)) != cudaSuccess)
+    return e;
+  if ((e = stream_after(g, 5, w, s)) != cudaSuccess) return e;
+  return stream_after(g, 5, g.red, s);
 }
 
 }  // namespace snk

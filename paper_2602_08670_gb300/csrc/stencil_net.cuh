@@ -101,11 +101,13 @@ void acts_free(Acts& acts);
 struct Grads {
   uint16_t* dr = nullptr;       // cotangent of the raw outputs, BF16 [B][6][plane][8]
   uint16_t* da[2] = {};         // cotangents of hidden pre-activations, BF16 [B][4][plane][8]
-  float* part = nullptr;        // weight-gradient partial sums
+  float* part = nullptr;        // weight-gradient partial sums (two buffers, alternate layers)
+  float* part2 = nullptr;
   long long cells = 0, part_floats = 0;
-  static constexpr int NEV = 6;
+  static constexpr int NEV = 9;
   cudaStream_t aux = nullptr;   // the weight gradients run here, beside the dX convolutions
-  cudaEvent_t ev[NEV] = {};     // fork / join points between the two streams
+  cudaStream_t red = nullptr;   // their partial-sum reductions
+  cudaEvent_t ev[NEV] = {};     // fork / join points between the streams
 };
 long long backward_partials_floats(int B, int ny, int nx);
 cudaError_t backward_reserve(Grads& g, long long cells, long long partial_floats);
