@@ -60,7 +60,7 @@ def check_against_yardstick(q, qr, q32):
         assert e2 <= max(l2, 5 * y2) and ei <= max(li, 5 * yi), (c, err, yard)
 
 
-@pytest.mark.parametrize("ny,nx", [(64, 64), (16, 128), (32, 256), (16, 8)])
+@pytest.mark.parametrize("ny,nx", [(64, 64), (16, 128), (32, 256), (16, 8), (5, 128), (6, 64)])
 def test_cnn_raw_and_sides_match_oracle(fv, ny, nx):
     p = rand_params(1)
     net = gpu_net(fv, p)

@@ -49,7 +49,7 @@ def swe_state(n, seed, members=2):
     return W.as_f32_exact(q)
 
 
-@pytest.mark.parametrize("ny,nx", [(64, 64), (16, 128), (32, 256), (16, 8)])
+@pytest.mark.parametrize("ny,nx", [(64, 64), (16, 128), (32, 256), (16, 8), (5, 128), (6, 64)])
 def test_cnn_raw_matches_oracle(fv, ny, nx):
     p = rand_params(1)
     net = gpu_net(fv, p)
