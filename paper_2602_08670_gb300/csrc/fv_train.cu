@@ -466,6 +466,14 @@ struct fv_tape {
   float* dsn = nullptr;         // gradient of the last loss w.r.t. q_1 .. q_T
   double hmin_frac = 1e-3;
   bool have_forward = false;
+  // the backward's launch sequence, captured once (after one direct run)
+  // and replayed; keyed by the caller's buffers
+  cudaGraphExec_t bwd_exec = nullptr;
+  const float* bwd_dsn = nullptr;
+  const float* bwd_dparams = nullptr;
+  const float* bwd_dq0 = nullptr;
+  int bwd_calls = 0;
+  bool bwd_graph_off = false;   // a capture failed: run directly from then on
 };
 
 namespace fvk {
@@ -514,6 +522,7 @@ void tape_free(fv_tape* t) {
   cudaFree(t->hmin);
   cudaFree(t->ctrl);
   cudaFree(t->dp);
+  if (t->bwd_exec) cudaGraphExecDestroy(t->bwd_exec);
   snk::backward_free(t->grads);
   cudaFree(t->lam);
   cudaFree(t->lam1);
@@ -655,12 +664,11 @@ extern "C" int fv_tape_loss(fv_tape* t, const float* targets, const float* scale
   return FV_OK;
 }
 
-extern "C" int fv_tape_backward(fv_tape* t, const float* dsnaps, float* dparams, float* dq0) {
-  if (!t || !dparams) return fvh::fail(FV_EINVAL, "null argument");
-  if (!t->have_forward) return fvh::fail(FV_EINVAL, "fv_tape_forward has not run");
+namespace {
+// Every launch of the tape's backward on stream s (and the backward's own
+// side streams, joined back into s).
+int tape_backward_enqueue(fv_tape* t, const float* dsn, float* dparams, float* dq0, cudaStream_t s) {
   const long long sc = st_count(t);
-  const float* dsn = dsnaps ? dsnaps : t->dsn;
-  cudaStream_t s = t->stream;
   const snk::Net& N = t->net->n;
   const float dt = (float)t->dt;
   const int B = t->g.B, ny = t->g.ny, nx = t->g.nx;
@@ -704,6 +712,52 @@ extern "C" int fv_tape_backward(fv_tape* t, const float* dsnaps, float* dparams,
       FV_CUDA_TRY(fvk::launch_axpbypcz(t->lam, t->lam, 1.f, dsn + sc * (n - 1), 1.f, nullptr, 0.f, sc, s));
   }
   if (dq0) FV_CUDA_TRY(cudaMemcpyAsync(dq0, t->lam, sizeof(float) * sc, cudaMemcpyDeviceToDevice, s));
+  return FV_OK;
+}
+}  // namespace
+
+// The first call runs the launches directly (one-time set-up such as kernel
+// attributes happens there); later calls with the same buffers replay a CUDA
+// graph captured from the same sequence, which removes the per-launch host
+// and scheduling gaps of its ~300 launches.  The arithmetic is the same.
+extern "C" int fv_tape_backward(fv_tape* t, const float* dsnaps, float* dparams, float* dq0) {
+  if (!t || !dparams) return fvh::fail(FV_EINVAL, "null argument");
+  if (!t->have_forward) return fvh::fail(FV_EINVAL, "fv_tape_forward has not run");
+  const float* dsn = dsnaps ? dsnaps : t->dsn;
+  cudaStream_t s = t->stream;
+  const bool graph = !t->bwd_graph_off && t->bwd_calls++ > 0;
+  if (!graph) {
+    const int rc = tape_backward_enqueue(t, dsn, dparams, dq0, s);
+    if (rc != FV_OK) return rc;
+  } else {
+    if (t->bwd_exec && (t->bwd_dsn != dsn || t->bwd_dparams != dparams || t->bwd_dq0 != dq0)) {
+      cudaGraphExecDestroy(t->bwd_exec);
+      t->bwd_exec = nullptr;
+    }
+    if (!t->bwd_exec) {
+      cudaGraph_t gr = nullptr;
+      FV_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+      const int rc = tape_backward_enqueue(t, dsn, dparams, dq0, s);
+      const cudaError_t ce = cudaStreamEndCapture(s, &gr);
+      cudaError_t ie = cudaErrorUnknown;
+      if (rc == FV_OK && ce == cudaSuccess) ie = cudaGraphInstantiate(&t->bwd_exec, gr, 0);
+      if (gr) cudaGraphDestroy(gr);
+      if (rc != FV_OK || ce != cudaSuccess || ie != cudaSuccess) {
+        // capture not possible here: clear the capture's error and run directly
+        cudaGetLastError();
+        t->bwd_exec = nullptr;
+        t->bwd_graph_off = true;
+        const int rc2 = tape_backward_enqueue(t, dsn, dparams, dq0, s);
+        if (rc2 != FV_OK) return rc2;
+        FV_CUDA_TRY(cudaStreamSynchronize(s));
+        return fvs::net_check(t->net);
+      }
+      t->bwd_dsn = dsn;
+      t->bwd_dparams = dparams;
+      t->bwd_dq0 = dq0;
+    }
+    FV_CUDA_TRY(cudaGraphLaunch(t->bwd_exec, s));
+  }
   FV_CUDA_TRY(cudaStreamSynchronize(s));
   return fvs::net_check(t->net);
 }

@@ -1621,6 +1621,11 @@ cudaError_t backward_from_raw(const Net& net, const float* q, int B, int ny, int
   a.ny = ny;
   a.plane = plane;
   a.err = net.err;
+  // (the reductions of an earlier call were joined into s: its buffers are
+  // free, which the two buffer events restate from s, so that every wait
+  // below refers to work of this call, as a graph capture requires)
+  if ((e = cudaEventRecord(g.ev[6], s)) != cudaSuccess) return e;
+  if ((e = cudaEventRecord(g.ev[7], s)) != cudaSuccess) return e;
   if ((e = stream_after(g, 0, s, w)) != cudaSuccess) return e;
   // the reductions run on g.red; layers alternate between two partial
   // buffers, and a layer's partial sums wait for the reduction that last
@@ -1689,6 +1694,11 @@ cudaError_t backward_faces(const Net& net, const float* q, int B, int ny, int nx
   a.ny = ny;
   a.plane = plane;
   a.err = net.err;
+  // (the reductions of an earlier call were joined into s: its buffers are
+  // free, which the two buffer events restate from s, so that every wait
+  // below refers to work of this call, as a graph capture requires)
+  if ((e = cudaEventRecord(g.ev[6], s)) != cudaSuccess) return e;
+  if ((e = cudaEventRecord(g.ev[7], s)) != cudaSuccess) return e;
   if ((e = stream_after(g, 0, s, w)) != cudaSuccess) return e;
   // the reductions run on g.red; layers alternate between two partial
   // buffers, and a layer's partial sums wait for the reduction that last
