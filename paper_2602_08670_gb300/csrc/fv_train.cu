@@ -474,6 +474,11 @@ struct fv_tape {
   const float* bwd_dq0 = nullptr;
   int bwd_calls = 0;
   bool bwd_graph_off = false;   // a capture failed: run directly from then on
+  // the forward's launches after the copy of q0, likewise (keyed by snaps)
+  cudaGraphExec_t fwd_exec = nullptr;
+  const float* fwd_snaps = nullptr;
+  int fwd_calls = 0;
+  bool fwd_graph_off = false;
 };
 
 namespace fvk {
@@ -523,6 +528,7 @@ void tape_free(fv_tape* t) {
   cudaFree(t->ctrl);
   cudaFree(t->dp);
   if (t->bwd_exec) cudaGraphExecDestroy(t->bwd_exec);
+  if (t->fwd_exec) cudaGraphExecDestroy(t->fwd_exec);
   snk::backward_free(t->grads);
   cudaFree(t->lam);
   cudaFree(t->lam1);
@@ -603,11 +609,10 @@ extern "C" int fv_tape_destroy(fv_tape* t) {
   return FV_OK;
 }
 
-extern "C" int fv_tape_forward(fv_tape* t, const float* q0, float* snaps) {
-  if (!t || !q0) return fvh::fail(FV_EINVAL, "null argument");
+namespace {
+// The forward's launches after the copy of q0 into the tape (stream s).
+int tape_forward_enqueue(fv_tape* t, float* snaps, cudaStream_t s) {
   const long long sc = st_count(t), plane = t->g.plane();
-  cudaStream_t s = t->stream;
-  FV_CUDA_TRY(cudaMemcpyAsync(t->states, q0, sizeof(float) * sc, cudaMemcpyDeviceToDevice, s));
   hmin_kernel<<<t->g.B, 256, 0, s>>>(t->states, t->hmin, plane, t->hmin_frac);
   FV_CUDA_TRY(cudaGetLastError());
   fvk::fixed_ctrl_kernel<<<(t->g.B + 127) / 128, 128, 0, s>>>(t->ctrl, t->g.B, t->dt);
@@ -634,6 +639,48 @@ extern "C" int fv_tape_forward(fv_tape* t, const float* q0, float* snaps) {
   if (snaps)
     FV_CUDA_TRY(cudaMemcpyAsync(snaps, t->states + sc, sizeof(float) * sc * t->T,
                                 cudaMemcpyDeviceToDevice, s));
+  return FV_OK;
+}
+}  // namespace
+
+// As the backward: the first call runs directly, later calls with the same
+// snaps buffer replay a captured graph of the launches after the copy of q0.
+extern "C" int fv_tape_forward(fv_tape* t, const float* q0, float* snaps) {
+  if (!t || !q0) return fvh::fail(FV_EINVAL, "null argument");
+  const long long sc = st_count(t);
+  cudaStream_t s = t->stream;
+  FV_CUDA_TRY(cudaMemcpyAsync(t->states, q0, sizeof(float) * sc, cudaMemcpyDeviceToDevice, s));
+  const bool graph = !t->fwd_graph_off && t->fwd_calls++ > 0;
+  if (!graph) {
+    const int rc = tape_forward_enqueue(t, snaps, s);
+    if (rc != FV_OK) return rc;
+  } else {
+    if (t->fwd_exec && t->fwd_snaps != snaps) {
+      cudaGraphExecDestroy(t->fwd_exec);
+      t->fwd_exec = nullptr;
+    }
+    bool direct = false;
+    if (!t->fwd_exec) {
+      cudaGraph_t gr = nullptr;
+      FV_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+      const int rc = tape_forward_enqueue(t, snaps, s);
+      const cudaError_t ce = cudaStreamEndCapture(s, &gr);
+      cudaError_t ie = cudaErrorUnknown;
+      if (rc == FV_OK && ce == cudaSuccess) ie = cudaGraphInstantiate(&t->fwd_exec, gr, 0);
+      if (gr) cudaGraphDestroy(gr);
+      if (rc != FV_OK || ce != cudaSuccess || ie != cudaSuccess) {
+        cudaGetLastError();
+        t->fwd_exec = nullptr;
+        t->fwd_graph_off = true;
+        direct = true;
+        const int rc2 = tape_forward_enqueue(t, snaps, s);
+        if (rc2 != FV_OK) return rc2;
+      } else {
+        t->fwd_snaps = snaps;
+      }
+    }
+    if (!direct) FV_CUDA_TRY(cudaGraphLaunch(t->fwd_exec, s));
+  }
   FV_CUDA_TRY(cudaStreamSynchronize(s));
   t->have_forward = true;
   std::vector<fvk::Ctrl> c(t->g.B);

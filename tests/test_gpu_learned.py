@@ -208,10 +208,11 @@ def test_rollout_gradients_match_oracle(fv, n, T, B, zero):
 
 
 def test_tape_backward_replayed_from_a_graph_is_the_same(fv):
-    """The first fv_tape_backward of a tape runs its launches directly; later
-    calls with the same buffers replay them from a captured CUDA graph.  The
-    gradients of the direct run, the capturing call and a replay agree bit
-    for bit, and a call with another dq0 buffer is captured anew."""
+    """The first fv_tape_forward / fv_tape_backward of a tape runs its
+    launches directly; later calls with the same buffers replay them from a
+    captured CUDA graph.  The losses and gradients of the direct run, the
+    capturing call and a replay agree bit for bit, and a call with another
+    dq0 buffer is captured anew."""
     p = rand_params(6, last_scale=0.1)
     n, T, B, dt = 64, 3, 2, 1e-3
     q0 = swe_state(n, 21, members=B)
@@ -221,8 +222,12 @@ def test_tape_backward_replayed_from_a_graph_is_the_same(fv):
                         for _ in range(T)])
     net = gpu_net(fv, p)
     tape = fv.fv_tape_create(net, B, n, n, T, dt)
-    fv.fv_tape_forward(tape, f32(q0).cuda())
-    fv.fv_tape_loss(tape, f32(targets).cuda(), [0.05, 0.02, 0.02])
+    # the forward likewise: direct, capture + launch, replay (same snaps buffer)
+    losses = []
+    for _ in range(3):
+        fv.fv_tape_forward(tape, f32(q0).cuda(), want_snaps=False)
+        losses.append(fv.fv_tape_loss(tape, f32(targets).cuda(), [0.05, 0.02, 0.02]))
+    assert losses[0] == losses[1] == losses[2], losses
     grads = []
     d = torch.zeros(fv.FV_NET_PARAMS, device="cuda")
     for _ in range(3):                      # direct, capture + launch, replay
