@@ -55,7 +55,6 @@ constexpr int RW = TILE + 2;            // row mode: staged row width (1-cell ha
 constexpr int NPOS_ROW = 3 * RW;        // row mode: 3 rows
 constexpr int NPOS_MAX = 3 * (TILE + 2 * 64);   // strip mode with nx <= 64 (CUDA-core dW)
 constexpr int GSLOT = 10;               // grouped mode: 8 cells + the x-neighbour on each side
-constexpr int NPOS_GRP = (TILE / 8 + 2 * 64 / 8) * GSLOT;   // grouped mode with nx <= 64
 constexpr uint32_t WAIT_ITERS = 1u << 22;
 
 enum { IN_STATE = 0, IN_ACT = 1 };
@@ -214,34 +213,24 @@ __device__ __forceinline__ void conv_stage(const ConvArgs& a, uint8_t* sA, int b
         for (int g = 1; g < CG; ++g) *reinterpret_cast<uint4*>(sA + (g * NP + n) * 16) = make_uint4(0, 0, 0, 0);
       }
     }
-    return;
-  }
-  for (int n = tid; n < npos; n += NT) {
-    int yy, xx;
-    if (ROW) {
-      const int dyi = n / RW, xi = n - dyi * RW;
-      yy = wrap1(y0 - 1 + dyi, ny);
-      xx = wrap1(x0 - 1 + xi, nx);
-    } else {
-      const int run = n / GSLOT, sl = n - run * GSLOT;
-      const int ry = run / gpr, gi = run - ry * gpr;  // x0 = 0: the tile starts a row
-      yy = wrap1(y0 - 1 + ry, ny);
-      xx = wrap1(8 * gi - 1 + sl, nx);
-    }
-    const long long cell = (long long)yy * nx + xx;
-    if constexpr (IN == IN_ACT) {
+  } else {
+    // activations: 16-byte records by cp.async
+    for (int n = tid; n < npos; n += NT) {
+      int yy, xx;
+      if (ROW) {
+        const int dyi = n / RW, xi = n - dyi * RW;
+        yy = wrap1(y0 - 1 + dyi, ny);
+        xx = wrap1(x0 - 1 + xi, nx);
+      } else {
+        const int run = n / GSLOT, sl = n - run * GSLOT;
+        const int ry = run / gpr, gi = run - ry * gpr;  // x0 = 0: the tile starts a row
+        yy = wrap1(y0 - 1 + ry, ny);
+        xx = wrap1(8 * gi - 1 + sl, nx);
+      }
+      const long long cell = (long long)yy * nx + xx;
 #pragma unroll
       for (int g = 0; g < CG; ++g)
         cp_async16(sA + (g * NP + n) * 16, a.x + (((long long)b * CG + g) * a.plane + cell) * 8);
-    } else {
-      const float* qb = a.q + (long long)b * 3 * a.plane;
-      const float h0 = (qb[cell] - a.mean0) * a.rstd0;
-      const float h1 = (qb[a.plane + cell] - a.mean1) * a.rstd1;
-      const float h2 = (qb[2 * a.plane + cell] - a.mean2) * a.rstd2;
-      uint4 v0 = make_uint4(pack_bf16x2(h0, h1), pack_bf16x2(h2, 0.f), 0u, 0u);
-      *reinterpret_cast<uint4*>(sA + n * 16) = v0;
-#pragma unroll
-      for (int g = 1; g < CG; ++g) *reinterpret_cast<uint4*>(sA + (g * NP + n) * 16) = make_uint4(0, 0, 0, 0);
     }
   }
 }
@@ -309,9 +298,11 @@ __device__ __forceinline__ void conv_epilogue(const ConvArgs& a, int b, long lon
       }
       *reinterpret_cast<uint4*>(a.y + (((long long)b * 4 + g) * a.plane + cell) * 8) =
           make_uint4(pk[0], pk[1], pk[2], pk[3]);
-      if (OUT == OUT_GELU && a.z)
-        *reinterpret_cast<uint4*>(a.z + (((long long)b * 4 + g) * a.plane + cell) * 8) =
-            make_uint4(pz[0], pz[1], pz[2], pz[3]);
+      if constexpr (OUT == OUT_GELU) {
+        if (a.z)
+          *reinterpret_cast<uint4*>(a.z + (((long long)b * 4 + g) * a.plane + cell) * 8) =
+              make_uint4(pz[0], pz[1], pz[2], pz[3]);
+      }
     }
   } else if constexpr (OUT == OUT_DQ) {
     // first layer's dX (3 channels of the normalised state): dq += dx / std
